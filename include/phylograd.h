@@ -1,0 +1,164 @@
+/*
+ * phylograd.h -- C ABI of the GB300 library for the phylogenetic log-likelihood and its
+ * linear-time branch-length gradient (Ji et al., "Gradients do grow on trees", arXiv 1905.12146).
+ *
+ * One evaluation runs, on the GPU:
+ *   1. P_{i,l} = e^{Q_i b_i r_l} for every branch i and rate category l, in FP64
+ *      (Section 2.1 transition matrices; Section 2.5 rate categories);
+ *   2. the post-order (pruning) pass p_k = (P_i p_i) o (P_j p_j)   (Section 2.3);
+ *   3. the site likelihoods L_p = sum_l w_l pi' p_root,l and logL = sum_p wt_p log L_p
+ *      (Section 2.3 root inner product, Section 2.5 mixture, sites i.i.d. per Section 2.1);
+ *   4. the pre-order pass q_i = P_i' [q_k o (P_j p_j)], q_root = pi   (Section 2.4) fused with
+ *      the gradient dlogL/db_i = sum_p wt_p sum_l r_l w_l qt_i,l' Q_i P_{i,l} p_i,l / L_p
+ *      (Section 2.5, with qt_i = q_k o (P_j p_j) the pre-order vector at the top of branch i,
+ *      which equals the paper's q_i' Q_i p_i because e^{Qb} and Q commute)  and optionally the
+ *      diagonal of the Hessian (Section 2.6, applied site by site).
+ *
+ * Conventions.  A problem has N >= 2 tips and 2N-1 nodes.  Tips are nodes 0..N-1, internal
+ * nodes N..2N-2 in any order, the root is the one node with parent -1 (the paper numbers tips
+ * 1..N and fixes the root at 2N-1, Section 2.1).  A branch is named by its child node, so
+ * per-branch arrays have 2N-1 entries and the root entry is ignored (input) or 0 (output).
+ * All matrices are row-major doubles.  Every call returns a pg_status; no C++ exception crosses
+ * this boundary.  The library owns all device memory it allocates; pointers passed in are
+ * borrowed for the duration of the call (synchronous calls) or until the stream reaches the
+ * enqueued work (asynchronous calls).
+ */
+#ifndef PHYLOGRAD_H
+#define PHYLOGRAD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum pg_status {
+    PG_OK = 0,
+    PG_ERR_INVALID = 1,     /* malformed tree, negative/NaN branch length, bad Q row, ... */
+    PG_ERR_OOM = 2,         /* device allocation failed or the context's HBM budget is full */
+    PG_ERR_CUDA = 3,        /* a CUDA runtime call failed (pg_last_error has the text)    */
+    PG_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up                         */
+    PG_ERR_NUMERIC = 5,     /* a site likelihood was 0, infinite or NaN                   */
+    PG_ERR_UNSUPPORTED = 6  /* valid input outside what this build implements              */
+} pg_status;
+
+typedef struct pg_ctx pg_ctx;         /* one CUDA device + memory budget                      */
+typedef struct pg_handle pg_handle;   /* one device-resident problem (tree, data, model)      */
+
+typedef struct pg_options {
+    int32_t device;             /* CUDA device ordinal                                       */
+    int32_t patterns_per_tile;  /* site patterns per thread block; multiple of 32, 0=default */
+    uint64_t hbm_budget_bytes;  /* cap on device bytes held by this context's handles; 0=none */
+} pg_options;
+
+/* Storage and arithmetic of the partial likelihood vectors.  FP32: partials in FP32 with FP64
+ * transition matrices split into FP32 hi/lo pairs, an exact-product form of the post-order
+ * update and FP64 site likelihoods (the fast path; its error against FP64 is stated per result).
+ * FP64: every partial and product in FP64 (for small problems, where latency and not memory
+ * traffic bounds the evaluation, and where FP32 rounding noise is a larger share of logL). */
+#define PG_PRECISION_FP32 0
+#define PG_PRECISION_FP64 1
+
+/*
+ * A problem, as in Section 2.1 (all pointers are host pointers, read during pg_upload only).
+ *   n_states m: 4 in this build (nucleotides); other m are rejected with PG_ERR_UNSUPPORTED.
+ *   n_categories C: 1..4 discrete rate categories (Section 2.5).
+ *   parent[2N-1]           parent node of each node, -1 for the root; every internal node must
+ *                          have exactly two children (binary tree, Section 2.1).
+ *   tip_states[N][P]       observed state of tip t at pattern p; a code >= m means missing or
+ *                          fully ambiguous, i.e. the all-ones partial vector (Section 2.1).
+ *   pattern_weights[P]     multiplicity of each site pattern, finite and >= 0.
+ *   Q[n_models][m][m]      CTMC generators: off-diagonals >= 0, rows summing to 0 (|row sum| <=
+ *                          1e-10 * max|Q|); neither reversibility nor stationarity is required.
+ *   branch_model[2N-1]     generator used on each branch (NULL: model 0 everywhere).
+ *   root_freqs[m]          root state distribution pi (>= 0, sums to 1 within 1e-10), not
+ *                          necessarily stationary.
+ *   cat_rates[C]           rate multipliers r_l >= 0; cat_weights[C] probabilities (sum 1).
+ *   precision              PG_PRECISION_FP32 or PG_PRECISION_FP64 (anything else: invalid).
+ */
+typedef struct pg_problem {
+    int32_t n_tips;
+    int32_t n_states;
+    int32_t n_patterns;
+    int32_t n_categories;
+    int32_t n_models;
+    int32_t precision;          /* PG_PRECISION_FP32 (0) or PG_PRECISION_FP64 (1), see below */
+    const int32_t *parent;
+    const uint8_t *tip_states;
+    const double *pattern_weights;
+    const double *Q;
+    const int32_t *branch_model;
+    const double *root_freqs;
+    const double *cat_rates;
+    const double *cat_weights;
+} pg_problem;
+
+typedef struct pg_handle_info {
+    int32_t n_tips, n_nodes, n_states, n_patterns, n_categories;
+    int32_t n_levels;            /* tree height = number of level-synchronous steps per pass */
+    int32_t n_tiles;             /* thread blocks per pass                                    */
+    int32_t patterns_per_tile;
+    uint64_t device_bytes;       /* device memory held by this handle                         */
+    uint64_t stream_bytes;       /* algorithmic HBM bytes of one evaluation's partial streams */
+    uint64_t flops;              /* algorithmic FP32 flops of one evaluation's two passes     */
+} pg_handle_info;
+
+/* Create a context on opt->device (NULL opt: device 0, defaults).  The context is not
+ * thread-safe; use one per host thread.  Errors: PG_ERR_INVALID (bad options), PG_ERR_CUDA. */
+pg_status pg_create(const pg_options *opt, pg_ctx **out);
+
+/* Destroy a context and every handle still attached to it. */
+pg_status pg_destroy(pg_ctx *ctx);
+
+/* Validate a problem and copy it to the device (tree levels, tip codes, weights, Q, pi, rates),
+ * allocating the partial-likelihood buffers it needs.  Errors: PG_ERR_INVALID (the problem breaks
+ * a rule above), PG_ERR_UNSUPPORTED (m != 4 or C > 4), PG_ERR_OOM (allocation or budget). */
+pg_status pg_upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out);
+
+/* Release a handle's device memory. */
+pg_status pg_free(pg_handle *h);
+
+/* Blocking evaluation with HOST pointers: b[2N-1] branch lengths (root entry ignored; each other
+ * entry finite and >= 0), outputs logL (scalar), grad[2N-1], hess[2N-1] (diagonal of the Hessian
+ * of logL in the branch lengths), site_logL[P]; any output may be NULL.  Copies b to the device
+ * and the results back.  Errors: PG_ERR_INVALID (bad b), PG_ERR_NUMERIC (a site likelihood 0 or
+ * not finite; outputs are still written), PG_ERR_CUDA. */
+pg_status pg_eval(pg_handle *h, const double *b, double *logL, double *grad, double *hess,
+                  double *site_logL);
+
+/* Asynchronous evaluation with DEVICE pointers on a CUDA stream (cudaStream_t passed as void*,
+ * NULL = legacy default stream).  Same arrays as pg_eval.  Nothing is checked on the host after
+ * enqueueing: an invalid b or a numeric failure is recorded on the device and reported by
+ * pg_eval_status.  One evaluation per handle may be in flight at a time (the handle's partial
+ * buffers are reused). */
+pg_status pg_eval_async(pg_handle *h, const double *d_b, double *d_logL, double *d_grad,
+                        double *d_hess, double *d_site_logL, void *stream);
+
+/* Evaluate k problems in as few launches as possible (problems are grouped by category count;
+ * each launch covers every tile of every problem in the group).  d_b[i], d_grad[i], d_hess[i]
+ * are per-problem DEVICE pointers (d_grad/d_hess may be NULL, or have NULL entries);
+ * d_logL[k] is one DEVICE array.  Results are bit-identical to k separate pg_eval_async calls.
+ * Errors: PG_ERR_INVALID (k < 0, a NULL handle, handles from different contexts). */
+pg_status pg_eval_batch_async(pg_handle *const *hs, int32_t k, const double *const *d_b,
+                              double *d_logL, double *const *d_grad, double *const *d_hess,
+                              void *stream);
+
+/* Wait for the handle's last evaluation and return its device-side status (PG_OK,
+ * PG_ERR_INVALID for a bad branch length, PG_ERR_NUMERIC for a failed site likelihood). */
+pg_status pg_eval_status(pg_handle *h);
+
+/* Sizes and algorithmic traffic of a handle (for measurement). */
+pg_status pg_get_info(const pg_handle *h, pg_handle_info *out);
+
+/* Static text for a status code. */
+const char *pg_status_string(pg_status s);
+
+/* Text of the last error raised on the calling thread ("" if none). */
+const char *pg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PHYLOGRAD_H */

@@ -1,0 +1,219 @@
+"""Thin ctypes binding of libphylograd.so (argument marshalling only).
+
+Every computation happens in the CUDA library; this module converts numpy arrays and torch
+device tensors into the pointers and sizes of the C ABI in ``include/phylograd.h`` and turns
+status codes into exceptions.  If the library has not been built, importing works but the first
+call raises ``RuntimeError``: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libphylograd.so")
+
+PRECISIONS = {"fp32": 0, "fp64": 1}
+PG_OK, PG_ERR_INVALID, PG_ERR_OOM, PG_ERR_CUDA, PG_ERR_TIMEOUT, PG_ERR_NUMERIC, PG_ERR_UNSUPPORTED = range(7)
+
+EXPORTED = ("pg_create", "pg_destroy", "pg_upload", "pg_free", "pg_eval", "pg_eval_async",
+            "pg_eval_batch_async", "pg_eval_status", "pg_get_info", "pg_status_string",
+            "pg_last_error")
+
+
+class PhyloGradError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"[{status}] {message}")
+        self.status = status
+
+
+class pg_options(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("patterns_per_tile", ctypes.c_int32),
+                ("hbm_budget_bytes", ctypes.c_uint64)]
+
+
+class pg_problem(ctypes.Structure):
+    _fields_ = [("n_tips", ctypes.c_int32), ("n_states", ctypes.c_int32),
+                ("n_patterns", ctypes.c_int32), ("n_categories", ctypes.c_int32),
+                ("n_models", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("parent", ctypes.c_void_p), ("tip_states", ctypes.c_void_p),
+                ("pattern_weights", ctypes.c_void_p), ("Q", ctypes.c_void_p),
+                ("branch_model", ctypes.c_void_p), ("root_freqs", ctypes.c_void_p),
+                ("cat_rates", ctypes.c_void_p), ("cat_weights", ctypes.c_void_p)]
+
+
+class pg_handle_info(ctypes.Structure):
+    _fields_ = [("n_tips", ctypes.c_int32), ("n_nodes", ctypes.c_int32),
+                ("n_states", ctypes.c_int32), ("n_patterns", ctypes.c_int32),
+                ("n_categories", ctypes.c_int32), ("n_levels", ctypes.c_int32),
+                ("n_tiles", ctypes.c_int32), ("patterns_per_tile", ctypes.c_int32),
+                ("device_bytes", ctypes.c_uint64), ("stream_bytes", ctypes.c_uint64),
+                ("flops", ctypes.c_uint64)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the shared library (raises if it is missing: build it with ``build()`` first)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA library first "
+                           "(python -m paper_1905_12146_gb300.build)")
+    lib = ctypes.CDLL(path)
+    vp, i32 = ctypes.c_void_p, ctypes.c_int32
+    sig = {
+        "pg_create": ([ctypes.POINTER(pg_options), ctypes.POINTER(vp)], i32),
+        "pg_destroy": ([vp], i32),
+        "pg_upload": ([vp, ctypes.POINTER(pg_problem), ctypes.POINTER(vp)], i32),
+        "pg_free": ([vp], i32),
+        "pg_eval": ([vp, vp, vp, vp, vp, vp], i32),
+        "pg_eval_async": ([vp, vp, vp, vp, vp, vp, vp], i32),
+        "pg_eval_batch_async": ([vp, i32, vp, vp, vp, vp, vp], i32),
+        "pg_eval_status": ([vp], i32),
+        "pg_get_info": ([vp, ctypes.POINTER(pg_handle_info)], i32),
+        "pg_status_string": ([i32], ctypes.c_char_p),
+        "pg_last_error": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def check(status: int):
+    if status != PG_OK:
+        lib = load()
+        raise PhyloGradError(status, f"{lib.pg_status_string(status).decode()}: "
+                                     f"{lib.pg_last_error().decode()}")
+
+
+def _np_ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def _dev_ptr(t):
+    """Device pointer of a torch CUDA tensor (or an int address, or None)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+class Context:
+    """One CUDA device with an optional device-memory budget (pg_create / pg_destroy)."""
+
+    def __init__(self, device: int = 0, patterns_per_tile: int = 0, hbm_budget_bytes: int = 0):
+        lib = load()
+        opt = pg_options(device, patterns_per_tile, hbm_budget_bytes)
+        out = ctypes.c_void_p()
+        check(lib.pg_create(ctypes.byref(opt), ctypes.byref(out)))
+        self._ptr = out
+        self.device = device
+
+    def upload(self, problem: dict, precision: str | None = None) -> "Handle":
+        return Handle(self, problem, precision)
+
+    def close(self):
+        if self._ptr:
+            load().pg_destroy(self._ptr)
+            self._ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Handle:
+    """A device-resident problem (pg_upload); evaluations via pg_eval / pg_eval_async."""
+
+    def __init__(self, ctx: Context, problem: dict, precision: str | None = None):
+        lib = load()
+        precision = precision or problem.get("precision", "fp32")
+        if precision not in PRECISIONS:
+            raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
+        self.ctx = ctx
+        parent = np.ascontiguousarray(problem["parent"], dtype=np.int32)
+        tips = np.ascontiguousarray(problem["tip_states"], dtype=np.uint8)
+        w = np.ascontiguousarray(problem["weights"], dtype=np.float64)
+        Q = np.ascontiguousarray(problem["Q"], dtype=np.float64)
+        if Q.ndim == 2:
+            Q = Q[None]
+        bm = problem.get("branch_model")
+        bm = None if bm is None else np.ascontiguousarray(bm, dtype=np.int32)
+        pi = np.ascontiguousarray(problem["root_freqs"], dtype=np.float64)
+        rates = np.ascontiguousarray(problem["cat_rates"], dtype=np.float64)
+        cw = np.ascontiguousarray(problem["cat_weights"], dtype=np.float64)
+        n = parent.shape[0]
+        pr = pg_problem((n + 1) // 2, Q.shape[1], tips.shape[1] if tips.ndim == 2 else 0,
+                        rates.shape[0], Q.shape[0], PRECISIONS[precision], _np_ptr(parent), _np_ptr(tips),
+                        _np_ptr(w), _np_ptr(Q), _np_ptr(bm), _np_ptr(pi), _np_ptr(rates),
+                        _np_ptr(cw))
+        out = ctypes.c_void_p()
+        check(lib.pg_upload(ctx._ptr, ctypes.byref(pr), ctypes.byref(out)))
+        self._ptr = out
+        self.n_nodes = n
+        self.n_patterns = pr.n_patterns
+
+    def info(self) -> pg_handle_info:
+        info = pg_handle_info()
+        check(load().pg_get_info(self._ptr, ctypes.byref(info)))
+        return info
+
+    def eval(self, b, grad=True, hess=False, site=False):
+        """Blocking evaluation with host arrays (pg_eval).  Returns a dict."""
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        if b.shape != (self.n_nodes,):
+            raise ValueError(f"b must have shape ({self.n_nodes},)")
+        logL = np.zeros(1)
+        g = np.zeros(self.n_nodes) if grad else None
+        h = np.zeros(self.n_nodes) if hess else None
+        s = np.zeros(self.n_patterns) if site else None
+        st = load().pg_eval(self._ptr, _np_ptr(b), _np_ptr(logL), _np_ptr(g), _np_ptr(h), _np_ptr(s))
+        out = {"logL": float(logL[0]), "grad": g, "hess": h, "site_logL": s, "status": st}
+        if st not in (PG_OK, PG_ERR_NUMERIC):
+            check(st)
+        return out
+
+    def eval_async(self, d_b, d_logL, d_grad=None, d_hess=None, d_site=None, stream=None):
+        """Enqueue an evaluation on ``stream`` (a torch.cuda.Stream, a raw handle or None) with
+        device tensors/pointers."""
+        s = None
+        if stream is not None:
+            s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        check(load().pg_eval_async(self._ptr, _dev_ptr(d_b), _dev_ptr(d_logL), _dev_ptr(d_grad),
+                                   _dev_ptr(d_hess), _dev_ptr(d_site), s))
+
+    def status(self) -> int:
+        return load().pg_eval_status(self._ptr)
+
+    def close(self):
+        if self._ptr:
+            load().pg_free(self._ptr)
+            self._ptr = None
+
+
+def eval_batch_async(handles, d_b, d_logL, d_grad=None, d_hess=None, stream=None):
+    """pg_eval_batch_async over a list of handles with per-problem device tensors."""
+    k = len(handles)
+    VP = ctypes.c_void_p * max(k, 1)
+    hs = VP(*[h._ptr.value for h in handles])
+    bs = VP(*[_dev_ptr(x) for x in d_b])
+    gs = VP(*[_dev_ptr(x) for x in d_grad]) if d_grad is not None else None
+    hh = VP(*[_dev_ptr(x) for x in d_hess]) if d_hess is not None else None
+    s = None
+    if stream is not None:
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    check(load().pg_eval_batch_async(ctypes.cast(hs, ctypes.c_void_p), k,
+                                     ctypes.cast(bs, ctypes.c_void_p), _dev_ptr(d_logL),
+                                     None if gs is None else ctypes.cast(gs, ctypes.c_void_p),
+                                     None if hh is None else ctypes.cast(hh, ctypes.c_void_p), s))

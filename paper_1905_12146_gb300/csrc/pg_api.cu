@@ -1,0 +1,585 @@
+// Host side of the C ABI declared in include/phylograd.h: validation of a problem (Section 2.1
+// assumptions: rooted binary tree, CTMC generators, root distribution, rate categories of
+// Section 2.5), level scheduling of the tree, the device layout of one problem and the launches
+// of one (or a batch of) evaluation(s).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "phylograd.h"
+#include "pg_internal.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+pg_status fail(pg_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define PG_CUDA(call)                                                                          \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) return fail(PG_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+// Makes ctx's device current for the duration of a call and restores the caller's device.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = (prev == dev) || (cudaSetDevice(dev) == cudaSuccess);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+struct pg_ctx {
+    int device = 0;
+    int n_sm = 1;
+    int blocks_per_sm[2][pg::kMaxCat + 1] = {};   // tree kernel occupancy [precision][C]
+    int max_range = 0;                            // cap on patterns per block (0 = kMaxRange)
+    uint64_t budget = 0;
+    uint64_t used = 0;
+    std::vector<pg_handle *> handles;
+};
+
+struct pg_handle {
+    pg_ctx *ctx = nullptr;
+    pg::ProbDesc desc{};     // device pointers; b and outputs are set per evaluation
+    void *block = nullptr;   // one device allocation holding every array of the problem
+    size_t bytes = 0;
+    int max_tiles = 0;       // blocks one evaluation of this problem may use
+    double *io_b = nullptr, *io_logL = nullptr, *io_grad = nullptr, *io_hess = nullptr,
+           *io_site = nullptr;   // device staging for the host-pointer pg_eval
+    pg_handle_info info{};
+    cudaStream_t last_stream = nullptr;
+};
+
+// ------------------------------------------------------------------------------------------
+// validation and tree preparation
+// ------------------------------------------------------------------------------------------
+
+namespace {
+
+struct TreePlan {
+    int root = -1;
+    std::vector<int4> ops;        // internal nodes sorted by height: {k, c0, c1, 0}
+    std::vector<int> level_off;   // [H + 1]
+};
+
+pg_status plan_tree(int n_tips, const int32_t *parent, TreePlan &tp) {
+    const int n = 2 * n_tips - 1;
+    std::vector<int> kid0(n, -1), kid1(n, -1);
+    for (int i = 0; i < n; ++i) {
+        const int p = parent[i];
+        if (p == -1) {
+            if (tp.root >= 0) return fail(PG_ERR_INVALID, "more than one root (nodes %d and %d)", tp.root, i);
+            tp.root = i;
+            continue;
+        }
+        if (p < n_tips || p >= n || p == i)
+            return fail(PG_ERR_INVALID, "parent[%d] = %d is not an internal node", i, p);
+        if (kid0[p] < 0) kid0[p] = i;
+        else if (kid1[p] < 0) kid1[p] = i;
+        else return fail(PG_ERR_INVALID, "node %d has more than two children (binary tree required)", p);
+    }
+    if (tp.root < 0) return fail(PG_ERR_INVALID, "no root (no node with parent -1)");
+    if (tp.root < n_tips) return fail(PG_ERR_INVALID, "the root %d is a tip", tp.root);
+    for (int k = n_tips; k < n; ++k)
+        if (kid1[k] < 0) return fail(PG_ERR_INVALID, "internal node %d has fewer than two children", k);
+    // depth-first order from the root; every node must be reached exactly once (no cycles)
+    std::vector<int> order;
+    order.reserve(n);
+    std::vector<int> stack{tp.root};
+    while (!stack.empty()) {
+        const int k = stack.back();
+        stack.pop_back();
+        if ((int)order.size() >= n) return fail(PG_ERR_INVALID, "the parent array contains a cycle");
+        order.push_back(k);
+        if (k >= n_tips) { stack.push_back(kid1[k]); stack.push_back(kid0[k]); }
+    }
+    if ((int)order.size() != n) return fail(PG_ERR_INVALID, "the parent array contains a cycle");
+    std::vector<int> height(n, 0);
+    int H = 0;
+    for (int o = n - 1; o >= 0; --o) {
+        const int k = order[o];
+        if (k < n_tips) continue;
+        height[k] = 1 + std::max(height[kid0[k]], height[kid1[k]]);
+        H = std::max(H, height[k]);
+    }
+    // counting sort of internal nodes by height (level h-1 holds height h)
+    tp.level_off.assign(H + 1, 0);
+    for (int k = n_tips; k < n; ++k) tp.level_off[height[k]]++;
+    for (int h = 1; h <= H; ++h) tp.level_off[h] += tp.level_off[h - 1];
+    tp.ops.assign(n_tips - 1, int4{});
+    std::vector<int> fill(tp.level_off.begin(), tp.level_off.end() - 1);
+    for (int k = n_tips; k < n; ++k) {
+        const int lv = height[k] - 1;
+        tp.ops[fill[lv]++] = int4{k, kid0[k], kid1[k], 0};
+    }
+    return PG_OK;
+}
+
+pg_status check_model(const pg_problem *pr) {
+    const int m = pr->n_states, C = pr->n_categories, M = pr->n_models;
+    if (!pr->Q || !pr->root_freqs || !pr->cat_rates || !pr->cat_weights)
+        return fail(PG_ERR_INVALID, "Q, root_freqs, cat_rates and cat_weights are required");
+    for (int md = 0; md < M; ++md) {
+        const double *Q = pr->Q + (size_t)md * m * m;
+        double mx = 0.0;
+        for (int t = 0; t < m * m; ++t) {
+            if (!std::isfinite(Q[t])) return fail(PG_ERR_INVALID, "Q[%d] has a non-finite entry", md);
+            mx = std::max(mx, std::fabs(Q[t]));
+        }
+        for (int i = 0; i < m; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < m; ++j) {
+                if (i != j && Q[i * m + j] < 0.0)
+                    return fail(PG_ERR_INVALID, "Q[%d][%d][%d] < 0 off the diagonal", md, i, j);
+                s += Q[i * m + j];
+            }
+            if (std::fabs(s) > 1e-10 * std::max(mx, 1e-300) && mx > 0.0)
+                return fail(PG_ERR_INVALID, "row %d of Q[%d] sums to %g, not 0", i, md, s);
+        }
+    }
+    double s = 0.0;
+    for (int i = 0; i < m; ++i) {
+        if (!(pr->root_freqs[i] >= 0.0) || !std::isfinite(pr->root_freqs[i]))
+            return fail(PG_ERR_INVALID, "root_freqs[%d] is negative or not finite", i);
+        s += pr->root_freqs[i];
+    }
+    if (std::fabs(s - 1.0) > 1e-10) return fail(PG_ERR_INVALID, "root_freqs sum to %.17g, not 1", s);
+    s = 0.0;
+    for (int l = 0; l < C; ++l) {
+        if (!(pr->cat_weights[l] >= 0.0) || !std::isfinite(pr->cat_weights[l]))
+            return fail(PG_ERR_INVALID, "cat_weights[%d] is negative or not finite", l);
+        if (!(pr->cat_rates[l] >= 0.0) || !std::isfinite(pr->cat_rates[l]))
+            return fail(PG_ERR_INVALID, "cat_rates[%d] is negative or not finite", l);
+        s += pr->cat_weights[l];
+    }
+    if (std::fabs(s - 1.0) > 1e-10) return fail(PG_ERR_INVALID, "cat_weights sum to %.17g, not 1", s);
+    const int n = 2 * pr->n_tips - 1;
+    if (pr->branch_model)
+        for (int i = 0; i < n; ++i)
+            if (pr->branch_model[i] < 0 || pr->branch_model[i] >= M)
+                return fail(PG_ERR_INVALID, "branch_model[%d] = %d outside [0, %d)", i, pr->branch_model[i], M);
+    for (int p = 0; p < pr->n_patterns; ++p)
+        if (!(pr->pattern_weights[p] >= 0.0) || !std::isfinite(pr->pattern_weights[p]))
+            return fail(PG_ERR_INVALID, "pattern_weights[%d] is negative or not finite", p);
+    return PG_OK;
+}
+
+// Blocks for one problem evaluated alone: every SM filled to the tree kernel's occupancy.
+int single_target(const pg_ctx *ctx, const pg::ProbDesc &d) {
+    return std::min(4 * ctx->n_sm, ctx->n_sm * ctx->blocks_per_sm[d.precision][d.C]);
+}
+
+// Carves one device allocation into aligned arrays.
+struct Carver {
+    size_t off = 0;
+    template <class T>
+    size_t take(size_t count) {
+        const size_t at = align_up(off, 256);
+        off = at + count * sizeof(T);
+        return at;
+    }
+};
+
+// Splits the P patterns of a problem into `target` blocks of contiguous ranges (fewer when the
+// ranges would otherwise hold less than one pattern or more than max_range).
+void set_tiling(pg::ProbDesc &d, int target, int max_range) {
+    const int P = d.P;
+    if (P <= 0) {
+        d.n_tiles = d.range_len = d.pieces = d.n_tg = 0;
+        return;
+    }
+    int T = std::max(1, std::min(target, P));
+    T = std::max(T, (P + max_range - 1) / max_range);
+    const int L = (P + T - 1) / T;
+    T = (P + L - 1) / L;
+    d.n_tiles = T;
+    d.range_len = L;
+    d.pieces = (L + 31) / 32 + 1;
+    d.n_tg = T * d.pieces;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------------------------
+
+extern "C" {
+
+const char *pg_status_string(pg_status s) {
+    switch (s) {
+        case PG_OK: return "ok";
+        case PG_ERR_INVALID: return "invalid argument";
+        case PG_ERR_OOM: return "out of device memory or over the context budget";
+        case PG_ERR_CUDA: return "CUDA runtime error";
+        case PG_ERR_TIMEOUT: return "device-side wait timed out";
+        case PG_ERR_NUMERIC: return "a site likelihood was zero or not finite";
+        case PG_ERR_UNSUPPORTED: return "unsupported by this build";
+    }
+    return "unknown status";
+}
+
+const char *pg_last_error(void) { return g_err.c_str(); }
+
+pg_status pg_create(const pg_options *opt, pg_ctx **out) {
+    if (!out) return fail(PG_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    pg_options o{};
+    if (opt) o = *opt;
+    int ndev = 0;
+    PG_CUDA(cudaGetDeviceCount(&ndev));
+    if (o.device < 0 || o.device >= ndev) return fail(PG_ERR_INVALID, "device %d not present (%d devices)", o.device, ndev);
+    if (o.patterns_per_tile < 0 || o.patterns_per_tile > pg::kMaxRange)
+        return fail(PG_ERR_INVALID, "patterns_per_tile must be in [0, %d]", pg::kMaxRange);
+    pg_ctx *c = new (std::nothrow) pg_ctx;
+    if (!c) return fail(PG_ERR_OOM, "host allocation failed");
+    c->device = o.device;
+    c->max_range = o.patterns_per_tile;
+    c->budget = o.hbm_budget_bytes;
+    DeviceGuard g(c->device);
+    if (!g.ok) { delete c; return fail(PG_ERR_CUDA, "cannot select device %d", o.device); }
+    if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || c->n_sm < 1) {
+        delete c;
+        return fail(PG_ERR_CUDA, "cannot read the SM count of device %d", o.device);
+    }
+    for (int f = 0; f < 2; ++f)
+        for (int C = 1; C <= pg::kMaxCat; ++C) c->blocks_per_sm[f][C] = pg::tree_blocks_per_sm(C, f == 1);
+    *out = c;
+    return PG_OK;
+}
+
+pg_status pg_free(pg_handle *h) {
+    if (!h) return PG_OK;
+    pg_ctx *c = h->ctx;
+    DeviceGuard g(c->device);
+    if (h->block) cudaFree(h->block);
+    c->used -= h->bytes;
+    c->handles.erase(std::remove(c->handles.begin(), c->handles.end(), h), c->handles.end());
+    delete h;
+    return PG_OK;
+}
+
+pg_status pg_destroy(pg_ctx *ctx) {
+    if (!ctx) return PG_OK;
+    while (!ctx->handles.empty()) pg_free(ctx->handles.back());
+    delete ctx;
+    return PG_OK;
+}
+
+pg_status pg_upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out) {
+    if (!ctx || !pr || !out) return fail(PG_ERR_INVALID, "NULL argument");
+    *out = nullptr;
+    const int N = pr->n_tips, m = pr->n_states, P = pr->n_patterns, C = pr->n_categories;
+    if (N < 2) return fail(PG_ERR_INVALID, "n_tips = %d (at least 2 required)", N);
+    if (m < 2) return fail(PG_ERR_INVALID, "n_states = %d (at least 2 required)", m);
+    if (P < 0) return fail(PG_ERR_INVALID, "n_patterns = %d", P);
+    if (C < 1) return fail(PG_ERR_INVALID, "n_categories = %d", C);
+    if (pr->n_models < 1) return fail(PG_ERR_INVALID, "n_models = %d", pr->n_models);
+    if (pr->precision != PG_PRECISION_FP32 && pr->precision != PG_PRECISION_FP64)
+        return fail(PG_ERR_INVALID, "precision = %d", pr->precision);
+    const bool f64 = pr->precision == PG_PRECISION_FP64;
+    if (m != pg::kStates) return fail(PG_ERR_UNSUPPORTED, "n_states = %d: this build implements 4 states", m);
+    if (C > pg::kMaxCat) return fail(PG_ERR_UNSUPPORTED, "n_categories = %d: at most %d", C, pg::kMaxCat);
+    if (!pr->parent) return fail(PG_ERR_INVALID, "parent is NULL");
+    if (P > 0 && (!pr->tip_states || !pr->pattern_weights))
+        return fail(PG_ERR_INVALID, "tip_states and pattern_weights are required when n_patterns > 0");
+    if ((int64_t)N * 2 - 1 > (int64_t)1 << 30) return fail(PG_ERR_UNSUPPORTED, "tree too large");
+    TreePlan tp;
+    pg_status st = plan_tree(N, pr->parent, tp);
+    if (st != PG_OK) return st;
+    st = check_model(pr);
+    if (st != PG_OK) return st;
+
+    const int n = 2 * N - 1;
+    const int H = (int)tp.level_off.size() - 1;
+    // a launch uses at most max_tiles blocks for this problem, each a range of <= kMaxRange
+    // patterns; its slot arrays hold n_tiles * (ceil(range/32) + 1) <= P/32 + 3 * max_tiles
+    const int max_tiles = 4 * ctx->n_sm;
+    const int max_range = ctx->max_range ? ctx->max_range : pg::kMaxRange;
+    if ((int64_t)max_tiles * max_range < (int64_t)P)
+        return fail(PG_ERR_UNSUPPORTED, "n_patterns = %d exceeds %d on this device", P, max_tiles * max_range);
+    const int slot_cap = (P + 31) / 32 + 3 * max_tiles + 2;
+    const int M = pr->n_models;
+
+    Carver cv;
+    const size_t o_ops = cv.take<int4>(N - 1), o_lv = cv.take<int>(H + 1);
+    const size_t o_tips = cv.take<uint8_t>((size_t)N * P), o_w = cv.take<double>(P);
+    const size_t o_Qd = cv.take<double>((size_t)M * 16), o_Qf = cv.take<float4>((size_t)M * 4);
+    const size_t o_bm = pr->branch_model ? cv.take<int>(n) : 0;
+    const size_t o_P = f64 ? cv.take<double2>((size_t)n * C * pg::kPtab64Pairs)
+                           : cv.take<float4>((size_t)n * C * pg::kPtabCols);
+    const size_t part = (size_t)(N - 1) * C * P * (f64 ? 2 : 1);   // float4 or 2 x double2
+    const size_t o_post = f64 ? cv.take<double2>(part) : cv.take<float4>(part);
+    const size_t o_pre = f64 ? cv.take<double2>(part) : cv.take<float4>(part);
+    const size_t o_pe = cv.take<int>((size_t)(N - 1) * P), o_qe = cv.take<int>((size_t)(N - 1) * P);
+    const size_t o_gp = cv.take<double>((size_t)n * slot_cap), o_hp = cv.take<double>((size_t)n * slot_cap);
+    const size_t o_lp = cv.take<double>(slot_cap), o_st = cv.take<int>(1);
+    const size_t o_ib = cv.take<double>(n), o_il = cv.take<double>(1), o_ig = cv.take<double>(n);
+    const size_t o_ih = cv.take<double>(n), o_is = cv.take<double>(std::max(P, 1));
+    const size_t bytes = align_up(cv.off, 256);
+    if (ctx->budget && ctx->used + bytes > ctx->budget)
+        return fail(PG_ERR_OOM, "problem needs %zu bytes, %llu of %llu budget in use", bytes,
+                    (unsigned long long)ctx->used, (unsigned long long)ctx->budget);
+
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(PG_ERR_CUDA, "cannot select device %d", ctx->device);
+    void *block = nullptr;
+    cudaError_t ce = cudaMalloc(&block, bytes);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PG_ERR_OOM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(ce));
+    }
+    char *base = static_cast<char *>(block);
+    pg_handle *h = new (std::nothrow) pg_handle;
+    if (!h) { cudaFree(block); return fail(PG_ERR_OOM, "host allocation failed"); }
+    h->ctx = ctx;
+    h->block = block;
+    h->bytes = bytes;
+    h->max_tiles = max_tiles;
+
+    std::vector<float4> Qf((size_t)M * 4);
+    for (int md = 0; md < M; ++md)
+        for (int c = 0; c < 4; ++c) {
+            const double *Q = pr->Q + (size_t)md * 16;
+            Qf[md * 4 + c] = make_float4((float)Q[c], (float)Q[4 + c], (float)Q[8 + c], (float)Q[12 + c]);
+        }
+    auto cp = [&](size_t off, const void *src, size_t nbytes) -> cudaError_t {
+        if (nbytes == 0) return cudaSuccess;
+        return cudaMemcpy(base + off, src, nbytes, cudaMemcpyHostToDevice);
+    };
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cp(o_ops, tp.ops.data(), sizeof(int4) * tp.ops.size());
+    if (e == cudaSuccess) e = cp(o_lv, tp.level_off.data(), sizeof(int) * tp.level_off.size());
+    if (e == cudaSuccess && P > 0) e = cp(o_tips, pr->tip_states, (size_t)N * P);
+    if (e == cudaSuccess && P > 0) e = cp(o_w, pr->pattern_weights, sizeof(double) * P);
+    if (e == cudaSuccess) e = cp(o_Qd, pr->Q, sizeof(double) * 16 * M);
+    if (e == cudaSuccess) e = cp(o_Qf, Qf.data(), sizeof(float4) * Qf.size());
+    if (e == cudaSuccess && pr->branch_model) e = cp(o_bm, pr->branch_model, sizeof(int) * n);
+    if (e == cudaSuccess) e = cudaMemset(base + o_st, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        cudaFree(block);
+        delete h;
+        return fail(PG_ERR_CUDA, "upload: %s", cudaGetErrorString(e));
+    }
+
+    pg::ProbDesc &d = h->desc;
+    d.ops = reinterpret_cast<const int4 *>(base + o_ops);
+    d.level_off = reinterpret_cast<const int *>(base + o_lv);
+    d.tips = reinterpret_cast<const uint8_t *>(base + o_tips);
+    d.weights = reinterpret_cast<const double *>(base + o_w);
+    d.Qd = reinterpret_cast<const double *>(base + o_Qd);
+    d.Qf = reinterpret_cast<const float4 *>(base + o_Qf);
+    d.bmodel = pr->branch_model ? reinterpret_cast<const int *>(base + o_bm) : nullptr;
+    d.Ptab = f64 ? nullptr : reinterpret_cast<float4 *>(base + o_P);
+    d.Ptab64 = f64 ? reinterpret_cast<double2 *>(base + o_P) : nullptr;
+    d.post = base + o_post;
+    d.pre = base + o_pre;
+    d.pe = reinterpret_cast<int *>(base + o_pe);
+    d.qe = reinterpret_cast<int *>(base + o_qe);
+    d.gpart = reinterpret_cast<double *>(base + o_gp);
+    d.hpart = reinterpret_cast<double *>(base + o_hp);
+    d.lpart = reinterpret_cast<double *>(base + o_lp);
+    d.status = reinterpret_cast<int *>(base + o_st);
+    h->io_b = reinterpret_cast<double *>(base + o_ib);
+    h->io_logL = reinterpret_cast<double *>(base + o_il);
+    h->io_grad = reinterpret_cast<double *>(base + o_ig);
+    h->io_hess = reinterpret_cast<double *>(base + o_ih);
+    h->io_site = reinterpret_cast<double *>(base + o_is);
+    d.n_tips = N;
+    d.n_nodes = n;
+    d.root = tp.root;
+    d.n_levels = H;
+    d.P = P;
+    d.slot_cap = slot_cap;
+    d.C = C;
+    d.n_models = M;
+    d.precision = pr->precision;
+    for (int s = 0; s < pg::kStates; ++s) { d.pi[s] = pr->root_freqs[s]; d.pif[s] = (float)pr->root_freqs[s]; }
+    for (int l = 0; l < pg::kMaxCat; ++l) {
+        const bool on = l < C;
+        d.cw[l] = on ? pr->cat_weights[l] : 0.0;
+        d.rates[l] = on ? pr->cat_rates[l] : 0.0;
+        d.gw[l] = on ? (float)(pr->cat_rates[l] * pr->cat_weights[l]) : 0.f;
+        d.gw2[l] = on ? (float)(pr->cat_rates[l] * pr->cat_rates[l] * pr->cat_weights[l]) : 0.f;
+    }
+
+    pg_handle_info &I = h->info;
+    I.n_tips = N;
+    I.n_nodes = n;
+    I.n_states = m;
+    I.n_patterns = P;
+    I.n_categories = C;
+    I.n_levels = H;
+    {
+        pg::ProbDesc tmp = d;
+        set_tiling(tmp, single_target(ctx, tmp), max_range);
+        I.n_tiles = tmp.n_tiles;
+        I.patterns_per_tile = tmp.range_len;
+    }
+    I.device_bytes = bytes;
+    // post: write N-2 non-root internal partials, read them once as children; pre: read q of the
+    // N-2 non-root internal nodes, read their p again, write their q; plus the tip codes twice.
+    const uint64_t node_stream = (uint64_t)P * ((f64 ? 32ull : 16ull) * C + 4ull);   // partial + exponent
+    I.stream_bytes = 5ull * (uint64_t)(N - 2) * node_stream + 2ull * (uint64_t)N * P;
+    I.flops = (uint64_t)(N - 1) * P * C * (68ull + 216ull);
+
+    ctx->used += bytes;
+    ctx->handles.push_back(h);
+    *out = h;
+    return PG_OK;
+}
+
+pg_status pg_get_info(const pg_handle *h, pg_handle_info *out) {
+    if (!h || !out) return fail(PG_ERR_INVALID, "NULL argument");
+    *out = h->info;
+    return PG_OK;
+}
+
+namespace {
+
+void fill_args_one(pg::BatchArgs<1> &a, const pg::ProbDesc &d) {
+    a.n = 1;
+    a.tile_base[0] = 0;
+    a.tile_base[1] = d.n_tiles;
+    a.mat_base[0] = 0;
+    a.mat_base[1] = d.n_nodes * d.C;
+    a.red_base[0] = 0;
+    a.red_base[1] = d.n_nodes + 1;
+    a.d[0] = d;
+}
+
+}  // namespace
+
+pg_status pg_eval_async(pg_handle *h, const double *d_b, double *d_logL, double *d_grad,
+                        double *d_hess, double *d_site_logL, void *stream) {
+    if (!h || !d_b) return fail(PG_ERR_INVALID, "NULL handle or branch lengths");
+    DeviceGuard g(h->ctx->device);
+    if (!g.ok) return fail(PG_ERR_CUDA, "cannot select device %d", h->ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    pg::BatchArgs<1> a;
+    pg::ProbDesc d = h->desc;
+    d.b = d_b;
+    d.out_logL = d_logL;
+    d.out_grad = d_grad;
+    d.out_hess = d_hess;
+    d.out_site = d_site_logL;
+    set_tiling(d, single_target(h->ctx, d), h->ctx->max_range ? h->ctx->max_range : pg::kMaxRange);
+    fill_args_one(a, d);
+    cudaError_t e = pg::launch_eval_nt<1>(a, d_hess != nullptr, s);
+    if (e != cudaSuccess) return fail(PG_ERR_CUDA, "launch: %s", cudaGetErrorString(e));
+    h->last_stream = s;
+    return PG_OK;
+}
+
+pg_status pg_eval_batch_async(pg_handle *const *hs, int32_t k, const double *const *d_b,
+                              double *d_logL, double *const *d_grad, double *const *d_hess,
+                              void *stream) {
+    if (k < 0 || (k > 0 && (!hs || !d_b || !d_logL))) return fail(PG_ERR_INVALID, "bad batch arguments");
+    if (k == 0) return PG_OK;
+    for (int i = 0; i < k; ++i) {
+        if (!hs[i] || !d_b[i]) return fail(PG_ERR_INVALID, "batch entry %d is NULL", i);
+        if (hs[i]->ctx != hs[0]->ctx) return fail(PG_ERR_INVALID, "batch mixes contexts");
+    }
+    DeviceGuard g(hs[0]->ctx->device);
+    if (!g.ok) return fail(PG_ERR_CUDA, "cannot select device %d", hs[0]->ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    auto *a = new (std::nothrow) pg::BatchArgs<pg::kMaxBatch>;
+    if (!a) return fail(PG_ERR_OOM, "host allocation failed");
+    for (int key = 0; key < 2 * pg::kMaxCat; ++key) {
+        const int C = 1 + key / 2, prec = key % 2;
+        std::vector<int> idx;
+        for (int i = 0; i < k; ++i)
+            if (hs[i]->desc.C == C && hs[i]->desc.precision == prec) idx.push_back(i);
+        for (size_t at = 0; at < idx.size(); at += pg::kMaxBatch) {
+            const int cnt = (int)std::min<size_t>(pg::kMaxBatch, idx.size() - at);
+            a->n = cnt;
+            a->tile_base[0] = a->mat_base[0] = a->red_base[0] = 0;
+            bool hess = false;
+            // blocks in proportion to each problem's partial-stream work, one wave in total
+            double work = 0.0;
+            for (int j = 0; j < cnt; ++j) work += (double)hs[idx[at + j]]->info.stream_bytes + 1.0;
+            const pg_ctx *cx = hs[0]->ctx;
+            const int slots = cx->n_sm * cx->blocks_per_sm[prec][C];
+            const int max_range = cx->max_range ? cx->max_range : pg::kMaxRange;
+            for (int j = 0; j < cnt; ++j) {
+                const int i = idx[at + j];
+                pg::ProbDesc d = hs[i]->desc;
+                const double share = ((double)hs[i]->info.stream_bytes + 1.0) / work;
+                set_tiling(d, std::min(hs[i]->max_tiles, std::max(1, (int)(slots * share))), max_range);
+                d.b = d_b[i];
+                d.out_logL = d_logL + i;
+                d.out_grad = d_grad ? d_grad[i] : nullptr;
+                d.out_hess = d_hess ? d_hess[i] : nullptr;
+                d.out_site = nullptr;
+                hess = hess || d.out_hess;
+                a->d[j] = d;
+                a->tile_base[j + 1] = a->tile_base[j] + d.n_tiles;
+                a->mat_base[j + 1] = a->mat_base[j] + d.n_nodes * d.C;
+                a->red_base[j + 1] = a->red_base[j] + d.n_nodes + 1;
+                hs[i]->last_stream = s;
+            }
+            cudaError_t e = pg::launch_eval_nt<pg::kMaxBatch>(*a, hess, s);
+            if (e != cudaSuccess) { delete a; return fail(PG_ERR_CUDA, "launch: %s", cudaGetErrorString(e)); }
+        }
+    }
+    delete a;
+    return PG_OK;
+}
+
+pg_status pg_eval_status(pg_handle *h) {
+    if (!h) return fail(PG_ERR_INVALID, "NULL handle");
+    DeviceGuard g(h->ctx->device);
+    PG_CUDA(cudaStreamSynchronize(h->last_stream));
+    int st = 0;
+    PG_CUDA(cudaMemcpy(&st, h->desc.status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st) PG_CUDA(cudaMemset(h->desc.status, 0, sizeof(int)));
+    if (st & pg::kStatusBadLength) return fail(PG_ERR_INVALID, "a branch length was negative or not finite");
+    if (st & pg::kStatusNumeric) return fail(PG_ERR_NUMERIC, "a site likelihood was zero or not finite");
+    return PG_OK;
+}
+
+pg_status pg_eval(pg_handle *h, const double *b, double *logL, double *grad, double *hess,
+                  double *site_logL) {
+    if (!h || !b) return fail(PG_ERR_INVALID, "NULL handle or branch lengths");
+    DeviceGuard g(h->ctx->device);
+    if (!g.ok) return fail(PG_ERR_CUDA, "cannot select device %d", h->ctx->device);
+    const int n = h->desc.n_nodes, P = h->desc.P;
+    PG_CUDA(cudaMemcpy(h->io_b, b, sizeof(double) * n, cudaMemcpyHostToDevice));
+    pg_status st = pg_eval_async(h, h->io_b, h->io_logL, grad ? h->io_grad : nullptr,
+                                 hess ? h->io_hess : nullptr, site_logL ? h->io_site : nullptr, nullptr);
+    if (st != PG_OK) return st;
+    PG_CUDA(cudaStreamSynchronize(nullptr));
+    if (logL) PG_CUDA(cudaMemcpy(logL, h->io_logL, sizeof(double), cudaMemcpyDeviceToHost));
+    if (grad) PG_CUDA(cudaMemcpy(grad, h->io_grad, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    if (hess) PG_CUDA(cudaMemcpy(hess, h->io_hess, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    if (site_logL && P > 0) PG_CUDA(cudaMemcpy(site_logL, h->io_site, sizeof(double) * P, cudaMemcpyDeviceToHost));
+    return pg_eval_status(h);
+}
+
+}  // extern "C"

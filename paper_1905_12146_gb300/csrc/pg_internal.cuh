@@ -1,0 +1,85 @@
+// Internal structures shared by the host side (pg_api.cu) and the kernels (pg_nt.cu).
+// Not part of the C ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace pg {
+
+constexpr int kStates = 4;      // nucleotide state space handled by the kernels in pg_nt.cu
+constexpr int kMaxCat = 4;      // rate categories held in registers per pattern
+constexpr int kMaxBatch = 32;   // problems per batched launch (kernel-parameter descriptors)
+constexpr int kMaxRange = 1024;  // patterns per thread block of the tree kernel (shared arrays)
+constexpr int kBlock = 256;      // threads per block of the tree kernel
+// FP32 transition table per (branch, category), float4 columns of the 4x4 matrices:
+//   [0..4]  P hi (columns 0..3, then the row sums = P applied to the all-ones vector)
+//   [5..9]  P lo (the FP32 residual P - hi of the same entries)
+//   [10..13] D hi, [14..17] D lo, with D = P - I
+constexpr int kPtabCols = 18;
+constexpr int kColPlo = 5, kColDhi = 10, kColDlo = 14;
+// FP64 transition table per (branch, category): 5 columns of 4 doubles as double2 pairs
+constexpr int kPtab64Pairs = 10;
+
+// device status bits (sticky until read by pg_eval_status / pg_eval)
+constexpr int kStatusBadLength = 1;
+constexpr int kStatusNumeric = 2;
+
+// Everything one problem's kernels need.  Lives in kernel parameter space (by value), so a
+// launch never depends on host memory that may change afterwards.
+struct ProbDesc {
+    // tree: internal-node operations sorted by height, {k, c0, c1, 0} as node ids
+    const int4 *ops;
+    const int *level_off;          // [n_levels + 1] offsets into ops
+    // data
+    const uint8_t *tips;           // [N][P], code >= 4 = all-ones
+    const double *weights;         // [P]
+    // model
+    const double *b;               // [n] branch lengths of this evaluation (device)
+    const double *Qd;              // [n_models][4][4] FP64 row-major
+    const float4 *Qf;              // [n_models][4] FP32 columns of Q
+    const int *bmodel;             // [n] or nullptr (model 0)
+    float4 *Ptab;                  // FP32: [n][C][kPtabCols]
+    double2 *Ptab64;               // FP64: [n][C][kPtab64Pairs]
+    // pass buffers: FP32 float4 [N-1][C][P], FP64 double2 [N-1][C][P][2]
+    void *post;                    // post-order partials of internal nodes
+    void *pre;                     // pre-order partials of internal nodes
+    int *pe;                       // [N-1][P] log2 scale of post partials
+    int *qe;                       // [N-1][P] log2 scale of pre partials
+    double *gpart;                 // [n][slot_cap] per-(block, piece) gradient sums
+    double *hpart;                 // [n][slot_cap] per-(block, piece) Hessian-diagonal sums
+    double *lpart;                 // [slot_cap] per-(block, piece) log-likelihood sums
+    int *status;
+    // outputs of this evaluation (device, may be null)
+    double *out_logL, *out_grad, *out_hess, *out_site;
+    // sizes
+    int n_tips, n_nodes, root, n_levels;
+    int P;                         // site patterns (rows of every partial array are P long)
+    int slot_cap;                  // capacity of the per-branch slot arrays
+    // tiling of this launch: n_tiles blocks, each a contiguous range of range_len patterns
+    // (the last one shorter); a node's pairs in one block span at most pieces 32-lane chunks
+    int n_tiles, range_len, pieces, n_tg;   // n_tg = n_tiles * pieces used slots
+    int C, n_models;
+    int precision;                 // 0 FP32 partials, 1 FP64 partials
+    double pi[kStates], cw[kMaxCat], rates[kMaxCat];
+    float pif[kStates], gw[kMaxCat], gw2[kMaxCat];   // FP32 pi, r_l w_l, r_l^2 w_l
+};
+
+template <int MAXB>
+struct BatchArgs {
+    int n;
+    int tile_base[MAXB + 1];   // prefix sums of n_tiles   (tree kernel blocks)
+    int mat_base[MAXB + 1];    // prefix sums of n * C     (P-build threads)
+    int red_base[MAXB + 1];    // prefix sums of n + 1     (reduce warps)
+    ProbDesc d[MAXB];
+};
+
+// launchers (pg_nt.cu); every problem of one launch shares C and precision
+template <int MAXB>
+cudaError_t launch_eval_nt(const BatchArgs<MAXB> &args, bool hess, cudaStream_t s);
+// resident blocks per SM of the tree kernel for C categories and the given precision
+int tree_blocks_per_sm(int C, bool f64);
+
+}  // namespace pg

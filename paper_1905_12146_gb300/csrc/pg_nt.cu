@@ -1,0 +1,986 @@
+// Nucleotide (m = 4) kernels: FP64 transition matrices, the fused post-order / root /
+// pre-order / gradient pass, and the deterministic per-branch reduction.
+//
+// Work decomposition.  Site patterns are independent (Section 2.1), so the tree kernel gives each
+// thread block a tile of 32*G patterns and lets it walk the WHOLE tree for that tile: the
+// post-order pass level by level from the tips (Section 2.3), the root likelihood, then the
+// pre-order pass level by level from the root (Section 2.4) with the branch gradient
+// (Section 2.5) computed on the way down.  Levels are synchronised with __syncthreads only; no
+// block ever waits for another block, so an evaluation is three launches whatever the tree
+// height.  Inside a level a warp takes (node, group of 32 patterns) tasks; a lane owns one
+// pattern and all C rate categories of it, so the per-pattern power-of-two rescaling needs no
+// cross-lane traffic.
+//
+// FP32 numerics.  Partials are stored in FP32.  Round-to-nearest is unbiased only when the
+// discarded bits are uniformly distributed; in the pruning update the bulk of each state's
+// value is one large term (the transition matrix is close to I for short branches) to which
+// small terms of widely spread magnitudes are added, and those additions lose slightly more
+// than they gain.  Over a thousand nodes that bias, not random rounding, dominates the error
+// of logL.  Three measures remove it:
+//   * P = I + D, so a child's contribution is a = p + S with S = D p small and computed from
+//     an FP32 hi/lo split of D; the parent's value (p0 + S0)(p1 + S1) is formed as the exact
+//     product p0 p1 (value + FMA residual) plus the small cross terms, and rounded once;
+//   * tip children use P's columns as an FP32 hi/lo pair (P applied to a 0/1 vector is a column,
+//     or the row sums for the all-ones vector);
+//   * every tip vector of pattern p is multiplied by a pattern-specific factor r_p in [1, 2)
+//     (the lowbias32 integer hash of p), so exactly representable sub-patterns shared by many
+//     sites get different mantissas at different sites.  Each tip contributes r_p once, so L_p
+//     carries r_p^N and log L_p loses N log r_p, subtracted in FP64.
+// The root likelihood, the logarithm and all sums over patterns and tiles are FP64.  The
+// pre-order pass feeds only the gradient and uses plain FP32.
+//
+// FP64 numerics.  Every partial, product and sum in FP64 (no dither, no splitting).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "pg_internal.cuh"
+
+namespace pg {
+namespace {
+
+// ------------------------------------------------------------------------------------------
+// small helpers
+// ------------------------------------------------------------------------------------------
+
+__device__ __forceinline__ float4 f4(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
+__device__ __forceinline__ float4 mul(float4 a, float4 b) { return f4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w); }
+__device__ __forceinline__ float4 scal(float4 a, float s) { return f4(a.x * s, a.y * s, a.z * s, a.w * s); }
+__device__ __forceinline__ float dot(float4 a, float4 b) { return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x))); }
+__device__ __forceinline__ float hmax(float4 a) { return fmaxf(fmaxf(a.x, a.y), fmaxf(a.z, a.w)); }
+__device__ __forceinline__ float4 fma4(float4 col, float s, float4 acc) {
+    return f4(fmaf(col.x, s, acc.x), fmaf(col.y, s, acc.y), fmaf(col.z, s, acc.z), fmaf(col.w, s, acc.w));
+}
+
+// y = M v with M given by its four columns
+__device__ __forceinline__ float4 matvec(const float4 (&col)[4], float4 v) {
+    float4 a = scal(col[0], v.x);
+    a = fma4(col[1], v.y, a);
+    a = fma4(col[2], v.z, a);
+    return fma4(col[3], v.w, a);
+}
+// y = M' v with M given by its four columns
+__device__ __forceinline__ float4 matvec_t(const float4 (&col)[4], float4 v) {
+    return f4(dot(col[0], v), dot(col[1], v), dot(col[2], v), dot(col[3], v));
+}
+// y = (Mhi + Mlo) v, the small half first
+__device__ __forceinline__ float4 matvec_hilo(const float4 *hi, const float4 *lo, float4 v) {
+    float4 a = scal(__ldg(lo), v.x);
+    a = fma4(__ldg(lo + 1), v.y, a);
+    a = fma4(__ldg(lo + 2), v.z, a);
+    a = fma4(__ldg(lo + 3), v.w, a);
+    a = fma4(__ldg(hi), v.x, a);
+    a = fma4(__ldg(hi + 1), v.y, a);
+    a = fma4(__ldg(hi + 2), v.z, a);
+    return fma4(__ldg(hi + 3), v.w, a);
+}
+
+__device__ __forceinline__ void load_cols(const float4 *p, float4 (&c)[4]) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) c[t] = __ldg(p + t);
+}
+
+// (x0 + s0)(x1 + s1) rounded once: exact product x0*x1 (value + FMA residual) plus cross terms
+__device__ __forceinline__ float prod_split(float x0, float s0, float x1, float s1) {
+    const float h = x0 * x1;
+    const float res = fmaf(x0, x1, -h);
+    const float small = fmaf(s0, x1 + s1, x0 * s1);
+    return h + (res + small);
+}
+
+// Pattern-specific factor in [1, 2): lowbias32 integer hash (C. Wellons) of the pattern index
+// as a 23-bit mantissa.
+__device__ __forceinline__ float pattern_factor(uint32_t p) {
+    uint32_t x = p + 0x9E3779B9u;
+    x ^= x >> 16; x *= 0x21F0AAADu;
+    x ^= x >> 15; x *= 0x735A2D97u;
+    x ^= x >> 15;
+    return __uint_as_float(0x3F800000u | (x >> 9));
+}
+
+// e such that mx * 2^-e lies in [1, 2) (0 for zero / non-finite, which are left as they are)
+__device__ __forceinline__ int scale_exponent(float mx) {
+    int bits = __float_as_int(mx);
+    int e = ((bits >> 23) & 0xff) - 127;
+    if (e == -127) {
+        if (mx == 0.0f) return 0;
+        int ee;
+        frexpf(mx, &ee);
+        return ee - 1;
+    }
+    if (e == 128) return 0;
+    return e;
+}
+__device__ __forceinline__ int scale_exponent64(double mx) {
+    if (!(mx > 0.0) || isinf(mx)) return 0;
+    int e;
+    frexp(mx, &e);
+    return e - 1;
+}
+
+__device__ __forceinline__ float pow2f(int e) {   // 2^e, e in [-126, 127]
+    return __int_as_float((e + 127) << 23);
+}
+__device__ __forceinline__ float4 scale4(float4 v, int e) {   // v * 2^-e exactly
+    if (e >= -126 && e <= 126) return scal(v, pow2f(-e));
+    return f4(ldexpf(v.x, -e), ldexpf(v.y, -e), ldexpf(v.z, -e), ldexpf(v.w, -e));
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int MAXB>
+__device__ __forceinline__ int find_problem(const int (&base)[MAXB + 1], int n, int x) {
+    int lo = 0, hi = n;   // base[lo] <= x < base[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (base[mid] <= x) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// ------------------------------------------------------------------------------------------
+// K1: transition matrices in FP64 (Sections 2.1, 2.5): P = e^{Q b r} by truncated Taylor series
+// of degree 12 with scaling and squaring, ||A / 2^s||_1 <= 1/4 (truncation < 3e-18).
+// ------------------------------------------------------------------------------------------
+
+__device__ void mat4_mul(const double (&A)[16], const double (&B)[16], double (&C)[16]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            double s = A[i * 4] * B[j];
+            s = fma(A[i * 4 + 1], B[4 + j], s);
+            s = fma(A[i * 4 + 2], B[8 + j], s);
+            C[i * 4 + j] = fma(A[i * 4 + 3], B[12 + j], s);
+        }
+}
+
+__device__ void expm4_taylor(double (&X)[16], double (&E)[16]) {
+    double nrm = 0.0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        nrm = fmax(nrm, fabs(X[j]) + fabs(X[4 + j]) + fabs(X[8 + j]) + fabs(X[12 + j]));
+    int s = 0;
+    while (nrm > 0.25 && s < 1100) { nrm *= 0.5; ++s; }
+    const double sc = ldexp(1.0, -s);
+#pragma unroll
+    for (int t = 0; t < 16; ++t) X[t] *= sc;
+    // Horner: E = I + X/1 (I + X/2 (I + ... (I + X/12)))  evaluated from the inside out
+#pragma unroll
+    for (int t = 0; t < 16; ++t) E[t] = (t % 5 == 0) ? 1.0 : 0.0;
+    double T[16];
+#pragma unroll 1
+    for (int k = 12; k >= 1; --k) {
+        mat4_mul(X, E, T);
+        const double inv = 1.0 / (double)k;
+#pragma unroll
+        for (int t = 0; t < 16; ++t) E[t] = T[t] * inv + ((t % 5 == 0) ? 1.0 : 0.0);
+    }
+#pragma unroll 1
+    for (int q = 0; q < s; ++q) {
+        mat4_mul(E, E, T);
+#pragma unroll
+        for (int t = 0; t < 16; ++t) E[t] = T[t];
+    }
+}
+
+template <int MAXB>
+__global__ void __launch_bounds__(128) pmatrix4_kernel(const __grid_constant__ BatchArgs<MAXB> a) {
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= a.mat_base[a.n]) return;
+    const int pid = find_problem<MAXB>(a.mat_base, a.n, gid);
+    const ProbDesc &d = a.d[pid];
+    const int item = gid - a.mat_base[pid];
+    const int i = item / d.C, l = item - i * d.C;
+    if (i == d.root) return;
+    double bl = d.b[i];
+    if (!(bl >= 0.0) || isinf(bl)) {
+        atomicOr(d.status, kStatusBadLength);
+        bl = 0.0;
+    }
+    const int model = d.bmodel ? d.bmodel[i] : 0;
+    const double t = bl * d.rates[l];
+    double X[16], E[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) X[u] = d.Qd[model * 16 + u] * t;
+    expm4_taylor(X, E);
+    double rs[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) rs[r] = (E[r * 4] + E[r * 4 + 1]) + (E[r * 4 + 2] + E[r * 4 + 3]);
+    if (d.precision == 1) {
+        double2 *out = d.Ptab64 + ((size_t)i * d.C + l) * kPtab64Pairs;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            const double v0 = c < 4 ? E[c] : rs[0], v1 = c < 4 ? E[4 + c] : rs[1];
+            const double v2 = c < 4 ? E[8 + c] : rs[2], v3 = c < 4 ? E[12 + c] : rs[3];
+            out[2 * c] = make_double2(v0, v1);
+            out[2 * c + 1] = make_double2(v2, v3);
+        }
+        return;
+    }
+    float4 *out = d.Ptab + ((size_t)i * d.C + l) * kPtabCols;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+        float hi[4], lo[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const double v = (c < 4) ? E[r * 4 + c] : rs[r];
+            hi[r] = (float)v;
+            lo[r] = (float)(v - (double)hi[r]);
+        }
+        out[c] = f4(hi[0], hi[1], hi[2], hi[3]);
+        out[kColPlo + c] = f4(lo[0], lo[1], lo[2], lo[3]);
+        if (c < 4) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const double v = E[r * 4 + c] - (r == c ? 1.0 : 0.0);
+                hi[r] = (float)v;
+                lo[r] = (float)(v - (double)hi[r]);
+            }
+            out[kColDhi + c] = f4(hi[0], hi[1], hi[2], hi[3]);
+            out[kColDlo + c] = f4(lo[0], lo[1], lo[2], lo[3]);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// K2-K4: the tree pass for one contiguous range of patterns per thread block
+// ------------------------------------------------------------------------------------------
+//
+// A block owns patterns [p0, p0 + cnt).  At a level with nd nodes its work is the nd * cnt
+// (node, pattern) pairs, pattern-fastest; warps take 32 consecutive pairs at a time, so lanes stay
+// busy for any range length and a warp may straddle node boundaries.  Sums over patterns (logL,
+// branch gradients) are reduced per node segment of the warp and written to a fixed slot
+// (block, piece), piece = the warp's 32-pair chunk counted from the node's first chunk; the
+// reduction kernel adds the slots of a branch in a fixed order.
+
+// Adds v over the lanes of each node segment of this warp and hands (node, piece, sum) to
+// emit on lane 0; also zero-fills the slots a node does not use (by its first chunk's warp).
+template <class Emit>
+__device__ __forceinline__ void segment_sums(int u, bool active, double v, int chunk, int cnt,
+                                             int pieces, Emit &&emit) {
+    const int lane = threadIdx.x & 31;
+    const int u_lo = __shfl_sync(0xffffffffu, u, 0), u_hi = __shfl_sync(0xffffffffu, u, 31);
+    for (int us = u_lo; us <= u_hi; ++us) {
+        const double s = warp_sum((active && u == us) ? v : 0.0);
+        const int first = (us * cnt) >> 5, last = ((us + 1) * cnt - 1) >> 5;
+        if (lane == 0) {
+            emit(us, chunk - first, s);
+            if (chunk == first)
+                for (int pc = last - first + 1; pc < pieces; ++pc) emit(us, pc, 0.0);
+        }
+    }
+}
+
+// ---- FP64 partials ------------------------------------------------------------------------
+
+struct D4 {
+    double v[4];
+};
+
+__device__ __forceinline__ D4 ld_d4(const double2 *base, size_t idx) {
+    const double2 a = base[2 * idx], b = base[2 * idx + 1];
+    return D4{{a.x, a.y, b.x, b.y}};
+}
+__device__ __forceinline__ void st_d4(double2 *base, size_t idx, const D4 &x) {
+    base[2 * idx] = make_double2(x.v[0], x.v[1]);
+    base[2 * idx + 1] = make_double2(x.v[2], x.v[3]);
+}
+// column c of a P64 table: P[0..3][c]
+__device__ __forceinline__ D4 col64(const double2 *P, int c) {
+    const double2 a = __ldg(P + 2 * c), b = __ldg(P + 2 * c + 1);
+    return D4{{a.x, a.y, b.x, b.y}};
+}
+__device__ __forceinline__ D4 matvec64(const double2 *P, const D4 &x) {
+    D4 a{{0, 0, 0, 0}};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const D4 col = col64(P, c);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) a.v[s] = fma(col.v[s], x.v[c], a.v[s]);
+    }
+    return a;
+}
+__device__ __forceinline__ D4 matvec64_t(const double2 *P, const D4 &x) {
+    D4 a;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const D4 col = col64(P, c);
+        a.v[c] = fma(col.v[3], x.v[3], fma(col.v[2], x.v[2], fma(col.v[1], x.v[1], col.v[0] * x.v[0])));
+    }
+    return a;
+}
+__device__ __forceinline__ D4 matvecQ64(const double *Q, const D4 &x) {   // row-major Q
+    D4 a;
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+        a.v[s] = fma(Q[s * 4 + 3], x.v[3], fma(Q[s * 4 + 2], x.v[2], fma(Q[s * 4 + 1], x.v[1], Q[s * 4] * x.v[0])));
+    return a;
+}
+__device__ __forceinline__ double dot64(const D4 &a, const D4 &b) {
+    return fma(a.v[3], b.v[3], fma(a.v[2], b.v[2], fma(a.v[1], b.v[1], a.v[0] * b.v[0])));
+}
+
+template <int C>
+__device__ __forceinline__ void post_pair64(const ProbDesc &d, const int4 op, const int p, const bool active,
+                                           double &L, int &E) {
+    const int N = d.n_tips, Pn = d.P;
+    const int k = op.x, c0 = op.y, c1 = op.z;
+    const bool t0 = c0 < N, t1 = c1 < N;
+    const bool root = (k == d.root);
+    const double2 *post = static_cast<const double2 *>(d.post);
+    int y0 = 0, y1 = 0;
+    E = 0;
+    if (t0) y0 = min((int)d.tips[(size_t)c0 * Pn + p], 4); else E += d.pe[(size_t)(c0 - N) * Pn + p];
+    if (t1) y1 = min((int)d.tips[(size_t)c1 * Pn + p], 4); else E += d.pe[(size_t)(c1 - N) * Pn + p];
+    D4 v[C];
+    double mx = 0.0;
+    L = 0.0;
+#pragma unroll
+    for (int l = 0; l < C; ++l) {
+        const double2 *P0 = d.Ptab64 + ((size_t)c0 * C + l) * kPtab64Pairs;
+        const double2 *P1 = d.Ptab64 + ((size_t)c1 * C + l) * kPtab64Pairs;
+        const D4 a0 = t0 ? col64(P0, y0) : matvec64(P0, ld_d4(post, ((size_t)(c0 - N) * C + l) * Pn + p));
+        const D4 a1 = t1 ? col64(P1, y1) : matvec64(P1, ld_d4(post, ((size_t)(c1 - N) * C + l) * Pn + p));
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            v[l].v[s] = a0.v[s] * a1.v[s];
+            mx = fmax(mx, v[l].v[s]);
+        }
+        if (root) {
+            double s = 0.0;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) s = fma(d.pi[t], v[l].v[t], s);
+            L = fma(d.cw[l], s, L);
+        }
+    }
+    if (root || !active) return;
+    const int e = scale_exponent64(mx);
+    double2 *out = static_cast<double2 *>(d.post);
+#pragma unroll
+    for (int l = 0; l < C; ++l) {
+        D4 w;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) w.v[s] = ldexp(v[l].v[s], -e);
+        st_d4(out, ((size_t)(k - N) * C + l) * Pn + p, w);
+    }
+    d.pe[(size_t)(k - N) * Pn + p] = E + e;
+}
+
+template <int C, bool HESS>
+__device__ __forceinline__ void pre_pair64(const ProbDesc &d, const int4 op, const int p, const bool active,
+                                          double (&g)[2], double (&h)[2], int &dEsum) {
+    const int N = d.n_tips, Pn = d.P;
+    const int k = op.x, c0 = op.y, c1 = op.z;
+    const bool t0 = c0 < N, t1 = c1 < N;
+    const bool root = (k == d.root);
+    const double2 *post = static_cast<const double2 *>(d.post);
+    double2 *pre = static_cast<double2 *>(d.pre);
+    const int Eq = root ? 0 : d.qe[(size_t)(k - N) * Pn + p];
+    int E0 = 0, E1 = 0, y0 = 0, y1 = 0;
+    if (t0) y0 = min((int)d.tips[(size_t)c0 * Pn + p], 4); else E0 = d.pe[(size_t)(c0 - N) * Pn + p];
+    if (t1) y1 = min((int)d.tips[(size_t)c1 * Pn + p], 4); else E1 = d.pe[(size_t)(c1 - N) * Pn + p];
+    const double *Q0 = d.Qd + 16 * (d.bmodel ? d.bmodel[c0] : 0);
+    const double *Q1 = d.Qd + 16 * (d.bmodel ? d.bmodel[c1] : 0);
+    double m0 = 0, m1 = 0;
+    g[0] = g[1] = h[0] = h[1] = 0.0;
+    D4 q0[C], q1[C];
+#pragma unroll
+    for (int l = 0; l < C; ++l) {
+        const D4 qk = root ? D4{{d.pi[0], d.pi[1], d.pi[2], d.pi[3]}}
+                           : ld_d4(pre, ((size_t)(k - N) * C + l) * Pn + p);
+        const double2 *P0 = d.Ptab64 + ((size_t)c0 * C + l) * kPtab64Pairs;
+        const double2 *P1 = d.Ptab64 + ((size_t)c1 * C + l) * kPtab64Pairs;
+        const D4 a0 = t0 ? col64(P0, y0) : matvec64(P0, ld_d4(post, ((size_t)(c0 - N) * C + l) * Pn + p));
+        const D4 a1 = t1 ? col64(P1, y1) : matvec64(P1, ld_d4(post, ((size_t)(c1 - N) * C + l) * Pn + p));
+        D4 qt0, qt1;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) { qt0.v[s] = qk.v[s] * a1.v[s]; qt1.v[s] = qk.v[s] * a0.v[s]; }
+        const D4 u0 = matvecQ64(Q0, a0), u1 = matvecQ64(Q1, a1);
+        g[0] = fma(d.rates[l] * d.cw[l], dot64(qt0, u0), g[0]);
+        g[1] = fma(d.rates[l] * d.cw[l], dot64(qt1, u1), g[1]);
+        if (HESS) {
+            h[0] = fma(d.rates[l] * d.rates[l] * d.cw[l], dot64(qt0, matvecQ64(Q0, u0)), h[0]);
+            h[1] = fma(d.rates[l] * d.rates[l] * d.cw[l], dot64(qt1, matvecQ64(Q1, u1)), h[1]);
+        }
+        if (!t0) {
+            q0[l] = matvec64_t(P0, qt0);
+#pragma unroll
+            for (int s = 0; s < 4; ++s) m0 = fmax(m0, q0[l].v[s]);
+        }
+        if (!t1) {
+            q1[l] = matvec64_t(P1, qt1);
+#pragma unroll
+            for (int s = 0; s < 4; ++s) m1 = fmax(m1, q1[l].v[s]);
+        }
+    }
+    if (!t0 && active) {
+        const int e = scale_exponent64(m0);
+#pragma unroll
+        for (int l = 0; l < C; ++l) {
+            D4 w;
+#pragma unroll
+            for (int s = 0; s < 4; ++s) w.v[s] = ldexp(q0[l].v[s], -e);
+            st_d4(pre, ((size_t)(c0 - N) * C + l) * Pn + p, w);
+        }
+        d.qe[(size_t)(c0 - N) * Pn + p] = Eq + E1 + e;
+    }
+    if (!t1 && active) {
+        const int e = scale_exponent64(m1);
+#pragma unroll
+        for (int l = 0; l < C; ++l) {
+            D4 w;
+#pragma unroll
+            for (int s = 0; s < 4; ++s) w.v[s] = ldexp(q1[l].v[s], -e);
+            st_d4(pre, ((size_t)(c1 - N) * C + l) * Pn + p, w);
+        }
+        d.qe[(size_t)(c1 - N) * Pn + p] = Eq + E0 + e;
+    }
+    dEsum = Eq + E0 + E1;
+}
+
+// ---- FP32 kernel: per-warp double-buffered cp.async prefetch of the partials ------------------
+//
+// A warp's next 32 pairs are independent of the pairs it is computing (same level), so their
+// partial vectors are copied global -> shared (cp.async, 16 B per copy, L2 only) while the current
+// ones are processed.  Shared memory, not registers, holds the bytes in flight.
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// where a lane's pair lives and its small inputs (loaded into registers at prefetch time)
+struct PairMeta {
+    int4 op;
+    int u, q, p;
+    int e0, e1, eq;   // log2 scales of the children's post partials and of q_k
+    int y0, y1;       // tip codes of tip children
+    bool active;
+};
+
+// items per lane in a stage: post needs both children (2C float4), pre also q_k (3C)
+template <int C>
+__host__ __device__ constexpr int stage_items() { return 3 * C; }
+
+template <int C>
+__host__ __device__ constexpr size_t f32_stage_bytes(int warps) {
+    return (size_t)warps * 2 * stage_items<C>() * 32 * sizeof(float4);
+}
+
+template <int C, bool PRE>
+__device__ __forceinline__ void prefetch_pair(const ProbDesc &d, int o0, int cnt, int p0, int npairs, int chunk,
+                                              float4 *slot, PairMeta &m) {
+    const int lane = threadIdx.x & 31;
+    const int N = d.n_tips, Pn = d.P;
+    const int j = chunk * 32 + lane;
+    m.active = j < npairs;
+    const int jj = m.active ? j : npairs - 1;
+    m.u = jj / cnt;
+    m.q = jj - m.u * cnt;
+    m.p = p0 + m.q;
+    m.op = __ldg(d.ops + o0 + m.u);
+    const float4 *post = static_cast<const float4 *>(d.post);
+    const int c0 = m.op.y, c1 = m.op.z, k = m.op.x;
+    m.e0 = m.e1 = m.eq = m.y0 = m.y1 = 0;
+    if (c0 < N) m.y0 = min((int)__ldg(d.tips + (size_t)c0 * Pn + m.p), 4);
+    else {
+        m.e0 = __ldcg(d.pe + (size_t)(c0 - N) * Pn + m.p);
+#pragma unroll
+        for (int l = 0; l < C; ++l) cp_async16(slot + l * 32, post + ((size_t)(c0 - N) * C + l) * Pn + m.p);
+    }
+    if (c1 < N) m.y1 = min((int)__ldg(d.tips + (size_t)c1 * Pn + m.p), 4);
+    else {
+        m.e1 = __ldcg(d.pe + (size_t)(c1 - N) * Pn + m.p);
+#pragma unroll
+        for (int l = 0; l < C; ++l) cp_async16(slot + (C + l) * 32, post + ((size_t)(c1 - N) * C + l) * Pn + m.p);
+    }
+    if (PRE && k != d.root) {
+        const float4 *pre = static_cast<const float4 *>(d.pre);
+        m.eq = __ldcg(d.qe + (size_t)(k - N) * Pn + m.p);
+#pragma unroll
+        for (int l = 0; l < C; ++l) cp_async16(slot + (2 * C + l) * 32, pre + ((size_t)(k - N) * C + l) * Pn + m.p);
+    }
+}
+
+// Post-order update of internal node m.op.x for pattern m.p (Section 2.3); at the root returns
+// the site likelihood L (Section 2.3 root inner product with the Section 2.5 mixture) and its
+// log2 scale E instead of storing a partial.
+template <int C>
+__device__ __forceinline__ void post_compute32(const ProbDesc &d, const PairMeta &m, const float4 *slot,
+                                               double &L, int &E) {
+    const int N = d.n_tips, Pn = d.P;
+    const int k = m.op.x, c0 = m.op.y, c1 = m.op.z;
+    const bool t0 = c0 < N, t1 = c1 < N;
+    const bool root = (k == d.root);
+    const float r = pattern_factor((uint32_t)m.p);
+    E = m.e0 + m.e1;
+    float4 v[C];
+    float mx = 0.0f;
+    L = 0.0;
+#pragma unroll
+    for (int l = 0; l < C; ++l) {
+        const float4 *P0 = d.Ptab + ((size_t)c0 * C + l) * kPtabCols;
+        const float4 *P1 = d.Ptab + ((size_t)c1 * C + l) * kPtabCols;
+        float4 x0, x1, s0 = f4(0.f, 0.f, 0.f, 0.f), s1 = f4(0.f, 0.f, 0.f, 0.f);
+        if (t0) {
+            const float4 hi = __ldg(P0 + m.y0), lo = __ldg(P0 + kColPlo + m.y0);
+            x0 = f4(fmaf(hi.x, r, lo.x * r), fmaf(hi.y, r, lo.y * r), fmaf(hi.z, r, lo.z * r), fmaf(hi.w, r, lo.w * r));
+        } else {
+            x0 = slot[l * 32];
+            s0 = matvec_hilo(P0 + kColDhi, P0 + kColDlo, x0);
+        }
+        if (t1) {
+            const float4 hi = __ldg(P1 + m.y1), lo = __ldg(P1 + kColPlo + m.y1);
+            x1 = f4(fmaf(hi.x, r, lo.x * r), fmaf(hi.y, r, lo.y * r), fmaf(hi.z, r, lo.z * r), fmaf(hi.w, r, lo.w * r));
+        } else {
+            x1 = slot[(C + l) * 32];
+            s1 = matvec_hilo(P1 + kColDhi, P1 + kColDlo, x1);
+        }
+        if (root) {
+            double s = d.pi[0] * (((double)x0.x + s0.x) * ((double)x1.x + s1.x));
+            s = fma(d.pi[1], ((double)x0.y + s0.y) * ((double)x1.y + s1.y), s);
+            s = fma(d.pi[2], ((double)x0.z + s0.z) * ((double)x1.z + s1.z), s);
+            s = fma(d.pi[3], ((double)x0.w + s0.w) * ((double)x1.w + s1.w), s);
+            L = fma(d.cw[l], s, L);
+        } else {
+            v[l] = f4(prod_split(x0.x, s0.x, x1.x, s1.x), prod_split(x0.y, s0.y, x1.y, s1.y),
+                      prod_split(x0.z, s0.z, x1.z, s1.z), prod_split(x0.w, s0.w, x1.w, s1.w));
+            mx = fmaxf(mx, hmax(v[l]));
+        }
+    }
+    if (root || !m.active) return;
+    const int e = scale_exponent(mx);
+    float4 *out = static_cast<float4 *>(d.post);
+#pragma unroll
+    for (int l = 0; l < C; ++l) __stcg(out + ((size_t)(k - N) * C + l) * Pn + m.p, scale4(v[l], e));
+    __stcg(d.pe + (size_t)(k - N) * Pn + m.p, E + e);
+}
+
+// Pre-order step at internal node k for pattern p (Section 2.4): the top-of-branch vectors
+// qt_c = q_k o (P_s p_s) of both children, their gradient terms (Section 2.5) and Hessian terms
+// (Section 2.6), and q_c = P_c' qt_c stored for internal children.  The terms are relative to
+// 2^{Eq + E0 + E1} (returned in dEsum).
+template <int C, bool HESS>
+__device__ __forceinline__ void pre_compute32(const ProbDesc &d, const PairMeta &m, const float4 *slot,
+                                              float (&g)[2], float (&h)[2], int &dEsum) {
+    const int N = d.n_tips, Pn = d.P;
+    const int k = m.op.x, c0 = m.op.y, c1 = m.op.z;
+    const bool t0 = c0 < N, t1 = c1 < N;
+    const bool root = (k == d.root);
+    const float r = pattern_factor((uint32_t)m.p);
+    float4 *pre = static_cast<float4 *>(d.pre);
+    float4 a0[C], a1[C];
+#pragma unroll
+    for (int l = 0; l < C; ++l) {
+        const float4 *P0 = d.Ptab + ((size_t)c0 * C + l) * kPtabCols;
+        const float4 *P1 = d.Ptab + ((size_t)c1 * C + l) * kPtabCols;
+        if (t0) a0[l] = scal(__ldg(P0 + m.y0), r);
+        else { float4 H[4]; load_cols(P0, H); a0[l] = matvec(H, slot[l * 32]); }
+        if (t1) a1[l] = scal(__ldg(P1 + m.y1), r);
+        else { float4 H[4]; load_cols(P1, H); a1[l] = matvec(H, slot[(C + l) * 32]); }
+    }
+    g[0] = g[1] = h[0] = h[1] = 0.f;
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const int c = side ? c1 : c0;
+        const bool tip = side ? t1 : t0;
+        float4 Qc[4];
+        load_cols(d.Qf + 4 * (d.bmodel ? d.bmodel[c] : 0), Qc);
+        float4 q[C];
+        float mq = 0.f, gs = 0.f, hs = 0.f;
+#pragma unroll
+        for (int l = 0; l < C; ++l) {
+            const float4 qk = root ? f4(d.pif[0], d.pif[1], d.pif[2], d.pif[3]) : slot[(2 * C + l) * 32];
+            const float4 qt = mul(qk, side ? a0[l] : a1[l]);   // top of branch c
+            const float4 u = matvec(Qc, side ? a1[l] : a0[l]);
+            gs = fmaf(d.gw[l], dot(qt, u), gs);
+            if (HESS) hs = fmaf(d.gw2[l], dot(qt, matvec(Qc, u)), hs);
+            if (!tip) {
+                float4 H[4];
+                load_cols(d.Ptab + ((size_t)c * C + l) * kPtabCols, H);
+                q[l] = matvec_t(H, qt);
+                mq = fmaxf(mq, hmax(q[l]));
+            }
+        }
+        g[side] = gs;
+        h[side] = hs;
+        if (!tip && m.active) {
+            const int e = scale_exponent(mq);
+#pragma unroll
+            for (int l = 0; l < C; ++l) __stcg(pre + ((size_t)(c - N) * C + l) * Pn + m.p, scale4(q[l], e));
+            __stcg(d.qe + (size_t)(c - N) * Pn + m.p, m.eq + (side ? m.e0 : m.e1) + e);
+        }
+    }
+    dEsum = m.eq + m.e0 + m.e1;
+}
+
+// per-pattern values of the block's range, after the stage buffers in dynamic shared memory
+struct RangeArrays {
+    float *invL;   // 1 / Lhat_p  (Lhat in [0.5, 1))
+    int *Eroot;    // log2 scale of L_p (with the r_p^N factor inside)
+    float *w;      // pattern weight
+};
+
+template <int C>
+__device__ __forceinline__ void post_level_chunk(const ProbDesc &d, const PairMeta &m, const float4 *slot,
+                                                 int chunk, int cnt, int pieces, int slot0, RangeArrays &ra) {
+    double L;
+    int E;
+    post_compute32<C>(d, m, slot, L, E);
+    if (m.op.x != d.root) return;   // uniform: the root is alone on its level
+    int e2 = 0;
+    const double f = (L > 0.0 && isfinite(L)) ? frexp(L, &e2) : L;
+    const int Er = E + e2;
+    const double wgt = d.weights[m.p];
+    const double lp = log(f) + (double)Er * 0.69314718055994530942 -
+                      (double)d.n_tips * log((double)pattern_factor((uint32_t)m.p));
+    if (m.active) {
+        ra.invL[m.q] = (float)(1.0 / f);
+        ra.Eroot[m.q] = Er;
+        ra.w[m.q] = (float)wgt;
+        if (!(f > 0.0) || !isfinite(lp)) atomicOr(d.status, kStatusNumeric);
+        if (d.out_site) d.out_site[m.p] = lp;
+    }
+    segment_sums(m.u, m.active, (m.active && wgt != 0.0) ? wgt * lp : 0.0, chunk, cnt, pieces,
+                 [&](int, int pc, double s) { d.lpart[slot0 + pc] = s; });
+}
+
+template <int C, bool HESS>
+__device__ __forceinline__ void pre_level_chunk(const ProbDesc &d, const PairMeta &m, const float4 *slot,
+                                                int o0, int chunk, int cnt, int pieces, int slot0,
+                                                const RangeArrays &ra) {
+    float g[2], h[2];
+    int dEsum;
+    pre_compute32<C, HESS>(d, m, slot, g, h, dEsum);
+    const double wt = m.active ? (double)ra.w[m.q] : 0.0;
+    const int dE = dEsum - ra.Eroot[m.q];
+    const float inv = ra.invL[m.q];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const float dd = ldexpf(g[s], dE) * inv;
+        const double dg = wt != 0.0 ? wt * (double)dd : 0.0;
+        segment_sums(m.u, m.active, dg, chunk, cnt, pieces, [&](int us, int pc, double v) {
+            const int4 o = __ldg(d.ops + o0 + us);
+            d.gpart[(size_t)(s ? o.z : o.y) * d.slot_cap + slot0 + pc] = v;
+        });
+        if (HESS) {
+            const double dh = wt != 0.0 ? wt * (double)(ldexpf(h[s], dE) * inv - dd * dd) : 0.0;
+            segment_sums(m.u, m.active, dh, chunk, cnt, pieces, [&](int us, int pc, double v) {
+                const int4 o = __ldg(d.ops + o0 + us);
+                d.hpart[(size_t)(s ? o.z : o.y) * d.slot_cap + slot0 + pc] = v;
+            });
+        }
+    }
+}
+
+template <int C, bool HESS, int MAXB>
+__global__ void __launch_bounds__(kBlock, 2) tree4f_kernel(const __grid_constant__ BatchArgs<MAXB> a) {
+    extern __shared__ float4 dyn[];
+    const int pid = (MAXB == 1) ? 0 : find_problem<MAXB>(a.tile_base, a.n, (int)blockIdx.x);
+    const ProbDesc &d = a.d[pid];
+    const int tile = (int)blockIdx.x - a.tile_base[pid];
+    const int p0 = tile * d.range_len;
+    const int cnt = min(d.range_len, d.P - p0);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int W = blockDim.x >> 5;
+    const int pieces = d.pieces;
+    const int slot0 = tile * pieces;
+    constexpr int IT = stage_items<C>();
+    float4 *st0 = dyn + (size_t)(warp * 2) * IT * 32 + lane;
+    float4 *st1 = st0 + IT * 32;
+    RangeArrays ra;
+    {
+        char *tail = reinterpret_cast<char *>(dyn + (size_t)W * 2 * IT * 32);
+        ra.invL = reinterpret_cast<float *>(tail);
+        ra.Eroot = reinterpret_cast<int *>(tail + sizeof(float) * d.range_len);
+        ra.w = reinterpret_cast<float *>(tail + 2 * sizeof(float) * d.range_len);
+    }
+    PairMeta m0, m1;
+
+    // post-order, tips to root (Section 2.3)
+    for (int lv = 0; lv < d.n_levels; ++lv) {
+        const int o0 = d.level_off[lv], npairs = (d.level_off[lv + 1] - o0) * cnt;
+        int chunk = warp;
+        if (chunk * 32 < npairs) prefetch_pair<C, false>(d, o0, cnt, p0, npairs, chunk, st0, m0);
+        cp_async_commit();
+        while (chunk * 32 < npairs) {
+            int next = chunk + W;
+            if (next * 32 < npairs) prefetch_pair<C, false>(d, o0, cnt, p0, npairs, next, st1, m1);
+            cp_async_commit();
+            cp_async_wait1();
+            __syncwarp();
+            post_level_chunk<C>(d, m0, st0, chunk, cnt, pieces, slot0, ra);
+            chunk = next;
+            if (chunk * 32 >= npairs) break;
+            next = chunk + W;
+            if (next * 32 < npairs) prefetch_pair<C, false>(d, o0, cnt, p0, npairs, next, st0, m0);
+            cp_async_commit();
+            cp_async_wait1();
+            __syncwarp();
+            post_level_chunk<C>(d, m1, st1, chunk, cnt, pieces, slot0, ra);
+            chunk = next;
+        }
+        cp_async_wait0();
+        __syncthreads();
+    }
+    // pre-order, root to tips (Section 2.4) with the gradient (Section 2.5)
+    for (int lv = d.n_levels - 1; lv >= 0; --lv) {
+        const int o0 = d.level_off[lv], npairs = (d.level_off[lv + 1] - o0) * cnt;
+        int chunk = warp;
+        if (chunk * 32 < npairs) prefetch_pair<C, true>(d, o0, cnt, p0, npairs, chunk, st0, m0);
+        cp_async_commit();
+        while (chunk * 32 < npairs) {
+            int next = chunk + W;
+            if (next * 32 < npairs) prefetch_pair<C, true>(d, o0, cnt, p0, npairs, next, st1, m1);
+            cp_async_commit();
+            cp_async_wait1();
+            __syncwarp();
+            pre_level_chunk<C, HESS>(d, m0, st0, o0, chunk, cnt, pieces, slot0, ra);
+            chunk = next;
+            if (chunk * 32 >= npairs) break;
+            next = chunk + W;
+            if (next * 32 < npairs) prefetch_pair<C, true>(d, o0, cnt, p0, npairs, next, st0, m0);
+            cp_async_commit();
+            cp_async_wait1();
+            __syncwarp();
+            pre_level_chunk<C, HESS>(d, m1, st1, o0, chunk, cnt, pieces, slot0, ra);
+            chunk = next;
+        }
+        cp_async_wait0();
+        __syncthreads();
+    }
+}
+
+// ---- FP64 kernel: direct loads ------------------------------------------------------------
+
+struct TileShared64 {
+    int Eroot[kMaxRange];
+    double w[kMaxRange];
+    double invL64[kMaxRange];
+};
+
+template <int C, bool HESS, int MAXB>
+__global__ void __launch_bounds__(kBlock, 1) tree4d_kernel(const __grid_constant__ BatchArgs<MAXB> a) {
+    __shared__ TileShared64 sh;
+    const int pid = (MAXB == 1) ? 0 : find_problem<MAXB>(a.tile_base, a.n, (int)blockIdx.x);
+    const ProbDesc &d = a.d[pid];
+    const int tile = (int)blockIdx.x - a.tile_base[pid];
+    const int p0 = tile * d.range_len;
+    const int cnt = min(d.range_len, d.P - p0);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int W = blockDim.x >> 5;
+    const int pieces = d.pieces;
+    const int slot0 = tile * pieces;
+
+    for (int lv = 0; lv < d.n_levels; ++lv) {
+        const int o0 = d.level_off[lv], nd = d.level_off[lv + 1] - o0;
+        const int npairs = nd * cnt;
+        for (int chunk = warp; chunk * 32 < npairs; chunk += W) {
+            const int j = chunk * 32 + lane;
+            const bool active = j < npairs;
+            const int jj = active ? j : npairs - 1;
+            const int u = jj / cnt, q = jj - u * cnt;
+            const int p = p0 + q;
+            const int4 op = __ldg(d.ops + o0 + u);
+            double L;
+            int E;
+            post_pair64<C>(d, op, p, active, L, E);
+            if (op.x != d.root) continue;   // uniform: the root is alone on its level
+            int e2 = 0;
+            const double f = (L > 0.0 && isfinite(L)) ? frexp(L, &e2) : L;
+            const int Er = E + e2;
+            const double wgt = d.weights[p];
+            const double lp = log(f) + (double)Er * 0.69314718055994530942;
+            if (active) {
+                sh.invL64[q] = 1.0 / f;
+                sh.Eroot[q] = Er;
+                sh.w[q] = wgt;
+                if (!(f > 0.0) || !isfinite(lp)) atomicOr(d.status, kStatusNumeric);
+                if (d.out_site) d.out_site[p] = lp;
+            }
+            segment_sums(u, active, (active && wgt != 0.0) ? wgt * lp : 0.0, chunk, cnt, pieces,
+                         [&](int, int pc, double s) { d.lpart[slot0 + pc] = s; });
+        }
+        __syncthreads();
+    }
+    for (int lv = d.n_levels - 1; lv >= 0; --lv) {
+        const int o0 = d.level_off[lv], nd = d.level_off[lv + 1] - o0;
+        const int npairs = nd * cnt;
+        for (int chunk = warp; chunk * 32 < npairs; chunk += W) {
+            const int j = chunk * 32 + lane;
+            const bool active = j < npairs;
+            const int jj = active ? j : npairs - 1;
+            const int u = jj / cnt, q = jj - u * cnt;
+            const int p = p0 + q;
+            const int4 op = __ldg(d.ops + o0 + u);
+            int dEsum;
+            double g[2], h[2];
+            pre_pair64<C, HESS>(d, op, p, active, g, h, dEsum);
+            const double wt = active ? sh.w[q] : 0.0;
+            const int dE = dEsum - sh.Eroot[q];
+            const double inv = sh.invL64[q];
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const double dd = ldexp(g[s], dE) * inv;
+                const double dg = wt != 0.0 ? wt * dd : 0.0;
+                segment_sums(u, active, dg, chunk, cnt, pieces, [&](int us, int pc, double v) {
+                    const int4 o = __ldg(d.ops + o0 + us);
+                    d.gpart[(size_t)(s ? o.z : o.y) * d.slot_cap + slot0 + pc] = v;
+                });
+                if (HESS) {
+                    const double dh = wt != 0.0 ? wt * (ldexp(h[s], dE) * inv - dd * dd) : 0.0;
+                    segment_sums(u, active, dh, chunk, cnt, pieces, [&](int us, int pc, double v) {
+                        const int4 o = __ldg(d.ops + o0 + us);
+                        d.hpart[(size_t)(s ? o.z : o.y) * d.slot_cap + slot0 + pc] = v;
+                    });
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// K5: fixed-order reduction over tile groups: one warp per branch (grad, hess), one per logL
+// ------------------------------------------------------------------------------------------
+
+template <int MAXB>
+__global__ void __launch_bounds__(256) reduce_kernel(const __grid_constant__ BatchArgs<MAXB> a, int want_hess) {
+    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (gw >= a.red_base[a.n]) return;
+    const int pid = find_problem<MAXB>(a.red_base, a.n, gw);
+    const ProbDesc &d = a.d[pid];
+    const int item = gw - a.red_base[pid];
+    if (item == d.n_nodes) {
+        double s = 0.0;
+        for (int j = lane; j < d.n_tg; j += 32) s += d.lpart[j];
+        s = warp_sum(s);
+        if (lane == 0 && d.out_logL) *d.out_logL = s;
+        return;
+    }
+    double g = 0.0, h = 0.0;
+    if (item != d.root) {
+        const double *gp = d.gpart + (size_t)item * d.slot_cap;
+        for (int j = lane; j < d.n_tg; j += 32) g += gp[j];
+        g = warp_sum(g);
+        if (want_hess) {
+            const double *hp = d.hpart + (size_t)item * d.slot_cap;
+            for (int j = lane; j < d.n_tg; j += 32) h += hp[j];
+            h = warp_sum(h);
+        }
+    }
+    if (lane == 0) {
+        if (d.out_grad) d.out_grad[item] = g;
+        if (want_hess && d.out_hess) d.out_hess[item] = h;
+    }
+}
+
+template <int C>
+size_t f32_dyn_smem(int range_len) {
+    return f32_stage_bytes<C>(kBlock / 32) + (size_t)range_len * (2 * sizeof(float) + sizeof(int));
+}
+
+template <int C, bool HESS, int MAXB>
+cudaError_t launch_tree(const BatchArgs<MAXB> &args, bool f64, cudaStream_t s) {
+    const int blocks = args.tile_base[args.n];
+    if (f64) {
+        tree4d_kernel<C, HESS, MAXB><<<blocks, kBlock, 0, s>>>(args);
+    } else {
+        int rl = 0;
+        for (int i = 0; i < args.n; ++i) rl = rl > args.d[i].range_len ? rl : args.d[i].range_len;
+        const size_t smem = f32_dyn_smem<C>(rl);
+        static bool configured = false;   // one attribute call per instantiation
+        if (!configured) {
+            cudaError_t e = cudaFuncSetAttribute(tree4f_kernel<C, HESS, MAXB>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)f32_dyn_smem<C>(kMaxRange));
+            if (e != cudaSuccess) return e;
+            configured = true;
+        }
+        tree4f_kernel<C, HESS, MAXB><<<blocks, kBlock, smem, s>>>(args);
+    }
+    return cudaGetLastError();
+}
+
+template <int MAXB, bool HESS>
+cudaError_t launch_tree_c(const BatchArgs<MAXB> &args, int C, bool f64, cudaStream_t s) {
+    switch (C) {
+        case 1: return launch_tree<1, HESS, MAXB>(args, f64, s);
+        case 2: return launch_tree<2, HESS, MAXB>(args, f64, s);
+        case 3: return launch_tree<3, HESS, MAXB>(args, f64, s);
+        case 4: return launch_tree<4, HESS, MAXB>(args, f64, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int C, bool F64>
+int occupancy_of() {
+    int k = 0;
+    cudaError_t e;
+    if (F64) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, tree4d_kernel<C, true, kMaxBatch>, kBlock, 0);
+    } else {
+        const size_t smem = f32_dyn_smem<C>(64);
+        e = cudaFuncSetAttribute(tree4f_kernel<C, true, kMaxBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)f32_dyn_smem<C>(kMaxRange));
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, tree4f_kernel<C, true, kMaxBatch>, kBlock, smem);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return k > 0 ? k : 1;
+}
+
+}  // namespace
+
+int tree_blocks_per_sm(int C, bool f64) {
+    switch (C * 2 + (f64 ? 1 : 0)) {
+        case 2: return occupancy_of<1, false>();
+        case 3: return occupancy_of<1, true>();
+        case 4: return occupancy_of<2, false>();
+        case 5: return occupancy_of<2, true>();
+        case 6: return occupancy_of<3, false>();
+        case 7: return occupancy_of<3, true>();
+        case 8: return occupancy_of<4, false>();
+        case 9: return occupancy_of<4, true>();
+        default: return 1;
+    }
+}
+
+// All problems in args share the category count args.d[0].C and the precision args.d[0].precision.
+template <int MAXB>
+cudaError_t launch_eval_nt(const BatchArgs<MAXB> &args, bool hess, cudaStream_t s) {
+    if (args.n <= 0) return cudaSuccess;
+    const int nmat = args.mat_base[args.n];
+    if (nmat > 0) {
+        pmatrix4_kernel<MAXB><<<(nmat + 127) / 128, 128, 0, s>>>(args);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (args.tile_base[args.n] > 0) {
+        const bool f64 = args.d[0].precision == 1;
+        cudaError_t e = hess ? launch_tree_c<MAXB, true>(args, args.d[0].C, f64, s)
+                             : launch_tree_c<MAXB, false>(args, args.d[0].C, f64, s);
+        if (e != cudaSuccess) return e;
+    }
+    const int warps = args.red_base[args.n];
+    reduce_kernel<MAXB><<<(warps + 7) / 8, 256, 0, s>>>(args, hess ? 1 : 0);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_eval_nt<1>(const BatchArgs<1> &, bool, cudaStream_t);
+template cudaError_t launch_eval_nt<kMaxBatch>(const BatchArgs<kMaxBatch> &, bool, cudaStream_t);
+
+}  // namespace pg
