@@ -70,6 +70,8 @@ struct pg_handle {
     void *block = nullptr;   // one device allocation holding every array of the problem
     size_t bytes = 0;
     int max_tiles = 0;       // blocks one evaluation of this problem may use
+    int cut = 0;             // levels [0, cut) run as level kernels when evaluated alone
+    std::vector<int> level_off;   // host copy of the level offsets
     double *io_b = nullptr, *io_logL = nullptr, *io_grad = nullptr, *io_hess = nullptr,
            *io_site = nullptr;   // device staging for the host-pointer pg_eval
     pg_handle_info info{};
@@ -324,22 +326,40 @@ pg_status pg_upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out) {
     const int max_range = ctx->max_range ? ctx->max_range : pg::kMaxRange;
     if ((int64_t)max_tiles * max_range < (int64_t)P)
         return fail(PG_ERR_UNSUPPORTED, "n_patterns = %d exceeds %d on this device", P, max_tiles * max_range);
-    const int slot_cap = (P + 31) / 32 + 3 * max_tiles + 2;
+    const int Ps = (P + 15) / 16 * 16;   // row stride of per-pattern arrays (16-byte rows for TMA)
+    const int level_ranges = (P + pg::kLevelRange - 1) / pg::kLevelRange;
+    const int slot_cap = std::max((P + 31) / 32 + 3 * max_tiles + 2, level_ranges);
+    // FP32 problems evaluated alone run every level with at least two blocks per SM of
+    // (node, 256-pattern) work as its own launch; the narrower levels near the root stay fused
+    int cut = 0;
+    if (!f64) {
+        while (cut < H - 1 && (int64_t)(tp.level_off[cut + 1] - tp.level_off[cut]) * level_ranges >= 2 * ctx->n_sm)
+            ++cut;
+    }
+    std::vector<uint8_t> wide(n, 0);
+    for (int lv = 0; lv < cut; ++lv)
+        for (int o = tp.level_off[lv]; o < tp.level_off[lv + 1]; ++o) {
+            wide[tp.ops[o].y] = 1;
+            wide[tp.ops[o].z] = 1;
+        }
     const int M = pr->n_models;
 
     Carver cv;
     const size_t o_ops = cv.take<int4>(N - 1), o_lv = cv.take<int>(H + 1);
-    const size_t o_tips = cv.take<uint8_t>((size_t)N * P), o_w = cv.take<double>(P);
+    const size_t o_tips = cv.take<uint8_t>((size_t)N * Ps), o_w = cv.take<double>(Ps);
+    const size_t o_wf = cv.take<float>(Ps);
     const size_t o_Qd = cv.take<double>((size_t)M * 16), o_Qf = cv.take<float4>((size_t)M * 4);
     const size_t o_bm = pr->branch_model ? cv.take<int>(n) : 0;
     const size_t o_P = f64 ? cv.take<double2>((size_t)n * C * pg::kPtab64Pairs)
                            : cv.take<float4>((size_t)n * C * pg::kPtabCols);
-    const size_t part = (size_t)(N - 1) * C * P * (f64 ? 2 : 1);   // float4 or 2 x double2
+    const size_t part = (size_t)(N - 1) * C * Ps * (f64 ? 2 : 1);   // float4 or 2 x double2
     const size_t o_post = f64 ? cv.take<double2>(part) : cv.take<float4>(part);
     const size_t o_pre = f64 ? cv.take<double2>(part) : cv.take<float4>(part);
-    const size_t o_pe = cv.take<int>((size_t)(N - 1) * P), o_qe = cv.take<int>((size_t)(N - 1) * P);
+    const size_t o_pe = cv.take<int>((size_t)(N - 1) * Ps), o_qe = cv.take<int>((size_t)(N - 1) * Ps);
     const size_t o_gp = cv.take<double>((size_t)n * slot_cap), o_hp = cv.take<double>((size_t)n * slot_cap);
     const size_t o_lp = cv.take<double>(slot_cap), o_st = cv.take<int>(1);
+    const size_t o_wide = cv.take<uint8_t>(n), o_sinv = cv.take<float>(std::max(Ps, 16));
+    const size_t o_ser = cv.take<int>(std::max(Ps, 16));
     const size_t o_ib = cv.take<double>(n), o_il = cv.take<double>(1), o_ig = cv.take<double>(n);
     const size_t o_ih = cv.take<double>(n), o_is = cv.take<double>(std::max(P, 1));
     const size_t bytes = align_up(cv.off, 256);
@@ -376,11 +396,16 @@ pg_status pg_upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out) {
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cp(o_ops, tp.ops.data(), sizeof(int4) * tp.ops.size());
     if (e == cudaSuccess) e = cp(o_lv, tp.level_off.data(), sizeof(int) * tp.level_off.size());
-    if (e == cudaSuccess && P > 0) e = cp(o_tips, pr->tip_states, (size_t)N * P);
+    std::vector<float> wf(Ps, 0.f);
+    for (int p = 0; p < P; ++p) wf[p] = (float)pr->pattern_weights[p];
+    if (e == cudaSuccess && P > 0)
+        e = cudaMemcpy2D(base + o_tips, Ps, pr->tip_states, P, P, N, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && P > 0) e = cp(o_w, pr->pattern_weights, sizeof(double) * P);
+    if (e == cudaSuccess && P > 0) e = cp(o_wf, wf.data(), sizeof(float) * Ps);
     if (e == cudaSuccess) e = cp(o_Qd, pr->Q, sizeof(double) * 16 * M);
     if (e == cudaSuccess) e = cp(o_Qf, Qf.data(), sizeof(float4) * Qf.size());
     if (e == cudaSuccess && pr->branch_model) e = cp(o_bm, pr->branch_model, sizeof(int) * n);
+    if (e == cudaSuccess) e = cp(o_wide, wide.data(), wide.size());
     if (e == cudaSuccess) e = cudaMemset(base + o_st, 0, sizeof(int));
     if (e != cudaSuccess) {
         cudaFree(block);
@@ -393,6 +418,7 @@ pg_status pg_upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out) {
     d.level_off = reinterpret_cast<const int *>(base + o_lv);
     d.tips = reinterpret_cast<const uint8_t *>(base + o_tips);
     d.weights = reinterpret_cast<const double *>(base + o_w);
+    d.wf = reinterpret_cast<const float *>(base + o_wf);
     d.Qd = reinterpret_cast<const double *>(base + o_Qd);
     d.Qf = reinterpret_cast<const float4 *>(base + o_Qf);
     d.bmodel = pr->branch_model ? reinterpret_cast<const int *>(base + o_bm) : nullptr;
@@ -406,6 +432,13 @@ pg_status pg_upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out) {
     d.hpart = reinterpret_cast<double *>(base + o_hp);
     d.lpart = reinterpret_cast<double *>(base + o_lp);
     d.status = reinterpret_cast<int *>(base + o_st);
+    d.wide = reinterpret_cast<const uint8_t *>(base + o_wide);
+    d.site_invL = reinterpret_cast<float *>(base + o_sinv);
+    d.site_Er = reinterpret_cast<int *>(base + o_ser);
+    d.level_ranges = level_ranges;
+    d.cut = 0;
+    h->cut = cut;
+    h->level_off = tp.level_off;
     h->io_b = reinterpret_cast<double *>(base + o_ib);
     h->io_logL = reinterpret_cast<double *>(base + o_il);
     h->io_grad = reinterpret_cast<double *>(base + o_ig);
@@ -416,6 +449,7 @@ pg_status pg_upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out) {
     d.root = tp.root;
     d.n_levels = H;
     d.P = P;
+    d.Ps = Ps;
     d.slot_cap = slot_cap;
     d.C = C;
     d.n_models = M;
@@ -490,8 +524,16 @@ pg_status pg_eval_async(pg_handle *h, const double *d_b, double *d_logL, double 
     d.out_hess = d_hess;
     d.out_site = d_site_logL;
     set_tiling(d, single_target(h->ctx, d), h->ctx->max_range ? h->ctx->max_range : pg::kMaxRange);
+    d.cut = d.P > 0 ? h->cut : 0;
     fill_args_one(a, d);
-    cudaError_t e = pg::launch_eval_nt<1>(a, d_hess != nullptr, s);
+    const bool hess = d_hess != nullptr;
+    cudaError_t e = pg::launch_pmatrix<1>(a, s);
+    for (int lv = 0; e == cudaSuccess && lv < d.cut; ++lv)
+        e = pg::launch_post_level(d, h->level_off[lv], h->level_off[lv + 1] - h->level_off[lv], h->ctx->n_sm, s);
+    if (e == cudaSuccess) e = pg::launch_tree<1>(a, hess, s);
+    for (int lv = d.cut - 1; e == cudaSuccess && lv >= 0; --lv)
+        e = pg::launch_pre_level(d, h->level_off[lv], h->level_off[lv + 1] - h->level_off[lv], hess, h->ctx->n_sm, s);
+    if (e == cudaSuccess) e = pg::launch_reduce<1>(a, hess, s);
     if (e != cudaSuccess) return fail(PG_ERR_CUDA, "launch: %s", cudaGetErrorString(e));
     h->last_stream = s;
     return PG_OK;
@@ -537,6 +579,7 @@ pg_status pg_eval_batch_async(pg_handle *const *hs, int32_t k, const double *con
                 d.out_grad = d_grad ? d_grad[i] : nullptr;
                 d.out_hess = d_hess ? d_hess[i] : nullptr;
                 d.out_site = nullptr;
+                d.cut = 0;   // batched problems run every level in the fused kernel
                 hess = hess || d.out_hess;
                 a->d[j] = d;
                 a->tile_base[j + 1] = a->tile_base[j] + d.n_tiles;
@@ -561,6 +604,7 @@ pg_status pg_eval_status(pg_handle *h) {
     if (st) PG_CUDA(cudaMemset(h->desc.status, 0, sizeof(int)));
     if (st & pg::kStatusBadLength) return fail(PG_ERR_INVALID, "a branch length was negative or not finite");
     if (st & pg::kStatusNumeric) return fail(PG_ERR_NUMERIC, "a site likelihood was zero or not finite");
+    if (st & pg::kStatusTimeout) return fail(PG_ERR_TIMEOUT, "a device-side wait for staged data gave up");
     return PG_OK;
 }
 

@@ -14,18 +14,23 @@ constexpr int kMaxCat = 4;      // rate categories held in registers per pattern
 constexpr int kMaxBatch = 32;   // problems per batched launch (kernel-parameter descriptors)
 constexpr int kMaxRange = 1024;  // patterns per thread block of the tree kernel (shared arrays)
 constexpr int kBlock = 256;      // threads per block of the tree kernel
+constexpr int kLevelRange = 128; // patterns per item (and threads per block) of the level kernels
 // FP32 transition table per (branch, category), float4 columns of the 4x4 matrices:
-//   [0..4]  P hi (columns 0..3, then the row sums = P applied to the all-ones vector)
-//   [5..9]  P lo (the FP32 residual P - hi of the same entries)
-//   [10..13] D hi, [14..17] D lo, with D = P - I
-constexpr int kPtabCols = 18;
-constexpr int kColPlo = 5, kColDhi = 10, kColDlo = 14;
+//   [0..4]   P hi (columns 0..3, then the row sums = P applied to the all-ones vector)
+//   [5..9]   G = Q P in the same column layout (the generator applied to a column of P)
+//   [10..14] P lo (the FP32 residual P - hi of the same entries)
+//   [15..18] D hi, [19..22] D lo, with D = P - I
+constexpr int kPtabCols = 23;
+constexpr int kColG = 5, kColPlo = 10, kColDhi = 15, kColDlo = 19;
 // FP64 transition table per (branch, category): 5 columns of 4 doubles as double2 pairs
 constexpr int kPtab64Pairs = 10;
 
 // device status bits (sticky until read by pg_eval_status / pg_eval)
 constexpr int kStatusBadLength = 1;
 constexpr int kStatusNumeric = 2;
+constexpr int kStatusTimeout = 4;
+// bound on a block's wait for its own bulk copies (SM clocks, about one second)
+constexpr long long kWaitLimitCycles = 2000000000LL;
 
 // Everything one problem's kernels need.  Lives in kernel parameter space (by value), so a
 // launch never depends on host memory that may change afterwards.
@@ -52,11 +57,20 @@ struct ProbDesc {
     double *hpart;                 // [n][slot_cap] per-(block, piece) Hessian-diagonal sums
     double *lpart;                 // [slot_cap] per-(block, piece) log-likelihood sums
     int *status;
+    // levels [0, cut) run as one launch per level (level kernels), [cut, n_levels) in the fused
+    // tree kernel; wide[i] = 1 when branch i's parent lies below the cut
+    int cut;
+    const uint8_t *wide;
+    float *site_invL;              // [P] 1 / Lhat_p, written at the root for the level kernels
+    int *site_Er;                  // [P] log2 scale of L_p
+    int level_ranges;              // ceil(P / kLevelRange): slots per wide branch
     // outputs of this evaluation (device, may be null)
     double *out_logL, *out_grad, *out_hess, *out_site;
     // sizes
     int n_tips, n_nodes, root, n_levels;
-    int P;                         // site patterns (rows of every partial array are P long)
+    int P;                         // site patterns
+    int Ps;                        // row stride of every per-pattern array: P rounded up to 16
+    const float *wf;               // [Ps] pattern weights in FP32 (gradient terms)
     int slot_cap;                  // capacity of the per-branch slot arrays
     // tiling of this launch: n_tiles blocks, each a contiguous range of range_len patterns
     // (the last one shorter); a node's pairs in one block span at most pieces 32-lane chunks
@@ -79,7 +93,16 @@ struct BatchArgs {
 // launchers (pg_nt.cu); every problem of one launch shares C and precision
 template <int MAXB>
 cudaError_t launch_eval_nt(const BatchArgs<MAXB> &args, bool hess, cudaStream_t s);
+template <int MAXB>
+cudaError_t launch_pmatrix(const BatchArgs<MAXB> &args, cudaStream_t s);
+template <int MAXB>
+cudaError_t launch_tree(const BatchArgs<MAXB> &args, bool hess, cudaStream_t s);
+template <int MAXB>
+cudaError_t launch_reduce(const BatchArgs<MAXB> &args, bool hess, cudaStream_t s);
 // resident blocks per SM of the tree kernel for C categories and the given precision
 int tree_blocks_per_sm(int C, bool f64);
+// one post-order (pre-order) level [o0, o0 + nd) of a single FP32 problem (pg_levels.cu)
+cudaError_t launch_post_level(const ProbDesc &d, int o0, int nd, int n_sm, cudaStream_t s);
+cudaError_t launch_pre_level(const ProbDesc &d, int o0, int nd, bool hess, int n_sm, cudaStream_t s);
 
 }  // namespace pg

@@ -1,0 +1,368 @@
+// Level kernels for the wide tree levels of a single FP32 problem.
+//
+// Near the tips a level holds hundreds of nodes, so one launch per level has enough independent
+// (node, pattern) work to fill the GPU by itself.  An item is one node of the level and a range of
+// kLevelRange patterns (one per thread).  Blocks are persistent: each walks the items
+// blockIdx.x, blockIdx.x + gridDim.x, ... through a ring of STAGES shared-memory stages.  Thread 0
+// stages an item with a handful of 1-D bulk copies (TMA), one per contiguous row segment (the
+// children's partial rows per rate category, q_k's rows, the log2 scales, tip codes, the
+// per-pattern site values and the node's two branch tables), STAGES - 1 items ahead of the one
+// the block computes.  Bytes in flight are bounded by shared memory, not by registers, and no
+// block depends on another within a launch.
+//
+// The arithmetic is that of the fused tree kernel (pg_nt.cu): the exact-product post-order update
+// of Section 2.3, and the pre-order step of Section 2.4 with the branch gradient (Section 2.5) and
+// Hessian diagonal (Section 2.6).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "pg_device.cuh"
+#include "pg_internal.cuh"
+
+namespace pg {
+namespace {
+
+using namespace dev;
+
+constexpr int R = kLevelRange;
+
+template <int C>
+struct PostStage {
+    float4 x0[C][R], x1[C][R];   // children's partial rows
+    int e0[R], e1[R];            // children's log2 scales
+    uint8_t y0[R], y1[R];        // tip codes
+    float4 tab[2][C][kPtabCols]; // both branches' tables
+};
+
+template <int C>
+struct PreStage {
+    float4 qk[C][R], x0[C][R], x1[C][R];
+    int eq[R], e0[R], e1[R];
+    int er[R];                   // log2 scale of L_p
+    float inv[R];                // 1 / Lhat_p
+    float w[R];                  // pattern weights
+    uint8_t y0[R], y1[R];
+    float4 tab[2][C][10];        // P hi columns and row sums, then G = Q P alike, both branches
+    float4 qtab[2][4];           // Q columns of both children's models
+};
+
+template <class Stage, int STAGES>
+struct Ring {
+    Stage st[STAGES];
+    uint64_t bar[STAGES];
+    double red[R / 32][4];
+};
+
+__device__ __forceinline__ unsigned round16(unsigned b) { return (b + 15u) & ~15u; }
+
+struct Item {
+    int4 op;
+    int rg, p0, cnt;
+};
+
+__device__ __forceinline__ Item item_of(const ProbDesc &d, int o0, int nr, int j) {
+    Item it;
+    const int u = j / nr;
+    it.rg = j - u * nr;
+    it.op = __ldg(d.ops + o0 + u);
+    it.p0 = it.rg * R;
+    it.cnt = min(R, d.P - it.p0);
+    return it;
+}
+
+template <int C>
+__device__ void issue_post(const ProbDesc &d, const Item &it, PostStage<C> &sm, uint64_t *bar) {
+    const int N = d.n_tips, Ps = d.Ps, c0 = it.op.y, c1 = it.op.z, p0 = it.p0;
+    const bool t0 = c0 < N, t1 = c1 < N;
+    const float4 *post = static_cast<const float4 *>(d.post);
+    const unsigned rowb = (unsigned)it.cnt * 16u, eb = round16(it.cnt * 4u), yb = round16((unsigned)it.cnt);
+    unsigned bytes = 2u * C * kPtabCols * 16u;
+    bytes += t0 ? yb : (C * rowb + eb);
+    bytes += t1 ? yb : (C * rowb + eb);
+    mbar_arrive_expect(bar, bytes);
+    bulk_load(sm.tab[0], d.Ptab + (size_t)c0 * C * kPtabCols, C * kPtabCols * 16u, bar);
+    bulk_load(sm.tab[1], d.Ptab + (size_t)c1 * C * kPtabCols, C * kPtabCols * 16u, bar);
+    if (t0) bulk_load(sm.y0, d.tips + (size_t)c0 * Ps + p0, yb, bar);
+    else {
+        bulk_load(sm.e0, d.pe + (size_t)(c0 - N) * Ps + p0, eb, bar);
+        for (int l = 0; l < C; ++l) bulk_load(sm.x0[l], post + ((size_t)(c0 - N) * C + l) * Ps + p0, rowb, bar);
+    }
+    if (t1) bulk_load(sm.y1, d.tips + (size_t)c1 * Ps + p0, yb, bar);
+    else {
+        bulk_load(sm.e1, d.pe + (size_t)(c1 - N) * Ps + p0, eb, bar);
+        for (int l = 0; l < C; ++l) bulk_load(sm.x1[l], post + ((size_t)(c1 - N) * C + l) * Ps + p0, rowb, bar);
+    }
+}
+
+template <int C>
+__device__ void issue_pre(const ProbDesc &d, const Item &it, PreStage<C> &sm, uint64_t *bar) {
+    const int N = d.n_tips, Ps = d.Ps, k = it.op.x, c0 = it.op.y, c1 = it.op.z, p0 = it.p0;
+    const bool t0 = c0 < N, t1 = c1 < N;
+    const float4 *post = static_cast<const float4 *>(d.post);
+    const float4 *pre = static_cast<const float4 *>(d.pre);
+    const unsigned rowb = (unsigned)it.cnt * 16u, eb = round16(it.cnt * 4u), yb = round16((unsigned)it.cnt);
+    unsigned bytes = C * rowb + eb + 3u * eb + 2u * C * 10u * 16u + 2u * 64u;
+    bytes += t0 ? yb : (C * rowb + eb);
+    bytes += t1 ? yb : (C * rowb + eb);
+    mbar_arrive_expect(bar, bytes);
+    for (int side = 0; side < 2; ++side) {
+        const int c = side ? c1 : c0;
+        for (int l = 0; l < C; ++l) bulk_load(sm.tab[side][l], d.Ptab + ((size_t)c * C + l) * kPtabCols, 10u * 16u, bar);
+        bulk_load(sm.qtab[side], d.Qf + 4 * (d.bmodel ? d.bmodel[c] : 0), 64u, bar);
+    }
+    bulk_load(sm.eq, d.qe + (size_t)(k - N) * Ps + p0, eb, bar);
+    for (int l = 0; l < C; ++l) bulk_load(sm.qk[l], pre + ((size_t)(k - N) * C + l) * Ps + p0, rowb, bar);
+    bulk_load(sm.er, d.site_Er + p0, eb, bar);
+    bulk_load(sm.inv, d.site_invL + p0, eb, bar);
+    bulk_load(sm.w, d.wf + p0, eb, bar);
+    if (t0) bulk_load(sm.y0, d.tips + (size_t)c0 * Ps + p0, yb, bar);
+    else {
+        bulk_load(sm.e0, d.pe + (size_t)(c0 - N) * Ps + p0, eb, bar);
+        for (int l = 0; l < C; ++l) bulk_load(sm.x0[l], post + ((size_t)(c0 - N) * C + l) * Ps + p0, rowb, bar);
+    }
+    if (t1) bulk_load(sm.y1, d.tips + (size_t)c1 * Ps + p0, yb, bar);
+    else {
+        bulk_load(sm.e1, d.pe + (size_t)(c1 - N) * Ps + p0, eb, bar);
+        for (int l = 0; l < C; ++l) bulk_load(sm.x1[l], post + ((size_t)(c1 - N) * C + l) * Ps + p0, rowb, bar);
+    }
+}
+
+// post-order update (Section 2.3) of one item from its stage
+template <int C>
+__device__ __forceinline__ void compute_post(const ProbDesc &d, const Item &it, const PostStage<C> &sm) {
+    const int t = threadIdx.x;
+    if (t >= it.cnt) return;
+    const int N = d.n_tips, Ps = d.Ps, k = it.op.x, c0 = it.op.y, c1 = it.op.z;
+    const bool t0 = c0 < N, t1 = c1 < N;
+    const int p = it.p0 + t;
+    const float r = pattern_factor((uint32_t)p);
+    const int y0 = t0 ? min((int)sm.y0[t], 4) : 0, y1 = t1 ? min((int)sm.y1[t], 4) : 0;
+    const int E = (t0 ? 0 : sm.e0[t]) + (t1 ? 0 : sm.e1[t]);
+    float4 v[C];
+    float mx = 0.0f;
+#pragma unroll
+    for (int l = 0; l < C; ++l) {
+        float4 x0, x1, s0 = f4(0.f, 0.f, 0.f, 0.f), s1 = f4(0.f, 0.f, 0.f, 0.f);
+        if (t0) {
+            const float4 hi = sm.tab[0][l][y0], lo = sm.tab[0][l][kColPlo + y0];
+            x0 = f4(fmaf(hi.x, r, lo.x * r), fmaf(hi.y, r, lo.y * r), fmaf(hi.z, r, lo.z * r), fmaf(hi.w, r, lo.w * r));
+        } else {
+            x0 = sm.x0[l][t];
+            s0 = matvec_hilo_v(&sm.tab[0][l][kColDhi], &sm.tab[0][l][kColDlo], x0);
+        }
+        if (t1) {
+            const float4 hi = sm.tab[1][l][y1], lo = sm.tab[1][l][kColPlo + y1];
+            x1 = f4(fmaf(hi.x, r, lo.x * r), fmaf(hi.y, r, lo.y * r), fmaf(hi.z, r, lo.z * r), fmaf(hi.w, r, lo.w * r));
+        } else {
+            x1 = sm.x1[l][t];
+            s1 = matvec_hilo_v(&sm.tab[1][l][kColDhi], &sm.tab[1][l][kColDlo], x1);
+        }
+        v[l] = f4(prod_split(x0.x, s0.x, x1.x, s1.x), prod_split(x0.y, s0.y, x1.y, s1.y),
+                  prod_split(x0.z, s0.z, x1.z, s1.z), prod_split(x0.w, s0.w, x1.w, s1.w));
+        mx = fmaxf(mx, hmax(v[l]));
+    }
+    const int e = scale_exponent(mx);
+    float4 *out = static_cast<float4 *>(d.post);
+#pragma unroll
+    for (int l = 0; l < C; ++l) __stcg(out + ((size_t)(k - N) * C + l) * Ps + p, scale4(v[l], e));
+    __stcg(d.pe + (size_t)(k - N) * Ps + p, E + e);
+}
+
+// pre-order step (Section 2.4) with the branch gradient (2.5) and Hessian diagonal (2.6) of one
+// item; the block's sums over its patterns go to the item's slot of both child branches
+template <int C, bool HESS>
+__device__ __forceinline__ void compute_pre(const ProbDesc &d, const Item &it, const PreStage<C> &sm,
+                                            double (&red)[R / 32][4]) {
+    const int N = d.n_tips, Ps = d.Ps, c0 = it.op.y, c1 = it.op.z;
+    const bool t0 = c0 < N, t1 = c1 < N;
+    const int t = threadIdx.x;
+    const bool active = t < it.cnt;
+    const int tt = active ? t : it.cnt - 1;
+    const int p = it.p0 + tt;
+    const float r = pattern_factor((uint32_t)p);
+    const int y0 = t0 ? min((int)sm.y0[tt], 4) : 0, y1 = t1 ? min((int)sm.y1[tt], 4) : 0;
+    const int Eq = sm.eq[tt], E0 = t0 ? 0 : sm.e0[tt], E1 = t1 ? 0 : sm.e1[tt];
+    const float inv = sm.inv[tt], wt = active ? sm.w[tt] : 0.f;
+    const int dE = Eq + E0 + E1 - sm.er[tt];
+    float4 q0[C], q1[C];
+    float m0 = 0.f, m1 = 0.f, g0 = 0.f, g1 = 0.f, h0 = 0.f, h1 = 0.f;
+#pragma unroll
+    for (int l = 0; l < C; ++l) {
+        const float4 a0 = t0 ? scal(sm.tab[0][l][y0], r) : matvec_p(sm.tab[0][l], sm.x0[l][tt]);
+        const float4 a1 = t1 ? scal(sm.tab[1][l][y1], r) : matvec_p(sm.tab[1][l], sm.x1[l][tt]);
+        const float4 qk = sm.qk[l][tt];
+        const float4 qt0 = mul(qk, a1), qt1 = mul(qk, a0);   // top of branches c0 and c1
+        // Q a_c: a gathered column of G = Q P for tips, a matvec otherwise
+        const float4 u0 = t0 ? scal(sm.tab[0][l][kColG + y0], r) : matvec_p(sm.qtab[0], a0);
+        const float4 u1 = t1 ? scal(sm.tab[1][l][kColG + y1], r) : matvec_p(sm.qtab[1], a1);
+        g0 = fmaf(d.gw[l], dot(qt0, u0), g0);
+        g1 = fmaf(d.gw[l], dot(qt1, u1), g1);
+        if (HESS) {
+            h0 = fmaf(d.gw2[l], dot(qt0, matvec_p(sm.qtab[0], u0)), h0);
+            h1 = fmaf(d.gw2[l], dot(qt1, matvec_p(sm.qtab[1], u1)), h1);
+        }
+        if (!t0) { q0[l] = matvec_tp(sm.tab[0][l], qt0); m0 = fmaxf(m0, hmax(q0[l])); }
+        if (!t1) { q1[l] = matvec_tp(sm.tab[1][l], qt1); m1 = fmaxf(m1, hmax(q1[l])); }
+    }
+    float4 *pre = static_cast<float4 *>(d.pre);
+    if (!t0 && active) {
+        const int e = scale_exponent(m0);
+#pragma unroll
+        for (int l = 0; l < C; ++l) __stcg(pre + ((size_t)(c0 - N) * C + l) * Ps + p, scale4(q0[l], e));
+        __stcg(d.qe + (size_t)(c0 - N) * Ps + p, Eq + E1 + e);
+    }
+    if (!t1 && active) {
+        const int e = scale_exponent(m1);
+#pragma unroll
+        for (int l = 0; l < C; ++l) __stcg(pre + ((size_t)(c1 - N) * C + l) * Ps + p, scale4(q1[l], e));
+        __stcg(d.qe + (size_t)(c1 - N) * Ps + p, Eq + E0 + e);
+    }
+    const float d0 = ldexpf(g0, dE) * inv, d1 = ldexpf(g1, dE) * inv;
+    float sums[4];
+    sums[0] = wt * d0;
+    sums[1] = wt * d1;
+    sums[2] = HESS ? wt * (ldexpf(h0, dE) * inv - d0 * d0) : 0.f;
+    sums[3] = HESS ? wt * (ldexpf(h1, dE) * inv - d1 * d1) : 0.f;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int s = 0; s < (HESS ? 4 : 2); ++s) {   // 32 patterns summed in FP32, warps combined in FP64
+        const float v = warp_sum_f(wt != 0.f ? sums[s] : 0.f);
+        if (lane == 0) red[warp][s] = (double)v;
+    }
+    __syncthreads();
+    if (threadIdx.x < (HESS ? 4 : 2)) {
+        const int s = threadIdx.x;
+        double v = 0.0;
+#pragma unroll
+        for (int w = 0; w < R / 32; ++w) v += red[w][s];
+        double *dst = (s < 2) ? d.gpart : d.hpart;
+        dst[(size_t)((s & 1) ? c1 : c0) * d.slot_cap + it.rg] = v;
+    }
+}
+
+// The persistent, staged walk over a level's items shared by both passes.
+template <class Stage, int STAGES, class Issue, class Compute>
+__device__ __forceinline__ void staged_walk(const ProbDesc &d, int o0, int nr, int n_items,
+                                            Ring<Stage, STAGES> &ring, Issue &&issue, Compute &&compute) {
+    const int G = gridDim.x, b = blockIdx.x;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) mbar_init(&ring.bar[s], 1);
+        for (int i = 0; i < STAGES - 1; ++i) {
+            const int j = b + i * G;
+            if (j < n_items) issue(item_of(d, o0, nr, j), ring.st[i], &ring.bar[i]);
+        }
+    }
+    __syncthreads();
+    for (int i = 0;; ++i) {
+        const int j = b + i * G;
+        if (j >= n_items) break;
+        const int s = i % STAGES;
+        if (threadIdx.x == 0) {   // refill the stage freed at the end of the previous iteration
+            const int jn = b + (i + STAGES - 1) * G;
+            if (jn < n_items) {
+                const int sn = (i + STAGES - 1) % STAGES;
+                issue(item_of(d, o0, nr, jn), ring.st[sn], &ring.bar[sn]);
+            }
+        }
+        const bool ok = mbar_wait_bounded(&ring.bar[s], (unsigned)(i / STAGES) & 1u, kWaitLimitCycles);
+        if (__syncthreads_or(!ok)) {
+            // give up: record the time-out; thread 0 lets every copy it issued land before leaving
+            if (threadIdx.x == 0) {
+                atomicOr(d.status, kStatusTimeout);
+                for (int q = 0; q < STAGES; ++q) {
+                    const int iq = i + q;
+                    if (b + iq * G < n_items) mbar_wait_bounded(&ring.bar[iq % STAGES], (unsigned)(iq / STAGES) & 1u, kWaitLimitCycles);
+                }
+            }
+            return;
+        }
+        compute(item_of(d, o0, nr, j), ring.st[s]);
+        __syncthreads();   // the stage is read by everyone before it is refilled
+    }
+}
+
+template <int C, int STAGES>
+__global__ void __launch_bounds__(R) post_level_kernel(const __grid_constant__ ProbDesc d, int o0, int nr, int n_items) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto &ring = *reinterpret_cast<Ring<PostStage<C>, STAGES> *>(smem_raw);
+    staged_walk(d, o0, nr, n_items, ring,
+                [&](const Item &it, PostStage<C> &st, uint64_t *bar) { issue_post<C>(d, it, st, bar); },
+                [&](const Item &it, const PostStage<C> &st) { compute_post<C>(d, it, st); });
+}
+
+template <int C, bool HESS, int STAGES>
+__global__ void __launch_bounds__(R) pre_level_kernel(const __grid_constant__ ProbDesc d, int o0, int nr, int n_items) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto &ring = *reinterpret_cast<Ring<PreStage<C>, STAGES> *>(smem_raw);
+    staged_walk(d, o0, nr, n_items, ring,
+                [&](const Item &it, PreStage<C> &st, uint64_t *bar) { issue_pre<C>(d, it, st, bar); },
+                [&](const Item &it, const PreStage<C> &st) { compute_pre<C, HESS>(d, it, st, ring.red); });
+}
+
+constexpr int kPostStages = 3, kPreStages = 2;
+
+// blocks of a persistent level launch: every resident slot, at most one per item
+template <class K>
+int persistent_blocks(K kernel, size_t smem, int n_sm, int n_items, bool &configured, int &per_sm) {
+    if (!configured) {
+        if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, R, smem) != cudaSuccess) return -1;
+        if (per_sm < 1) per_sm = 1;
+        configured = true;
+    }
+    return n_items < n_sm * per_sm ? n_items : n_sm * per_sm;
+}
+
+template <int C>
+cudaError_t post_c(const ProbDesc &d, int o0, int nd, int n_sm, cudaStream_t s) {
+    static bool configured = false;   // attribute and occupancy, once per instantiation
+    static int per_sm = 1;
+    const int nr = d.level_ranges, n_items = nd * nr;
+    const size_t smem = sizeof(Ring<PostStage<C>, kPostStages>);
+    const int blocks = persistent_blocks(post_level_kernel<C, kPostStages>, smem, n_sm, n_items, configured, per_sm);
+    if (blocks < 0) return cudaErrorInvalidConfiguration;
+    post_level_kernel<C, kPostStages><<<blocks, R, smem, s>>>(d, o0, nr, n_items);
+    return cudaGetLastError();
+}
+
+template <int C, bool HESS>
+cudaError_t pre_c(const ProbDesc &d, int o0, int nd, int n_sm, cudaStream_t s) {
+    static bool configured = false;
+    static int per_sm = 1;
+    const int nr = d.level_ranges, n_items = nd * nr;
+    const size_t smem = sizeof(Ring<PreStage<C>, kPreStages>);
+    const int blocks = persistent_blocks(pre_level_kernel<C, HESS, kPreStages>, smem, n_sm, n_items, configured, per_sm);
+    if (blocks < 0) return cudaErrorInvalidConfiguration;
+    pre_level_kernel<C, HESS, kPreStages><<<blocks, R, smem, s>>>(d, o0, nr, n_items);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_post_level(const ProbDesc &d, int o0, int nd, int n_sm, cudaStream_t s) {
+    switch (d.C) {
+        case 1: return post_c<1>(d, o0, nd, n_sm, s);
+        case 2: return post_c<2>(d, o0, nd, n_sm, s);
+        case 3: return post_c<3>(d, o0, nd, n_sm, s);
+        case 4: return post_c<4>(d, o0, nd, n_sm, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_pre_level(const ProbDesc &d, int o0, int nd, bool hess, int n_sm, cudaStream_t s) {
+    switch (d.C * 2 + (hess ? 1 : 0)) {
+        case 2: return pre_c<1, false>(d, o0, nd, n_sm, s);
+        case 3: return pre_c<1, true>(d, o0, nd, n_sm, s);
+        case 4: return pre_c<2, false>(d, o0, nd, n_sm, s);
+        case 5: return pre_c<2, true>(d, o0, nd, n_sm, s);
+        case 6: return pre_c<3, false>(d, o0, nd, n_sm, s);
+        case 7: return pre_c<3, true>(d, o0, nd, n_sm, s);
+        case 8: return pre_c<4, false>(d, o0, nd, n_sm, s);
+        case 9: return pre_c<4, true>(d, o0, nd, n_sm, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace pg

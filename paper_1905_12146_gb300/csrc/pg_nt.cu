@@ -35,103 +35,13 @@
 #include <cmath>
 #include <cstdint>
 
+#include "pg_device.cuh"
 #include "pg_internal.cuh"
 
 namespace pg {
 namespace {
 
-// ------------------------------------------------------------------------------------------
-// small helpers
-// ------------------------------------------------------------------------------------------
-
-__device__ __forceinline__ float4 f4(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
-__device__ __forceinline__ float4 mul(float4 a, float4 b) { return f4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w); }
-__device__ __forceinline__ float4 scal(float4 a, float s) { return f4(a.x * s, a.y * s, a.z * s, a.w * s); }
-__device__ __forceinline__ float dot(float4 a, float4 b) { return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x))); }
-__device__ __forceinline__ float hmax(float4 a) { return fmaxf(fmaxf(a.x, a.y), fmaxf(a.z, a.w)); }
-__device__ __forceinline__ float4 fma4(float4 col, float s, float4 acc) {
-    return f4(fmaf(col.x, s, acc.x), fmaf(col.y, s, acc.y), fmaf(col.z, s, acc.z), fmaf(col.w, s, acc.w));
-}
-
-// y = M v with M given by its four columns
-__device__ __forceinline__ float4 matvec(const float4 (&col)[4], float4 v) {
-    float4 a = scal(col[0], v.x);
-    a = fma4(col[1], v.y, a);
-    a = fma4(col[2], v.z, a);
-    return fma4(col[3], v.w, a);
-}
-// y = M' v with M given by its four columns
-__device__ __forceinline__ float4 matvec_t(const float4 (&col)[4], float4 v) {
-    return f4(dot(col[0], v), dot(col[1], v), dot(col[2], v), dot(col[3], v));
-}
-// y = (Mhi + Mlo) v, the small half first
-__device__ __forceinline__ float4 matvec_hilo(const float4 *hi, const float4 *lo, float4 v) {
-    float4 a = scal(__ldg(lo), v.x);
-    a = fma4(__ldg(lo + 1), v.y, a);
-    a = fma4(__ldg(lo + 2), v.z, a);
-    a = fma4(__ldg(lo + 3), v.w, a);
-    a = fma4(__ldg(hi), v.x, a);
-    a = fma4(__ldg(hi + 1), v.y, a);
-    a = fma4(__ldg(hi + 2), v.z, a);
-    return fma4(__ldg(hi + 3), v.w, a);
-}
-
-__device__ __forceinline__ void load_cols(const float4 *p, float4 (&c)[4]) {
-#pragma unroll
-    for (int t = 0; t < 4; ++t) c[t] = __ldg(p + t);
-}
-
-// (x0 + s0)(x1 + s1) rounded once: exact product x0*x1 (value + FMA residual) plus cross terms
-__device__ __forceinline__ float prod_split(float x0, float s0, float x1, float s1) {
-    const float h = x0 * x1;
-    const float res = fmaf(x0, x1, -h);
-    const float small = fmaf(s0, x1 + s1, x0 * s1);
-    return h + (res + small);
-}
-
-// Pattern-specific factor in [1, 2): lowbias32 integer hash (C. Wellons) of the pattern index
-// as a 23-bit mantissa.
-__device__ __forceinline__ float pattern_factor(uint32_t p) {
-    uint32_t x = p + 0x9E3779B9u;
-    x ^= x >> 16; x *= 0x21F0AAADu;
-    x ^= x >> 15; x *= 0x735A2D97u;
-    x ^= x >> 15;
-    return __uint_as_float(0x3F800000u | (x >> 9));
-}
-
-// e such that mx * 2^-e lies in [1, 2) (0 for zero / non-finite, which are left as they are)
-__device__ __forceinline__ int scale_exponent(float mx) {
-    int bits = __float_as_int(mx);
-    int e = ((bits >> 23) & 0xff) - 127;
-    if (e == -127) {
-        if (mx == 0.0f) return 0;
-        int ee;
-        frexpf(mx, &ee);
-        return ee - 1;
-    }
-    if (e == 128) return 0;
-    return e;
-}
-__device__ __forceinline__ int scale_exponent64(double mx) {
-    if (!(mx > 0.0) || isinf(mx)) return 0;
-    int e;
-    frexp(mx, &e);
-    return e - 1;
-}
-
-__device__ __forceinline__ float pow2f(int e) {   // 2^e, e in [-126, 127]
-    return __int_as_float((e + 127) << 23);
-}
-__device__ __forceinline__ float4 scale4(float4 v, int e) {   // v * 2^-e exactly
-    if (e >= -126 && e <= 126) return scal(v, pow2f(-e));
-    return f4(ldexpf(v.x, -e), ldexpf(v.y, -e), ldexpf(v.z, -e), ldexpf(v.w, -e));
-}
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
+using namespace dev;
 
 template <int MAXB>
 __device__ __forceinline__ int find_problem(const int (&base)[MAXB + 1], int n, int x) {
@@ -224,16 +134,25 @@ __global__ void __launch_bounds__(128) pmatrix4_kernel(const __grid_constant__ B
         return;
     }
     float4 *out = d.Ptab + ((size_t)i * d.C + l) * kPtabCols;
+    const double *Qm = d.Qd + model * 16;
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
-        float hi[4], lo[4];
+        float hi[4], lo[4], gq[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const double v = (c < 4) ? E[r * 4 + c] : rs[r];
             hi[r] = (float)v;
             lo[r] = (float)(v - (double)hi[r]);
         }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {   // (Q P)[r][c], and Q applied to the row sums for c = 4
+            double g = 0.0;
+#pragma unroll
+            for (int t2 = 0; t2 < 4; ++t2) g = fma(Qm[r * 4 + t2], (c < 4) ? E[t2 * 4 + c] : rs[t2], g);
+            gq[r] = (float)g;
+        }
         out[c] = f4(hi[0], hi[1], hi[2], hi[3]);
+        out[kColG + c] = f4(gq[0], gq[1], gq[2], gq[3]);
         out[kColPlo + c] = f4(lo[0], lo[1], lo[2], lo[3]);
         if (c < 4) {
 #pragma unroll
@@ -329,7 +248,7 @@ __device__ __forceinline__ double dot64(const D4 &a, const D4 &b) {
 template <int C>
 __device__ __forceinline__ void post_pair64(const ProbDesc &d, const int4 op, const int p, const bool active,
                                            double &L, int &E) {
-    const int N = d.n_tips, Pn = d.P;
+    const int N = d.n_tips, Pn = d.Ps;
     const int k = op.x, c0 = op.y, c1 = op.z;
     const bool t0 = c0 < N, t1 = c1 < N;
     const bool root = (k == d.root);
@@ -375,7 +294,7 @@ __device__ __forceinline__ void post_pair64(const ProbDesc &d, const int4 op, co
 template <int C, bool HESS>
 __device__ __forceinline__ void pre_pair64(const ProbDesc &d, const int4 op, const int p, const bool active,
                                           double (&g)[2], double (&h)[2], int &dEsum) {
-    const int N = d.n_tips, Pn = d.P;
+    const int N = d.n_tips, Pn = d.Ps;
     const int k = op.x, c0 = op.y, c1 = op.z;
     const bool t0 = c0 < N, t1 = c1 < N;
     const bool root = (k == d.root);
@@ -480,7 +399,7 @@ template <int C, bool PRE>
 __device__ __forceinline__ void prefetch_pair(const ProbDesc &d, int o0, int cnt, int p0, int npairs, int chunk,
                                               float4 *slot, PairMeta &m) {
     const int lane = threadIdx.x & 31;
-    const int N = d.n_tips, Pn = d.P;
+    const int N = d.n_tips, Pn = d.Ps;
     const int j = chunk * 32 + lane;
     m.active = j < npairs;
     const int jj = m.active ? j : npairs - 1;
@@ -517,7 +436,7 @@ __device__ __forceinline__ void prefetch_pair(const ProbDesc &d, int o0, int cnt
 template <int C>
 __device__ __forceinline__ void post_compute32(const ProbDesc &d, const PairMeta &m, const float4 *slot,
                                                double &L, int &E) {
-    const int N = d.n_tips, Pn = d.P;
+    const int N = d.n_tips, Pn = d.Ps;
     const int k = m.op.x, c0 = m.op.y, c1 = m.op.z;
     const bool t0 = c0 < N, t1 = c1 < N;
     const bool root = (k == d.root);
@@ -572,7 +491,7 @@ __device__ __forceinline__ void post_compute32(const ProbDesc &d, const PairMeta
 template <int C, bool HESS>
 __device__ __forceinline__ void pre_compute32(const ProbDesc &d, const PairMeta &m, const float4 *slot,
                                               float (&g)[2], float (&h)[2], int &dEsum) {
-    const int N = d.n_tips, Pn = d.P;
+    const int N = d.n_tips, Pn = d.Ps;
     const int k = m.op.x, c0 = m.op.y, c1 = m.op.z;
     const bool t0 = c0 < N, t1 = c1 < N;
     const bool root = (k == d.root);
@@ -647,6 +566,8 @@ __device__ __forceinline__ void post_level_chunk(const ProbDesc &d, const PairMe
         ra.invL[m.q] = (float)(1.0 / f);
         ra.Eroot[m.q] = Er;
         ra.w[m.q] = (float)wgt;
+        d.site_invL[m.p] = (float)(1.0 / f);
+        d.site_Er[m.p] = Er;
         if (!(f > 0.0) || !isfinite(lp)) atomicOr(d.status, kStatusNumeric);
         if (d.out_site) d.out_site[m.p] = lp;
     }
@@ -706,8 +627,8 @@ __global__ void __launch_bounds__(kBlock, 2) tree4f_kernel(const __grid_constant
     }
     PairMeta m0, m1;
 
-    // post-order, tips to root (Section 2.3)
-    for (int lv = 0; lv < d.n_levels; ++lv) {
+    // post-order, tips to root (Section 2.3); levels below d.cut were done by the level kernels
+    for (int lv = d.cut; lv < d.n_levels; ++lv) {
         const int o0 = d.level_off[lv], npairs = (d.level_off[lv + 1] - o0) * cnt;
         int chunk = warp;
         if (chunk * 32 < npairs) prefetch_pair<C, false>(d, o0, cnt, p0, npairs, chunk, st0, m0);
@@ -732,8 +653,8 @@ __global__ void __launch_bounds__(kBlock, 2) tree4f_kernel(const __grid_constant
         cp_async_wait0();
         __syncthreads();
     }
-    // pre-order, root to tips (Section 2.4) with the gradient (Section 2.5)
-    for (int lv = d.n_levels - 1; lv >= 0; --lv) {
+    // pre-order, root to tips (Section 2.4) with the gradient (Section 2.5), down to d.cut
+    for (int lv = d.n_levels - 1; lv >= d.cut; --lv) {
         const int o0 = d.level_off[lv], npairs = (d.level_off[lv + 1] - o0) * cnt;
         int chunk = warp;
         if (chunk * 32 < npairs) prefetch_pair<C, true>(d, o0, cnt, p0, npairs, chunk, st0, m0);
@@ -870,12 +791,14 @@ __global__ void __launch_bounds__(256) reduce_kernel(const __grid_constant__ Bat
     }
     double g = 0.0, h = 0.0;
     if (item != d.root) {
+        // branches below the cut were reduced per level-kernel block, the others per fused slot
+        const int ns = (d.cut > 0 && d.wide[item]) ? d.level_ranges : d.n_tg;
         const double *gp = d.gpart + (size_t)item * d.slot_cap;
-        for (int j = lane; j < d.n_tg; j += 32) g += gp[j];
+        for (int j = lane; j < ns; j += 32) g += gp[j];
         g = warp_sum(g);
         if (want_hess) {
             const double *hp = d.hpart + (size_t)item * d.slot_cap;
-            for (int j = lane; j < d.n_tg; j += 32) h += hp[j];
+            for (int j = lane; j < ns; j += 32) h += hp[j];
             h = warp_sum(h);
         }
     }
@@ -891,7 +814,7 @@ size_t f32_dyn_smem(int range_len) {
 }
 
 template <int C, bool HESS, int MAXB>
-cudaError_t launch_tree(const BatchArgs<MAXB> &args, bool f64, cudaStream_t s) {
+cudaError_t launch_tree_cc(const BatchArgs<MAXB> &args, bool f64, cudaStream_t s) {
     const int blocks = args.tile_base[args.n];
     if (f64) {
         tree4d_kernel<C, HESS, MAXB><<<blocks, kBlock, 0, s>>>(args);
@@ -915,10 +838,10 @@ cudaError_t launch_tree(const BatchArgs<MAXB> &args, bool f64, cudaStream_t s) {
 template <int MAXB, bool HESS>
 cudaError_t launch_tree_c(const BatchArgs<MAXB> &args, int C, bool f64, cudaStream_t s) {
     switch (C) {
-        case 1: return launch_tree<1, HESS, MAXB>(args, f64, s);
-        case 2: return launch_tree<2, HESS, MAXB>(args, f64, s);
-        case 3: return launch_tree<3, HESS, MAXB>(args, f64, s);
-        case 4: return launch_tree<4, HESS, MAXB>(args, f64, s);
+        case 1: return launch_tree_cc<1, HESS, MAXB>(args, f64, s);
+        case 2: return launch_tree_cc<2, HESS, MAXB>(args, f64, s);
+        case 3: return launch_tree_cc<3, HESS, MAXB>(args, f64, s);
+        case 4: return launch_tree_cc<4, HESS, MAXB>(args, f64, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -961,26 +884,41 @@ int tree_blocks_per_sm(int C, bool f64) {
 
 // All problems in args share the category count args.d[0].C and the precision args.d[0].precision.
 template <int MAXB>
-cudaError_t launch_eval_nt(const BatchArgs<MAXB> &args, bool hess, cudaStream_t s) {
-    if (args.n <= 0) return cudaSuccess;
+cudaError_t launch_pmatrix(const BatchArgs<MAXB> &args, cudaStream_t s) {
     const int nmat = args.mat_base[args.n];
-    if (nmat > 0) {
-        pmatrix4_kernel<MAXB><<<(nmat + 127) / 128, 128, 0, s>>>(args);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    if (args.tile_base[args.n] > 0) {
-        const bool f64 = args.d[0].precision == 1;
-        cudaError_t e = hess ? launch_tree_c<MAXB, true>(args, args.d[0].C, f64, s)
-                             : launch_tree_c<MAXB, false>(args, args.d[0].C, f64, s);
-        if (e != cudaSuccess) return e;
-    }
+    if (args.n <= 0 || nmat <= 0) return cudaSuccess;
+    pmatrix4_kernel<MAXB><<<(nmat + 127) / 128, 128, 0, s>>>(args);
+    return cudaGetLastError();
+}
+
+template <int MAXB>
+cudaError_t launch_tree(const BatchArgs<MAXB> &args, bool hess, cudaStream_t s) {
+    if (args.n <= 0 || args.tile_base[args.n] <= 0) return cudaSuccess;
+    const bool f64 = args.d[0].precision == 1;
+    return hess ? launch_tree_c<MAXB, true>(args, args.d[0].C, f64, s)
+                : launch_tree_c<MAXB, false>(args, args.d[0].C, f64, s);
+}
+
+template <int MAXB>
+cudaError_t launch_reduce(const BatchArgs<MAXB> &args, bool hess, cudaStream_t s) {
+    if (args.n <= 0) return cudaSuccess;
     const int warps = args.red_base[args.n];
     reduce_kernel<MAXB><<<(warps + 7) / 8, 256, 0, s>>>(args, hess ? 1 : 0);
     return cudaGetLastError();
 }
 
+template <int MAXB>
+cudaError_t launch_eval_nt(const BatchArgs<MAXB> &args, bool hess, cudaStream_t s) {
+    cudaError_t e = launch_pmatrix<MAXB>(args, s);
+    if (e == cudaSuccess) e = launch_tree<MAXB>(args, hess, s);
+    if (e == cudaSuccess) e = launch_reduce<MAXB>(args, hess, s);
+    return e;
+}
+
 template cudaError_t launch_eval_nt<1>(const BatchArgs<1> &, bool, cudaStream_t);
+template cudaError_t launch_pmatrix<1>(const BatchArgs<1> &, cudaStream_t);
+template cudaError_t launch_tree<1>(const BatchArgs<1> &, bool, cudaStream_t);
+template cudaError_t launch_reduce<1>(const BatchArgs<1> &, bool, cudaStream_t);
 template cudaError_t launch_eval_nt<kMaxBatch>(const BatchArgs<kMaxBatch> &, bool, cudaStream_t);
 
 }  // namespace pg
