@@ -1,0 +1,342 @@
+#!/usr/bin/env python3
+"""Throughput of logL + branch-gradient evaluations on one GB300 (or N, as independent replicas).
+
+Workload (default): the nucleotide configuration -- a 1,000-taxon Yule tree with b ~ Exp(0.01), a
+general non-reversible 4x4 generator, 4 discrete-gamma rate categories (shape 0.5) and 10,000
+site patterns simulated down the tree with 2% all-ones ambiguous tip cells; one evaluation is
+logL plus the 1,998 branch gradients (FP32 partials, FP64 transition matrices and sums).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+One JSON line is printed by rank 0.  ``value`` is evaluations/s with every input resident in HBM
+(device branch lengths, device outputs), timed with CUDA events; ``e2e`` is the same metric through
+the blocking host-pointer call (branch lengths copied from pinned host memory, logL and gradient
+copied back each step).  ``roofline`` is for the dominant kernel (the pre-order level kernels),
+``cpu_baseline`` the FP64 CPU oracle on a bounded sample of the same workload.
+``--impl reference`` times that oracle alone (there is no reference GPU implementation).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "logL+branch-gradient evals/s"
+UNIT = "evals/s"
+WORKLOAD = ("nucleotide: 1,000-taxon Yule tree, b~Exp(0.01), non-reversible 4x4 Q, 4 gamma "
+            "categories (shape 0.5), 10,000 simulated patterns, 2% ambiguous tips")
+
+
+def _rank_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    for name in ("pg_levels.cu", "pg_device.cuh", "pg_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1905_12146_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_from_profile():
+    """DRAM bytes per evaluation of the pre-order level kernels from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "pre_level_kernel_nucleotide.md")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    kv = {}
+    for ln in lines:
+        if ln.startswith("- ") and ":" in ln:
+            k, v = ln[2:].split(":", 1)
+            kv[k.strip()] = v.strip().strip("`")
+    if kv.get("kernel_source_sha256_16") != _kernel_hash():
+        return None
+    try:
+        return float(kv["dram_bytes_per_eval"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.2)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        # under load: samples in the upper half of the observed range
+        hi = sorted(sm)[len(sm) // 2:]
+        return {"sm_mhz": statistics.median(hi), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _cpu_baseline(problem, seconds: float = 12.0):
+    """The FP64 oracle on a bounded sample of the workload (the first patterns of the
+    alignment), scaled to evaluations/s of the full workload."""
+    from oracle import oracle
+    oracle.build()
+    P = problem["weights"].shape[0]
+    sample = min(P, 1000)
+    t0 = time.perf_counter()
+    oracle.evaluate(problem, patterns=slice(0, sample))
+    t1 = time.perf_counter()
+    per = t1 - t0
+    reps = max(1, min(20, int(seconds / max(per, 1e-3))))
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.evaluate(problem, patterns=slice(0, sample))
+    per = (time.perf_counter() - t0) / reps
+    full = per * P / sample
+    return {"value": 1.0 / full, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{sample} of {P} patterns, {reps} evaluations (single thread, FP64), "
+                      f"time scaled by {P / sample:g} to the full alignment",
+            "seconds_per_full_eval": full}
+
+
+def run_reference(args):
+    rank, world, _ = _rank_env()
+    if world > 1 and rank != 0:
+        return 0
+    from oracle import oracle
+    from paper_1905_12146_gb300 import workloads
+    oracle.build()
+    pr = workloads.config_nucleotide()
+    P = pr["weights"].shape[0]
+    # size each step so that warm-up + timed steps take about two minutes in total
+    t0 = time.perf_counter()
+    oracle.evaluate(pr, patterns=slice(0, 100))
+    per_pattern = (time.perf_counter() - t0) / 100
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    sample = int(max(16, min(P, budget / max(per_pattern, 1e-6))))
+    for _ in range(args.warmup):
+        oracle.evaluate(pr, patterns=slice(0, sample))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.evaluate(pr, patterns=slice(0, sample))
+    elapsed = time.perf_counter() - t0
+    full = elapsed / args.steps * P / sample
+    value = 1.0 / full
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * full,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_tips": 1000, "n_patterns": P, "n_categories": 4,
+                   "n_states": 4},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{sample} of {P} patterns per step, scaled to the full "
+                                   "alignment (single thread, FP64)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_1905_12146_gb300 import _native, workloads
+
+    rank, world, local = _rank_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (the library has no CPU path)")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    pr = workloads.config_nucleotide()
+    ctx = _native.Context(local)
+    h = ctx.upload(pr, "fp32")
+    info = h.info()
+    dev = torch.device("cuda", local)
+    n = pr["parent"].shape[0]
+    b = torch.tensor(pr["b"], device=dev)
+    logL = torch.zeros(1, dtype=torch.float64, device=dev)
+    grad = torch.zeros(n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        h.eval_async(b, logL, grad, stream=stream)
+    torch.cuda.synchronize(dev)
+    if h.status() != 0:
+        raise SystemExit(f"evaluation failed with status {h.status()}")
+
+    # timed region: device-resident inputs and outputs, CUDA events on the launching stream
+    h.set_phase_timing(True)
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clocks:
+        start.record(stream)
+        for _ in range(args.steps):
+            h.eval_async(b, logL, grad, stream=stream)
+        stop.record(stream)
+        torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
+    ms = start.elapsed_time(stop)
+    pt = h.phase_times()
+    h.set_phase_timing(False)
+    status = h.status()
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * args.steps / (ms / 1e3)
+
+    # end to end: the blocking host-pointer call, pinned host buffers, copies inside the region
+    b_host = torch.tensor(pr["b"]).pin_memory()
+    out_logL = torch.zeros(1, dtype=torch.float64).pin_memory()
+    out_grad = torch.zeros(n, dtype=torch.float64).pin_memory()
+    lib = _native.load()
+    e2e_steps = max(1, args.steps // 2)
+    for _ in range(2):
+        lib.pg_eval(h._ptr, b_host.data_ptr(), out_logL.data_ptr(), out_grad.data_ptr(), None, None)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        st = lib.pg_eval(h._ptr, b_host.data_ptr(), out_logL.data_ptr(), out_grad.data_ptr(), None, None)
+        if st != 0:
+            raise SystemExit(f"pg_eval failed with status {st}")
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
+           "d2h_bytes_per_step": 8 + 8 * n}
+
+    peak, peak_kind = _peaks()
+    pre_ms = pt.pre_levels_ms / max(pt.evals, 1)
+    pre_gbs = pt.pre_levels_bytes / (pre_ms * 1e-3) / 1e9 if pre_ms > 0 else None
+    traffic = _traffic_from_profile()
+    roofline = {"bound": "hbm", "kernel": "pre_level_kernel (pre-order levels, all launches of one "
+                                           "evaluation)",
+                "achieved": pre_gbs, "peak": peak, "unit": "GB/s",
+                "frac": (pre_gbs / peak) if pre_gbs else None, "peak_source": f"{peak_kind} hbm_gbs",
+                "traffic": traffic,
+                "algorithmic_bytes": pt.pre_levels_bytes}
+    total_ms = pt.total_ms / max(pt.evals, 1)
+    eval_bytes = pt.post_levels_bytes + pt.fused_bytes + pt.pre_levels_bytes
+    phases = {"pmatrix_ms": pt.pmatrix_ms / max(pt.evals, 1),
+              "post_levels_ms": pt.post_levels_ms / max(pt.evals, 1),
+              "fused_ms": pt.fused_ms / max(pt.evals, 1), "pre_levels_ms": pre_ms,
+              "reduce_ms": pt.reduce_ms / max(pt.evals, 1), "eval_ms": total_ms,
+              "eval_algorithmic_bytes": eval_bytes,
+              "eval_frac_of_peak": eval_bytes / (total_ms * 1e-3) / 1e9 / peak if total_ms else None}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_tips": 1000, "n_patterns": int(info.n_patterns),
+                   "n_categories": 4, "n_states": 4, "partials": "fp32",
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "no flush: each evaluation streams ~3.4 GB of partials, 26x the 129 MB L2",
+                   "status": status},
+        "roofline": roofline,
+        "phases": phases,
+        "e2e": e2e,
+        "gpu_launches": pt.launches_per_eval * args.steps,
+        "clocks": clocks.summary(),
+    }
+    if rank == 0 and world == 1:
+        line["cpu_baseline"] = _cpu_baseline(pr)
+    h.close()
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=800)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=("gpu", "reference"), default="gpu")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    from paper_1905_12146_gb300 import build
+    build.build()
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -151,6 +151,27 @@ pg_status pg_eval_status(pg_handle *h);
 /* Sizes and algorithmic traffic of a handle (for measurement). */
 pg_status pg_get_info(const pg_handle *h, pg_handle_info *out);
 
+/* Device time of one evaluation's phases, summed over every evaluation since timing was enabled.
+ * Phases, in launch order: FP64 transition matrices; post-order levels run one launch per level
+ * (the wide levels near the tips); the fused kernel (the remaining levels, the root and their
+ * pre-order steps); pre-order levels run one launch per level; the per-branch reduction.  The
+ * *_bytes fields are the algorithmic HBM bytes of one evaluation's phase (partials, log2 scales and
+ * tip codes each read or written once). */
+typedef struct pg_phase_times {
+    double pmatrix_ms, post_levels_ms, fused_ms, pre_levels_ms, reduce_ms, total_ms;
+    int32_t evals;                     /* evaluations summed                                  */
+    int32_t launches_per_eval;         /* kernels one evaluation launches                     */
+    uint64_t post_levels_bytes, fused_bytes, pre_levels_bytes;
+} pg_phase_times;
+
+/* Enable (1) or disable (0) per-phase timing of this handle's evaluations: CUDA events are recorded
+ * on the evaluation's stream between phases (asynchronously, no host synchronisation).  Enabling
+ * clears the accumulated times. */
+pg_status pg_set_phase_timing(pg_handle *h, int enable);
+
+/* Waits for the timed evaluations and returns their summed phase times. */
+pg_status pg_get_phase_times(pg_handle *h, pg_phase_times *out);
+
 /* Static text for a status code. */
 const char *pg_status_string(pg_status s);
 

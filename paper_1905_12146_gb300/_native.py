@@ -19,8 +19,8 @@ PRECISIONS = {"fp32": 0, "fp64": 1}
 PG_OK, PG_ERR_INVALID, PG_ERR_OOM, PG_ERR_CUDA, PG_ERR_TIMEOUT, PG_ERR_NUMERIC, PG_ERR_UNSUPPORTED = range(7)
 
 EXPORTED = ("pg_create", "pg_destroy", "pg_upload", "pg_free", "pg_eval", "pg_eval_async",
-            "pg_eval_batch_async", "pg_eval_status", "pg_get_info", "pg_status_string",
-            "pg_last_error")
+            "pg_eval_batch_async", "pg_eval_status", "pg_get_info", "pg_set_phase_timing",
+            "pg_get_phase_times", "pg_status_string", "pg_last_error")
 
 
 class PhyloGradError(RuntimeError):
@@ -53,6 +53,15 @@ class pg_handle_info(ctypes.Structure):
                 ("flops", ctypes.c_uint64)]
 
 
+class pg_phase_times(ctypes.Structure):
+    _fields_ = [("pmatrix_ms", ctypes.c_double), ("post_levels_ms", ctypes.c_double),
+                ("fused_ms", ctypes.c_double), ("pre_levels_ms", ctypes.c_double),
+                ("reduce_ms", ctypes.c_double), ("total_ms", ctypes.c_double),
+                ("evals", ctypes.c_int32), ("launches_per_eval", ctypes.c_int32),
+                ("post_levels_bytes", ctypes.c_uint64), ("fused_bytes", ctypes.c_uint64),
+                ("pre_levels_bytes", ctypes.c_uint64)]
+
+
 _lib = None
 
 
@@ -76,6 +85,8 @@ def load(path: str = LIB_PATH):
         "pg_eval_batch_async": ([vp, i32, vp, vp, vp, vp, vp], i32),
         "pg_eval_status": ([vp], i32),
         "pg_get_info": ([vp, ctypes.POINTER(pg_handle_info)], i32),
+        "pg_set_phase_timing": ([vp, i32], i32),
+        "pg_get_phase_times": ([vp, ctypes.POINTER(pg_phase_times)], i32),
         "pg_status_string": ([i32], ctypes.c_char_p),
         "pg_last_error": ([], ctypes.c_char_p),
     }
@@ -192,6 +203,14 @@ class Handle:
             s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
         check(load().pg_eval_async(self._ptr, _dev_ptr(d_b), _dev_ptr(d_logL), _dev_ptr(d_grad),
                                    _dev_ptr(d_hess), _dev_ptr(d_site), s))
+
+    def set_phase_timing(self, enable: bool):
+        check(load().pg_set_phase_timing(self._ptr, 1 if enable else 0))
+
+    def phase_times(self) -> pg_phase_times:
+        out = pg_phase_times()
+        check(load().pg_get_phase_times(self._ptr, ctypes.byref(out)))
+        return out
 
     def status(self) -> int:
         return load().pg_eval_status(self._ptr)

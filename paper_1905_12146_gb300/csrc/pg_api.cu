@@ -72,6 +72,9 @@ struct pg_handle {
     int max_tiles = 0;       // blocks one evaluation of this problem may use
     int cut = 0;             // levels [0, cut) run as level kernels when evaluated alone
     std::vector<int> level_off;   // host copy of the level offsets
+    bool timing = false;
+    std::vector<cudaEvent_t> events;   // 6 per timed evaluation
+    uint64_t post_levels_bytes = 0, fused_bytes = 0, pre_levels_bytes = 0;
     double *io_b = nullptr, *io_logL = nullptr, *io_grad = nullptr, *io_hess = nullptr,
            *io_site = nullptr;   // device staging for the host-pointer pg_eval
     pg_handle_info info{};
@@ -280,6 +283,7 @@ pg_status pg_free(pg_handle *h) {
     if (!h) return PG_OK;
     pg_ctx *c = h->ctx;
     DeviceGuard g(c->device);
+    for (cudaEvent_t x : h->events) cudaEventDestroy(x);
     if (h->block) cudaFree(h->block);
     c->used -= h->bytes;
     c->handles.erase(std::remove(c->handles.begin(), c->handles.end(), h), c->handles.end());
@@ -439,6 +443,25 @@ pg_status pg_upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out) {
     d.cut = 0;
     h->cut = cut;
     h->level_off = tp.level_off;
+    {
+        // algorithmic bytes per node: partial + log2 scale per internal node stream, tip codes
+        const uint64_t row = (uint64_t)P * ((f64 ? 32ull : 16ull) * C + 4ull), tiprow = (uint64_t)P;
+        for (int lv = 0; lv < H; ++lv) {
+            uint64_t post_b = 0, pre_b = 0;
+            for (int o = tp.level_off[lv]; o < tp.level_off[lv + 1]; ++o) {
+                const int4 op = tp.ops[o];
+                const bool root = op.x == tp.root;
+                post_b += root ? 0 : row;                     // write p_k (the root's is not stored)
+                pre_b += root ? 0 : row;                      // read q_k
+                for (int c : {op.y, op.z}) {
+                    post_b += c < N ? tiprow : row;           // read p_c or the tip codes
+                    pre_b += c < N ? tiprow : 2 * row;        // read p_c and write q_c, or tip codes
+                }
+            }
+            if (lv < cut) { h->post_levels_bytes += post_b; h->pre_levels_bytes += pre_b; }
+            else h->fused_bytes += post_b + pre_b;
+        }
+    }
     h->io_b = reinterpret_cast<double *>(base + o_ib);
     h->io_logL = reinterpret_cast<double *>(base + o_il);
     h->io_grad = reinterpret_cast<double *>(base + o_ig);
@@ -527,13 +550,26 @@ pg_status pg_eval_async(pg_handle *h, const double *d_b, double *d_logL, double 
     d.cut = d.P > 0 ? h->cut : 0;
     fill_args_one(a, d);
     const bool hess = d_hess != nullptr;
+    cudaEvent_t ev[6] = {};
+    if (h->timing) {
+        for (auto &x : ev)
+            if (cudaEventCreate(&x) != cudaSuccess) return fail(PG_ERR_CUDA, "cudaEventCreate failed");
+        h->events.insert(h->events.end(), ev, ev + 6);
+    }
+    auto mark = [&](int i) { if (h->timing) cudaEventRecord(ev[i], s); };
+    mark(0);
     cudaError_t e = pg::launch_pmatrix<1>(a, s);
+    mark(1);
     for (int lv = 0; e == cudaSuccess && lv < d.cut; ++lv)
         e = pg::launch_post_level(d, h->level_off[lv], h->level_off[lv + 1] - h->level_off[lv], h->ctx->n_sm, s);
+    mark(2);
     if (e == cudaSuccess) e = pg::launch_tree<1>(a, hess, s);
+    mark(3);
     for (int lv = d.cut - 1; e == cudaSuccess && lv >= 0; --lv)
         e = pg::launch_pre_level(d, h->level_off[lv], h->level_off[lv + 1] - h->level_off[lv], hess, h->ctx->n_sm, s);
+    mark(4);
     if (e == cudaSuccess) e = pg::launch_reduce<1>(a, hess, s);
+    mark(5);
     if (e != cudaSuccess) return fail(PG_ERR_CUDA, "launch: %s", cudaGetErrorString(e));
     h->last_stream = s;
     return PG_OK;
@@ -592,6 +628,40 @@ pg_status pg_eval_batch_async(pg_handle *const *hs, int32_t k, const double *con
         }
     }
     delete a;
+    return PG_OK;
+}
+
+pg_status pg_set_phase_timing(pg_handle *h, int enable) {
+    if (!h) return fail(PG_ERR_INVALID, "NULL handle");
+    DeviceGuard g(h->ctx->device);
+    for (cudaEvent_t x : h->events) cudaEventDestroy(x);
+    h->events.clear();
+    h->timing = enable != 0;
+    return PG_OK;
+}
+
+pg_status pg_get_phase_times(pg_handle *h, pg_phase_times *out) {
+    if (!h || !out) return fail(PG_ERR_INVALID, "NULL argument");
+    DeviceGuard g(h->ctx->device);
+    pg_phase_times t{};
+    double *ph[5] = {&t.pmatrix_ms, &t.post_levels_ms, &t.fused_ms, &t.pre_levels_ms, &t.reduce_ms};
+    for (size_t b = 0; b + 6 <= h->events.size(); b += 6) {
+        PG_CUDA(cudaEventSynchronize(h->events[b + 5]));
+        for (int i = 0; i < 5; ++i) {
+            float ms = 0.f;
+            PG_CUDA(cudaEventElapsedTime(&ms, h->events[b + i], h->events[b + i + 1]));
+            *ph[i] += ms;
+        }
+        float ms = 0.f;
+        PG_CUDA(cudaEventElapsedTime(&ms, h->events[b], h->events[b + 5]));
+        t.total_ms += ms;
+        t.evals += 1;
+    }
+    t.launches_per_eval = h->desc.P > 0 ? 3 + 2 * h->cut : 2;
+    t.post_levels_bytes = h->post_levels_bytes;
+    t.fused_bytes = h->fused_bytes;
+    t.pre_levels_bytes = h->pre_levels_bytes;
+    *out = t;
     return PG_OK;
 }
 
