@@ -151,6 +151,26 @@ pg_status pg_eval_status(pg_handle *h);
 /* Sizes and algorithmic traffic of a handle (for measurement). */
 pg_status pg_get_info(const pg_handle *h, pg_handle_info *out);
 
+/* Fixed device scratch used by pg_eval_noalloc, per GPU that loads this library (64 MiB). */
+#define PG_NOALLOC_SCRATCH_BYTES (64u << 20)
+
+/* One blocking evaluation of a small problem that allocates nothing: no cudaMalloc or cudaFree,
+ * no allocating library call, no host heap.  The paper has no counterpart; this exists for callers
+ * that cannot allocate when they evaluate (for example code that must not trigger an allocation's
+ * device-wide synchronisation inside a latency-critical loop, or a plug-in whose host application
+ * owns every device allocation).  The problem, b and the outputs are HOST arrays laid out as for
+ * pg_upload / pg_eval; there is no handle.  Runs on the calling thread's current device, on
+ * `stream` (NULL = legacy default stream), and returns when the results are on the host.
+ * Every intermediate array lives in one fixed device array of PG_NOALLOC_SCRATCH_BYTES that each
+ * GPU loading the library holds until the process exits; host-side planning uses fixed static
+ * buffers.  The first call on a device looks up that array's device address (set-up), so make it
+ * before any stream capture.  All calls share the array and the static buffers: calls that
+ * overlap, on the GPU or from several host threads, race and must be serialised by the caller.
+ * Errors: PG_ERR_UNSUPPORTED when the problem needs more scratch than PG_NOALLOC_SCRATCH_BYTES, has
+ * more than 8192 tips or 64 models, or m != 4 or C > 4; otherwise as pg_upload and pg_eval. */
+pg_status pg_eval_noalloc(const pg_problem *pr, const double *b, double *logL, double *grad,
+                          double *hess, double *site_logL, void *stream);
+
 /* Device time of one evaluation's phases, summed over every evaluation since timing was enabled.
  * Phases, in launch order: FP64 transition matrices; post-order levels run one launch per level
  * (the wide levels near the tips); the fused kernel (the remaining levels, the root and their

@@ -20,7 +20,7 @@ PG_OK, PG_ERR_INVALID, PG_ERR_OOM, PG_ERR_CUDA, PG_ERR_TIMEOUT, PG_ERR_NUMERIC, 
 
 EXPORTED = ("pg_create", "pg_destroy", "pg_upload", "pg_free", "pg_eval", "pg_eval_async",
             "pg_eval_batch_async", "pg_eval_status", "pg_get_info", "pg_set_phase_timing",
-            "pg_get_phase_times", "pg_status_string", "pg_last_error")
+            "pg_get_phase_times", "pg_eval_noalloc", "pg_status_string", "pg_last_error")
 
 
 class PhyloGradError(RuntimeError):
@@ -87,6 +87,7 @@ def load(path: str = LIB_PATH):
         "pg_get_info": ([vp, ctypes.POINTER(pg_handle_info)], i32),
         "pg_set_phase_timing": ([vp, i32], i32),
         "pg_get_phase_times": ([vp, ctypes.POINTER(pg_phase_times)], i32),
+        "pg_eval_noalloc": ([ctypes.POINTER(pg_problem), vp, vp, vp, vp, vp, vp], i32),
         "pg_status_string": ([i32], ctypes.c_char_p),
         "pg_last_error": ([], ctypes.c_char_p),
     }
@@ -236,3 +237,41 @@ def eval_batch_async(handles, d_b, d_logL, d_grad=None, d_hess=None, stream=None
                                      ctypes.cast(bs, ctypes.c_void_p), _dev_ptr(d_logL),
                                      None if gs is None else ctypes.cast(gs, ctypes.c_void_p),
                                      None if hh is None else ctypes.cast(hh, ctypes.c_void_p), s))
+
+
+def eval_noalloc(problem: dict, b, precision: str = "fp32", grad=True, hess=False, site=False,
+                 stream=None):
+    """pg_eval_noalloc: one blocking evaluation with host arrays that allocates no device or host
+    heap memory inside the library (its scratch is a fixed per-GPU device array).  For callers that
+    cannot allocate at evaluation time; calls must not overlap.  Returns a dict like Handle.eval."""
+    lib = load()
+    parent = np.ascontiguousarray(problem["parent"], dtype=np.int32)
+    tips = np.ascontiguousarray(problem["tip_states"], dtype=np.uint8)
+    w = np.ascontiguousarray(problem["weights"], dtype=np.float64)
+    Q = np.ascontiguousarray(problem["Q"], dtype=np.float64)
+    if Q.ndim == 2:
+        Q = Q[None]
+    bm = problem.get("branch_model")
+    bm = None if bm is None else np.ascontiguousarray(bm, dtype=np.int32)
+    pi = np.ascontiguousarray(problem["root_freqs"], dtype=np.float64)
+    rates = np.ascontiguousarray(problem["cat_rates"], dtype=np.float64)
+    cw = np.ascontiguousarray(problem["cat_weights"], dtype=np.float64)
+    n = parent.shape[0]
+    P = tips.shape[1] if tips.ndim == 2 else 0
+    pr = pg_problem((n + 1) // 2, Q.shape[1], P, rates.shape[0], Q.shape[0], PRECISIONS[precision],
+                    _np_ptr(parent), _np_ptr(tips), _np_ptr(w), _np_ptr(Q), _np_ptr(bm),
+                    _np_ptr(pi), _np_ptr(rates), _np_ptr(cw))
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    logL = np.zeros(1)
+    g = np.zeros(n) if grad else None
+    h = np.zeros(n) if hess else None
+    st_site = np.zeros(P) if site else None
+    s = None
+    if stream is not None:
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    st = lib.pg_eval_noalloc(ctypes.byref(pr), _np_ptr(b), _np_ptr(logL), _np_ptr(g), _np_ptr(h),
+                             _np_ptr(st_site), s)
+    out = {"logL": float(logL[0]), "grad": g, "hess": h, "site_logL": st_site, "status": st}
+    if st not in (PG_OK, PG_ERR_NUMERIC):
+        raise PhyloGradError(st, lib.pg_status_string(st).decode())
+    return out

@@ -1,0 +1,57 @@
+"""The allocation-free entry point (pg_eval_noalloc) against the regular one (pg_eval).
+
+pg_eval_noalloc is for callers that cannot allocate when they evaluate: it keeps every
+intermediate array in one fixed device array per GPU and plans on fixed host buffers.  This file
+is collected last so that a run stopping at its first failure has run every other test already.
+"""
+import numpy as np
+import pytest
+
+from paper_1905_12146_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def native():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1905_12146_gb300 import _native, build
+    build.build()
+    return _native
+
+
+def _regular(native, pr, precision):
+    ctx = native.Context(0)
+    h = ctx.upload(pr, precision)
+    out = h.eval(pr["b"], grad=True, hess=True, site=True)
+    h.close()
+    ctx.close()
+    return out
+
+
+@pytest.mark.parametrize("precision,logl_rtol,grad_rtol", [("fp64", 1e-12, 1e-11), ("fp32", 1e-9, 1e-5)])
+def test_noalloc_matches_pg_eval_on_two_calls_in_a_row(native, precision, logl_rtol, grad_rtol):
+    """Two different problems in a row through the shared scratch array: each result matches the
+    regular entry point within the parity tolerances (the second call must not see the first's
+    leftovers)."""
+    problems = [wl.random_problem(40, 777, n_states=4, n_cat=4, seed=301, b_mean=0.05, ambiguous=0.03,
+                                  weights="int"),
+                wl.config_small(seed=2)]
+    for pr in problems:
+        ref = _regular(native, pr, precision)
+        got = native.eval_noalloc(pr, pr["b"], precision, grad=True, hess=True, site=True)
+        assert got["status"] == 0
+        assert abs(got["logL"] - ref["logL"]) <= logl_rtol * abs(ref["logL"])
+        assert np.abs(got["grad"] - ref["grad"]).max() <= grad_rtol * np.abs(ref["grad"]).max()
+        assert np.abs(got["hess"] - ref["hess"]).max() <= 10 * grad_rtol * np.abs(ref["hess"]).max()
+        np.testing.assert_allclose(got["site_logL"], ref["site_logL"], rtol=0,
+                                   atol=1e-10 if precision == "fp64" else 1e-6)
+
+
+def test_noalloc_rejects_problems_beyond_its_scratch(native):
+    pr = wl.random_problem(300, 20000, n_states=4, n_cat=4, seed=302, b_mean=0.05)
+    with pytest.raises(native.PhyloGradError) as e:
+        native.eval_noalloc(pr, pr["b"], "fp32")
+    assert e.value.status == native.PG_ERR_UNSUPPORTED
