@@ -332,7 +332,8 @@ pg_status pg_upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out) {
         return fail(PG_ERR_UNSUPPORTED, "n_patterns = %d exceeds %d on this device", P, max_tiles * max_range);
     const int Ps = (P + 15) / 16 * 16;   // row stride of per-pattern arrays (16-byte rows for TMA)
     const int level_ranges = (P + pg::kLevelRange - 1) / pg::kLevelRange;
-    const int slot_cap = std::max((P + 31) / 32 + 3 * max_tiles + 2, level_ranges);
+    // wide branches use one slot per (range, consumer warp) of the level kernels
+    const int slot_cap = std::max((P + 31) / 32 + 3 * max_tiles + 2, level_ranges * (pg::kLevelRange / 32));
     // FP32 problems evaluated alone run every level with at least two blocks per SM of
     // (node, 256-pattern) work as its own launch; the narrower levels near the root stay fused
     int cut = 0;

@@ -146,6 +146,10 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned b
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
 }
+// a plain arrival (no transactions)
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
     unsigned ok;
     asm volatile(

@@ -63,7 +63,7 @@ struct ProbDesc {
     const uint8_t *wide;
     float *site_invL;              // [P] 1 / Lhat_p, written at the root for the level kernels
     int *site_Er;                  // [P] log2 scale of L_p
-    int level_ranges;              // ceil(P / kLevelRange): slots per wide branch
+    int level_ranges;              // ceil(P / kLevelRange); a wide branch has 4 slots per range
     // outputs of this evaluation (device, may be null)
     double *out_logL, *out_grad, *out_hess, *out_site;
     // sizes

@@ -2,13 +2,14 @@
 //
 // Near the tips a level holds hundreds of nodes, so one launch per level has enough independent
 // (node, pattern) work to fill the GPU by itself.  An item is one node of the level and a range of
-// kLevelRange patterns (one per thread).  Blocks are persistent: each walks the items
-// blockIdx.x, blockIdx.x + gridDim.x, ... through a ring of STAGES shared-memory stages.  Thread 0
-// stages an item with a handful of 1-D bulk copies (TMA), one per contiguous row segment (the
-// children's partial rows per rate category, q_k's rows, the log2 scales, tip codes, the
-// per-pattern site values and the node's two branch tables), STAGES - 1 items ahead of the one
-// the block computes.  Bytes in flight are bounded by shared memory, not by registers, and no
-// block depends on another within a launch.
+// kLevelRange patterns.  Blocks are persistent and warp-specialised: they walk the items
+// blockIdx.x, blockIdx.x + gridDim.x, ... through a ring of STAGES shared-memory stages.  A producer
+// warp stages each item with a handful of 1-D bulk copies (TMA), one per contiguous row segment (the
+// children's partial rows per rate category, q_k's rows, the log2 scales, tip codes, the per-pattern
+// site values and the node's two branch tables), signalling a "full" mbarrier; kConsumerWarps
+// consumer warps each compute 32 patterns of the item and release the stage on an "empty" mbarrier.
+// No block-wide barrier is taken inside the loop.  Bytes in flight are bounded by shared memory, not
+// by registers, and no block depends on another within a launch.
 //
 // The arithmetic is that of the fused tree kernel (pg_nt.cu): the exact-product post-order update
 // of Section 2.3, and the pre-order step of Section 2.4 with the branch gradient (Section 2.5) and
@@ -48,11 +49,14 @@ struct PreStage {
     float4 qtab[2][4];           // Q columns of both children's models
 };
 
+constexpr int kConsumerWarps = R / 32;
+constexpr int kLevelThreads = R + 32;   // consumers + one producer warp
+
 template <class Stage, int STAGES>
 struct Ring {
     Stage st[STAGES];
-    uint64_t bar[STAGES];
-    double red[R / 32][4];
+    uint64_t full[STAGES];    // producer: arrive with the stage's transaction bytes
+    uint64_t empty[STAGES];   // consumers: one arrival per consumer warp when done reading
 };
 
 __device__ __forceinline__ unsigned round16(unsigned b) { return (b + 15u) & ~15u; }
@@ -131,8 +135,7 @@ __device__ void issue_pre(const ProbDesc &d, const Item &it, PreStage<C> &sm, ui
 
 // post-order update (Section 2.3) of one item from its stage
 template <int C>
-__device__ __forceinline__ void compute_post(const ProbDesc &d, const Item &it, const PostStage<C> &sm) {
-    const int t = threadIdx.x;
+__device__ __forceinline__ void compute_post(const ProbDesc &d, const Item &it, const PostStage<C> &sm, int t) {
     if (t >= it.cnt) return;
     const int N = d.n_tips, Ps = d.Ps, k = it.op.x, c0 = it.op.y, c1 = it.op.z;
     const bool t0 = c0 < N, t1 = c1 < N;
@@ -170,14 +173,13 @@ __device__ __forceinline__ void compute_post(const ProbDesc &d, const Item &it, 
     __stcg(d.pe + (size_t)(k - N) * Ps + p, E + e);
 }
 
-// pre-order step (Section 2.4) with the branch gradient (2.5) and Hessian diagonal (2.6) of one
-// item; the block's sums over its patterns go to the item's slot of both child branches
+// pre-order step (Section 2.4) with the branch gradient (2.5) and Hessian diagonal (2.6) for the
+// calling warp's 32 patterns of one item; the warp's sums go to its own slot of both child branches
+// (slot = 4 * range + warp; the reduction adds the slots in a fixed order)
 template <int C, bool HESS>
-__device__ __forceinline__ void compute_pre(const ProbDesc &d, const Item &it, const PreStage<C> &sm,
-                                            double (&red)[R / 32][4]) {
+__device__ __forceinline__ void compute_pre(const ProbDesc &d, const Item &it, const PreStage<C> &sm, int t) {
     const int N = d.n_tips, Ps = d.Ps, c0 = it.op.y, c1 = it.op.z;
     const bool t0 = c0 < N, t1 = c1 < N;
-    const int t = threadIdx.x;
     const bool active = t < it.cnt;
     const int tt = active ? t : it.cnt - 1;
     const int p = it.p0 + tt;
@@ -225,90 +227,92 @@ __device__ __forceinline__ void compute_pre(const ProbDesc &d, const Item &it, c
     sums[1] = wt * d1;
     sums[2] = HESS ? wt * (ldexpf(h0, dE) * inv - d0 * d0) : 0.f;
     sums[3] = HESS ? wt * (ldexpf(h1, dE) * inv - d1 * d1) : 0.f;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lane = t & 31, slot = it.rg * kConsumerWarps + (t >> 5);
 #pragma unroll
-    for (int s = 0; s < (HESS ? 4 : 2); ++s) {   // 32 patterns summed in FP32, warps combined in FP64
+    for (int s = 0; s < (HESS ? 4 : 2); ++s) {   // 32 patterns summed in FP32
         const float v = warp_sum_f(wt != 0.f ? sums[s] : 0.f);
-        if (lane == 0) red[warp][s] = (double)v;
-    }
-    __syncthreads();
-    if (threadIdx.x < (HESS ? 4 : 2)) {
-        const int s = threadIdx.x;
-        double v = 0.0;
-#pragma unroll
-        for (int w = 0; w < R / 32; ++w) v += red[w][s];
-        double *dst = (s < 2) ? d.gpart : d.hpart;
-        dst[(size_t)((s & 1) ? c1 : c0) * d.slot_cap + it.rg] = v;
+        if (lane == 0) {
+            double *dst = (s < 2) ? d.gpart : d.hpart;
+            dst[(size_t)((s & 1) ? c1 : c0) * d.slot_cap + slot] = (double)v;
+        }
     }
 }
 
-// The persistent, staged walk over a level's items shared by both passes.
+// The persistent, warp-specialised walk over a level's items shared by both passes.  Warp
+// kConsumerWarps is the producer: its lane 0 refills stage s once the consumers released it and
+// issues the item's bulk copies.  Consumer warps wait for the stage to be full, compute their 32
+// patterns and release it.  Every wait is bounded; a warp that gives up records PG_ERR_TIMEOUT and
+// leaves (the producer first lets the copies it issued land).
 template <class Stage, int STAGES, class Issue, class Compute>
 __device__ __forceinline__ void staged_walk(const ProbDesc &d, int o0, int nr, int n_items,
                                             Ring<Stage, STAGES> &ring, Issue &&issue, Compute &&compute) {
     const int G = gridDim.x, b = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) mbar_init(&ring.bar[s], 1);
-        for (int i = 0; i < STAGES - 1; ++i) {
-            const int j = b + i * G;
-            if (j < n_items) issue(item_of(d, o0, nr, j), ring.st[i], &ring.bar[i]);
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&ring.full[s], 1);
+            mbar_init(&ring.empty[s], kConsumerWarps);
         }
     }
-    __syncthreads();
-    for (int i = 0;; ++i) {
+    __syncthreads();   // barriers initialised before anyone uses them
+    if (warp == kConsumerWarps) {   // producer
+        if (lane != 0) return;
+        int i = 0;
+        for (;; ++i) {
+            const int j = b + i * G;
+            if (j >= n_items) break;
+            const int s = i % STAGES, use = i / STAGES;
+            if (use > 0 && !mbar_wait_bounded(&ring.empty[s], (unsigned)(use - 1) & 1u, kWaitLimitCycles)) {
+                atomicOr(d.status, kStatusTimeout);
+                break;
+            }
+            issue(item_of(d, o0, nr, j), ring.st[s], &ring.full[s]);
+        }
+        // let every copy issued by this warp land before the block may leave
+        for (int q = (i > STAGES ? i - STAGES : 0); q < i; ++q)
+            mbar_wait_bounded(&ring.full[q % STAGES], (unsigned)(q / STAGES) & 1u, kWaitLimitCycles);
+        return;
+    }
+    for (int i = 0;; ++i) {   // consumers
         const int j = b + i * G;
         if (j >= n_items) break;
         const int s = i % STAGES;
-        if (threadIdx.x == 0) {   // refill the stage freed at the end of the previous iteration
-            const int jn = b + (i + STAGES - 1) * G;
-            if (jn < n_items) {
-                const int sn = (i + STAGES - 1) % STAGES;
-                issue(item_of(d, o0, nr, jn), ring.st[sn], &ring.bar[sn]);
-            }
-        }
-        const bool ok = mbar_wait_bounded(&ring.bar[s], (unsigned)(i / STAGES) & 1u, kWaitLimitCycles);
-        if (__syncthreads_or(!ok)) {
-            // give up: record the time-out; thread 0 lets every copy it issued land before leaving
-            if (threadIdx.x == 0) {
-                atomicOr(d.status, kStatusTimeout);
-                for (int q = 0; q < STAGES; ++q) {
-                    const int iq = i + q;
-                    if (b + iq * G < n_items) mbar_wait_bounded(&ring.bar[iq % STAGES], (unsigned)(iq / STAGES) & 1u, kWaitLimitCycles);
-                }
-            }
+        if (!mbar_wait_bounded(&ring.full[s], (unsigned)(i / STAGES) & 1u, kWaitLimitCycles)) {
+            if (lane == 0) atomicOr(d.status, kStatusTimeout);
             return;
         }
-        compute(item_of(d, o0, nr, j), ring.st[s]);
-        __syncthreads();   // the stage is read by everyone before it is refilled
+        compute(item_of(d, o0, nr, j), ring.st[s], threadIdx.x);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ring.empty[s]);
     }
 }
 
 template <int C, int STAGES>
-__global__ void __launch_bounds__(R) post_level_kernel(const __grid_constant__ ProbDesc d, int o0, int nr, int n_items) {
+__global__ void __launch_bounds__(kLevelThreads) post_level_kernel(const __grid_constant__ ProbDesc d, int o0, int nr, int n_items) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto &ring = *reinterpret_cast<Ring<PostStage<C>, STAGES> *>(smem_raw);
     staged_walk(d, o0, nr, n_items, ring,
                 [&](const Item &it, PostStage<C> &st, uint64_t *bar) { issue_post<C>(d, it, st, bar); },
-                [&](const Item &it, const PostStage<C> &st) { compute_post<C>(d, it, st); });
+                [&](const Item &it, const PostStage<C> &st, int t) { compute_post<C>(d, it, st, t); });
 }
 
 template <int C, bool HESS, int STAGES>
-__global__ void __launch_bounds__(R) pre_level_kernel(const __grid_constant__ ProbDesc d, int o0, int nr, int n_items) {
+__global__ void __launch_bounds__(kLevelThreads) pre_level_kernel(const __grid_constant__ ProbDesc d, int o0, int nr, int n_items) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto &ring = *reinterpret_cast<Ring<PreStage<C>, STAGES> *>(smem_raw);
     staged_walk(d, o0, nr, n_items, ring,
                 [&](const Item &it, PreStage<C> &st, uint64_t *bar) { issue_pre<C>(d, it, st, bar); },
-                [&](const Item &it, const PreStage<C> &st) { compute_pre<C, HESS>(d, it, st, ring.red); });
+                [&](const Item &it, const PreStage<C> &st, int t) { compute_pre<C, HESS>(d, it, st, t); });
 }
 
-constexpr int kPostStages = 3, kPreStages = 2;
+constexpr int kPostStages = 4, kPreStages = 3;
 
 // blocks of a persistent level launch: every resident slot, at most one per item
 template <class K>
 int persistent_blocks(K kernel, size_t smem, int n_sm, int n_items, bool &configured, int &per_sm) {
     if (!configured) {
         if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, R, smem) != cudaSuccess) return -1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kLevelThreads, smem) != cudaSuccess) return -1;
         if (per_sm < 1) per_sm = 1;
         configured = true;
     }
@@ -323,7 +327,7 @@ cudaError_t post_c(const ProbDesc &d, int o0, int nd, int n_sm, cudaStream_t s) 
     const size_t smem = sizeof(Ring<PostStage<C>, kPostStages>);
     const int blocks = persistent_blocks(post_level_kernel<C, kPostStages>, smem, n_sm, n_items, configured, per_sm);
     if (blocks < 0) return cudaErrorInvalidConfiguration;
-    post_level_kernel<C, kPostStages><<<blocks, R, smem, s>>>(d, o0, nr, n_items);
+    post_level_kernel<C, kPostStages><<<blocks, kLevelThreads, smem, s>>>(d, o0, nr, n_items);
     return cudaGetLastError();
 }
 
@@ -335,7 +339,7 @@ cudaError_t pre_c(const ProbDesc &d, int o0, int nd, int n_sm, cudaStream_t s) {
     const size_t smem = sizeof(Ring<PreStage<C>, kPreStages>);
     const int blocks = persistent_blocks(pre_level_kernel<C, HESS, kPreStages>, smem, n_sm, n_items, configured, per_sm);
     if (blocks < 0) return cudaErrorInvalidConfiguration;
-    pre_level_kernel<C, HESS, kPreStages><<<blocks, R, smem, s>>>(d, o0, nr, n_items);
+    pre_level_kernel<C, HESS, kPreStages><<<blocks, kLevelThreads, smem, s>>>(d, o0, nr, n_items);
     return cudaGetLastError();
 }
 
