@@ -72,6 +72,7 @@ struct pg_handle {
     int max_tiles = 0;       // blocks one evaluation of this problem may use
     int cut = 0;             // levels [0, cut) run as level kernels when evaluated alone
     std::vector<int> level_off;   // host copy of the level offsets
+    std::vector<uint8_t> level_cherry;   // 1 when every node of the level has two tip children
     bool timing = false;
     std::vector<cudaEvent_t> events;   // 6 per timed evaluation
     uint64_t post_levels_bytes = 0, fused_bytes = 0, pre_levels_bytes = 0;
@@ -347,6 +348,29 @@ pg_status pg_upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out) {
             wide[tp.ops[o].y] = 1;
             wide[tp.ops[o].z] = 1;
         }
+    // the top part (levels >= cut) for the shared-memory top kernel: children of top nodes coded
+    // as -1 - slot (a tip), their top index, or n_top + their boundary index
+    const int o_cut = tp.level_off[cut];
+    const int n_top = (N - 1) - o_cut;
+    std::vector<int> top_index(n, -1), bnd_index(n, -1);
+    for (int o = o_cut; o < N - 1; ++o) top_index[tp.ops[o].x] = o - o_cut;
+    std::vector<int2> top_code(std::max(n_top, 1));
+    std::vector<int> bnd_node;
+    int n_tip_children = 0;
+    for (int o = o_cut; o < N - 1; ++o) {
+        int cc[2];
+        for (int side = 0; side < 2; ++side) {
+            const int c = side ? tp.ops[o].z : tp.ops[o].y;
+            if (c < N) cc[side] = -1 - n_tip_children++;   // a tip: its slot among the top's tips
+            else if (top_index[c] >= 0) cc[side] = top_index[c];
+            else {
+                if (bnd_index[c] < 0) { bnd_index[c] = (int)bnd_node.size(); bnd_node.push_back(c); }
+                cc[side] = n_top + bnd_index[c];
+            }
+        }
+        top_code[o - o_cut] = int2{cc[0], cc[1]};
+    }
+    const int n_bnd = (int)bnd_node.size();
     const int M = pr->n_models;
 
     Carver cv;
@@ -354,6 +378,7 @@ pg_status pg_upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out) {
     const size_t o_tips = cv.take<uint8_t>((size_t)N * Ps), o_w = cv.take<double>(Ps);
     const size_t o_wf = cv.take<float>(Ps);
     const size_t o_Qd = cv.take<double>((size_t)M * 16), o_Qf = cv.take<float4>((size_t)M * 4);
+    const size_t o_Mp = cv.take<double>((size_t)M * (pg::kTaylorDeg + 1) * 16), o_qn = cv.take<double>(M);
     const size_t o_bm = pr->branch_model ? cv.take<int>(n) : 0;
     const size_t o_P = f64 ? cv.take<double2>((size_t)n * C * pg::kPtab64Pairs)
                            : cv.take<float4>((size_t)n * C * pg::kPtabCols);
@@ -365,6 +390,7 @@ pg_status pg_upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out) {
     const size_t o_lp = cv.take<double>(slot_cap), o_st = cv.take<int>(1);
     const size_t o_wide = cv.take<uint8_t>(n), o_sinv = cv.take<float>(std::max(Ps, 16));
     const size_t o_ser = cv.take<int>(std::max(Ps, 16));
+    const size_t o_tc = cv.take<int2>(top_code.size()), o_bn = cv.take<int>(std::max(n_bnd, 1));
     const size_t o_ib = cv.take<double>(n), o_il = cv.take<double>(1), o_ig = cv.take<double>(n);
     const size_t o_ih = cv.take<double>(n), o_is = cv.take<double>(std::max(P, 1));
     const size_t bytes = align_up(cv.off, 256);
@@ -388,6 +414,24 @@ pg_status pg_upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out) {
     h->bytes = bytes;
     h->max_tiles = max_tiles;
 
+    // Taylor coefficients Q^k / k! and ||Q||_1 per model (FP64, host, once per upload)
+    std::vector<double> Mpow((size_t)M * (pg::kTaylorDeg + 1) * 16), qnorm(M);
+    for (int md = 0; md < M; ++md) {
+        const double *Q = pr->Q + (size_t)md * 16;
+        double *Mk = Mpow.data() + (size_t)md * (pg::kTaylorDeg + 1) * 16;
+        for (int u = 0; u < 16; ++u) Mk[u] = (u % 5 == 0) ? 1.0 : 0.0;
+        for (int k = 1; k <= pg::kTaylorDeg; ++k)
+            for (int r = 0; r < 4; ++r)
+                for (int c = 0; c < 4; ++c) {
+                    double acc = 0.0;
+                    for (int t = 0; t < 4; ++t) acc += Mk[(k - 1) * 16 + r * 4 + t] * Q[t * 4 + c];
+                    Mk[k * 16 + r * 4 + c] = acc / (double)k;
+                }
+        double nrm = 0.0;
+        for (int c = 0; c < 4; ++c)
+            nrm = std::max(nrm, std::fabs(Q[c]) + std::fabs(Q[4 + c]) + std::fabs(Q[8 + c]) + std::fabs(Q[12 + c]));
+        qnorm[md] = nrm;
+    }
     std::vector<float4> Qf((size_t)M * 4);
     for (int md = 0; md < M; ++md)
         for (int c = 0; c < 4; ++c) {
@@ -409,8 +453,12 @@ pg_status pg_upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out) {
     if (e == cudaSuccess && P > 0) e = cp(o_wf, wf.data(), sizeof(float) * Ps);
     if (e == cudaSuccess) e = cp(o_Qd, pr->Q, sizeof(double) * 16 * M);
     if (e == cudaSuccess) e = cp(o_Qf, Qf.data(), sizeof(float4) * Qf.size());
+    if (e == cudaSuccess) e = cp(o_Mp, Mpow.data(), sizeof(double) * Mpow.size());
+    if (e == cudaSuccess) e = cp(o_qn, qnorm.data(), sizeof(double) * M);
     if (e == cudaSuccess && pr->branch_model) e = cp(o_bm, pr->branch_model, sizeof(int) * n);
     if (e == cudaSuccess) e = cp(o_wide, wide.data(), wide.size());
+    if (e == cudaSuccess) e = cp(o_tc, top_code.data(), sizeof(int2) * top_code.size());
+    if (e == cudaSuccess && n_bnd > 0) e = cp(o_bn, bnd_node.data(), sizeof(int) * n_bnd);
     if (e == cudaSuccess) e = cudaMemset(base + o_st, 0, sizeof(int));
     if (e != cudaSuccess) {
         cudaFree(block);
@@ -426,6 +474,8 @@ pg_status pg_upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out) {
     d.wf = reinterpret_cast<const float *>(base + o_wf);
     d.Qd = reinterpret_cast<const double *>(base + o_Qd);
     d.Qf = reinterpret_cast<const float4 *>(base + o_Qf);
+    d.Mpow = reinterpret_cast<const double *>(base + o_Mp);
+    d.qnorm = reinterpret_cast<const double *>(base + o_qn);
     d.bmodel = pr->branch_model ? reinterpret_cast<const int *>(base + o_bm) : nullptr;
     d.Ptab = f64 ? nullptr : reinterpret_cast<float4 *>(base + o_P);
     d.Ptab64 = f64 ? reinterpret_cast<double2 *>(base + o_P) : nullptr;
@@ -441,9 +491,17 @@ pg_status pg_upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out) {
     d.site_invL = reinterpret_cast<float *>(base + o_sinv);
     d.site_Er = reinterpret_cast<int *>(base + o_ser);
     d.level_ranges = level_ranges;
+    d.n_top = n_top;
+    d.n_bnd = n_bnd;
+    d.top_code = reinterpret_cast<const int2 *>(base + o_tc);
+    d.bnd_node = reinterpret_cast<const int *>(base + o_bn);
     d.cut = 0;
     h->cut = cut;
     h->level_off = tp.level_off;
+    h->level_cherry.assign(H, 1);
+    for (int lv = 0; lv < H; ++lv)
+        for (int o = tp.level_off[lv]; o < tp.level_off[lv + 1]; ++o)
+            if (tp.ops[o].y >= N || tp.ops[o].z >= N) h->level_cherry[lv] = 0;
     {
         // algorithmic bytes per node: partial + log2 scale per internal node stream, tip codes
         const uint64_t row = (uint64_t)P * ((f64 ? 32ull : 16ull) * C + 4ull), tiprow = (uint64_t)P;
@@ -547,8 +605,18 @@ pg_status pg_eval_async(pg_handle *h, const double *d_b, double *d_logL, double 
     d.out_grad = d_grad;
     d.out_hess = d_hess;
     d.out_site = d_site_logL;
-    set_tiling(d, single_target(h->ctx, d), h->ctx->max_range ? h->ctx->max_range : pg::kMaxRange);
+    const int max_range = h->ctx->max_range ? h->ctx->max_range : pg::kMaxRange;
     d.cut = d.P > 0 ? h->cut : 0;
+    // FP32: the levels from the cut up run in the shared-memory top kernel when its per-block
+    // partials fit (two blocks per SM, else one); otherwise in the fused kernel
+    bool use_top = false;
+    if (d.precision == PG_PRECISION_FP32 && d.P > 0) {
+        for (int k = 2; k >= 1 && !use_top; --k) {
+            set_tiling(d, k * h->ctx->n_sm, max_range);
+            use_top = (size_t)k * pg::top_smem_bytes(d) <= (size_t)220 * 1024;
+        }
+    }
+    if (!use_top) set_tiling(d, single_target(h->ctx, d), max_range);
     fill_args_one(a, d);
     const bool hess = d_hess != nullptr;
     cudaEvent_t ev[6] = {};
@@ -562,12 +630,14 @@ pg_status pg_eval_async(pg_handle *h, const double *d_b, double *d_logL, double 
     cudaError_t e = pg::launch_pmatrix<1>(a, s);
     mark(1);
     for (int lv = 0; e == cudaSuccess && lv < d.cut; ++lv)
-        e = pg::launch_post_level(d, h->level_off[lv], h->level_off[lv + 1] - h->level_off[lv], h->ctx->n_sm, s);
+        e = pg::launch_post_level(d, h->level_off[lv], h->level_off[lv + 1] - h->level_off[lv], h->ctx->n_sm,
+                                  h->level_cherry[lv] != 0, s);
     mark(2);
-    if (e == cudaSuccess) e = pg::launch_tree<1>(a, hess, s);
+    if (e == cudaSuccess) e = use_top ? pg::launch_top(a, hess, h->ctx->n_sm, s) : pg::launch_tree<1>(a, hess, s);
     mark(3);
     for (int lv = d.cut - 1; e == cudaSuccess && lv >= 0; --lv)
-        e = pg::launch_pre_level(d, h->level_off[lv], h->level_off[lv + 1] - h->level_off[lv], hess, h->ctx->n_sm, s);
+        e = pg::launch_pre_level(d, h->level_off[lv], h->level_off[lv + 1] - h->level_off[lv], hess, h->ctx->n_sm,
+                                 h->level_cherry[lv] != 0, s);
     mark(4);
     if (e == cudaSuccess) e = pg::launch_reduce<1>(a, hess, s);
     mark(5);

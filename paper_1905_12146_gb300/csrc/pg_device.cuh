@@ -124,6 +124,48 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// Adds v over the lanes of each node segment of this warp and hands (node, piece, sum) to
+// emit on lane 0; also zero-fills the slots a node does not use (by its first chunk's warp).
+template <class Emit>
+__device__ __forceinline__ void segment_sums(int u, bool active, double v, int chunk, int cnt,
+                                             int pieces, Emit &&emit) {
+    const int lane = threadIdx.x & 31;
+    const int u_lo = __shfl_sync(0xffffffffu, u, 0), u_hi = __shfl_sync(0xffffffffu, u, 31);
+    for (int us = u_lo; us <= u_hi; ++us) {
+        const double s = warp_sum((active && u == us) ? v : 0.0);
+        const int first = (us * cnt) >> 5, last = ((us + 1) * cnt - 1) >> 5;
+        if (lane == 0) {
+            emit(us, chunk - first, s);
+            if (chunk == first)
+                for (int pc = last - first + 1; pc < pieces; ++pc) emit(us, pc, 0.0);
+        }
+    }
+}
+
+// segment_sums with an FP32 warp reduction (32 FP32 terms), handed on as FP64
+template <class Emit>
+__device__ __forceinline__ void segment_sums_f(int u, bool active, float v, int chunk, int cnt, int pieces,
+                                               Emit &&emit) {
+    const int lane = threadIdx.x & 31;
+    const int u_lo = __shfl_sync(0xffffffffu, u, 0), u_hi = __shfl_sync(0xffffffffu, u, 31);
+    for (int us = u_lo; us <= u_hi; ++us) {
+        const float s = warp_sum_f((active && u == us) ? v : 0.f);
+        const int first = (us * cnt) >> 5, last = ((us + 1) * cnt - 1) >> 5;
+        if (lane == 0) {
+            emit(us, chunk - first, (double)s);
+            if (chunk == first)
+                for (int pc = last - first + 1; pc < pieces; ++pc) emit(us, pc, 0.0);
+        }
+    }
+}
+
+// ---- programmatic dependent launch --------------------------------------------------------------
+// Let the next kernel in the stream be scheduled now (its blocks still wait in pdl_wait), and wait
+// until the previous kernel has completed with its memory visible.  Both are no-ops for a kernel
+// launched without the programmatic-serialisation attribute.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
 // ---- shared-memory barriers and 1-D bulk (TMA) copies ------------------------------------------
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }

@@ -15,6 +15,7 @@ constexpr int kMaxBatch = 32;   // problems per batched launch (kernel-parameter
 constexpr int kMaxRange = 1024;  // patterns per thread block of the tree kernel (shared arrays)
 constexpr int kBlock = 256;      // threads per block of the tree kernel
 constexpr int kLevelRange = 128; // patterns per item (and threads per block) of the level kernels
+constexpr int kTaylorDeg = 12;   // degree of the Taylor polynomial of e^{Q t} (||Q t||_1 <= 1/4)
 // FP32 transition table per (branch, category), float4 columns of the 4x4 matrices:
 //   [0..4]   P hi (columns 0..3, then the row sums = P applied to the all-ones vector)
 //   [5..9]   G = Q P in the same column layout (the generator applied to a column of P)
@@ -44,6 +45,8 @@ struct ProbDesc {
     // model
     const double *b;               // [n] branch lengths of this evaluation (device)
     const double *Qd;              // [n_models][4][4] FP64 row-major
+    const double *Mpow;            // [n_models][kTaylorDeg + 1][16]: Q^k / k!, FP64 row-major
+    const double *qnorm;           // [n_models] ||Q||_1
     const float4 *Qf;              // [n_models][4] FP32 columns of Q
     const int *bmodel;             // [n] or nullptr (model 0)
     float4 *Ptab;                  // FP32: [n][C][kPtabCols]
@@ -64,6 +67,13 @@ struct ProbDesc {
     float *site_invL;              // [P] 1 / Lhat_p, written at the root for the level kernels
     int *site_Er;                  // [P] log2 scale of L_p
     int level_ranges;              // ceil(P / kLevelRange); a wide branch has 4 slots per range
+    // shared-memory-resident top part (levels >= cut) for the top kernel (pg_top.cu): n_top nodes
+    // ops[level_off[cut] ..], children coded per top node: -1 - s for the s-th tip child,
+    // [0, n_top) a top node, n_top + b the b-th boundary node (internal, below the cut;
+    // bnd_node[b] its node id)
+    int n_top, n_bnd;
+    const int2 *top_code;
+    const int *bnd_node;
     // outputs of this evaluation (device, may be null)
     double *out_logL, *out_grad, *out_hess, *out_site;
     // sizes
@@ -101,8 +111,13 @@ template <int MAXB>
 cudaError_t launch_reduce(const BatchArgs<MAXB> &args, bool hess, cudaStream_t s);
 // resident blocks per SM of the tree kernel for C categories and the given precision
 int tree_blocks_per_sm(int C, bool f64);
+// the levels [cut, n_levels) of a single FP32 problem with shared-memory-resident partials
+// (pg_top.cu); returns cudaErrorNotSupported when they do not fit
+cudaError_t launch_top(const BatchArgs<1> &args, bool hess, int n_sm, cudaStream_t s);
+size_t top_smem_bytes(const ProbDesc &d);
 // one post-order (pre-order) level [o0, o0 + nd) of a single FP32 problem (pg_levels.cu)
-cudaError_t launch_post_level(const ProbDesc &d, int o0, int nd, int n_sm, cudaStream_t s);
-cudaError_t launch_pre_level(const ProbDesc &d, int o0, int nd, bool hess, int n_sm, cudaStream_t s);
+// (cherry: every node of the level has two tip children)
+cudaError_t launch_post_level(const ProbDesc &d, int o0, int nd, int n_sm, bool cherry, cudaStream_t s);
+cudaError_t launch_pre_level(const ProbDesc &d, int o0, int nd, bool hess, int n_sm, bool cherry, cudaStream_t s);
 
 }  // namespace pg

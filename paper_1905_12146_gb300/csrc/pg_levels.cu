@@ -29,17 +29,19 @@ using namespace dev;
 
 constexpr int R = kLevelRange;
 
-template <int C>
+// CHERRY: every node of the level has two tip children (height-1 nodes), so a stage carries no
+// child partial rows
+template <int C, bool CHERRY = false>
 struct PostStage {
-    float4 x0[C][R], x1[C][R];   // children's partial rows
+    float4 x0[C][CHERRY ? 1 : R], x1[C][CHERRY ? 1 : R];   // children's partial rows
     int e0[R], e1[R];            // children's log2 scales
     uint8_t y0[R], y1[R];        // tip codes
     float4 tab[2][C][kPtabCols]; // both branches' tables
 };
 
-template <int C>
+template <int C, bool CHERRY = false>
 struct PreStage {
-    float4 qk[C][R], x0[C][R], x1[C][R];
+    float4 qk[C][R], x0[C][CHERRY ? 1 : R], x1[C][CHERRY ? 1 : R];
     int eq[R], e0[R], e1[R];
     int er[R];                   // log2 scale of L_p
     float inv[R];                // 1 / Lhat_p
@@ -76,8 +78,8 @@ __device__ __forceinline__ Item item_of(const ProbDesc &d, int o0, int nr, int j
     return it;
 }
 
-template <int C>
-__device__ void issue_post(const ProbDesc &d, const Item &it, PostStage<C> &sm, uint64_t *bar) {
+template <int C, bool CHERRY>
+__device__ void issue_post(const ProbDesc &d, const Item &it, PostStage<C, CHERRY> &sm, uint64_t *bar) {
     const int N = d.n_tips, Ps = d.Ps, c0 = it.op.y, c1 = it.op.z, p0 = it.p0;
     const bool t0 = c0 < N, t1 = c1 < N;
     const float4 *post = static_cast<const float4 *>(d.post);
@@ -89,19 +91,19 @@ __device__ void issue_post(const ProbDesc &d, const Item &it, PostStage<C> &sm, 
     bulk_load(sm.tab[0], d.Ptab + (size_t)c0 * C * kPtabCols, C * kPtabCols * 16u, bar);
     bulk_load(sm.tab[1], d.Ptab + (size_t)c1 * C * kPtabCols, C * kPtabCols * 16u, bar);
     if (t0) bulk_load(sm.y0, d.tips + (size_t)c0 * Ps + p0, yb, bar);
-    else {
+    else if constexpr (!CHERRY) {
         bulk_load(sm.e0, d.pe + (size_t)(c0 - N) * Ps + p0, eb, bar);
         for (int l = 0; l < C; ++l) bulk_load(sm.x0[l], post + ((size_t)(c0 - N) * C + l) * Ps + p0, rowb, bar);
     }
     if (t1) bulk_load(sm.y1, d.tips + (size_t)c1 * Ps + p0, yb, bar);
-    else {
+    else if constexpr (!CHERRY) {
         bulk_load(sm.e1, d.pe + (size_t)(c1 - N) * Ps + p0, eb, bar);
         for (int l = 0; l < C; ++l) bulk_load(sm.x1[l], post + ((size_t)(c1 - N) * C + l) * Ps + p0, rowb, bar);
     }
 }
 
-template <int C>
-__device__ void issue_pre(const ProbDesc &d, const Item &it, PreStage<C> &sm, uint64_t *bar) {
+template <int C, bool CHERRY>
+__device__ void issue_pre(const ProbDesc &d, const Item &it, PreStage<C, CHERRY> &sm, uint64_t *bar) {
     const int N = d.n_tips, Ps = d.Ps, k = it.op.x, c0 = it.op.y, c1 = it.op.z, p0 = it.p0;
     const bool t0 = c0 < N, t1 = c1 < N;
     const float4 *post = static_cast<const float4 *>(d.post);
@@ -122,49 +124,61 @@ __device__ void issue_pre(const ProbDesc &d, const Item &it, PreStage<C> &sm, ui
     bulk_load(sm.inv, d.site_invL + p0, eb, bar);
     bulk_load(sm.w, d.wf + p0, eb, bar);
     if (t0) bulk_load(sm.y0, d.tips + (size_t)c0 * Ps + p0, yb, bar);
-    else {
+    else if constexpr (!CHERRY) {
         bulk_load(sm.e0, d.pe + (size_t)(c0 - N) * Ps + p0, eb, bar);
         for (int l = 0; l < C; ++l) bulk_load(sm.x0[l], post + ((size_t)(c0 - N) * C + l) * Ps + p0, rowb, bar);
     }
     if (t1) bulk_load(sm.y1, d.tips + (size_t)c1 * Ps + p0, yb, bar);
-    else {
+    else if constexpr (!CHERRY) {
         bulk_load(sm.e1, d.pe + (size_t)(c1 - N) * Ps + p0, eb, bar);
         for (int l = 0; l < C; ++l) bulk_load(sm.x1[l], post + ((size_t)(c1 - N) * C + l) * Ps + p0, rowb, bar);
     }
 }
 
 // post-order update (Section 2.3) of one item from its stage
-template <int C>
-__device__ __forceinline__ void compute_post(const ProbDesc &d, const Item &it, const PostStage<C> &sm, int t) {
+template <int C, bool CHERRY>
+__device__ __forceinline__ void compute_post(const ProbDesc &d, const Item &it, const PostStage<C, CHERRY> &sm, int t) {
     if (t >= it.cnt) return;
     const int N = d.n_tips, Ps = d.Ps, k = it.op.x, c0 = it.op.y, c1 = it.op.z;
-    const bool t0 = c0 < N, t1 = c1 < N;
+    const bool t0 = CHERRY || c0 < N, t1 = CHERRY || c1 < N;
     const int p = it.p0 + t;
     const float r = pattern_factor((uint32_t)p);
     const int y0 = t0 ? min((int)sm.y0[t], 4) : 0, y1 = t1 ? min((int)sm.y1[t], 4) : 0;
     const int E = (t0 ? 0 : sm.e0[t]) + (t1 ? 0 : sm.e1[t]);
     float4 v[C];
     float mx = 0.0f;
+    if (CHERRY || (t0 && t1)) {   // a cherry: both contributions are (hi + lo) columns times r, one product each
 #pragma unroll
-    for (int l = 0; l < C; ++l) {
-        float4 x0, x1, s0 = f4(0.f, 0.f, 0.f, 0.f), s1 = f4(0.f, 0.f, 0.f, 0.f);
-        if (t0) {
-            const float4 hi = sm.tab[0][l][y0], lo = sm.tab[0][l][kColPlo + y0];
-            x0 = f4(fmaf(hi.x, r, lo.x * r), fmaf(hi.y, r, lo.y * r), fmaf(hi.z, r, lo.z * r), fmaf(hi.w, r, lo.w * r));
-        } else {
-            x0 = sm.x0[l][t];
-            s0 = matvec_hilo_v(&sm.tab[0][l][kColDhi], &sm.tab[0][l][kColDlo], x0);
+        for (int l = 0; l < C; ++l) {
+            const float4 h0 = sm.tab[0][l][y0], l0 = sm.tab[0][l][kColPlo + y0];
+            const float4 h1 = sm.tab[1][l][y1], l1 = sm.tab[1][l][kColPlo + y1];
+            const float4 x0 = f4(fmaf(h0.x, r, l0.x * r), fmaf(h0.y, r, l0.y * r), fmaf(h0.z, r, l0.z * r), fmaf(h0.w, r, l0.w * r));
+            const float4 x1 = f4(fmaf(h1.x, r, l1.x * r), fmaf(h1.y, r, l1.y * r), fmaf(h1.z, r, l1.z * r), fmaf(h1.w, r, l1.w * r));
+            v[l] = mul(x0, x1);
+            mx = fmaxf(mx, hmax(v[l]));
         }
-        if (t1) {
-            const float4 hi = sm.tab[1][l][y1], lo = sm.tab[1][l][kColPlo + y1];
-            x1 = f4(fmaf(hi.x, r, lo.x * r), fmaf(hi.y, r, lo.y * r), fmaf(hi.z, r, lo.z * r), fmaf(hi.w, r, lo.w * r));
-        } else {
-            x1 = sm.x1[l][t];
-            s1 = matvec_hilo_v(&sm.tab[1][l][kColDhi], &sm.tab[1][l][kColDlo], x1);
+    } else if constexpr (!CHERRY) {
+#pragma unroll
+        for (int l = 0; l < C; ++l) {
+            float4 x0, x1, s0 = f4(0.f, 0.f, 0.f, 0.f), s1 = f4(0.f, 0.f, 0.f, 0.f);
+            if (t0) {
+                const float4 hi = sm.tab[0][l][y0], lo = sm.tab[0][l][kColPlo + y0];
+                x0 = f4(fmaf(hi.x, r, lo.x * r), fmaf(hi.y, r, lo.y * r), fmaf(hi.z, r, lo.z * r), fmaf(hi.w, r, lo.w * r));
+            } else {
+                x0 = sm.x0[l][t];
+                s0 = matvec_hilo_v(&sm.tab[0][l][kColDhi], &sm.tab[0][l][kColDlo], x0);
+            }
+            if (t1) {
+                const float4 hi = sm.tab[1][l][y1], lo = sm.tab[1][l][kColPlo + y1];
+                x1 = f4(fmaf(hi.x, r, lo.x * r), fmaf(hi.y, r, lo.y * r), fmaf(hi.z, r, lo.z * r), fmaf(hi.w, r, lo.w * r));
+            } else {
+                x1 = sm.x1[l][t];
+                s1 = matvec_hilo_v(&sm.tab[1][l][kColDhi], &sm.tab[1][l][kColDlo], x1);
+            }
+            v[l] = f4(prod_split(x0.x, s0.x, x1.x, s1.x), prod_split(x0.y, s0.y, x1.y, s1.y),
+                      prod_split(x0.z, s0.z, x1.z, s1.z), prod_split(x0.w, s0.w, x1.w, s1.w));
+            mx = fmaxf(mx, hmax(v[l]));
         }
-        v[l] = f4(prod_split(x0.x, s0.x, x1.x, s1.x), prod_split(x0.y, s0.y, x1.y, s1.y),
-                  prod_split(x0.z, s0.z, x1.z, s1.z), prod_split(x0.w, s0.w, x1.w, s1.w));
-        mx = fmaxf(mx, hmax(v[l]));
     }
     const int e = scale_exponent(mx);
     float4 *out = static_cast<float4 *>(d.post);
@@ -176,10 +190,10 @@ __device__ __forceinline__ void compute_post(const ProbDesc &d, const Item &it, 
 // pre-order step (Section 2.4) with the branch gradient (2.5) and Hessian diagonal (2.6) for the
 // calling warp's 32 patterns of one item; the warp's sums go to its own slot of both child branches
 // (slot = 4 * range + warp; the reduction adds the slots in a fixed order)
-template <int C, bool HESS>
-__device__ __forceinline__ void compute_pre(const ProbDesc &d, const Item &it, const PreStage<C> &sm, int t) {
+template <int C, bool HESS, bool CHERRY>
+__device__ __forceinline__ void compute_pre(const ProbDesc &d, const Item &it, const PreStage<C, CHERRY> &sm, int t) {
     const int N = d.n_tips, Ps = d.Ps, c0 = it.op.y, c1 = it.op.z;
-    const bool t0 = c0 < N, t1 = c1 < N;
+    const bool t0 = CHERRY || c0 < N, t1 = CHERRY || c1 < N;
     const bool active = t < it.cnt;
     const int tt = active ? t : it.cnt - 1;
     const int p = it.p0 + tt;
@@ -192,8 +206,8 @@ __device__ __forceinline__ void compute_pre(const ProbDesc &d, const Item &it, c
     float m0 = 0.f, m1 = 0.f, g0 = 0.f, g1 = 0.f, h0 = 0.f, h1 = 0.f;
 #pragma unroll
     for (int l = 0; l < C; ++l) {
-        const float4 a0 = t0 ? scal(sm.tab[0][l][y0], r) : matvec_p(sm.tab[0][l], sm.x0[l][tt]);
-        const float4 a1 = t1 ? scal(sm.tab[1][l][y1], r) : matvec_p(sm.tab[1][l], sm.x1[l][tt]);
+        const float4 a0 = t0 ? scal(sm.tab[0][l][y0], r) : matvec_p(sm.tab[0][l], sm.x0[l][CHERRY ? 0 : tt]);
+        const float4 a1 = t1 ? scal(sm.tab[1][l][y1], r) : matvec_p(sm.tab[1][l], sm.x1[l][CHERRY ? 0 : tt]);
         const float4 qk = sm.qk[l][tt];
         const float4 qt0 = mul(qk, a1), qt1 = mul(qk, a0);   // top of branches c0 and c1
         // Q a_c: a gathered column of G = Q P for tips, a matvec otherwise
@@ -255,6 +269,8 @@ __device__ __forceinline__ void staged_walk(const ProbDesc &d, int o0, int nr, i
         }
     }
     __syncthreads();   // barriers initialised before anyone uses them
+    pdl_launch_dependents();
+    pdl_wait();        // the previous level's partials are complete and visible
     if (warp == kConsumerWarps) {   // producer
         if (lane != 0) return;
         int i = 0;
@@ -287,25 +303,27 @@ __device__ __forceinline__ void staged_walk(const ProbDesc &d, int o0, int nr, i
     }
 }
 
-template <int C, int STAGES>
+template <int C, int STAGES, bool CHERRY>
 __global__ void __launch_bounds__(kLevelThreads) post_level_kernel(const __grid_constant__ ProbDesc d, int o0, int nr, int n_items) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto &ring = *reinterpret_cast<Ring<PostStage<C>, STAGES> *>(smem_raw);
+    using St = PostStage<C, CHERRY>;
+    auto &ring = *reinterpret_cast<Ring<St, STAGES> *>(smem_raw);
     staged_walk(d, o0, nr, n_items, ring,
-                [&](const Item &it, PostStage<C> &st, uint64_t *bar) { issue_post<C>(d, it, st, bar); },
-                [&](const Item &it, const PostStage<C> &st, int t) { compute_post<C>(d, it, st, t); });
+                [&](const Item &it, St &st, uint64_t *bar) { issue_post<C, CHERRY>(d, it, st, bar); },
+                [&](const Item &it, const St &st, int t) { compute_post<C, CHERRY>(d, it, st, t); });
 }
 
-template <int C, bool HESS, int STAGES>
+template <int C, bool HESS, int STAGES, bool CHERRY>
 __global__ void __launch_bounds__(kLevelThreads) pre_level_kernel(const __grid_constant__ ProbDesc d, int o0, int nr, int n_items) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto &ring = *reinterpret_cast<Ring<PreStage<C>, STAGES> *>(smem_raw);
+    using St = PreStage<C, CHERRY>;
+    auto &ring = *reinterpret_cast<Ring<St, STAGES> *>(smem_raw);
     staged_walk(d, o0, nr, n_items, ring,
-                [&](const Item &it, PreStage<C> &st, uint64_t *bar) { issue_pre<C>(d, it, st, bar); },
-                [&](const Item &it, const PreStage<C> &st, int t) { compute_pre<C, HESS>(d, it, st, t); });
+                [&](const Item &it, St &st, uint64_t *bar) { issue_pre<C, CHERRY>(d, it, st, bar); },
+                [&](const Item &it, const St &st, int t) { compute_pre<C, HESS, CHERRY>(d, it, st, t); });
 }
 
-constexpr int kPostStages = 4, kPreStages = 3;
+constexpr int kPostStages = 2, kPreStages = 2, kCherryStages = 3;
 
 // blocks of a persistent level launch: every resident slot, at most one per item
 template <class K>
@@ -319,52 +337,81 @@ int persistent_blocks(K kernel, size_t smem, int n_sm, int n_items, bool &config
     return n_items < n_sm * per_sm ? n_items : n_sm * per_sm;
 }
 
-template <int C>
+// launch with programmatic stream serialisation: the kernel may be scheduled while the previous
+// one drains, and waits for it in pdl_wait()
+template <class K>
+cudaError_t launch_pdl(K kernel, int blocks, size_t smem, cudaStream_t s, const ProbDesc &d, int o0, int nr, int n_items) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3(kLevelThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, d, o0, nr, n_items);
+}
+
+template <int C, bool CHERRY>
 cudaError_t post_c(const ProbDesc &d, int o0, int nd, int n_sm, cudaStream_t s) {
     static bool configured = false;   // attribute and occupancy, once per instantiation
     static int per_sm = 1;
+    constexpr int ST = CHERRY ? kCherryStages : kPostStages;
     const int nr = d.level_ranges, n_items = nd * nr;
-    const size_t smem = sizeof(Ring<PostStage<C>, kPostStages>);
-    const int blocks = persistent_blocks(post_level_kernel<C, kPostStages>, smem, n_sm, n_items, configured, per_sm);
+    const size_t smem = sizeof(Ring<PostStage<C, CHERRY>, ST>);
+    const int blocks = persistent_blocks(post_level_kernel<C, ST, CHERRY>, smem, n_sm, n_items, configured, per_sm);
     if (blocks < 0) return cudaErrorInvalidConfiguration;
-    post_level_kernel<C, kPostStages><<<blocks, kLevelThreads, smem, s>>>(d, o0, nr, n_items);
-    return cudaGetLastError();
+    return launch_pdl(post_level_kernel<C, ST, CHERRY>, blocks, smem, s, d, o0, nr, n_items);
 }
 
-template <int C, bool HESS>
+template <int C, bool HESS, bool CHERRY>
 cudaError_t pre_c(const ProbDesc &d, int o0, int nd, int n_sm, cudaStream_t s) {
     static bool configured = false;
     static int per_sm = 1;
+    constexpr int ST = CHERRY ? kCherryStages : kPreStages;
     const int nr = d.level_ranges, n_items = nd * nr;
-    const size_t smem = sizeof(Ring<PreStage<C>, kPreStages>);
-    const int blocks = persistent_blocks(pre_level_kernel<C, HESS, kPreStages>, smem, n_sm, n_items, configured, per_sm);
+    const size_t smem = sizeof(Ring<PreStage<C, CHERRY>, ST>);
+    const int blocks = persistent_blocks(pre_level_kernel<C, HESS, ST, CHERRY>, smem, n_sm, n_items, configured, per_sm);
     if (blocks < 0) return cudaErrorInvalidConfiguration;
-    pre_level_kernel<C, HESS, kPreStages><<<blocks, kLevelThreads, smem, s>>>(d, o0, nr, n_items);
-    return cudaGetLastError();
+    return launch_pdl(pre_level_kernel<C, HESS, ST, CHERRY>, blocks, smem, s, d, o0, nr, n_items);
 }
 
 }  // namespace
 
-cudaError_t launch_post_level(const ProbDesc &d, int o0, int nd, int n_sm, cudaStream_t s) {
-    switch (d.C) {
-        case 1: return post_c<1>(d, o0, nd, n_sm, s);
-        case 2: return post_c<2>(d, o0, nd, n_sm, s);
-        case 3: return post_c<3>(d, o0, nd, n_sm, s);
-        case 4: return post_c<4>(d, o0, nd, n_sm, s);
+cudaError_t launch_post_level(const ProbDesc &d, int o0, int nd, int n_sm, bool cherry, cudaStream_t s) {
+    switch (d.C * 2 + (cherry ? 1 : 0)) {
+        case 2: return post_c<1, false>(d, o0, nd, n_sm, s);
+        case 3: return post_c<1, true>(d, o0, nd, n_sm, s);
+        case 4: return post_c<2, false>(d, o0, nd, n_sm, s);
+        case 5: return post_c<2, true>(d, o0, nd, n_sm, s);
+        case 6: return post_c<3, false>(d, o0, nd, n_sm, s);
+        case 7: return post_c<3, true>(d, o0, nd, n_sm, s);
+        case 8: return post_c<4, false>(d, o0, nd, n_sm, s);
+        case 9: return post_c<4, true>(d, o0, nd, n_sm, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_pre_level(const ProbDesc &d, int o0, int nd, bool hess, int n_sm, cudaStream_t s) {
-    switch (d.C * 2 + (hess ? 1 : 0)) {
-        case 2: return pre_c<1, false>(d, o0, nd, n_sm, s);
-        case 3: return pre_c<1, true>(d, o0, nd, n_sm, s);
-        case 4: return pre_c<2, false>(d, o0, nd, n_sm, s);
-        case 5: return pre_c<2, true>(d, o0, nd, n_sm, s);
-        case 6: return pre_c<3, false>(d, o0, nd, n_sm, s);
-        case 7: return pre_c<3, true>(d, o0, nd, n_sm, s);
-        case 8: return pre_c<4, false>(d, o0, nd, n_sm, s);
-        case 9: return pre_c<4, true>(d, o0, nd, n_sm, s);
+cudaError_t launch_pre_level(const ProbDesc &d, int o0, int nd, bool hess, int n_sm, bool cherry, cudaStream_t s) {
+    switch (d.C * 4 + (hess ? 2 : 0) + (cherry ? 1 : 0)) {
+        case 4: return pre_c<1, false, false>(d, o0, nd, n_sm, s);
+        case 5: return pre_c<1, false, true>(d, o0, nd, n_sm, s);
+        case 6: return pre_c<1, true, false>(d, o0, nd, n_sm, s);
+        case 7: return pre_c<1, true, true>(d, o0, nd, n_sm, s);
+        case 8: return pre_c<2, false, false>(d, o0, nd, n_sm, s);
+        case 9: return pre_c<2, false, true>(d, o0, nd, n_sm, s);
+        case 10: return pre_c<2, true, false>(d, o0, nd, n_sm, s);
+        case 11: return pre_c<2, true, true>(d, o0, nd, n_sm, s);
+        case 12: return pre_c<3, false, false>(d, o0, nd, n_sm, s);
+        case 13: return pre_c<3, false, true>(d, o0, nd, n_sm, s);
+        case 14: return pre_c<3, true, false>(d, o0, nd, n_sm, s);
+        case 15: return pre_c<3, true, true>(d, o0, nd, n_sm, s);
+        case 16: return pre_c<4, false, false>(d, o0, nd, n_sm, s);
+        case 17: return pre_c<4, false, true>(d, o0, nd, n_sm, s);
+        case 18: return pre_c<4, true, false>(d, o0, nd, n_sm, s);
+        case 19: return pre_c<4, true, true>(d, o0, nd, n_sm, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -40,6 +40,8 @@ int g_kid0[kMaxNodes], g_kid1[kMaxNodes], g_order[kMaxNodes], g_height[kMaxNodes
 int4 g_ops[kMaxTips];
 int g_level_off[kMaxTips + 1];
 float4 g_qf[kMaxModels * 4];
+double g_mpow[kMaxModels * (pg::kTaylorDeg + 1) * 16];
+double g_qnorm[kMaxModels];
 
 // statuses only: formatting a message could allocate
 pg_status noalloc_fail(pg_status s, const char *, ...) { return s; }
@@ -193,6 +195,7 @@ extern "C" pg_status pg_eval_noalloc(const pg_problem *pr, const double *b, doub
     const size_t o_ops = take(sizeof(int4) * (N - 1)), o_lv = take(sizeof(int) * (H + 1));
     const size_t o_tips = take((size_t)N * Ps), o_w = take(sizeof(double) * Ps);
     const size_t o_Qd = take(sizeof(double) * 16 * M), o_Qf = take(sizeof(float4) * 4 * M);
+    const size_t o_Mp = take(sizeof(double) * (pg::kTaylorDeg + 1) * 16 * M), o_qn = take(sizeof(double) * M);
     const size_t o_bm = take(pr->branch_model ? sizeof(int) * n : 0);
     const size_t o_P = take(f64 ? sizeof(double2) * n * C * pg::kPtab64Pairs : sizeof(float4) * n * C * pg::kPtabCols);
     const size_t part = (size_t)(N - 1) * C * Ps * (f64 ? 2 * sizeof(double2) : sizeof(float4));
@@ -207,11 +210,26 @@ extern "C" pg_status pg_eval_noalloc(const pg_problem *pr, const double *b, doub
         return noalloc_fail(PG_ERR_UNSUPPORTED, "problem needs %zu bytes of scratch; the fixed array holds %u",
                             off, (unsigned)PG_NOALLOC_SCRATCH_BYTES);
 
-    for (int md = 0; md < M; ++md)
-        for (int c = 0; c < 4; ++c) {
-            const double *Q = pr->Q + (size_t)md * 16;
+    for (int md = 0; md < M; ++md) {
+        const double *Q = pr->Q + (size_t)md * 16;
+        for (int c = 0; c < 4; ++c)
             g_qf[md * 4 + c] = make_float4((float)Q[c], (float)Q[4 + c], (float)Q[8 + c], (float)Q[12 + c]);
+        double *Mk = g_mpow + (size_t)md * (pg::kTaylorDeg + 1) * 16;   // Q^k / k!
+        for (int u = 0; u < 16; ++u) Mk[u] = (u % 5 == 0) ? 1.0 : 0.0;
+        for (int k = 1; k <= pg::kTaylorDeg; ++k)
+            for (int r = 0; r < 4; ++r)
+                for (int c = 0; c < 4; ++c) {
+                    double acc = 0.0;
+                    for (int t = 0; t < 4; ++t) acc += Mk[(k - 1) * 16 + r * 4 + t] * Q[t * 4 + c];
+                    Mk[k * 16 + r * 4 + c] = acc / (double)k;
+                }
+        double nrm = 0.0;
+        for (int c = 0; c < 4; ++c) {
+            const double cs = std::fabs(Q[c]) + std::fabs(Q[4 + c]) + std::fabs(Q[8 + c]) + std::fabs(Q[12 + c]);
+            nrm = cs > nrm ? cs : nrm;
         }
+        g_qnorm[md] = nrm;
+    }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     NOALLOC_CUDA(cudaMemcpyAsync(base + o_ops, g_ops, sizeof(int4) * (N - 1), cudaMemcpyHostToDevice, s));
     NOALLOC_CUDA(cudaMemcpyAsync(base + o_lv, g_level_off, sizeof(int) * (H + 1), cudaMemcpyHostToDevice, s));
@@ -221,6 +239,9 @@ extern "C" pg_status pg_eval_noalloc(const pg_problem *pr, const double *b, doub
     }
     NOALLOC_CUDA(cudaMemcpyAsync(base + o_Qd, pr->Q, sizeof(double) * 16 * M, cudaMemcpyHostToDevice, s));
     NOALLOC_CUDA(cudaMemcpyAsync(base + o_Qf, g_qf, sizeof(float4) * 4 * M, cudaMemcpyHostToDevice, s));
+    NOALLOC_CUDA(cudaMemcpyAsync(base + o_Mp, g_mpow, sizeof(double) * (pg::kTaylorDeg + 1) * 16 * M,
+                                 cudaMemcpyHostToDevice, s));
+    NOALLOC_CUDA(cudaMemcpyAsync(base + o_qn, g_qnorm, sizeof(double) * M, cudaMemcpyHostToDevice, s));
     if (pr->branch_model)
         NOALLOC_CUDA(cudaMemcpyAsync(base + o_bm, pr->branch_model, sizeof(int) * n, cudaMemcpyHostToDevice, s));
     NOALLOC_CUDA(cudaMemcpyAsync(base + o_ib, b, sizeof(double) * n, cudaMemcpyHostToDevice, s));
@@ -235,6 +256,8 @@ extern "C" pg_status pg_eval_noalloc(const pg_problem *pr, const double *b, doub
     d.weights = reinterpret_cast<const double *>(base + o_w);
     d.Qd = reinterpret_cast<const double *>(base + o_Qd);
     d.Qf = reinterpret_cast<const float4 *>(base + o_Qf);
+    d.Mpow = reinterpret_cast<const double *>(base + o_Mp);
+    d.qnorm = reinterpret_cast<const double *>(base + o_qn);
     d.bmodel = pr->branch_model ? reinterpret_cast<const int *>(base + o_bm) : nullptr;
     d.Ptab = f64 ? nullptr : reinterpret_cast<float4 *>(base + o_P);
     d.Ptab64 = f64 ? reinterpret_cast<double2 *>(base + o_P) : nullptr;

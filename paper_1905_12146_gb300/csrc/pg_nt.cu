@@ -54,116 +54,90 @@ __device__ __forceinline__ int find_problem(const int (&base)[MAXB + 1], int n, 
 }
 
 // ------------------------------------------------------------------------------------------
-// K1: transition matrices in FP64 (Sections 2.1, 2.5): P = e^{Q b r} by truncated Taylor series
-// of degree 12 with scaling and squaring, ||A / 2^s||_1 <= 1/4 (truncation < 3e-18).
+// K1: transition matrices in FP64 (Sections 2.1, 2.5): P = e^{Q b r} by the truncated Taylor
+// series of degree 12 with scaling and squaring, ||Q x||_1 <= 1/4 with x = b r / 2^s (truncation
+// < 3e-18), and G = Q P.  The matrix coefficients Q^k / k! are computed once per model on upload,
+// so each entry of e^{Q x} is a scalar polynomial in x (12 FP64 FMAs) before the squarings.
 // ------------------------------------------------------------------------------------------
 
-__device__ void mat4_mul(const double (&A)[16], const double (&B)[16], double (&C)[16]) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            double s = A[i * 4] * B[j];
-            s = fma(A[i * 4 + 1], B[4 + j], s);
-            s = fma(A[i * 4 + 2], B[8 + j], s);
-            C[i * 4 + j] = fma(A[i * 4 + 3], B[12 + j], s);
-        }
-}
-
-__device__ void expm4_taylor(double (&X)[16], double (&E)[16]) {
-    double nrm = 0.0;
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-        nrm = fmax(nrm, fabs(X[j]) + fabs(X[4 + j]) + fabs(X[8 + j]) + fabs(X[12 + j]));
-    int s = 0;
-    while (nrm > 0.25 && s < 1100) { nrm *= 0.5; ++s; }
-    const double sc = ldexp(1.0, -s);
-#pragma unroll
-    for (int t = 0; t < 16; ++t) X[t] *= sc;
-    // Horner: E = I + X/1 (I + X/2 (I + ... (I + X/12)))  evaluated from the inside out
-#pragma unroll
-    for (int t = 0; t < 16; ++t) E[t] = (t % 5 == 0) ? 1.0 : 0.0;
-    double T[16];
-#pragma unroll 1
-    for (int k = 12; k >= 1; --k) {
-        mat4_mul(X, E, T);
-        const double inv = 1.0 / (double)k;
-#pragma unroll
-        for (int t = 0; t < 16; ++t) E[t] = T[t] * inv + ((t % 5 == 0) ? 1.0 : 0.0);
-    }
-#pragma unroll 1
-    for (int q = 0; q < s; ++q) {
-        mat4_mul(E, E, T);
-#pragma unroll
-        for (int t = 0; t < 16; ++t) E[t] = T[t];
-    }
+// Sixteen lanes hold one 4x4 FP64 matrix, lane 4i+j holding entry (i, j); X (the scaled
+// generator) is kept whole in every lane, so a product X E needs four shuffles of E per entry.
+__device__ __forceinline__ double col_entry(double e, int k, int j, unsigned mask) {   // E[k][j]
+    return __shfl_sync(mask, e, k * 4 + j, 16);
 }
 
 template <int MAXB>
 __global__ void __launch_bounds__(128) pmatrix4_kernel(const __grid_constant__ BatchArgs<MAXB> a) {
-    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= a.mat_base[a.n]) return;
-    const int pid = find_problem<MAXB>(a.mat_base, a.n, gid);
+    const int gid = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    const int mat = gid >> 4, lane16 = gid & 15, i = lane16 >> 2, j = lane16 & 3;
+    const int total = a.mat_base[a.n];
+    // whole 16-lane groups stay together; groups past the end leave together
+    if (mat >= total) return;
+    const unsigned mask = 0xFFFFu << (threadIdx.x & 16);
+    const int pid = find_problem<MAXB>(a.mat_base, a.n, mat);
     const ProbDesc &d = a.d[pid];
-    const int item = gid - a.mat_base[pid];
-    const int i = item / d.C, l = item - i * d.C;
-    if (i == d.root) return;
-    double bl = d.b[i];
+    const int item = mat - a.mat_base[pid];
+    const int br = item / d.C, l = item - br * d.C;
+    if (br == d.root) return;   // uniform within the group
+    double bl = d.b[br];
     if (!(bl >= 0.0) || isinf(bl)) {
-        atomicOr(d.status, kStatusBadLength);
+        if (lane16 == 0) atomicOr(d.status, kStatusBadLength);
         bl = 0.0;
     }
-    const int model = d.bmodel ? d.bmodel[i] : 0;
+    const int model = d.bmodel ? d.bmodel[br] : 0;
+    const double *Qm = d.Qd + model * 16;
     const double t = bl * d.rates[l];
-    double X[16], E[16];
+    double nrm = d.qnorm[model] * fabs(t);
+    int sq = 0;
+    while (nrm > 0.25 && sq < 1100) { nrm *= 0.5; ++sq; }
+    const double x = t * ldexp(1.0, -sq);
+    double Qr[4];   // row i of Q
 #pragma unroll
-    for (int u = 0; u < 16; ++u) X[u] = d.Qd[model * 16 + u] * t;
-    expm4_taylor(X, E);
-    double rs[4];
+    for (int k = 0; k < 4; ++k) Qr[k] = Qm[i * 4 + k];
+    const double id = (i == j) ? 1.0 : 0.0;
+    // entry (i, j) of e^{Q x} = sum_k (Q^k / k!)_ij x^k, the Q^k / k! precomputed per model
+    const double *Mk = d.Mpow + (size_t)model * (kTaylorDeg + 1) * 16 + lane16;
+    double E = Mk[kTaylorDeg * 16];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) rs[r] = (E[r * 4] + E[r * 4 + 1]) + (E[r * 4 + 2] + E[r * 4 + 3]);
-    if (d.precision == 1) {
-        double2 *out = d.Ptab64 + ((size_t)i * d.C + l) * kPtab64Pairs;
-#pragma unroll
-        for (int c = 0; c < 5; ++c) {
-            const double v0 = c < 4 ? E[c] : rs[0], v1 = c < 4 ? E[4 + c] : rs[1];
-            const double v2 = c < 4 ? E[8 + c] : rs[2], v3 = c < 4 ? E[12 + c] : rs[3];
-            out[2 * c] = make_double2(v0, v1);
-            out[2 * c + 1] = make_double2(v2, v3);
-        }
+    for (int k = kTaylorDeg - 1; k >= 0; --k) E = fma(E, x, Mk[k * 16]);
+#pragma unroll 1
+    for (int q = 0; q < sq; ++q) {   // squaring: E[i][j] = sum_k E[i][k] E[k][j]
+        const double r0 = __shfl_sync(mask, E, i * 4 + 0, 16), r1 = __shfl_sync(mask, E, i * 4 + 1, 16);
+        const double r2 = __shfl_sync(mask, E, i * 4 + 2, 16), r3 = __shfl_sync(mask, E, i * 4 + 3, 16);
+        double s = r0 * col_entry(E, 0, j, mask);
+        s = fma(r1, col_entry(E, 1, j, mask), s);
+        s = fma(r2, col_entry(E, 2, j, mask), s);
+        E = fma(r3, col_entry(E, 3, j, mask), s);
+    }
+    // G = Q P (entry (i, j)); row sums of P and of G (P and G applied to the all-ones vector)
+    double g = Qr[0] * col_entry(E, 0, j, mask);
+    g = fma(Qr[1], col_entry(E, 1, j, mask), g);
+    g = fma(Qr[2], col_entry(E, 2, j, mask), g);
+    g = fma(Qr[3], col_entry(E, 3, j, mask), g);
+    double rs = E + __shfl_xor_sync(mask, E, 1, 16);
+    rs += __shfl_xor_sync(mask, rs, 2, 16);
+    double gs = g + __shfl_xor_sync(mask, g, 1, 16);
+    gs += __shfl_xor_sync(mask, gs, 2, 16);
+    if (d.precision == 1) {   // FP64 table: column c as two double2 = P[0..3][c]
+        double *out = reinterpret_cast<double *>(d.Ptab64 + ((size_t)br * d.C + l) * kPtab64Pairs);
+        out[j * 4 + i] = E;
+        if (j == 0) out[16 + i] = rs;
         return;
     }
-    float4 *out = d.Ptab + ((size_t)i * d.C + l) * kPtabCols;
-    const double *Qm = d.Qd + model * 16;
-#pragma unroll
-    for (int c = 0; c < 5; ++c) {
-        float hi[4], lo[4], gq[4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const double v = (c < 4) ? E[r * 4 + c] : rs[r];
-            hi[r] = (float)v;
-            lo[r] = (float)(v - (double)hi[r]);
-        }
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {   // (Q P)[r][c], and Q applied to the row sums for c = 4
-            double g = 0.0;
-#pragma unroll
-            for (int t2 = 0; t2 < 4; ++t2) g = fma(Qm[r * 4 + t2], (c < 4) ? E[t2 * 4 + c] : rs[t2], g);
-            gq[r] = (float)g;
-        }
-        out[c] = f4(hi[0], hi[1], hi[2], hi[3]);
-        out[kColG + c] = f4(gq[0], gq[1], gq[2], gq[3]);
-        out[kColPlo + c] = f4(lo[0], lo[1], lo[2], lo[3]);
-        if (c < 4) {
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const double v = E[r * 4 + c] - (r == c ? 1.0 : 0.0);
-                hi[r] = (float)v;
-                lo[r] = (float)(v - (double)hi[r]);
-            }
-            out[kColDhi + c] = f4(hi[0], hi[1], hi[2], hi[3]);
-            out[kColDlo + c] = f4(lo[0], lo[1], lo[2], lo[3]);
-        }
+    float *out = reinterpret_cast<float *>(d.Ptab + ((size_t)br * d.C + l) * kPtabCols);
+    const float hi = (float)E, lo = (float)(E - (double)hi);
+    const double dd = E - id;
+    const float dhi = (float)dd, dlo = (float)(dd - (double)dhi);
+    out[j * 4 + i] = hi;
+    out[(kColPlo + j) * 4 + i] = lo;
+    out[(kColG + j) * 4 + i] = (float)g;
+    out[(kColDhi + j) * 4 + i] = dhi;
+    out[(kColDlo + j) * 4 + i] = dlo;
+    if (j == 0) {
+        const float rhi = (float)rs;
+        out[4 * 4 + i] = rhi;
+        out[(kColPlo + 4) * 4 + i] = (float)(rs - (double)rhi);
+        out[(kColG + 4) * 4 + i] = (float)gs;
     }
 }
 
@@ -177,24 +151,6 @@ __global__ void __launch_bounds__(128) pmatrix4_kernel(const __grid_constant__ B
 // branch gradients) are reduced per node segment of the warp and written to a fixed slot
 // (block, piece), piece = the warp's 32-pair chunk counted from the node's first chunk; the
 // reduction kernel adds the slots of a branch in a fixed order.
-
-// Adds v over the lanes of each node segment of this warp and hands (node, piece, sum) to
-// emit on lane 0; also zero-fills the slots a node does not use (by its first chunk's warp).
-template <class Emit>
-__device__ __forceinline__ void segment_sums(int u, bool active, double v, int chunk, int cnt,
-                                             int pieces, Emit &&emit) {
-    const int lane = threadIdx.x & 31;
-    const int u_lo = __shfl_sync(0xffffffffu, u, 0), u_hi = __shfl_sync(0xffffffffu, u, 31);
-    for (int us = u_lo; us <= u_hi; ++us) {
-        const double s = warp_sum((active && u == us) ? v : 0.0);
-        const int first = (us * cnt) >> 5, last = ((us + 1) * cnt - 1) >> 5;
-        if (lane == 0) {
-            emit(us, chunk - first, s);
-            if (chunk == first)
-                for (int pc = last - first + 1; pc < pieces; ++pc) emit(us, pc, 0.0);
-        }
-    }
-}
 
 // ---- FP64 partials ------------------------------------------------------------------------
 
@@ -887,7 +843,7 @@ template <int MAXB>
 cudaError_t launch_pmatrix(const BatchArgs<MAXB> &args, cudaStream_t s) {
     const int nmat = args.mat_base[args.n];
     if (args.n <= 0 || nmat <= 0) return cudaSuccess;
-    pmatrix4_kernel<MAXB><<<(nmat + 127) / 128, 128, 0, s>>>(args);
+    pmatrix4_kernel<MAXB><<<(nmat * 16 + 127) / 128, 128, 0, s>>>(args);
     return cudaGetLastError();
 }
 
