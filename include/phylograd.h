@@ -138,11 +138,62 @@ pg_status pg_eval_async(pg_handle *h, const double *d_b, double *d_logL, double 
 /* Evaluate k problems in as few launches as possible (problems are grouped by category count;
  * each launch covers every tile of every problem in the group).  d_b[i], d_grad[i], d_hess[i]
  * are per-problem DEVICE pointers (d_grad/d_hess may be NULL, or have NULL entries);
- * d_logL[k] is one DEVICE array.  Results are bit-identical to k separate pg_eval_async calls.
+ * d_logL[k] is one DEVICE array.  The patterns of a problem are split into blocks according to
+ * the whole batch, so results agree with separate pg_eval_async calls to rounding order (the
+ * per-block partial sums differ), and are identical for the same batch composition.
  * Errors: PG_ERR_INVALID (k < 0, a NULL handle, handles from different contexts). */
 pg_status pg_eval_batch_async(pg_handle *const *hs, int32_t k, const double *const *d_b,
                               double *d_logL, double *const *d_grad, double *const *d_hess,
                               void *stream);
+
+/* The two halves of pg_eval_async, for reverse-mode differentiation (a torch.autograd.Function
+ * whose forward is the pruning and whose backward is the pre-order pass).
+ *
+ * pg_forward_async: the P build, the post-order pass (Section 2.3) and the root (Section 2.5
+ * mixture): d_logL (DEVICE scalar) and optionally d_site_logL [P].  The post-order partials and
+ * the per-pattern root values stay in the handle.
+ *
+ * pg_backward_async: the pre-order pass (Section 2.4), the branch gradient (Section 2.5) and the
+ * Hessian diagonal (Section 2.6) from the partials that the last forward pass (or pg_eval*) on
+ * this handle left, for the branch lengths of that pass.  The gradient written to d_grad [2N-1]
+ * is multiplied by *d_gscale (DEVICE scalar, e.g. the upstream gradient of logL; NULL = 1);
+ * d_hess is not scaled.  The levels near the root, whose partials the forward pass kept on chip
+ * only, are recomputed.  Enqueue it on the forward's stream (or order the streams): it reads what
+ * the forward wrote.  Any later forward or evaluation on the handle replaces those partials.
+ * Errors: PG_ERR_INVALID (NULL handle, no forward pass enqueued on the handle yet). */
+pg_status pg_forward_async(pg_handle *h, const double *d_b, double *d_logL, double *d_site_logL, void *stream);
+pg_status pg_backward_async(pg_handle *h, const double *d_gscale, double *d_grad, double *d_hess, void *stream);
+
+/* Batched forms of the two halves, grouped and launched as pg_eval_batch_async.  d_gscale is a
+ * DEVICE array [k] (entry i scales problem i's gradient) or NULL. */
+pg_status pg_forward_batch_async(pg_handle *const *hs, int32_t k, const double *const *d_b, double *d_logL,
+                                 void *stream);
+pg_status pg_backward_batch_async(pg_handle *const *hs, int32_t k, const double *d_gscale,
+                                  double *const *d_grad, double *const *d_hess, void *stream);
+
+/* Random-effects clock (Section 2.1: a branch length is the branch's rate times the time elapsed
+ * along it; Section 5.1: the rate is a tree-wise mean mu times a branch effect eps_i):
+ *     b_i = mu * eps_i * (t_i - t_parent(i)),   b_root = 0,
+ * with node times t in forward time (a child is later than its parent; b_i < 0 is reported by
+ * the evaluation as PG_ERR_INVALID).  For each of k problems (handle hs[i] supplies the tree)
+ * d_eps[i], d_t[i], d_b[i] are DEVICE arrays [2N-1] (root entries ignored) and d_mu is a DEVICE
+ * array [k].  pg_clock_lengths_async writes d_b. */
+pg_status pg_clock_lengths_async(pg_handle *const *hs, int32_t k, const double *const *d_eps,
+                                 const double *d_mu, const double *const *d_t, double *const *d_b,
+                                 void *stream);
+
+/* The chain rule of the branch gradient g = d_grad_b[i] (DEVICE [2N-1], e.g. from
+ * pg_backward_async) through the clock above:
+ *     d/d eps_i = mu dt_i g_i,   d/d rate_i = dt_i g_i,   d/d mu = sum_i eps_i dt_i g_i,
+ *     d/d t_k = rate_k g_k - sum over the children c of k of rate_c g_c,
+ * with dt_i = t_i - t_parent(i) and rate_i = mu eps_i; root entries are 0.  Outputs (DEVICE,
+ * each may be NULL): d_grad_eps[i], d_grad_t[i], d_grad_rate[i] [2N-1] and d_grad_mu [k].  The
+ * sum over branches for mu is taken in a fixed order (the same bits on every call).
+ * Errors: PG_ERR_INVALID (NULL handle or input array). */
+pg_status pg_clock_grad_async(pg_handle *const *hs, int32_t k, const double *const *d_eps, const double *d_mu,
+                              const double *const *d_t, const double *const *d_grad_b,
+                              double *const *d_grad_eps, double *d_grad_mu, double *const *d_grad_t,
+                              double *const *d_grad_rate, void *stream);
 
 /* Wait for the handle's last evaluation and return its device-side status (PG_OK,
  * PG_ERR_INVALID for a bad branch length, PG_ERR_NUMERIC for a failed site likelihood). */

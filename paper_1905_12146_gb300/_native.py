@@ -20,7 +20,9 @@ PG_OK, PG_ERR_INVALID, PG_ERR_OOM, PG_ERR_CUDA, PG_ERR_TIMEOUT, PG_ERR_NUMERIC, 
 
 EXPORTED = ("pg_create", "pg_destroy", "pg_upload", "pg_free", "pg_eval", "pg_eval_async",
             "pg_eval_batch_async", "pg_eval_status", "pg_get_info", "pg_set_phase_timing",
-            "pg_get_phase_times", "pg_eval_noalloc", "pg_status_string", "pg_last_error")
+            "pg_get_phase_times", "pg_eval_noalloc", "pg_status_string", "pg_last_error",
+            "pg_forward_async", "pg_backward_async", "pg_forward_batch_async",
+            "pg_backward_batch_async", "pg_clock_lengths_async", "pg_clock_grad_async")
 
 
 class PhyloGradError(RuntimeError):
@@ -88,6 +90,12 @@ def load(path: str = LIB_PATH):
         "pg_set_phase_timing": ([vp, i32], i32),
         "pg_get_phase_times": ([vp, ctypes.POINTER(pg_phase_times)], i32),
         "pg_eval_noalloc": ([ctypes.POINTER(pg_problem), vp, vp, vp, vp, vp, vp], i32),
+        "pg_forward_async": ([vp, vp, vp, vp, vp], i32),
+        "pg_backward_async": ([vp, vp, vp, vp, vp], i32),
+        "pg_forward_batch_async": ([vp, i32, vp, vp, vp], i32),
+        "pg_backward_batch_async": ([vp, i32, vp, vp, vp, vp], i32),
+        "pg_clock_lengths_async": ([vp, i32, vp, vp, vp, vp, vp], i32),
+        "pg_clock_grad_async": ([vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp], i32),
         "pg_status_string": ([i32], ctypes.c_char_p),
         "pg_last_error": ([], ctypes.c_char_p),
     }
@@ -108,6 +116,20 @@ def check(status: int):
 
 def _np_ptr(a):
     return None if a is None else a.ctypes.data
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr_array(items):
+    """A C array of device pointers (None entries become NULL); None for a missing list."""
+    if items is None:
+        return None
+    arr = (ctypes.c_void_p * max(len(items), 1))(*[_dev_ptr(x) for x in items])
+    return ctypes.cast(arr, ctypes.c_void_p), arr   # keep arr alive alongside the pointer
 
 
 def _dev_ptr(t):
@@ -205,6 +227,16 @@ class Handle:
         check(load().pg_eval_async(self._ptr, _dev_ptr(d_b), _dev_ptr(d_logL), _dev_ptr(d_grad),
                                    _dev_ptr(d_hess), _dev_ptr(d_site), s))
 
+    def forward_async(self, d_b, d_logL, d_site=None, stream=None):
+        """pg_forward_async: P build, post-order and root (logL only); partials stay resident."""
+        check(load().pg_forward_async(self._ptr, _dev_ptr(d_b), _dev_ptr(d_logL), _dev_ptr(d_site),
+                                      _stream(stream)))
+
+    def backward_async(self, d_gscale, d_grad, d_hess=None, stream=None):
+        """pg_backward_async: pre-order pass and gradient (times *d_gscale) from the last forward."""
+        check(load().pg_backward_async(self._ptr, _dev_ptr(d_gscale), _dev_ptr(d_grad), _dev_ptr(d_hess),
+                                       _stream(stream)))
+
     def set_phase_timing(self, enable: bool):
         check(load().pg_set_phase_timing(self._ptr, 1 if enable else 0))
 
@@ -237,6 +269,47 @@ def eval_batch_async(handles, d_b, d_logL, d_grad=None, d_hess=None, stream=None
                                      ctypes.cast(bs, ctypes.c_void_p), _dev_ptr(d_logL),
                                      None if gs is None else ctypes.cast(gs, ctypes.c_void_p),
                                      None if hh is None else ctypes.cast(hh, ctypes.c_void_p), s))
+
+
+def _handles(handles):
+    k = len(handles)
+    hs = (ctypes.c_void_p * max(k, 1))(*[h._ptr.value for h in handles])
+    return k, ctypes.cast(hs, ctypes.c_void_p), hs
+
+
+def _arg(pa):
+    return None if pa is None else pa[0]
+
+
+def forward_batch_async(handles, d_b, d_logL, stream=None):
+    """pg_forward_batch_async: logL of every problem into the device array d_logL [k]."""
+    k, hp, _keep = _handles(handles)
+    bs = _ptr_array(d_b)
+    check(load().pg_forward_batch_async(hp, k, _arg(bs), _dev_ptr(d_logL), _stream(stream)))
+
+
+def backward_batch_async(handles, d_gscale, d_grad, d_hess=None, stream=None):
+    """pg_backward_batch_async: gradient of problem i times d_gscale[i] into d_grad[i]."""
+    k, hp, _keep = _handles(handles)
+    gs, hh = _ptr_array(d_grad), _ptr_array(d_hess)
+    check(load().pg_backward_batch_async(hp, k, _dev_ptr(d_gscale), _arg(gs), _arg(hh), _stream(stream)))
+
+
+def clock_lengths_async(handles, d_eps, d_mu, d_t, d_b, stream=None):
+    """pg_clock_lengths_async: b_i = mu eps_i (t_i - t_parent(i)) per problem."""
+    k, hp, _keep = _handles(handles)
+    e, t, b = _ptr_array(d_eps), _ptr_array(d_t), _ptr_array(d_b)
+    check(load().pg_clock_lengths_async(hp, k, _arg(e), _dev_ptr(d_mu), _arg(t), _arg(b), _stream(stream)))
+
+
+def clock_grad_async(handles, d_eps, d_mu, d_t, d_grad_b, d_grad_eps=None, d_grad_mu=None, d_grad_t=None,
+                     d_grad_rate=None, stream=None):
+    """pg_clock_grad_async: chain rule of dlogL/db to eps, mu, node times and rates."""
+    k, hp, _keep = _handles(handles)
+    e, t, g = _ptr_array(d_eps), _ptr_array(d_t), _ptr_array(d_grad_b)
+    ge, gt, gr = _ptr_array(d_grad_eps), _ptr_array(d_grad_t), _ptr_array(d_grad_rate)
+    check(load().pg_clock_grad_async(hp, k, _arg(e), _dev_ptr(d_mu), _arg(t), _arg(g), _arg(ge),
+                                     _dev_ptr(d_grad_mu), _arg(gt), _arg(gr), _stream(stream)))
 
 
 def eval_noalloc(problem: dict, b, precision: str = "fp32", grad=True, hess=False, site=False,

@@ -59,7 +59,7 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
         objs = list(ex.map(lambda s: _compile(nvcc, s, extra), sources))
     tmp = LIB + f".{os.getpid()}.tmp"
     libdir = _cuda_libdir(nvcc)
-    subprocess.run([nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
+    subprocess.run([nvcc, *ARCH, "-shared", "-cudart", "shared", "-Xlinker", "--no-undefined", "-o", tmp, *objs,
                     "-Xlinker", f"-rpath,{libdir}"], check=True)
     os.replace(tmp, LIB)
     return LIB

@@ -80,6 +80,7 @@ struct pg_handle {
            *io_site = nullptr;   // device staging for the host-pointer pg_eval
     pg_handle_info info{};
     cudaStream_t last_stream = nullptr;
+    bool have_post = false;   // an enqueued post-order left partials a backward pass can use
 };
 
 // ------------------------------------------------------------------------------------------
@@ -391,6 +392,7 @@ pg_status pg_upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out) {
     const size_t o_wide = cv.take<uint8_t>(n), o_sinv = cv.take<float>(std::max(Ps, 16));
     const size_t o_ser = cv.take<int>(std::max(Ps, 16));
     const size_t o_tc = cv.take<int2>(top_code.size()), o_bn = cv.take<int>(std::max(n_bnd, 1));
+    const size_t o_par = cv.take<int>(n);
     const size_t o_ib = cv.take<double>(n), o_il = cv.take<double>(1), o_ig = cv.take<double>(n);
     const size_t o_ih = cv.take<double>(n), o_is = cv.take<double>(std::max(P, 1));
     const size_t bytes = align_up(cv.off, 256);
@@ -459,6 +461,7 @@ pg_status pg_upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out) {
     if (e == cudaSuccess) e = cp(o_wide, wide.data(), wide.size());
     if (e == cudaSuccess) e = cp(o_tc, top_code.data(), sizeof(int2) * top_code.size());
     if (e == cudaSuccess && n_bnd > 0) e = cp(o_bn, bnd_node.data(), sizeof(int) * n_bnd);
+    if (e == cudaSuccess) e = cp(o_par, pr->parent, sizeof(int) * n);
     if (e == cudaSuccess) e = cudaMemset(base + o_st, 0, sizeof(int));
     if (e != cudaSuccess) {
         cudaFree(block);
@@ -495,6 +498,7 @@ pg_status pg_upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out) {
     d.n_bnd = n_bnd;
     d.top_code = reinterpret_cast<const int2 *>(base + o_tc);
     d.bnd_node = reinterpret_cast<const int *>(base + o_bn);
+    d.parent = reinterpret_cast<const int *>(base + o_par);
     d.cut = 0;
     h->cut = cut;
     h->level_off = tp.level_off;
@@ -592,12 +596,14 @@ void fill_args_one(pg::BatchArgs<1> &a, const pg::ProbDesc &d) {
 
 }  // namespace
 
-pg_status pg_eval_async(pg_handle *h, const double *d_b, double *d_logL, double *d_grad,
-                        double *d_hess, double *d_site_logL, void *stream) {
-    if (!h || !d_b) return fail(PG_ERR_INVALID, "NULL handle or branch lengths");
-    DeviceGuard g(h->ctx->device);
-    if (!g.ok) return fail(PG_ERR_CUDA, "cannot select device %d", h->ctx->device);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
+namespace {
+
+// One problem alone: the P build and the wide post-order levels as level kernels, the levels from
+// the cut up in the shared-memory top kernel (or the fused kernel), the pre-order levels, the
+// fixed-order reduction.  skip = kSkipPre enqueues the forward part (logL), kSkipPost the backward
+// part (gradient, Hessian diagonal) on the partials the last forward part left in the handle.
+pg_status enqueue_single(pg_handle *h, int skip, const double *d_b, double *d_logL, double *d_grad,
+                         double *d_hess, double *d_site_logL, const double *d_gscale, cudaStream_t s) {
     pg::BatchArgs<1> a;
     pg::ProbDesc d = h->desc;
     d.b = d_b;
@@ -605,6 +611,9 @@ pg_status pg_eval_async(pg_handle *h, const double *d_b, double *d_logL, double 
     d.out_grad = d_grad;
     d.out_hess = d_hess;
     d.out_site = d_site_logL;
+    d.gscale = d_gscale;
+    d.skip = skip;
+    const bool fwd = !(skip & pg::kSkipPost), bwd = !(skip & pg::kSkipPre);
     const int max_range = h->ctx->max_range ? h->ctx->max_range : pg::kMaxRange;
     d.cut = d.P > 0 ? h->cut : 0;
     // FP32: the levels from the cut up run in the shared-memory top kernel when its per-block
@@ -618,24 +627,26 @@ pg_status pg_eval_async(pg_handle *h, const double *d_b, double *d_logL, double 
     }
     if (!use_top) set_tiling(d, single_target(h->ctx, d), max_range);
     fill_args_one(a, d);
-    const bool hess = d_hess != nullptr;
+    const bool hess = bwd && d_hess != nullptr;
+    const bool timed = h->timing && fwd && bwd;
     cudaEvent_t ev[6] = {};
-    if (h->timing) {
+    if (timed) {
         for (auto &x : ev)
             if (cudaEventCreate(&x) != cudaSuccess) return fail(PG_ERR_CUDA, "cudaEventCreate failed");
         h->events.insert(h->events.end(), ev, ev + 6);
     }
-    auto mark = [&](int i) { if (h->timing) cudaEventRecord(ev[i], s); };
+    auto mark = [&](int i) { if (timed) cudaEventRecord(ev[i], s); };
+    cudaError_t e = cudaSuccess;
     mark(0);
-    cudaError_t e = pg::launch_pmatrix<1>(a, s);
+    if (fwd) e = pg::launch_pmatrix<1>(a, s);
     mark(1);
-    for (int lv = 0; e == cudaSuccess && lv < d.cut; ++lv)
+    for (int lv = 0; fwd && e == cudaSuccess && lv < d.cut; ++lv)
         e = pg::launch_post_level(d, h->level_off[lv], h->level_off[lv + 1] - h->level_off[lv], h->ctx->n_sm,
                                   h->level_cherry[lv] != 0, s);
     mark(2);
     if (e == cudaSuccess) e = use_top ? pg::launch_top(a, hess, h->ctx->n_sm, s) : pg::launch_tree<1>(a, hess, s);
     mark(3);
-    for (int lv = d.cut - 1; e == cudaSuccess && lv >= 0; --lv)
+    for (int lv = d.cut - 1; bwd && e == cudaSuccess && lv >= 0; --lv)
         e = pg::launch_pre_level(d, h->level_off[lv], h->level_off[lv + 1] - h->level_off[lv], hess, h->ctx->n_sm,
                                  h->level_cherry[lv] != 0, s);
     mark(4);
@@ -643,21 +654,17 @@ pg_status pg_eval_async(pg_handle *h, const double *d_b, double *d_logL, double 
     mark(5);
     if (e != cudaSuccess) return fail(PG_ERR_CUDA, "launch: %s", cudaGetErrorString(e));
     h->last_stream = s;
+    if (fwd) h->have_post = true;
     return PG_OK;
 }
 
-pg_status pg_eval_batch_async(pg_handle *const *hs, int32_t k, const double *const *d_b,
-                              double *d_logL, double *const *d_grad, double *const *d_hess,
-                              void *stream) {
-    if (k < 0 || (k > 0 && (!hs || !d_b || !d_logL))) return fail(PG_ERR_INVALID, "bad batch arguments");
-    if (k == 0) return PG_OK;
-    for (int i = 0; i < k; ++i) {
-        if (!hs[i] || !d_b[i]) return fail(PG_ERR_INVALID, "batch entry %d is NULL", i);
-        if (hs[i]->ctx != hs[0]->ctx) return fail(PG_ERR_INVALID, "batch mixes contexts");
-    }
+// k problems in as few launches as possible: grouped by category count and precision, each
+// launch covers every tile of every problem of the group, every level in the fused kernel
+pg_status enqueue_batch(pg_handle *const *hs, int32_t k, int skip, const double *const *d_b, double *d_logL,
+                        double *const *d_grad, double *const *d_hess, const double *d_gscale, cudaStream_t s) {
+    const bool fwd = !(skip & pg::kSkipPost), bwd = !(skip & pg::kSkipPre);
     DeviceGuard g(hs[0]->ctx->device);
     if (!g.ok) return fail(PG_ERR_CUDA, "cannot select device %d", hs[0]->ctx->device);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     auto *a = new (std::nothrow) pg::BatchArgs<pg::kMaxBatch>;
     if (!a) return fail(PG_ERR_OOM, "host allocation failed");
     for (int key = 0; key < 2 * pg::kMaxCat; ++key) {
@@ -681,11 +688,13 @@ pg_status pg_eval_batch_async(pg_handle *const *hs, int32_t k, const double *con
                 pg::ProbDesc d = hs[i]->desc;
                 const double share = ((double)hs[i]->info.stream_bytes + 1.0) / work;
                 set_tiling(d, std::min(hs[i]->max_tiles, std::max(1, (int)(slots * share))), max_range);
-                d.b = d_b[i];
-                d.out_logL = d_logL + i;
-                d.out_grad = d_grad ? d_grad[i] : nullptr;
-                d.out_hess = d_hess ? d_hess[i] : nullptr;
+                d.b = d_b ? d_b[i] : nullptr;
+                d.out_logL = d_logL ? d_logL + i : nullptr;
+                d.out_grad = (bwd && d_grad) ? d_grad[i] : nullptr;
+                d.out_hess = (bwd && d_hess) ? d_hess[i] : nullptr;
                 d.out_site = nullptr;
+                d.gscale = d_gscale ? d_gscale + i : nullptr;
+                d.skip = skip;
                 d.cut = 0;   // batched problems run every level in the fused kernel
                 hess = hess || d.out_hess;
                 a->d[j] = d;
@@ -693,13 +702,151 @@ pg_status pg_eval_batch_async(pg_handle *const *hs, int32_t k, const double *con
                 a->mat_base[j + 1] = a->mat_base[j] + d.n_nodes * d.C;
                 a->red_base[j + 1] = a->red_base[j] + d.n_nodes + 1;
                 hs[i]->last_stream = s;
+                if (fwd) hs[i]->have_post = true;
             }
-            cudaError_t e = pg::launch_eval_nt<pg::kMaxBatch>(*a, hess, s);
+            cudaError_t e = cudaSuccess;
+            if (fwd) e = pg::launch_pmatrix<pg::kMaxBatch>(*a, s);
+            if (e == cudaSuccess) e = pg::launch_tree<pg::kMaxBatch>(*a, hess, s);
+            if (e == cudaSuccess) e = pg::launch_reduce<pg::kMaxBatch>(*a, hess, s);
             if (e != cudaSuccess) { delete a; return fail(PG_ERR_CUDA, "launch: %s", cudaGetErrorString(e)); }
         }
     }
     delete a;
     return PG_OK;
+}
+
+pg_status check_batch(pg_handle *const *hs, int32_t k) {
+    if (k < 0 || (k > 0 && !hs)) return fail(PG_ERR_INVALID, "bad batch arguments");
+    for (int i = 0; i < k; ++i) {
+        if (!hs[i]) return fail(PG_ERR_INVALID, "batch entry %d is NULL", i);
+        if (hs[i]->ctx != hs[0]->ctx) return fail(PG_ERR_INVALID, "batch mixes contexts");
+    }
+    return PG_OK;
+}
+
+}  // namespace
+
+pg_status pg_eval_async(pg_handle *h, const double *d_b, double *d_logL, double *d_grad,
+                        double *d_hess, double *d_site_logL, void *stream) {
+    if (!h || !d_b) return fail(PG_ERR_INVALID, "NULL handle or branch lengths");
+    DeviceGuard g(h->ctx->device);
+    if (!g.ok) return fail(PG_ERR_CUDA, "cannot select device %d", h->ctx->device);
+    return enqueue_single(h, 0, d_b, d_logL, d_grad, d_hess, d_site_logL, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+pg_status pg_forward_async(pg_handle *h, const double *d_b, double *d_logL, double *d_site_logL, void *stream) {
+    if (!h || !d_b) return fail(PG_ERR_INVALID, "NULL handle or branch lengths");
+    DeviceGuard g(h->ctx->device);
+    if (!g.ok) return fail(PG_ERR_CUDA, "cannot select device %d", h->ctx->device);
+    return enqueue_single(h, pg::kSkipPre, d_b, d_logL, nullptr, nullptr, d_site_logL, nullptr,
+                          static_cast<cudaStream_t>(stream));
+}
+
+pg_status pg_backward_async(pg_handle *h, const double *d_gscale, double *d_grad, double *d_hess, void *stream) {
+    if (!h) return fail(PG_ERR_INVALID, "NULL handle");
+    if (!h->have_post) return fail(PG_ERR_INVALID, "no forward pass has been enqueued on this handle");
+    DeviceGuard g(h->ctx->device);
+    if (!g.ok) return fail(PG_ERR_CUDA, "cannot select device %d", h->ctx->device);
+    return enqueue_single(h, pg::kSkipPost, nullptr, nullptr, d_grad, d_hess, nullptr, d_gscale,
+                          static_cast<cudaStream_t>(stream));
+}
+
+pg_status pg_eval_batch_async(pg_handle *const *hs, int32_t k, const double *const *d_b,
+                              double *d_logL, double *const *d_grad, double *const *d_hess,
+                              void *stream) {
+    if (pg_status st = check_batch(hs, k); st != PG_OK) return st;
+    if (k > 0 && (!d_b || !d_logL)) return fail(PG_ERR_INVALID, "bad batch arguments");
+    for (int i = 0; i < k; ++i)
+        if (!d_b[i]) return fail(PG_ERR_INVALID, "batch entry %d is NULL", i);
+    if (k == 0) return PG_OK;
+    return enqueue_batch(hs, k, 0, d_b, d_logL, d_grad, d_hess, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+pg_status pg_forward_batch_async(pg_handle *const *hs, int32_t k, const double *const *d_b, double *d_logL,
+                                 void *stream) {
+    if (pg_status st = check_batch(hs, k); st != PG_OK) return st;
+    if (k > 0 && (!d_b || !d_logL)) return fail(PG_ERR_INVALID, "bad batch arguments");
+    for (int i = 0; i < k; ++i)
+        if (!d_b[i]) return fail(PG_ERR_INVALID, "batch entry %d is NULL", i);
+    if (k == 0) return PG_OK;
+    return enqueue_batch(hs, k, pg::kSkipPre, d_b, d_logL, nullptr, nullptr, nullptr,
+                         static_cast<cudaStream_t>(stream));
+}
+
+pg_status pg_backward_batch_async(pg_handle *const *hs, int32_t k, const double *d_gscale,
+                                  double *const *d_grad, double *const *d_hess, void *stream) {
+    if (pg_status st = check_batch(hs, k); st != PG_OK) return st;
+    for (int i = 0; i < k; ++i)
+        if (!hs[i]->have_post) return fail(PG_ERR_INVALID, "batch entry %d has no forward pass", i);
+    if (k == 0) return PG_OK;
+    return enqueue_batch(hs, k, pg::kSkipPost, nullptr, nullptr, d_grad, d_hess, d_gscale,
+                         static_cast<cudaStream_t>(stream));
+}
+
+namespace {
+
+pg_status enqueue_clock(pg_handle *const *hs, int32_t k, bool grad, const double *const *d_eps,
+                        const double *d_mu, const double *const *d_t, double *const *d_b,
+                        const double *const *d_grad_b, double *const *d_grad_eps, double *d_grad_mu,
+                        double *const *d_grad_t, double *const *d_grad_rate, cudaStream_t s) {
+    if (pg_status st = check_batch(hs, k); st != PG_OK) return st;
+    if (k > 0 && (!d_eps || !d_mu || !d_t || (grad ? !d_grad_b : !d_b)))
+        return fail(PG_ERR_INVALID, "bad clock arguments");
+    for (int i = 0; i < k; ++i)
+        if (!d_eps[i] || !d_t[i] || (grad ? !d_grad_b[i] : !d_b[i]))
+            return fail(PG_ERR_INVALID, "clock entry %d has a NULL array", i);
+    if (k == 0) return PG_OK;
+    DeviceGuard g(hs[0]->ctx->device);
+    if (!g.ok) return fail(PG_ERR_CUDA, "cannot select device %d", hs[0]->ctx->device);
+    auto *a = new (std::nothrow) pg::ClockArgs<pg::kMaxClock>;
+    if (!a) return fail(PG_ERR_OOM, "host allocation failed");
+    for (int at = 0; at < k; at += pg::kMaxClock) {
+        a->n = std::min(pg::kMaxClock, k - at);
+        for (int j = 0; j < a->n; ++j) {
+            const int i = at + j;
+            const pg::ProbDesc &d = hs[i]->desc;
+            pg::ClockDesc c{};
+            c.parent = d.parent;
+            c.ops = d.ops;
+            c.n_tips = d.n_tips;
+            c.n_nodes = d.n_nodes;
+            c.root = d.root;
+            c.eps = d_eps[i];
+            c.mu = d_mu + i;
+            c.t = d_t[i];
+            if (grad) {
+                c.g = d_grad_b[i];
+                c.g_eps = d_grad_eps ? d_grad_eps[i] : nullptr;
+                c.g_mu = d_grad_mu ? d_grad_mu + i : nullptr;
+                c.g_t = d_grad_t ? d_grad_t[i] : nullptr;
+                c.g_rate = d_grad_rate ? d_grad_rate[i] : nullptr;
+            } else {
+                c.b = d_b[i];
+            }
+            a->c[j] = c;
+        }
+        cudaError_t e = pg::launch_clock(*a, grad, s);
+        if (e != cudaSuccess) { delete a; return fail(PG_ERR_CUDA, "launch: %s", cudaGetErrorString(e)); }
+    }
+    delete a;
+    return PG_OK;
+}
+
+}  // namespace
+
+pg_status pg_clock_lengths_async(pg_handle *const *hs, int32_t k, const double *const *d_eps,
+                                 const double *d_mu, const double *const *d_t, double *const *d_b,
+                                 void *stream) {
+    return enqueue_clock(hs, k, false, d_eps, d_mu, d_t, d_b, nullptr, nullptr, nullptr, nullptr, nullptr,
+                         static_cast<cudaStream_t>(stream));
+}
+
+pg_status pg_clock_grad_async(pg_handle *const *hs, int32_t k, const double *const *d_eps, const double *d_mu,
+                              const double *const *d_t, const double *const *d_grad_b,
+                              double *const *d_grad_eps, double *d_grad_mu, double *const *d_grad_t,
+                              double *const *d_grad_rate, void *stream) {
+    return enqueue_clock(hs, k, true, d_eps, d_mu, d_t, nullptr, d_grad_b, d_grad_eps, d_grad_mu, d_grad_t,
+                         d_grad_rate, static_cast<cudaStream_t>(stream));
 }
 
 pg_status pg_set_phase_timing(pg_handle *h, int enable) {

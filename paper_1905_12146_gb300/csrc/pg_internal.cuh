@@ -76,6 +76,12 @@ struct ProbDesc {
     const int *bnd_node;
     // outputs of this evaluation (device, may be null)
     double *out_logL, *out_grad, *out_hess, *out_site;
+    // parts of the evaluation this launch leaves out (kSkipPost / kSkipPre bits; 0 = all of it).
+    // A launch that skips the post-order reads the partials and site arrays that an earlier
+    // launch left in the handle; gscale (device scalar, may be null = 1) multiplies the gradient
+    int skip;
+    const double *gscale;
+    const int *parent;             // [n] parent index, -1 at the root
     // sizes
     int n_tips, n_nodes, root, n_levels;
     int P;                         // site patterns
@@ -91,6 +97,9 @@ struct ProbDesc {
     float pif[kStates], gw[kMaxCat], gw2[kMaxCat];   // FP32 pi, r_l w_l, r_l^2 w_l
 };
 
+constexpr int kSkipPost = 1;   // forward part: P build, post-order levels, root and logL
+constexpr int kSkipPre = 2;    // backward part: pre-order levels, gradient and Hessian diagonal
+
 template <int MAXB>
 struct BatchArgs {
     int n;
@@ -99,6 +108,28 @@ struct BatchArgs {
     int red_base[MAXB + 1];    // prefix sums of n + 1     (reduce warps)
     ProbDesc d[MAXB];
 };
+
+// one problem of the clock parameterisation b_i = mu eps_i (t_i - t_parent(i)) (pg_clock.cu);
+// every array is [n_nodes] on the device, mu and g_mu are device scalars
+struct ClockDesc {
+    const int *parent;
+    const int4 *ops;               // internal nodes {k, c0, c1, 0}
+    int n_tips, n_nodes, root;
+    const double *eps, *mu, *t;
+    double *b;                     // lengths (forward)
+    const double *g;               // dlogL/db (backward)
+    double *g_eps, *g_mu, *g_t, *g_rate;   // outputs of the chain rule (each may be null)
+};
+
+constexpr int kMaxClock = 64;   // problems per clock launch
+
+template <int MAXB>
+struct ClockArgs {
+    int n;
+    ClockDesc c[MAXB];
+};
+
+cudaError_t launch_clock(const ClockArgs<kMaxClock> &a, bool grad, cudaStream_t s);
 
 // launchers (pg_nt.cu); every problem of one launch shares C and precision
 template <int MAXB>

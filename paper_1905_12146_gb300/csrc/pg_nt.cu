@@ -584,7 +584,7 @@ __global__ void __launch_bounds__(kBlock, 2) tree4f_kernel(const __grid_constant
     PairMeta m0, m1;
 
     // post-order, tips to root (Section 2.3); levels below d.cut were done by the level kernels
-    for (int lv = d.cut; lv < d.n_levels; ++lv) {
+    for (int lv = (d.skip & kSkipPost) ? d.n_levels : d.cut; lv < d.n_levels; ++lv) {
         const int o0 = d.level_off[lv], npairs = (d.level_off[lv + 1] - o0) * cnt;
         int chunk = warp;
         if (chunk * 32 < npairs) prefetch_pair<C, false>(d, o0, cnt, p0, npairs, chunk, st0, m0);
@@ -607,6 +607,15 @@ __global__ void __launch_bounds__(kBlock, 2) tree4f_kernel(const __grid_constant
             chunk = next;
         }
         cp_async_wait0();
+        __syncthreads();
+    }
+    if (d.skip & kSkipPre) return;
+    if (d.skip & kSkipPost) {   // the root's per-pattern values from the earlier post-order launch
+        for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+            ra.invL[q] = __ldcg(d.site_invL + p0 + q);
+            ra.Eroot[q] = __ldcg(d.site_Er + p0 + q);
+            ra.w[q] = (float)d.weights[p0 + q];
+        }
         __syncthreads();
     }
     // pre-order, root to tips (Section 2.4) with the gradient (Section 2.5), down to d.cut
@@ -689,6 +698,7 @@ __global__ void __launch_bounds__(kBlock, 1) tree4d_kernel(const __grid_constant
         }
         __syncthreads();
     }
+    if (d.skip & kSkipPre) return;   // (the FP64 kernel always recomputes the post-order)
     for (int lv = d.n_levels - 1; lv >= 0; --lv) {
         const int o0 = d.level_off[lv], nd = d.level_off[lv + 1] - o0;
         const int npairs = nd * cnt;
@@ -759,6 +769,7 @@ __global__ void __launch_bounds__(256) reduce_kernel(const __grid_constant__ Bat
         }
     }
     if (lane == 0) {
+        if (d.gscale) g *= *d.gscale;
         if (d.out_grad) d.out_grad[item] = g;
         if (want_hess && d.out_hess) d.out_hess[item] = h;
     }
@@ -876,5 +887,8 @@ template cudaError_t launch_pmatrix<1>(const BatchArgs<1> &, cudaStream_t);
 template cudaError_t launch_tree<1>(const BatchArgs<1> &, bool, cudaStream_t);
 template cudaError_t launch_reduce<1>(const BatchArgs<1> &, bool, cudaStream_t);
 template cudaError_t launch_eval_nt<kMaxBatch>(const BatchArgs<kMaxBatch> &, bool, cudaStream_t);
+template cudaError_t launch_pmatrix<kMaxBatch>(const BatchArgs<kMaxBatch> &, cudaStream_t);
+template cudaError_t launch_tree<kMaxBatch>(const BatchArgs<kMaxBatch> &, bool, cudaStream_t);
+template cudaError_t launch_reduce<kMaxBatch>(const BatchArgs<kMaxBatch> &, bool, cudaStream_t);
 
 }  // namespace pg

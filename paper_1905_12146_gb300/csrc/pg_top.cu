@@ -170,6 +170,9 @@ __global__ void __launch_bounds__(kBlock, 2) top_kernel(const __grid_constant__ 
                 invL[q] = (float)(1.0 / f);
                 Er[q] = Erq;
                 wv[q] = (float)wgt;
+            }
+            if (d.skip & kSkipPost) continue;   // recomputed for the pre-order only
+            if (active) {
                 d.site_invL[p] = (float)(1.0 / f);
                 d.site_Er[p] = Erq;
                 if (!(f > 0.0) || !isfinite(lp)) atomicOr(d.status, kStatusNumeric);
@@ -181,6 +184,7 @@ __global__ void __launch_bounds__(kBlock, 2) top_kernel(const __grid_constant__ 
         __syncthreads();
     }
 
+    if (d.skip & kSkipPre) return;
     // pre-order, top .. cut (Section 2.4) with the gradient (2.5) and Hessian diagonal (2.6)
     for (int lv = d.n_levels - 1; lv >= d.cut; --lv) {
         const int o0 = d.level_off[lv], npairs = (d.level_off[lv + 1] - o0) * cnt;
