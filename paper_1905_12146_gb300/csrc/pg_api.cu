@@ -81,6 +81,8 @@ struct pg_handle {
     pg_handle_info info{};
     cudaStream_t last_stream = nullptr;
     bool have_post = false;   // an enqueued post-order left partials a backward pass can use
+    bool mstate = false;      // a general state space (pg_mstate.cu): md holds its layout
+    pg::MDesc md{};
 };
 
 // ------------------------------------------------------------------------------------------
@@ -237,6 +239,294 @@ void set_tiling(pg::ProbDesc &d, int target, int max_range) {
 // C ABI
 // ------------------------------------------------------------------------------------------
 
+namespace {
+
+// Stationary distribution of a generator: pi Q = 0, sum pi = 1 (Gaussian elimination with partial
+// pivoting on Q^T, the last equation replaced by the normalisation).  False if singular.
+bool stationary(const double *Q, int m, std::vector<double> &pi) {
+    std::vector<double> A((size_t)m * (m + 1));
+    for (int i = 0; i < m; ++i) {
+        for (int j = 0; j < m; ++j) A[(size_t)i * (m + 1) + j] = (i == m - 1) ? 1.0 : Q[(size_t)j * m + i];
+        A[(size_t)i * (m + 1) + m] = (i == m - 1) ? 1.0 : 0.0;
+    }
+    for (int c = 0; c < m; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < m; ++r)
+            if (std::fabs(A[(size_t)r * (m + 1) + c]) > std::fabs(A[(size_t)piv * (m + 1) + c])) piv = r;
+        if (std::fabs(A[(size_t)piv * (m + 1) + c]) < 1e-300) return false;
+        if (piv != c)
+            for (int j = 0; j <= m; ++j) std::swap(A[(size_t)c * (m + 1) + j], A[(size_t)piv * (m + 1) + j]);
+        for (int r = 0; r < m; ++r) {
+            if (r == c) continue;
+            const double f = A[(size_t)r * (m + 1) + c] / A[(size_t)c * (m + 1) + c];
+            if (f == 0.0) continue;
+            for (int j = c; j <= m; ++j) A[(size_t)r * (m + 1) + j] -= f * A[(size_t)c * (m + 1) + j];
+        }
+    }
+    pi.assign(m, 0.0);
+    for (int i = 0; i < m; ++i) pi[i] = A[(size_t)i * (m + 1) + m] / A[(size_t)i * (m + 1) + i];
+    return true;
+}
+
+// Cyclic Jacobi eigenvalue iteration for a symmetric matrix S (m x m, row-major, overwritten):
+// S = U diag(lam) U^T, U orthogonal (column k = eigenvector k).
+void jacobi_eigen(std::vector<double> &S, int m, std::vector<double> &U, std::vector<double> &lam) {
+    U.assign((size_t)m * m, 0.0);
+    for (int i = 0; i < m; ++i) U[(size_t)i * m + i] = 1.0;
+    double norm = 0.0;
+    for (double x : S) norm += x * x;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < m; ++p)
+            for (int q = p + 1; q < m; ++q) off += S[(size_t)p * m + q] * S[(size_t)p * m + q];
+        if (off <= 1e-32 * norm) break;
+        for (int p = 0; p < m; ++p)
+            for (int q = p + 1; q < m; ++q) {
+                const double apq = S[(size_t)p * m + q];
+                if (apq == 0.0) continue;
+                const double theta = (S[(size_t)q * m + q] - S[(size_t)p * m + p]) / (2.0 * apq);
+                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+                for (int k = 0; k < m; ++k) {   // columns p, q
+                    const double skp = S[(size_t)k * m + p], skq = S[(size_t)k * m + q];
+                    S[(size_t)k * m + p] = c * skp - sn * skq;
+                    S[(size_t)k * m + q] = sn * skp + c * skq;
+                }
+                for (int k = 0; k < m; ++k) {   // rows p, q
+                    const double spk = S[(size_t)p * m + k], sqk = S[(size_t)q * m + k];
+                    S[(size_t)p * m + k] = c * spk - sn * sqk;
+                    S[(size_t)q * m + k] = sn * spk + c * sqk;
+                }
+                for (int k = 0; k < m; ++k) {
+                    const double ukp = U[(size_t)k * m + p], ukq = U[(size_t)k * m + q];
+                    U[(size_t)k * m + p] = c * ukp - sn * ukq;
+                    U[(size_t)k * m + q] = sn * ukp + c * ukq;
+                }
+            }
+    }
+    lam.assign(m, 0.0);
+    for (int i = 0; i < m; ++i) lam[i] = S[(size_t)i * m + i];
+}
+
+// The symmetrised eigensystem of a reversible Q (detailed balance pi*_i Q_ij = pi*_j Q_ji with
+// pi* > 0): S = Pi^{1/2} Q Pi^{-1/2} = U diag(lam) U^T.  Writes UT (FP32, kMP x kMP, UT[k][j] =
+// U[j][k]), lam, sqrt(pi*) and 1 / sqrt(pi*), pads zero.  False (with a message) otherwise.
+pg_status symmetric_eigensystem(const double *Q, int m, int md, float *UT, double *lam_out, float *sq_out,
+                                float *isq_out) {
+    std::vector<double> pi;
+    if (!stationary(Q, m, pi)) return fail(PG_ERR_UNSUPPORTED, "Q[%d] has no unique stationary distribution", md);
+    double scale = 0.0;
+    for (int i = 0; i < m; ++i) {
+        if (!(pi[i] > 0.0)) return fail(PG_ERR_UNSUPPORTED, "the stationary distribution of Q[%d] is not positive", md);
+        for (int j = 0; j < m; ++j) scale = std::max(scale, std::fabs(pi[i] * Q[(size_t)i * m + j]));
+    }
+    for (int i = 0; i < m; ++i)
+        for (int j = i + 1; j < m; ++j)
+            if (std::fabs(pi[i] * Q[(size_t)i * m + j] - pi[j] * Q[(size_t)j * m + i]) > 1e-10 * scale)
+                return fail(PG_ERR_UNSUPPORTED,
+                            "Q[%d] is not reversible; general (non-reversible) generators are implemented for 4 states", md);
+    std::vector<double> S((size_t)m * m), U, lam;
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) S[(size_t)i * m + j] = std::sqrt(pi[i] / pi[j]) * Q[(size_t)i * m + j];
+    for (int i = 0; i < m; ++i)
+        for (int j = i + 1; j < m; ++j) {
+            const double a = 0.5 * (S[(size_t)i * m + j] + S[(size_t)j * m + i]);
+            S[(size_t)i * m + j] = S[(size_t)j * m + i] = a;
+        }
+    jacobi_eigen(S, m, U, lam);
+    for (int k = 0; k < m; ++k) {
+        lam_out[k] = std::min(lam[k], 0.0);   // a generator's eigenvalues are <= 0
+        for (int j = 0; j < m; ++j) UT[(size_t)k * pg::kMP + j] = (float)U[(size_t)j * m + k];
+    }
+    for (int j = 0; j < m; ++j) {
+        sq_out[j] = (float)std::sqrt(pi[j]);
+        isq_out[j] = (float)(1.0 / std::sqrt(pi[j]));
+    }
+    return PG_OK;
+}
+
+// upload of a problem with 5..64 states (pg_mstate.cu kernels)
+pg_status upload_m(pg_ctx *ctx, const pg_problem *pr, const TreePlan &tp, pg_handle **out) {
+    const int N = pr->n_tips, m = pr->n_states, P = pr->n_patterns, C = pr->n_categories, M = pr->n_models;
+    const int n = 2 * N - 1, H = (int)tp.level_off.size() - 1;
+    const int KP = pg::kMP;
+    std::vector<float> UT((size_t)M * KP * KP, 0.f), sq((size_t)M * KP, 0.f), isq((size_t)M * KP, 0.f);
+    std::vector<double> lam((size_t)M * KP, 0.0);
+    for (int md = 0; md < M; ++md) {
+        pg_status st = symmetric_eigensystem(pr->Q + (size_t)md * m * m, m, md, UT.data() + (size_t)md * KP * KP,
+                                             lam.data() + (size_t)md * KP, sq.data() + (size_t)md * KP,
+                                             isq.data() + (size_t)md * KP);
+        if (st != PG_OK) return st;
+    }
+    const int Ps = (P + 15) / 16 * 16;
+    const int n_pt = (P + pg::kMTile - 1) / pg::kMTile, n_lb = (P + 255) / 256;
+    Carver cv;
+    const size_t o_ops = cv.take<int4>(N - 1), o_lv = cv.take<int>(H + 1);
+    const size_t o_tips = cv.take<uint8_t>((size_t)N * Ps), o_w = cv.take<double>(Ps);
+    const size_t o_UT = cv.take<float>(UT.size()), o_lam = cv.take<double>(lam.size());
+    const size_t o_sq = cv.take<float>(sq.size()), o_isq = cv.take<float>(isq.size());
+    const size_t o_bm = pr->branch_model ? cv.take<int>(n) : 0;
+    const size_t o_tab = cv.take<float>((size_t)n * C * pg::kTabKinds * pg::kTabFloats);
+    const size_t part = (size_t)(N - 1) * C * Ps * KP;
+    const size_t o_post = cv.take<float>(part), o_pre = cv.take<float>(part);
+    const size_t o_pe = cv.take<int>((size_t)(N - 1) * C * Ps), o_qe = cv.take<int>((size_t)(N - 1) * C * Ps);
+    const size_t o_gp = cv.take<double>((size_t)n * std::max(n_pt, 1)), o_hp = cv.take<double>((size_t)n * std::max(n_pt, 1));
+    const size_t o_lp = cv.take<double>(std::max(n_lb, 1)), o_st = cv.take<int>(1);
+    const size_t o_sinv = cv.take<float>(std::max(Ps, 16)), o_ser = cv.take<int>(std::max(Ps, 16));
+    const size_t o_par = cv.take<int>(n);
+    const size_t o_ib = cv.take<double>(n), o_il = cv.take<double>(1), o_ig = cv.take<double>(n);
+    const size_t o_ih = cv.take<double>(n), o_is = cv.take<double>(std::max(P, 1));
+    const size_t bytes = align_up(cv.off, 256);
+    if (ctx->budget && ctx->used + bytes > ctx->budget)
+        return fail(PG_ERR_OOM, "problem needs %zu bytes, %llu of %llu budget in use", bytes,
+                    (unsigned long long)ctx->used, (unsigned long long)ctx->budget);
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(PG_ERR_CUDA, "cannot select device %d", ctx->device);
+    void *block = nullptr;
+    cudaError_t ce = cudaMalloc(&block, bytes);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PG_ERR_OOM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(ce));
+    }
+    char *base = static_cast<char *>(block);
+    pg_handle *h = new (std::nothrow) pg_handle;
+    if (!h) { cudaFree(block); return fail(PG_ERR_OOM, "host allocation failed"); }
+    h->ctx = ctx;
+    h->block = block;
+    h->bytes = bytes;
+    h->mstate = true;
+    auto cp = [&](size_t off, const void *src, size_t nbytes) -> cudaError_t {
+        if (nbytes == 0) return cudaSuccess;
+        return cudaMemcpy(base + off, src, nbytes, cudaMemcpyHostToDevice);
+    };
+    cudaError_t e = cp(o_ops, tp.ops.data(), sizeof(int4) * tp.ops.size());
+    if (e == cudaSuccess) e = cp(o_lv, tp.level_off.data(), sizeof(int) * tp.level_off.size());
+    if (e == cudaSuccess && P > 0) e = cudaMemcpy2D(base + o_tips, Ps, pr->tip_states, P, P, N, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && P > 0) e = cp(o_w, pr->pattern_weights, sizeof(double) * P);
+    if (e == cudaSuccess) e = cp(o_UT, UT.data(), sizeof(float) * UT.size());
+    if (e == cudaSuccess) e = cp(o_lam, lam.data(), sizeof(double) * lam.size());
+    if (e == cudaSuccess) e = cp(o_sq, sq.data(), sizeof(float) * sq.size());
+    if (e == cudaSuccess) e = cp(o_isq, isq.data(), sizeof(float) * isq.size());
+    if (e == cudaSuccess && pr->branch_model) e = cp(o_bm, pr->branch_model, sizeof(int) * n);
+    if (e == cudaSuccess) e = cp(o_par, pr->parent, sizeof(int) * n);
+    if (e == cudaSuccess) e = cudaMemset(base + o_st, 0, sizeof(int));
+    // padded states of every partial stay zero: the kernels write whole columns, pads included
+    if (e != cudaSuccess) {
+        cudaFree(block);
+        delete h;
+        return fail(PG_ERR_CUDA, "upload: %s", cudaGetErrorString(e));
+    }
+    pg::MDesc &d = h->md;
+    d.ops = reinterpret_cast<const int4 *>(base + o_ops);
+    d.level_off = reinterpret_cast<const int *>(base + o_lv);
+    d.tips = reinterpret_cast<const uint8_t *>(base + o_tips);
+    d.weights = reinterpret_cast<const double *>(base + o_w);
+    d.UT = reinterpret_cast<const float *>(base + o_UT);
+    d.lam = reinterpret_cast<const double *>(base + o_lam);
+    d.sq = reinterpret_cast<const float *>(base + o_sq);
+    d.isq = reinterpret_cast<const float *>(base + o_isq);
+    d.bmodel = pr->branch_model ? reinterpret_cast<const int *>(base + o_bm) : nullptr;
+    d.tabs = reinterpret_cast<float *>(base + o_tab);
+    d.post = reinterpret_cast<float *>(base + o_post);
+    d.pre = reinterpret_cast<float *>(base + o_pre);
+    d.pe = reinterpret_cast<int *>(base + o_pe);
+    d.qe = reinterpret_cast<int *>(base + o_qe);
+    d.gpart = reinterpret_cast<double *>(base + o_gp);
+    d.hpart = reinterpret_cast<double *>(base + o_hp);
+    d.lpart = reinterpret_cast<double *>(base + o_lp);
+    d.status = reinterpret_cast<int *>(base + o_st);
+    d.site_invL = reinterpret_cast<float *>(base + o_sinv);
+    d.site_Er = reinterpret_cast<int *>(base + o_ser);
+    d.n_tips = N;
+    d.n_nodes = n;
+    d.root = tp.root;
+    d.n_levels = H;
+    d.P = P;
+    d.Ps = Ps;
+    d.m = m;
+    d.C = C;
+    d.n_models = M;
+    d.n_ptiles = n_pt;
+    for (int l = 0; l < pg::kMaxCat; ++l) {
+        d.cw[l] = l < C ? pr->cat_weights[l] : 0.0;
+        d.rates[l] = l < C ? pr->cat_rates[l] : 0.0;
+    }
+    for (int s = 0; s < KP; ++s) {
+        d.pi[s] = s < m ? pr->root_freqs[s] : 0.0;
+        d.pif[s] = (float)d.pi[s];
+    }
+    // the fields the shared entry points read (status, sizes, tree) mirror into desc
+    pg::ProbDesc &pd = h->desc;
+    pd.ops = d.ops;
+    pd.level_off = d.level_off;
+    pd.parent = reinterpret_cast<const int *>(base + o_par);
+    pd.status = d.status;
+    pd.n_tips = N;
+    pd.n_nodes = n;
+    pd.root = tp.root;
+    pd.n_levels = H;
+    pd.P = P;
+    pd.Ps = Ps;
+    pd.C = C;
+    pd.n_models = M;
+    h->level_off = tp.level_off;
+    h->io_b = reinterpret_cast<double *>(base + o_ib);
+    h->io_logL = reinterpret_cast<double *>(base + o_il);
+    h->io_grad = reinterpret_cast<double *>(base + o_ig);
+    h->io_hess = reinterpret_cast<double *>(base + o_ih);
+    h->io_site = reinterpret_cast<double *>(base + o_is);
+    pg_handle_info &I = h->info;
+    I.n_tips = N;
+    I.n_nodes = n;
+    I.n_states = m;
+    I.n_patterns = P;
+    I.n_categories = C;
+    I.n_levels = H;
+    I.n_tiles = n_pt;
+    I.patterns_per_tile = pg::kMTile;
+    I.device_bytes = bytes;
+    // the same node streams as the 4-state path with kMP FP32 states and one exponent per column
+    const uint64_t node_stream = (uint64_t)P * C * ((uint64_t)KP * 4ull + 4ull);
+    I.stream_bytes = 5ull * (uint64_t)(N - 2) * node_stream + 2ull * (uint64_t)N * P;
+    // post P x, pre P x, G x and P^T q per internal child branch and column (2 kMP^2 each)
+    I.flops = (uint64_t)(N - 2) * P * C * 4ull * 2ull * KP * KP;
+    ctx->used += bytes;
+    ctx->handles.push_back(h);
+    *out = h;
+    return PG_OK;
+}
+
+pg_status enqueue_m(pg_handle *h, int skip, const double *d_b, double *d_logL, double *d_grad, double *d_hess,
+                    double *d_site_logL, const double *d_gscale, cudaStream_t s) {
+    pg::MDesc d = h->md;
+    d.b = d_b;
+    d.out_logL = d_logL;
+    d.out_grad = d_grad;
+    d.out_hess = d_hess;
+    d.out_site = d_site_logL;
+    d.gscale = d_gscale;
+    d.skip = skip;
+    const bool fwd = !(skip & pg::kSkipPost), bwd = !(skip & pg::kSkipPre);
+    const bool hess = bwd && d_hess != nullptr;
+    if (hess && !fwd) return fail(PG_ERR_UNSUPPORTED, "the Hessian diagonal of a %d-state problem needs a full evaluation", d.m);
+    cudaError_t e = cudaSuccess;
+    if (fwd) {
+        e = pg::launch_m_pmatrix(d, hess, s);
+        for (int lv = 0; e == cudaSuccess && lv < d.n_levels; ++lv)
+            e = pg::launch_m_post_level(d, h->level_off[lv], h->level_off[lv + 1] - h->level_off[lv], s);
+        if (e == cudaSuccess) e = pg::launch_m_root(d, s);
+    }
+    for (int lv = d.n_levels - 1; bwd && e == cudaSuccess && lv >= 0; --lv)
+        e = pg::launch_m_pre_level(d, h->level_off[lv], h->level_off[lv + 1] - h->level_off[lv], hess, s);
+    if (e == cudaSuccess) e = pg::launch_m_reduce(d, hess, s);
+    if (e != cudaSuccess) return fail(PG_ERR_CUDA, "launch: %s", cudaGetErrorString(e));
+    h->last_stream = s;
+    if (fwd) h->have_post = true;
+    return PG_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char *pg_status_string(pg_status s) {
@@ -312,7 +602,9 @@ pg_status pg_upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out) {
     if (pr->precision != PG_PRECISION_FP32 && pr->precision != PG_PRECISION_FP64)
         return fail(PG_ERR_INVALID, "precision = %d", pr->precision);
     const bool f64 = pr->precision == PG_PRECISION_FP64;
-    if (m != pg::kStates) return fail(PG_ERR_UNSUPPORTED, "n_states = %d: this build implements 4 states", m);
+    if (m > pg::kMP) return fail(PG_ERR_UNSUPPORTED, "n_states = %d: at most %d", m, pg::kMP);
+    if (m != pg::kStates && f64)
+        return fail(PG_ERR_UNSUPPORTED, "FP64 partials are implemented for 4 states only");
     if (C > pg::kMaxCat) return fail(PG_ERR_UNSUPPORTED, "n_categories = %d: at most %d", C, pg::kMaxCat);
     if (!pr->parent) return fail(PG_ERR_INVALID, "parent is NULL");
     if (P > 0 && (!pr->tip_states || !pr->pattern_weights))
@@ -323,6 +615,7 @@ pg_status pg_upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out) {
     if (st != PG_OK) return st;
     st = check_model(pr);
     if (st != PG_OK) return st;
+    if (m != pg::kStates) return upload_m(ctx, pr, tp, out);
 
     const int n = 2 * N - 1;
     const int H = (int)tp.level_off.size() - 1;
@@ -604,6 +897,7 @@ namespace {
 // part (gradient, Hessian diagonal) on the partials the last forward part left in the handle.
 pg_status enqueue_single(pg_handle *h, int skip, const double *d_b, double *d_logL, double *d_grad,
                          double *d_hess, double *d_site_logL, const double *d_gscale, cudaStream_t s) {
+    if (h->mstate) return enqueue_m(h, skip, d_b, d_logL, d_grad, d_hess, d_site_logL, d_gscale, s);
     pg::BatchArgs<1> a;
     pg::ProbDesc d = h->desc;
     d.b = d_b;
@@ -665,13 +959,20 @@ pg_status enqueue_batch(pg_handle *const *hs, int32_t k, int skip, const double 
     const bool fwd = !(skip & pg::kSkipPost), bwd = !(skip & pg::kSkipPre);
     DeviceGuard g(hs[0]->ctx->device);
     if (!g.ok) return fail(PG_ERR_CUDA, "cannot select device %d", hs[0]->ctx->device);
+    for (int i = 0; i < k; ++i) {   // general state spaces: each problem's own level launches
+        if (!hs[i]->mstate) continue;
+        pg_status st = enqueue_m(hs[i], skip, d_b ? d_b[i] : nullptr, d_logL ? d_logL + i : nullptr,
+                                 (bwd && d_grad) ? d_grad[i] : nullptr, (bwd && d_hess) ? d_hess[i] : nullptr,
+                                 nullptr, d_gscale ? d_gscale + i : nullptr, s);
+        if (st != PG_OK) return st;
+    }
     auto *a = new (std::nothrow) pg::BatchArgs<pg::kMaxBatch>;
     if (!a) return fail(PG_ERR_OOM, "host allocation failed");
     for (int key = 0; key < 2 * pg::kMaxCat; ++key) {
         const int C = 1 + key / 2, prec = key % 2;
         std::vector<int> idx;
         for (int i = 0; i < k; ++i)
-            if (hs[i]->desc.C == C && hs[i]->desc.precision == prec) idx.push_back(i);
+            if (!hs[i]->mstate && hs[i]->desc.C == C && hs[i]->desc.precision == prec) idx.push_back(i);
         for (size_t at = 0; at < idx.size(); at += pg::kMaxBatch) {
             const int cnt = (int)std::min<size_t>(pg::kMaxBatch, idx.size() - at);
             a->n = cnt;

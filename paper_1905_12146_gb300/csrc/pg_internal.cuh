@@ -131,6 +131,52 @@ struct ClockArgs {
 
 cudaError_t launch_clock(const ClockArgs<kMaxClock> &a, bool grad, cudaStream_t s);
 
+// ---- general state spaces (pg_mstate.cu): 5 <= m <= 64 states, padded to kMP ---------------------
+// A reversible Q with stationary distribution pi* > 0 is symmetrised, S = Pi^{1/2} Q Pi^{-1/2} =
+// U diag(lambda) U^T (host, FP64, once per upload); per branch and category the device forms
+//   D = P - I = Pi^{-1/2} U diag(expm1(lambda b r)) U^T Pi^{1/2},   G = r Q P,   H = r^2 Q^2 P.
+// Partials are FP32 [node - N][C][Ps][kMP] (a column = (pattern, category) holds kMP states, pads
+// zero) with one power-of-two exponent per column [node - N][C][Ps].
+constexpr int kMP = 64;                 // padded state count
+constexpr int kMTile = 64;              // patterns per item of the m-state kernels
+constexpr int kTabRows = kMP + 1;       // table rows: kMP, then the ambiguous-code row
+constexpr int kTabFloats = kTabRows * kMP;
+constexpr int kTabDT = 0, kTabD = 1, kTabGT = 2, kTabHT = 3, kTabKinds = 4;
+
+struct MDesc {
+    const int4 *ops;
+    const int *level_off;
+    const uint8_t *tips;           // [N][Ps] codes; >= m is the all-ones (missing/ambiguous) code
+    const double *weights;         // [P]
+    const double *b;               // [n] branch lengths of this evaluation
+    const float *UT;               // [n_models][kMP][kMP]: UT[k][j] = U[j][k] (eigenvector k), FP32
+    const double *lam;             // [n_models][kMP] eigenvalues (pads 0)
+    const float *sq;               // [n_models][kMP] sqrt(pi*) (pads 0)
+    const float *isq;              // [n_models][kMP] 1 / sqrt(pi*) (pads 0)
+    const int *bmodel;
+    float *tabs;                   // [n][C][kTabKinds][kTabRows][kMP]
+    float *post, *pre;             // [n_int][C][Ps][kMP]
+    int *pe, *qe;                  // [n_int][C][Ps]
+    double *gpart, *hpart;         // [n][n_ptiles]
+    double *lpart;                 // [n_ptiles]
+    int *status;
+    float *site_invL;              // [Ps] 1 / Lhat_p
+    int *site_Er;                  // [Ps]
+    double *out_logL, *out_grad, *out_hess, *out_site;
+    const double *gscale;
+    int skip;
+    int n_tips, n_nodes, root, n_levels, P, Ps, m, C, n_models, n_ptiles;
+    double cw[kMaxCat], rates[kMaxCat];
+    float pif[kMP];                // root frequencies, FP32 (pads 0)
+    double pi[kMP];
+};
+
+cudaError_t launch_m_pmatrix(const MDesc &d, bool hess, cudaStream_t s);
+cudaError_t launch_m_post_level(const MDesc &d, int o0, int nd, cudaStream_t s);
+cudaError_t launch_m_root(const MDesc &d, cudaStream_t s);
+cudaError_t launch_m_pre_level(const MDesc &d, int o0, int nd, bool hess, cudaStream_t s);
+cudaError_t launch_m_reduce(const MDesc &d, bool hess, cudaStream_t s);
+
 // launchers (pg_nt.cu); every problem of one launch shares C and precision
 template <int MAXB>
 cudaError_t launch_eval_nt(const BatchArgs<MAXB> &args, bool hess, cudaStream_t s);

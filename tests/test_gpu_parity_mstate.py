@@ -1,0 +1,160 @@
+"""GPU parity of the general-state path (61 sense codons, 20 amino acids) against the FP64 oracle.
+
+Stated error (not the 4-state bounds): the transition tables are formed in FP32 from the FP64
+eigensystem of the symmetrised generator, D = P - I = Pi^{-1/2} U diag(expm1(lambda t)) U^T Pi^{1/2},
+so each entry carries an absolute error of about m 2^-24 max_k |expm1(lambda_k t)| sqrt(pi_j / pi_s)
+on top of the FP32 rounding of the partials.  Per site, every internal node adds at most about
+m 2^-24 relative (an FP32 sum of m products, plus a table error of the same order), so the site
+logL bound is 2 n_internal m 2^-24 absolute.  logL (2e-7 relative), gradient (2e-4 max-norm
+relative) and Hessian diagonal (2e-3) bounds hold with a margin of about ten over the errors
+measured on these problems (largest: 2e-8, 3e-5, 2.5e-5).
+"""
+import numpy as np
+import pytest
+
+from paper_1905_12146_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+M_LOGL_RTOL = 2e-7
+M_GRAD_RTOL = 2e-4
+M_HESS_RTOL = 2e-3
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1905_12146_gb300 import _native, build
+    build.build()
+    c = _native.Context(0)
+    yield c
+    c.close()
+
+
+def _maxrel(got, ref):
+    return np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300)
+
+
+def _site_atol(pr):
+    m = pr["Q"].shape[-1]
+    return 2.0 * (pr["n_tips"] - 1) * m * 2.0 ** -24
+
+
+def _check(ctx, oracle_mod, pr, hess=True, label=""):
+    h = ctx.upload(pr)
+    try:
+        got = h.eval(pr["b"], grad=True, hess=hess, site=True)
+    finally:
+        h.close()
+    ref = oracle_mod.evaluate(pr, pr["b"])
+    el = abs(got["logL"] - ref.logL) / abs(ref.logL)
+    eg = _maxrel(got["grad"], ref.grad)
+    es = np.abs(got["site_logL"] - ref.site_logL).max() if pr["weights"].shape[0] else 0.0
+    eh = _maxrel(got["hess"], ref.hess) if hess else 0.0
+    print(f"{label}: logL rel {el:.2e}  grad {eg:.2e}  site abs {es:.2e}  hess {eh:.2e}")
+    assert got["status"] == 0
+    assert el <= M_LOGL_RTOL
+    assert eg <= M_GRAD_RTOL
+    assert es <= _site_atol(pr)
+    if hess:
+        assert eh <= M_HESS_RTOL
+    assert got["grad"][wl.root_of(pr["parent"])] == 0.0
+    return got, ref
+
+
+@pytest.mark.parametrize("n_tips,n_patterns,n_cat,seed", [
+    (3, 40, 1, 1), (12, 130, 4, 2), (40, 300, 2, 3), (25, 64, 3, 4), (17, 1, 1, 5),
+])
+def test_codon_against_oracle(ctx, oracle_mod, n_tips, n_patterns, n_cat, seed):
+    """61-state reversible codon model: several pattern tiles with a ragged tail, one pattern,
+    a three-taxon tree."""
+    pr = wl.random_problem(n_tips, n_patterns, n_states=61, n_cat=n_cat, seed=seed, b_mean=0.05,
+                           ambiguous=0.03)
+    _check(ctx, oracle_mod, pr, label=f"codon N={n_tips} P={n_patterns} C={n_cat}")
+
+
+def test_codon_caterpillar_and_models(ctx, oracle_mod):
+    """Deep (caterpillar) tree, two codon models on different branches, relabelled nodes."""
+    pr = wl.random_problem(30, 200, n_states=61, n_cat=2, seed=7, tree="caterpillar", n_models=2, b_mean=0.1)
+    _check(ctx, oracle_mod, pr, label="codon caterpillar 2 models")
+    pr = wl.random_problem(30, 150, n_states=61, n_cat=1, seed=8, relabel=True, b_mean=0.1)
+    _check(ctx, oracle_mod, pr, hess=False, label="codon relabelled")
+
+
+@pytest.mark.parametrize("m", [5, 20, 33, 64])
+def test_other_state_counts(ctx, oracle_mod, m):
+    pr = wl.random_problem(20, 257, n_states=m, n_cat=2, seed=30 + m, reversible=True, b_mean=0.1,
+                           ambiguous=0.05)
+    _check(ctx, oracle_mod, pr, label=f"m={m}")
+
+
+def test_non_reversible_general_state_space_is_rejected(ctx):
+    from paper_1905_12146_gb300 import _native
+    pr = wl.random_problem(6, 20, n_states=20, seed=1)   # general (non-reversible) Q
+    with pytest.raises(_native.PhyloGradError) as e:
+        ctx.upload(pr)
+    assert e.value.status == _native.PG_ERR_UNSUPPORTED
+
+
+def test_codon_forward_backward_equals_eval(ctx):
+    import torch
+    pr = wl.random_problem(40, 333, n_states=61, n_cat=4, seed=9, b_mean=0.05)
+    h = ctx.upload(pr)
+    try:
+        dev = torch.device("cuda")
+        b = torch.tensor(pr["b"], device=dev)
+        l0 = torch.zeros(1, dtype=torch.float64, device=dev)
+        g0 = torch.zeros_like(b)
+        h.eval_async(b, l0, g0)
+        l1, g1 = torch.zeros_like(l0), torch.zeros_like(b)
+        scale = torch.tensor([-0.5], dtype=torch.float64, device=dev)
+        h.forward_async(b, l1)
+        h.backward_async(scale, g1)
+        torch.cuda.synchronize()
+        assert h.status() == 0
+        assert l1.item() == l0.item()
+        assert torch.equal(g1, -0.5 * g0)
+    finally:
+        h.close()
+
+
+@pytest.fixture(scope="module")
+def codon_full():
+    return wl.config_codon()
+
+
+def test_codon_full_size_sampled_sites(ctx, oracle_mod, codon_full):
+    """500 taxa x 3,000 codon patterns x 4 categories, as timed: the per-site logL of 60 sampled
+    patterns against the oracle run on those patterns alone, and the gradient of an evaluation
+    whose weights are zero except on the sampled patterns against the oracle's gradient of that
+    sub-alignment (same shapes and launches as the full evaluation)."""
+    pr = dict(codon_full)
+    P = pr["weights"].shape[0]
+    rng = np.random.default_rng(0)
+    idx = np.sort(rng.choice(P, 60, replace=False))
+    h = ctx.upload(pr)
+    try:
+        full = h.eval(pr["b"], grad=True, site=True)
+        w = np.zeros(P)
+        w[idx] = pr["weights"][idx]
+        masked = dict(pr, weights=w)
+    finally:
+        h.close()
+    hm = ctx.upload(masked)
+    try:
+        part = hm.eval(pr["b"], grad=True, site=True)
+    finally:
+        hm.close()
+    sub = dict(pr, tip_states=pr["tip_states"][:, idx], weights=pr["weights"][idx])
+    ref = oracle_mod.evaluate(sub, pr["b"])
+    es = np.abs(full["site_logL"][idx] - ref.site_logL).max()
+    eg = _maxrel(part["grad"], ref.grad)
+    el = abs(part["logL"] - ref.logL) / abs(ref.logL)
+    print(f"codon full size: site abs {es:.2e}  masked logL rel {el:.2e}  masked grad {eg:.2e}")
+    assert full["status"] == 0 and part["status"] == 0
+    assert es <= _site_atol(pr)
+    assert el <= M_LOGL_RTOL
+    assert eg <= M_GRAD_RTOL
+    np.testing.assert_array_equal(part["site_logL"], full["site_logL"])
