@@ -50,7 +50,12 @@ typedef struct pg_options {
     int32_t device;             /* CUDA device ordinal                                       */
     int32_t patterns_per_tile;  /* site patterns per thread block; multiple of 32, 0=default */
     uint64_t hbm_budget_bytes;  /* cap on device bytes held by this context's handles; 0=none */
+    uint32_t flags;             /* PG_FLAG_* below; 0 = defaults                              */
 } pg_options;
+
+/* Problems with 5..64 states run their products on the tensor cores (three-pass TF32 with FP32
+ * accumulation) unless this flag selects the CUDA-core (SIMT FP32) kernels. */
+#define PG_FLAG_SIMT_MSTATE 1u
 
 /* Storage and arithmetic of the partial likelihood vectors.  FP32: partials in FP32 with FP64
  * transition matrices split into FP32 hi/lo pairs, an exact-product form of the post-order

@@ -33,7 +33,10 @@ class PhyloGradError(RuntimeError):
 
 class pg_options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("patterns_per_tile", ctypes.c_int32),
-                ("hbm_budget_bytes", ctypes.c_uint64)]
+                ("hbm_budget_bytes", ctypes.c_uint64), ("flags", ctypes.c_uint32)]
+
+
+PG_FLAG_SIMT_MSTATE = 1
 
 
 class pg_problem(ctypes.Structure):
@@ -144,9 +147,9 @@ def _dev_ptr(t):
 class Context:
     """One CUDA device with an optional device-memory budget (pg_create / pg_destroy)."""
 
-    def __init__(self, device: int = 0, patterns_per_tile: int = 0, hbm_budget_bytes: int = 0):
+    def __init__(self, device: int = 0, patterns_per_tile: int = 0, hbm_budget_bytes: int = 0, flags: int = 0):
         lib = load()
-        opt = pg_options(device, patterns_per_tile, hbm_budget_bytes)
+        opt = pg_options(device, patterns_per_tile, hbm_budget_bytes, flags)
         out = ctypes.c_void_p()
         check(lib.pg_create(ctypes.byref(opt), ctypes.byref(out)))
         self._ptr = out

@@ -2,6 +2,7 @@
 // assumptions: rooted binary tree, CTMC generators, root distribution, rate categories of
 // Section 2.5), level scheduling of the tree, the device layout of one problem and the launches
 // of one (or a batch of) evaluation(s).
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -61,6 +62,7 @@ struct pg_ctx {
     int max_range = 0;                            // cap on patterns per block (0 = kMaxRange)
     uint64_t budget = 0;
     uint64_t used = 0;
+    uint32_t flags = 0;
     std::vector<pg_handle *> handles;
 };
 
@@ -83,6 +85,7 @@ struct pg_handle {
     bool have_post = false;   // an enqueued post-order left partials a backward pass can use
     bool mstate = false;      // a general state space (pg_mstate.cu): md holds its layout
     pg::MDesc md{};
+    alignas(64) CUtensorMap tm_post, tm_pre, tm_tab;   // TMA descriptors of the tensor-core kernels
 };
 
 // ------------------------------------------------------------------------------------------
@@ -345,6 +348,31 @@ pg_status symmetric_eigensystem(const double *Q, int m, int md, float *UT, doubl
     return PG_OK;
 }
 
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// FP32 tiled tensor map with 32-float (128-byte, swizzled) inner boxes; rows beyond a dimension's
+// extent read as zero and are not written
+pg_status encode_map(CUtensorMap *m, void *base, int rank, const cuuint64_t *dims, const cuuint64_t *strides,
+                     const cuuint32_t *box) {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q{};
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !p)
+            return fail(PG_ERR_CUDA, "the driver provides no cuTensorMapEncodeTiled");
+        fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    const cuuint32_t es[3] = {1, 1, 1};
+    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, base, dims, strides, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(PG_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return PG_OK;
+}
+
 // upload of a problem with 5..64 states (pg_mstate.cu kernels)
 pg_status upload_m(pg_ctx *ctx, const pg_problem *pr, const TreePlan &tp, pg_handle **out) {
     const int N = pr->n_tips, m = pr->n_states, P = pr->n_patterns, C = pr->n_categories, M = pr->n_models;
@@ -366,7 +394,9 @@ pg_status upload_m(pg_ctx *ctx, const pg_problem *pr, const TreePlan &tp, pg_han
     const size_t o_UT = cv.take<float>(UT.size()), o_lam = cv.take<double>(lam.size());
     const size_t o_sq = cv.take<float>(sq.size()), o_isq = cv.take<float>(isq.size());
     const size_t o_bm = pr->branch_model ? cv.take<int>(n) : 0;
-    const size_t o_tab = cv.take<float>((size_t)n * C * pg::kTabKinds * pg::kTabFloats);
+    const bool tc = !(ctx->flags & PG_FLAG_SIMT_MSTATE);
+    const size_t o_tab = cv.take<float>((size_t)n * C * (tc ? (size_t)pg::kTcKinds * KP * KP
+                                                              : (size_t)pg::kTabKinds * pg::kTabFloats));
     const size_t part = (size_t)(N - 1) * C * Ps * KP;
     const size_t o_post = cv.take<float>(part), o_pre = cv.take<float>(part);
     const size_t o_pe = cv.take<int>((size_t)(N - 1) * C * Ps), o_qe = cv.take<int>((size_t)(N - 1) * C * Ps);
@@ -447,6 +477,24 @@ pg_status upload_m(pg_ctx *ctx, const pg_problem *pr, const TreePlan &tp, pg_han
     d.C = C;
     d.n_models = M;
     d.n_ptiles = n_pt;
+    d.tc = tc ? 1 : 0;
+    d.n_gslots = tc ? (P + pg::kTcTile - 1) / pg::kTcTile : n_pt;
+    if (tc && P > 0) {
+        const cuuint64_t pdims[3] = {(cuuint64_t)KP, (cuuint64_t)P, (cuuint64_t)(N - 1) * C};
+        const cuuint64_t pstr[2] = {(cuuint64_t)KP * 4, (cuuint64_t)Ps * KP * 4};
+        const cuuint32_t pbox[3] = {32, (cuuint32_t)pg::kTcTile, 1};
+        const cuuint64_t tdims[2] = {(cuuint64_t)KP, (cuuint64_t)n * C * pg::kTcKinds * KP};
+        const cuuint64_t tstr[1] = {(cuuint64_t)KP * 4};
+        const cuuint32_t tbox[2] = {32, (cuuint32_t)KP};
+        pg_status st = encode_map(&h->tm_post, d.post, 3, pdims, pstr, pbox);
+        if (st == PG_OK) st = encode_map(&h->tm_pre, d.pre, 3, pdims, pstr, pbox);
+        if (st == PG_OK) st = encode_map(&h->tm_tab, d.tabs, 2, tdims, tstr, tbox);
+        if (st != PG_OK) {
+            cudaFree(block);
+            delete h;
+            return st;
+        }
+    }
     for (int l = 0; l < pg::kMaxCat; ++l) {
         d.cw[l] = l < C ? pr->cat_weights[l] : 0.0;
         d.rates[l] = l < C ? pr->cat_rates[l] : 0.0;
@@ -512,12 +560,18 @@ pg_status enqueue_m(pg_handle *h, int skip, const double *d_b, double *d_logL, d
     cudaError_t e = cudaSuccess;
     if (fwd) {
         e = pg::launch_m_pmatrix(d, hess, s);
-        for (int lv = 0; e == cudaSuccess && lv < d.n_levels; ++lv)
-            e = pg::launch_m_post_level(d, h->level_off[lv], h->level_off[lv + 1] - h->level_off[lv], s);
+        for (int lv = 0; e == cudaSuccess && lv < d.n_levels; ++lv) {
+            const int o0 = h->level_off[lv], nd = h->level_off[lv + 1] - o0;
+            e = d.tc ? pg::launch_m_post_level_tc(d, &h->tm_post, &h->tm_tab, o0, nd, s)
+                     : pg::launch_m_post_level(d, o0, nd, s);
+        }
         if (e == cudaSuccess) e = pg::launch_m_root(d, s);
     }
-    for (int lv = d.n_levels - 1; bwd && e == cudaSuccess && lv >= 0; --lv)
-        e = pg::launch_m_pre_level(d, h->level_off[lv], h->level_off[lv + 1] - h->level_off[lv], hess, s);
+    for (int lv = d.n_levels - 1; bwd && e == cudaSuccess && lv >= 0; --lv) {
+        const int o0 = h->level_off[lv], nd = h->level_off[lv + 1] - o0;
+        e = d.tc ? pg::launch_m_pre_level_tc(d, &h->tm_post, &h->tm_pre, &h->tm_tab, o0, nd, hess, s)
+                 : pg::launch_m_pre_level(d, o0, nd, hess, s);
+    }
     if (e == cudaSuccess) e = pg::launch_m_reduce(d, hess, s);
     if (e != cudaSuccess) return fail(PG_ERR_CUDA, "launch: %s", cudaGetErrorString(e));
     h->last_stream = s;
@@ -559,6 +613,7 @@ pg_status pg_create(const pg_options *opt, pg_ctx **out) {
     c->device = o.device;
     c->max_range = o.patterns_per_tile;
     c->budget = o.hbm_budget_bytes;
+    c->flags = o.flags;
     DeviceGuard g(c->device);
     if (!g.ok) { delete c; return fail(PG_ERR_CUDA, "cannot select device %d", o.device); }
     if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || c->n_sm < 1) {

@@ -166,16 +166,31 @@ struct MDesc {
     const double *gscale;
     int skip;
     int n_tips, n_nodes, root, n_levels, P, Ps, m, C, n_models, n_ptiles;
+    int n_gslots;                  // per-branch gradient slots: pattern tiles of the pre-order kernel
+    int tc;                        // 1: tensor-core kernels and table layout, 0: SIMT
     double cw[kMaxCat], rates[kMaxCat];
     float pif[kMP];                // root frequencies, FP32 (pads 0)
     double pi[kMP];
 };
+
+// Tensor-core layout of the transition tables (pg_mtc.cu): per (branch, category) kTcKinds tables
+// of kMP x kMP FP32, row-major W[s][k] (the K-major B operand of Y[p][s] = sum_k X[p][k] W[s][k]):
+// D = P - I, G, their TF32 remainders (W - trunc_tf32(W)), D^T and remainder, H and remainder.
+// The identity part of P x and P^T q is added to the products in FP32 by the kernels.
+constexpr int kTcD = 0, kTcG = 1, kTcDlo = 2, kTcGlo = 3, kTcDT = 4, kTcDTlo = 5, kTcH = 6, kTcHlo = 7, kTcKinds = 8;
+constexpr int kTcTile = 128;   // patterns per item of the tensor-core kernels (the MMA's M)
 
 cudaError_t launch_m_pmatrix(const MDesc &d, bool hess, cudaStream_t s);
 cudaError_t launch_m_post_level(const MDesc &d, int o0, int nd, cudaStream_t s);
 cudaError_t launch_m_root(const MDesc &d, cudaStream_t s);
 cudaError_t launch_m_pre_level(const MDesc &d, int o0, int nd, bool hess, cudaStream_t s);
 cudaError_t launch_m_reduce(const MDesc &d, bool hess, cudaStream_t s);
+// tensor-core level kernels; the maps describe d.post, d.pre (3-D: state, pattern, node * C +
+// category) and d.tabs (2-D: state, table row) with 128-byte swizzled 32-float boxes
+cudaError_t launch_m_post_level_tc(const MDesc &d, const void *tm_post, const void *tm_tab, int o0, int nd,
+                                   cudaStream_t s);
+cudaError_t launch_m_pre_level_tc(const MDesc &d, const void *tm_post, const void *tm_pre, const void *tm_tab,
+                                  int o0, int nd, bool hess, cudaStream_t s);
 
 // launchers (pg_nt.cu); every problem of one launch shares C and precision
 template <int MAXB>

@@ -144,6 +144,11 @@ __device__ __forceinline__ void store_scaled(float *rows, int *exps, const MDesc
 //   M = U diag(f) U^T (FP32),  X[s][j] = M[s][j] sqrt(pi*_j) / sqrt(pi*_s)
 // stored transposed (DT, GT, HT: row j = column j of X) plus the row sums as the ambiguous-code
 // row (1 + row sums of D for P), and D row-major for the pre-order product P^T q.
+// With TC the tables take the tensor-core layout instead: row-major D, G, H and D^T, each with its
+// TF32 remainder W - trunc_tf32(W) (kTcKinds tables of kMP x kMP per branch and category).
+__device__ __forceinline__ float tf32_rem(float x) { return x - __uint_as_float(__float_as_uint(x) & 0xffffe000u); }
+
+template <bool TC>
 __global__ void __launch_bounds__(kMThreads) m_pmatrix_kernel(const __grid_constant__ MDesc d, int kinds) {
     __shared__ __align__(16) float UT[kMP * kMP];
     __shared__ __align__(16) float W[kMP * kMP];
@@ -202,6 +207,32 @@ __global__ void __launch_bounds__(kMThreads) m_pmatrix_kernel(const __grid_const
                 rs[a] += acc[a][b];
             }
             rs[a] = sum16(rs[a]);
+        }
+        if (TC) {
+            float *base = d.tabs + (size_t)(c * d.C + l) * kTcKinds * kMP * kMP;
+            const int hk = kind == 0 ? kTcD : (kind == 1 ? kTcG : kTcH);
+            const int lk = kind == 0 ? kTcDlo : (kind == 1 ? kTcGlo : kTcHlo);
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {   // row-major
+                const int s = 4 * ts + a;
+                const float v[4] = {acc[a][0], acc[a][1], acc[a][2], acc[a][3]};
+                const size_t o = (size_t)s * kMP + 4 * tj;
+                *reinterpret_cast<float4 *>(base + (size_t)hk * kMP * kMP + o) = f4(v[0], v[1], v[2], v[3]);
+                *reinterpret_cast<float4 *>(base + (size_t)lk * kMP * kMP + o) =
+                    f4(tf32_rem(v[0]), tf32_rem(v[1]), tf32_rem(v[2]), tf32_rem(v[3]));
+            }
+            if (kind == 0) {
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {   // D^T: row j holds column j of D
+                    const int j = 4 * tj + b;
+                    const float v[4] = {acc[0][b], acc[1][b], acc[2][b], acc[3][b]};
+                    const size_t o = (size_t)j * kMP + 4 * ts;
+                    *reinterpret_cast<float4 *>(base + (size_t)kTcDT * kMP * kMP + o) = f4(v[0], v[1], v[2], v[3]);
+                    *reinterpret_cast<float4 *>(base + (size_t)kTcDTlo * kMP * kMP + o) =
+                        f4(tf32_rem(v[0]), tf32_rem(v[1]), tf32_rem(v[2]), tf32_rem(v[3]));
+                }
+            }
+            continue;
         }
         const int tk = kind == 0 ? kTabDT : (kind == 1 ? kTabGT : kTabHT);
         float *T = d.tabs + ((size_t)(c * d.C + l) * kTabKinds + tk) * kTabFloats;
@@ -446,8 +477,8 @@ __global__ void __launch_bounds__(kMThreads) m_pre_kernel(const __grid_constant_
             g += red[side][0][j];
             h += red[side][1][j];
         }
-        d.gpart[(size_t)cs[side] * d.n_ptiles + pt] = g;
-        if (HESS) d.hpart[(size_t)cs[side] * d.n_ptiles + pt] = h;
+        d.gpart[(size_t)cs[side] * d.n_gslots + pt] = g;
+        if (HESS) d.hpart[(size_t)cs[side] * d.n_gslots + pt] = h;
     }
 }
 
@@ -464,10 +495,10 @@ __global__ void __launch_bounds__(256) m_reduce_kernel(const __grid_constant__ M
     }
     double g = 0.0, h = 0.0;
     if (gw != d.root) {
-        for (int j = lane; j < d.n_ptiles; j += 32) g += d.gpart[(size_t)gw * d.n_ptiles + j];
+        for (int j = lane; j < d.n_gslots; j += 32) g += d.gpart[(size_t)gw * d.n_gslots + j];
         g = warp_sum(g);
         if (want_hess) {
-            for (int j = lane; j < d.n_ptiles; j += 32) h += d.hpart[(size_t)gw * d.n_ptiles + j];
+            for (int j = lane; j < d.n_gslots; j += 32) h += d.hpart[(size_t)gw * d.n_gslots + j];
             h = warp_sum(h);
         }
     }
@@ -485,7 +516,8 @@ constexpr size_t kPreSmem = sizeof(float) * (kTabFloats + 4 * kTileFloats);
 
 cudaError_t launch_m_pmatrix(const MDesc &d, bool hess, cudaStream_t s) {
     if (d.n_nodes * d.C <= 0) return cudaSuccess;
-    m_pmatrix_kernel<<<d.n_nodes * d.C, kMThreads, 0, s>>>(d, hess ? 3 : 2);
+    if (d.tc) m_pmatrix_kernel<true><<<d.n_nodes * d.C, kMThreads, 0, s>>>(d, hess ? 3 : 2);
+    else m_pmatrix_kernel<false><<<d.n_nodes * d.C, kMThreads, 0, s>>>(d, hess ? 3 : 2);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,616 @@
+// Tensor-core kernels of the general-state path (5..64 states): the products P x, G x, H x of the
+// post-order (Section 2.3) and pre-order (Section 2.4) passes and P^T q of the pre-order, as
+// Y[p][s] = sum_k X[p][k] W[s][k] on tcgen05 (kind::tf32, FP32 accumulation in tensor memory).
+// With P = I + D only D x and D^T q go through the tensor core; the identity part (x, q) is added
+// in FP32 by the threads.  The tensor core's accumulation truncates, and P x sums positive terms
+// only, so keeping the O(1) identity out of it keeps that bias to the size of D x.
+//
+// One item is a tile of kTcTile = 128 patterns (the MMA's M) of one node; thread t of the 128-thread
+// block owns pattern row t, which is TMEM lane t of every accumulator, so per-pattern reductions
+// (the largest state of a column, q . G x) stay in one thread.  Operand tiles [128 x 64] FP32 and
+// tables [64 x 64] arrive by TMA with 128-byte swizzling (the canonical K-major layout); a tip
+// child's rows are written as one-hot (or all-ones) rows, so tips and internal children share the
+// product.  Each product runs three TF32 passes, hi x hi + hi x lo + lo x hi, where the tensor core
+// truncates an FP32 operand to its TF32 part (hi) and lo = x - trunc(x) is formed by the threads
+// for the rows and stored with the tables: about FP32 accuracy (error ~2^-21 relative per term).
+// Results leave through a swizzled staging tile and a TMA store; exponents with plain stores.
+//
+// Every wait is bounded (kWaitLimitCycles); a block that gives up records PG_ERR_TIMEOUT, lets its
+// copies land, frees its tensor memory and returns.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "pg_device.cuh"
+#include "pg_internal.cuh"
+
+namespace pg {
+namespace {
+
+using namespace dev;
+
+constexpr int kTcThreads = 128;
+constexpr uint32_t kRowTile = kTcTile * kMP * 4;   // 32 KB: one [128 x 64] FP32 tile
+constexpr uint32_t kRowKB = kTcTile * 128;         // 16 KB: its 32-state half (one K block)
+constexpr uint32_t kTab = kMP * kMP * 4;           // 16 KB: one [64 x 64] table
+constexpr uint32_t kTabKB = kMP * 128;             // 8 KB: its 32-state half
+
+// ---- PTX wrappers ----------------------------------------------------------------------------------
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(slot)), "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols));
+}
+__device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// instruction descriptor: kind::tf32, FP32 accumulator, both operands K-major, M x N
+__device__ __forceinline__ uint32_t idesc_tf32(uint32_t M, uint32_t N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                 ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+// acc (+)= A[128 x 64] * B[n x 64]^T in 8 steps of K = 8 (two 32-state K blocks of 4 steps)
+__device__ __forceinline__ void mma_tile(uint32_t acc, uint32_t a, uint32_t b, uint32_t n, bool accumulate) {
+    const uint32_t id = idesc_tf32(kTcTile, n);
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+        const uint32_t kb = kk >> 2, ko = (kk & 3) * 32;
+        mma_tf32(acc, umma_desc(a + kb * kRowKB + ko), umma_desc(b + kb * n * 128 + ko), id,
+                 (accumulate || kk > 0) ? 1u : 0u);
+    }
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *m, int x, int y, uint64_t *bar) {
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
+                 ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(m)), "r"(x), "r"(y), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *m, int x, int y, int z, uint64_t *bar) {
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n"
+                 ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(m)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *m, const void *src, int x, int y, int z) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];\n"
+                 ::"l"(reinterpret_cast<uint64_t>(m)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(src))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+
+// byte offset of 16-byte chunk cc (states 4 cc .. 4 cc + 3) of row r of a swizzled tile of `rows`
+// rows: two 32-state K blocks, rows 128 bytes apart, chunk index XOR (row mod 8)
+__device__ __forceinline__ uint32_t sw(int r, int cc, int rows) {
+    return (uint32_t)((cc >> 3) * rows * 128 + r * 128 + (((cc & 7) ^ (r & 7)) << 4));
+}
+__device__ __forceinline__ float tf32_lo(float x) { return x - __uint_as_float(__float_as_uint(x) & 0xffffe000u); }
+__device__ __forceinline__ float4 lo4(float4 v) { return f4(tf32_lo(v.x), tf32_lo(v.y), tf32_lo(v.z), tf32_lo(v.w)); }
+
+__device__ __forceinline__ unsigned char *align1024(unsigned char *p) {
+    return reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(p) + 1023) & ~(uintptr_t)1023);
+}
+
+// one-hot (or, for a code >= m, all-ones over the m states) row t of a tip child, zero past cnt
+__device__ __forceinline__ void tip_row(unsigned char *X, const MDesc &d, int c, int p0, int cnt, int t) {
+    const int y = t < cnt ? (int)__ldg(d.tips + (size_t)c * d.Ps + p0 + t) : -1;
+    const bool amb = y >= d.m;
+#pragma unroll
+    for (int cc = 0; cc < kMP / 4; ++cc) {
+        float v[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int s = 4 * cc + j;
+            v[j] = (y >= 0 && (amb ? s < d.m : s == y)) ? 1.f : 0.f;
+        }
+        *reinterpret_cast<float4 *>(X + sw(t, cc, kTcTile)) = f4(v[0], v[1], v[2], v[3]);
+    }
+}
+// the TF32 remainders of row t of a loaded tile
+__device__ __forceinline__ void lo_row(const unsigned char *X, unsigned char *XL, int t) {
+#pragma unroll
+    for (int cc = 0; cc < kMP / 4; ++cc)
+        *reinterpret_cast<float4 *>(XL + sw(t, cc, kTcTile)) = lo4(*reinterpret_cast<const float4 *>(X + sw(t, cc, kTcTile)));
+}
+// a table (tables consecutive kinds k0 .. k0 + nk - 1 of (c, l), each 64 rows) into a swizzled
+// [64 nk x 64] operand at dst
+__device__ __forceinline__ void load_tables(unsigned char *dst, const CUtensorMap *tm, const MDesc &d, int c, int l,
+                                            int k0, int nk, uint64_t *bar) {
+    const int row0 = ((c * d.C + l) * kTcKinds + k0) * kMP;
+    for (int kb = 0; kb < 2; ++kb)
+        for (int j = 0; j < nk; ++j)
+            tma_load_2d(dst + kb * nk * kTabKB + j * kTabKB, tm, kb * 32, row0 + j * kMP, bar);
+}
+
+// every thread waits for the barrier's current phase; the phase advances only if all saw it
+__device__ __forceinline__ bool wait_all(uint64_t *bar, uint32_t &phase) {
+    const bool ok = __syncthreads_and(mbar_wait_bounded(bar, phase, kWaitLimitCycles)) != 0;
+    if (ok) phase ^= 1u;
+    return ok;
+}
+// after a wait gave up: let the copies or products behind both barriers finish (bounded)
+__device__ __forceinline__ void drain(uint64_t *bar, uint32_t ph_load, uint32_t ph_mma, bool load_pending,
+                                      bool mma_pending) {
+    if (load_pending) mbar_wait_bounded(&bar[0], ph_load, kWaitLimitCycles);
+    if (mma_pending) mbar_wait_bounded(&bar[1], ph_mma, kWaitLimitCycles);
+}
+
+// row t of a tile (states 16 ch .. 16 ch + 15) from a swizzled [128 x 64] tile
+__device__ __forceinline__ void row16(const unsigned char *X, int t, int ch, float v[16]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float4 x = *reinterpret_cast<const float4 *>(X + sw(t, ch * 4 + q, kTcTile));
+        v[4 * q] = x.x;
+        v[4 * q + 1] = x.y;
+        v[4 * q + 2] = x.z;
+        v[4 * q + 3] = x.w;
+    }
+}
+__device__ __forceinline__ void put16(unsigned char *X, int t, int ch, const float v[16], int e) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<float4 *>(X + sw(t, ch * 4 + q, kTcTile)) =
+            scale4(f4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]), e);
+}
+
+// q_c = qt + (D^T qt) for row t: the accumulator at ta plus the row of qt in X, scaled into
+// [1, 2) by its largest state and written to the staging tile (which may be X itself)
+__device__ __forceinline__ int store_sum_scaled(uint32_t ta, const unsigned char *X, unsigned char *stage, int t) {
+    float mx = 0.f;
+#pragma unroll
+    for (int ch = 0; ch < 4; ++ch) {
+        float a[16], x[16];
+        tmem_ld16(ta + ch * 16, a);
+        row16(X, t, ch, x);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) mx = fmaxf(mx, a[j] + x[j]);
+    }
+    const int e = scale_exponent(mx);
+#pragma unroll
+    for (int ch = 0; ch < 4; ++ch) {
+        float a[16], x[16];
+        tmem_ld16(ta + ch * 16, a);
+        row16(X, t, ch, x);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) a[j] += x[j];
+        put16(stage, t, ch, a, e);
+    }
+    return e;
+}
+
+// ---- post-order level: item = (node, category, 128-pattern tile) ------------------------------------
+__global__ void __launch_bounds__(kTcThreads, 1)
+m_post_tc_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtensorMap tm_post,
+                 const __grid_constant__ CUtensorMap tm_tab, int o0, int n_pt) {
+    extern __shared__ __align__(1024) unsigned char tc_raw[];
+    unsigned char *sm = align1024(tc_raw);
+    unsigned char *XA = sm, *XL = sm + kRowTile, *TB = sm + 2 * kRowTile;   // rows, remainders, P hi|lo
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ uint32_t tmem_slot;
+    const int C = d.C, N = d.n_tips, t = threadIdx.x, warp = t >> 5;
+    const int per_node = C * n_pt;
+    const int u = blockIdx.x / per_node, rem = blockIdx.x - u * per_node, l = rem / n_pt, pt = rem - l * n_pt;
+    const int4 op = __ldg(d.ops + o0 + u);
+    const int k = op.x, p0 = pt * kTcTile, cnt = min(kTcTile, d.P - p0);
+    if (warp == 0) tmem_alloc(&tmem_slot, 128);
+    if (t == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+    }
+    tc_before();
+    __syncthreads();
+    tc_after();
+    const uint32_t tmem = tmem_slot, lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    uint32_t ph_load = 0, ph_mma = 0;
+    bool ok = true, load_pending = false, mma_pending = false;
+    int E = 0;
+    float a0[kMP];   // P x of the first child: its D x (TMEM) plus its rows
+    for (int side = 0; side < 2 && ok; ++side) {
+        const int c = side ? op.z : op.y;
+        const bool tip = c < N;
+        if (t == 0) {
+            mbar_arrive_expect(&bar[0], 2 * kTab + (tip ? 0u : kRowTile));
+            load_tables(TB, &tm_tab, d, c, l, kTcD, 1, &bar[0]);
+            load_tables(TB + kTab, &tm_tab, d, c, l, kTcDlo, 1, &bar[0]);
+            if (!tip)
+                for (int kb = 0; kb < 2; ++kb) tma_load_3d(XA + kb * kRowKB, &tm_post, kb * 32, p0, (c - N) * C + l, &bar[0]);
+        }
+        if (tip) tip_row(XA, d, c, p0, cnt, t);
+        else if (t < cnt) E += __ldcg(d.pe + ((size_t)(c - N) * C + l) * d.Ps + p0 + t);
+        load_pending = true;
+        ok = wait_all(&bar[0], ph_load);
+        load_pending = !ok;
+        if (!ok) break;
+        if (!tip) lo_row(XA, XL, t);
+        fence_async_smem();
+        tc_before();
+        __syncthreads();
+        if (t == 0) {
+            tc_after();
+            const uint32_t acc = tmem + side * 64;
+            mma_tile(acc, smem_u32(XA), smem_u32(TB), kMP, false);
+            mma_tile(acc, smem_u32(XA), smem_u32(TB + kTab), kMP, true);
+            if (!tip) mma_tile(acc, smem_u32(XL), smem_u32(TB), kMP, true);
+            mma_commit(&bar[1]);
+        }
+        mma_pending = true;
+        ok = wait_all(&bar[1], ph_mma);
+        mma_pending = !ok;
+        if (ok && side == 0) {   // keep P x of the first child before its rows are replaced
+            tc_after();
+#pragma unroll
+            for (int ch = 0; ch < 4; ++ch) {
+                float a[16], x[16];
+                tmem_ld16(lane_base + ch * 16, a);
+                row16(XA, t, ch, x);
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 16; ++j) a0[16 * ch + j] = a[j] + x[j];
+            }
+            __syncthreads();   // every row read before the next copies land in XA
+        }
+    }
+    if (ok) {
+        tc_after();
+        float mx = 0.f;
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) {
+            float a[16], x[16];
+            tmem_ld16(lane_base + 64 + ch * 16, a);
+            row16(XA, t, ch, x);
+            tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 16; ++j) mx = fmaxf(mx, a0[16 * ch + j] * (a[j] + x[j]));
+        }
+        const int e = scale_exponent(mx);
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) {
+            float a[16], x[16];
+            tmem_ld16(lane_base + 64 + ch * 16, a);
+            row16(XA, t, ch, x);
+            tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 16; ++j) a[j] = a0[16 * ch + j] * (a[j] + x[j]);
+            put16(XA, t, ch, a, e);   // the row's own slots: read above, by this thread only
+        }
+        if (t < cnt) __stcg(d.pe + ((size_t)(k - N) * C + l) * d.Ps + p0 + t, E + e);
+        fence_async_smem();
+        __syncthreads();
+        if (t == 0) {
+            for (int kb = 0; kb < 2; ++kb) tma_store_3d(&tm_post, XA + kb * kRowKB, kb * 32, p0, (k - N) * C + l);
+            bulk_commit();
+            bulk_wait_read0();
+        }
+    } else if (t == 0) {
+        atomicOr(d.status, kStatusTimeout);
+        drain(bar, ph_load, ph_mma, load_pending, mma_pending);
+    }
+    tc_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 128);
+}
+
+// ---- pre-order level with the gradient: item = (node, 128-pattern tile), categories in turn -------------
+// Per category: A_c = x_c [D_c; G_c]^T (TMEM columns 128 side .. +127: D_c x_c | u_c = G_c x_c),
+// a_c = x_c + D_c x_c,
+// optionally H_c x_c (columns 256 + 64 side); qt_c = q_k o a_other (q_root = pi), the branch terms
+// qt_c . u_c (and qt_c . H_c x_c) 2^{E} / L_p; for an internal child q_c = P_c^T qt_c (columns
+// 128 side .. +63 again: D_c^T qt_c, plus qt_c) scaled and stored.
+template <bool HESS>
+__global__ void __launch_bounds__(kTcThreads, 1)
+m_pre_tc_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtensorMap tm_post,
+                const __grid_constant__ CUtensorMap tm_pre, const __grid_constant__ CUtensorMap tm_tab, int o0, int n_pt) {
+    extern __shared__ __align__(1024) unsigned char tc_raw[];
+    unsigned char *sm = align1024(tc_raw);
+    unsigned char *X[2] = {sm, sm + 2 * kRowTile};            // rows (hi) then remainders (lo) per child
+    unsigned char *TB = sm + 4 * kRowTile;                     // tables: up to [128 x 64] hi | lo
+    unsigned char *QK = sm + 4 * kRowTile + 2 * 2 * kTab;      // q_k rows
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ uint32_t tmem_slot;
+    __shared__ double red[2][2][kTcThreads / 32];
+    constexpr uint32_t kCols = HESS ? 512 : 256;
+    const int C = d.C, N = d.n_tips, t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int u = blockIdx.x / n_pt, pt = blockIdx.x - u * n_pt;
+    const int4 op = __ldg(d.ops + o0 + u);
+    const int k = op.x, p0 = pt * kTcTile, cnt = min(kTcTile, d.P - p0);
+    const bool root = k == d.root;
+    const int cs[2] = {op.y, op.z};
+    const bool tip[2] = {op.y < N, op.z < N};
+    if (warp == 0) tmem_alloc(&tmem_slot, kCols);
+    if (t == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+    }
+    tc_before();
+    __syncthreads();
+    tc_after();
+    const uint32_t tmem = tmem_slot, lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    const bool on = t < cnt;
+    const float inv = on ? __ldcg(d.site_invL + p0 + t) : 0.f;
+    const int Er = on ? __ldcg(d.site_Er + p0 + t) : 0;
+    float dsum[2] = {0.f, 0.f}, hsum[2] = {0.f, 0.f};
+    uint32_t ph_load = 0, ph_mma = 0;
+    bool ok = true, load_pending = false, mma_pending = false;
+    for (int l = 0; l < C && ok; ++l) {
+        const int Eq = (on && !root) ? __ldcg(d.qe + ((size_t)(k - N) * C + l) * d.Ps + p0 + t) : 0;
+        int Ex[2];
+        for (int side = 0; side < 2; ++side)
+            Ex[side] = (on && !tip[side]) ? __ldcg(d.pe + ((size_t)(cs[side] - N) * C + l) * d.Ps + p0 + t) : 0;
+        // rows of q_k and both children, [P; G] of child 0
+        if (t == 0) {
+            uint32_t bytes = 4 * kTab;
+            if (!root) bytes += kRowTile;
+            for (int side = 0; side < 2; ++side) bytes += tip[side] ? 0u : kRowTile;
+            mbar_arrive_expect(&bar[0], bytes);
+            if (!root)
+                for (int kb = 0; kb < 2; ++kb) tma_load_3d(QK + kb * kRowKB, &tm_pre, kb * 32, p0, (k - N) * C + l, &bar[0]);
+            for (int side = 0; side < 2; ++side)
+                if (!tip[side])
+                    for (int kb = 0; kb < 2; ++kb)
+                        tma_load_3d(X[side] + kb * kRowKB, &tm_post, kb * 32, p0, (cs[side] - N) * C + l, &bar[0]);
+            load_tables(TB, &tm_tab, d, cs[0], l, kTcD, 2, &bar[0]);
+            load_tables(TB + 2 * kTab, &tm_tab, d, cs[0], l, kTcDlo, 2, &bar[0]);
+        }
+        for (int side = 0; side < 2; ++side)
+            if (tip[side]) tip_row(X[side], d, cs[side], p0, cnt, t);
+        load_pending = true;
+        ok = wait_all(&bar[0], ph_load);
+        load_pending = !ok;
+        if (!ok) break;
+        for (int side = 0; side < 2; ++side)
+            if (!tip[side]) lo_row(X[side], X[side] + kRowTile, t);
+        fence_async_smem();
+        // the products of both children: [P; G] (then H) tables of child `side`
+        for (int side = 0; side < 2 && ok; ++side) {
+            for (int pass = 0; pass < (HESS ? 2 : 1) && ok; ++pass) {
+                if (side > 0 || pass > 0) {   // the next tables, once the previous products have read TB
+                    if (t == 0) {
+                        mbar_arrive_expect(&bar[0], pass ? 2 * kTab : 4 * kTab);
+                        if (pass) {
+                            load_tables(TB, &tm_tab, d, cs[side], l, kTcH, 1, &bar[0]);
+                            load_tables(TB + kTab, &tm_tab, d, cs[side], l, kTcHlo, 1, &bar[0]);
+                        } else {
+                            load_tables(TB, &tm_tab, d, cs[side], l, kTcD, 2, &bar[0]);
+                            load_tables(TB + 2 * kTab, &tm_tab, d, cs[side], l, kTcDlo, 2, &bar[0]);
+                        }
+                    }
+                    load_pending = true;
+        ok = wait_all(&bar[0], ph_load);
+        load_pending = !ok;
+                    if (!ok) break;
+                }
+                tc_before();
+                __syncthreads();
+                if (t == 0) {
+                    tc_after();
+                    const uint32_t n = pass ? kMP : 2 * kMP;
+                    const uint32_t acc = tmem + (pass ? 256 + 64 * side : 128 * side);
+                    const uint32_t xa = smem_u32(X[side]), xl = xa + kRowTile, tb = smem_u32(TB);
+                    const uint32_t tl = tb + n * kMP * 4;
+                    mma_tile(acc, xa, tb, n, false);
+                    mma_tile(acc, xa, tl, n, true);
+                    if (!tip[side]) mma_tile(acc, xl, tb, n, true);
+                    mma_commit(&bar[1]);
+                }
+                mma_pending = true;
+        ok = wait_all(&bar[1], ph_mma);
+        mma_pending = !ok;
+            }
+        }
+        if (!ok) break;
+        // qt_c = q_k o a_other, the branch terms, and qt of internal children as MMA operands
+        tc_after();
+        float dot[2] = {0.f, 0.f}, hdot[2] = {0.f, 0.f};
+#pragma unroll 1
+        for (int ch = 0; ch < 4; ++ch) {
+            float a0[16], u0[16], a1[16], u1[16], x0[16], x1[16];
+            tmem_ld16(lane_base + ch * 16, a0);
+            tmem_ld16(lane_base + 64 + ch * 16, u0);
+            tmem_ld16(lane_base + 128 + ch * 16, a1);
+            tmem_ld16(lane_base + 192 + ch * 16, u1);
+            row16(X[0], t, ch, x0);
+            row16(X[1], t, ch, x1);
+            tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {   // P x = x + D x
+                a0[j] += x0[j];
+                a1[j] += x1[j];
+            }
+            float qk[16];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 v = root ? f4(d.pif[16 * ch + 4 * q], d.pif[16 * ch + 4 * q + 1], d.pif[16 * ch + 4 * q + 2],
+                                           d.pif[16 * ch + 4 * q + 3])
+                                      : *reinterpret_cast<const float4 *>(QK + sw(t, ch * 4 + q, kTcTile));
+                qk[4 * q] = v.x;
+                qk[4 * q + 1] = v.y;
+                qk[4 * q + 2] = v.z;
+                qk[4 * q + 3] = v.w;
+            }
+            float q0[16], q1[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                q0[j] = qk[j] * a1[j];
+                q1[j] = qk[j] * a0[j];
+                dot[0] = fmaf(q0[j], u0[j], dot[0]);
+                dot[1] = fmaf(q1[j], u1[j], dot[1]);
+            }
+            if (HESS) {
+                float h0[16], h1[16];
+                tmem_ld16(lane_base + 256 + ch * 16, h0);
+                tmem_ld16(lane_base + 320 + ch * 16, h1);
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    hdot[0] = fmaf(q0[j], h0[j], hdot[0]);
+                    hdot[1] = fmaf(q1[j], h1[j], hdot[1]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 v0 = f4(q0[4 * q], q0[4 * q + 1], q0[4 * q + 2], q0[4 * q + 3]);
+                const float4 v1 = f4(q1[4 * q], q1[4 * q + 1], q1[4 * q + 2], q1[4 * q + 3]);
+                if (!tip[0]) {
+                    *reinterpret_cast<float4 *>(X[0] + sw(t, ch * 4 + q, kTcTile)) = v0;
+                    *reinterpret_cast<float4 *>(X[0] + kRowTile + sw(t, ch * 4 + q, kTcTile)) = lo4(v0);
+                }
+                if (!tip[1]) {
+                    *reinterpret_cast<float4 *>(X[1] + sw(t, ch * 4 + q, kTcTile)) = v1;
+                    *reinterpret_cast<float4 *>(X[1] + kRowTile + sw(t, ch * 4 + q, kTcTile)) = lo4(v1);
+                }
+            }
+        }
+        {
+            const int dE = Eq + Ex[0] + Ex[1] - Er;   // the same for both child branches
+            const float cw = (float)d.cw[l];
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                dsum[side] += cw * ldexpf(dot[side], dE) * inv;
+                if (HESS) hsum[side] += cw * ldexpf(hdot[side], dE) * inv;
+            }
+        }
+        fence_async_smem();
+        // q_c = P_c^T qt_c for the internal children, staged through QK (side 0) or X[0] (side 1)
+        for (int side = 0; side < 2 && ok; ++side) {
+            if (tip[side]) continue;
+            const int c = cs[side];
+            if (t == 0) {
+                mbar_arrive_expect(&bar[0], 2 * kTab);
+                load_tables(TB, &tm_tab, d, c, l, kTcDT, 1, &bar[0]);
+                load_tables(TB + kTab, &tm_tab, d, c, l, kTcDTlo, 1, &bar[0]);
+            }
+            tc_before();
+            load_pending = true;
+        ok = wait_all(&bar[0], ph_load);
+        load_pending = !ok;
+            if (!ok) break;
+            if (t == 0) {
+                tc_after();
+                const uint32_t acc = tmem + 128 * side;
+                const uint32_t xa = smem_u32(X[side]), xl = xa + kRowTile, tb = smem_u32(TB);
+                mma_tile(acc, xa, tb, kMP, false);
+                mma_tile(acc, xa, tb + kTab, kMP, true);
+                mma_tile(acc, xl, tb, kMP, true);
+                mma_commit(&bar[1]);
+            }
+            mma_pending = true;
+        ok = wait_all(&bar[1], ph_mma);
+        mma_pending = !ok;
+            if (!ok) break;
+            tc_after();
+            unsigned char *stage = side ? X[0] : QK;
+            const int e = store_sum_scaled(lane_base + 128 * side, X[side], stage, t);
+            if (on) __stcg(d.qe + ((size_t)(c - N) * C + l) * d.Ps + p0 + t, Eq + Ex[1 - side] + e);
+            fence_async_smem();
+            __syncthreads();
+            if (t == 0) {
+                for (int kb = 0; kb < 2; ++kb) tma_store_3d(&tm_pre, stage + kb * kRowKB, kb * 32, p0, (c - N) * C + l);
+                bulk_commit();
+                bulk_wait_read0();   // the staging tile is read before the next category's copies
+            }
+            __syncthreads();
+        }
+    }
+    if (ok) {
+        // per child branch: sum over the tile's patterns of w_p d_p and w_p (h_p - d_p^2)
+        const double w = on ? d.weights[p0 + t] : 0.0;
+        for (int side = 0; side < 2; ++side) {
+            double g = w != 0.0 ? w * (double)dsum[side] : 0.0;
+            double h = (HESS && w != 0.0) ? w * ((double)hsum[side] - (double)dsum[side] * (double)dsum[side]) : 0.0;
+            g = warp_sum(g);
+            h = warp_sum(h);
+            if (lane == 0) {
+                red[side][0][warp] = g;
+                red[side][1][warp] = h;
+            }
+        }
+        __syncthreads();
+        if (t < 2) {
+            double g = 0.0, h = 0.0;
+            for (int j = 0; j < kTcThreads / 32; ++j) {
+                g += red[t][0][j];
+                h += red[t][1][j];
+            }
+            d.gpart[(size_t)cs[t] * d.n_gslots + pt] = g;
+            if (HESS) d.hpart[(size_t)cs[t] * d.n_gslots + pt] = h;
+        }
+    } else if (t == 0) {
+        atomicOr(d.status, kStatusTimeout);
+        drain(bar, ph_load, ph_mma, load_pending, mma_pending);
+    }
+    tc_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, kCols);
+}
+
+constexpr size_t kPostTcSmem = 1024 + 2 * kRowTile + 2 * kTab;
+constexpr size_t kPreTcSmem = 1024 + 4 * kRowTile + 4 * kTab + kRowTile;
+
+}  // namespace
+
+cudaError_t launch_m_post_level_tc(const MDesc &d, const void *tm_post, const void *tm_tab, int o0, int nd,
+                                   cudaStream_t s) {
+    const int n_pt = (d.P + kTcTile - 1) / kTcTile;
+    if (nd <= 0 || n_pt <= 0) return cudaSuccess;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(m_post_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPostTcSmem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    m_post_tc_kernel<<<nd * d.C * n_pt, kTcThreads, kPostTcSmem, s>>>(
+        d, *static_cast<const CUtensorMap *>(tm_post), *static_cast<const CUtensorMap *>(tm_tab), o0, n_pt);
+    return cudaGetLastError();
+}
+
+template <bool HESS>
+cudaError_t launch_pre_tc(const MDesc &d, const void *tm_post, const void *tm_pre, const void *tm_tab, int o0, int nd,
+                          int n_pt, cudaStream_t s) {
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(m_pre_tc_kernel<HESS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPreTcSmem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    m_pre_tc_kernel<HESS><<<nd * n_pt, kTcThreads, kPreTcSmem, s>>>(
+        d, *static_cast<const CUtensorMap *>(tm_post), *static_cast<const CUtensorMap *>(tm_pre),
+        *static_cast<const CUtensorMap *>(tm_tab), o0, n_pt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_m_pre_level_tc(const MDesc &d, const void *tm_post, const void *tm_pre, const void *tm_tab,
+                                  int o0, int nd, bool hess, cudaStream_t s) {
+    const int n_pt = (d.P + kTcTile - 1) / kTcTile;
+    if (nd <= 0 || n_pt <= 0) return cudaSuccess;
+    return hess ? launch_pre_tc<true>(d, tm_post, tm_pre, tm_tab, o0, nd, n_pt, s)
+                : launch_pre_tc<false>(d, tm_post, tm_pre, tm_tab, o0, nd, n_pt, s);
+}
+
+}  // namespace pg
