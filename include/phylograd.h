@@ -97,6 +97,7 @@ typedef struct pg_problem {
     const double *root_freqs;
     const double *cat_rates;
     const double *cat_weights;
+    int32_t tip_stride;         /* row pitch of tip_states in bytes (>= n_patterns); 0 = n_patterns */
 } pg_problem;
 
 typedef struct pg_handle_info {
@@ -199,6 +200,51 @@ pg_status pg_clock_grad_async(pg_handle *const *hs, int32_t k, const double *con
                               const double *const *d_t, const double *const *d_grad_b,
                               double *const *d_grad_eps, double *d_grad_mu, double *const *d_grad_t,
                               double *const *d_grad_rate, void *stream);
+
+/* ---- serving: continuous batching of requests (no counterpart in the paper; the workload of
+ * independent logL + gradient requests that arrive over time) ----------------------------------
+ *
+ * A server owns one device arena and max_inflight slots (a CUDA stream each).  Requests queue in
+ * arrival order; a worker thread admits the oldest while a slot and room in the arena are free,
+ * evaluates each on its own slot with the launches of pg_eval_async (so its results are the same
+ * bits whether it runs alone or among others) and retires it when its copies complete.  Requests
+ * that arrive while others run are admitted as slots and memory free up and overlap with them on
+ * the device.  max_inflight = 1 gives the plain path: one request at a time, no overlap. */
+typedef struct pg_server pg_server;
+
+typedef struct pg_server_options {
+    int32_t max_inflight;   /* requests on the device at once (slots); 0 = 4                    */
+    int32_t reserved;
+    uint64_t arena_bytes;   /* device bytes for the requests' data; 0 = 60% of the free memory;
+                               counted against the context's budget                             */
+} pg_server_options;
+
+typedef struct pg_request {
+    const pg_problem *problem;   /* host; the struct and its arrays stay valid until completion  */
+    const double *b;             /* host [2N-1] branch lengths                                   */
+    double *logL;                /* host outputs, written at completion (each may be NULL)       */
+    double *grad;                /* [2N-1]                                                       */
+    double *hess;                /* [2N-1]                                                       */
+} pg_request;
+
+typedef struct pg_request_info {
+    int32_t status;              /* the request's pg_status                                      */
+    int32_t reserved;
+    double submit_s, start_s, done_s;   /* steady-clock seconds since the server was created:
+                                           submission, admission to the device, completion      */
+} pg_request_info;
+
+/* Errors: PG_ERR_INVALID (NULL ctx/out, max_inflight < 0), PG_ERR_OOM (arena larger than the
+ * budget or than the device can give), PG_ERR_CUDA. */
+pg_status pg_server_create(pg_ctx *ctx, const pg_server_options *opt, pg_server **out);
+/* Queue a request (non-blocking); *ticket identifies it for pg_server_wait. */
+pg_status pg_server_submit(pg_server *s, const pg_request *rq, uint64_t *ticket);
+/* Block until the request completes, fill *info (may be NULL) and return its status (a problem
+ * that cannot be uploaded, e.g. larger than the whole arena, completes with that error).  Each
+ * ticket is waited for once. */
+pg_status pg_server_wait(pg_server *s, uint64_t ticket, pg_request_info *info);
+/* Finish every queued request, then release the arena, streams and threads. */
+pg_status pg_server_destroy(pg_server *s);
 
 /* Wait for the handle's last evaluation and return its device-side status (PG_OK,
  * PG_ERR_INVALID for a bad branch length, PG_ERR_NUMERIC for a failed site likelihood). */

@@ -22,7 +22,8 @@ EXPORTED = ("pg_create", "pg_destroy", "pg_upload", "pg_free", "pg_eval", "pg_ev
             "pg_eval_batch_async", "pg_eval_status", "pg_get_info", "pg_set_phase_timing",
             "pg_get_phase_times", "pg_eval_noalloc", "pg_status_string", "pg_last_error",
             "pg_forward_async", "pg_backward_async", "pg_forward_batch_async",
-            "pg_backward_batch_async", "pg_clock_lengths_async", "pg_clock_grad_async")
+            "pg_backward_batch_async", "pg_clock_lengths_async", "pg_clock_grad_async",
+            "pg_server_create", "pg_server_submit", "pg_server_wait", "pg_server_destroy")
 
 
 class PhyloGradError(RuntimeError):
@@ -46,7 +47,23 @@ class pg_problem(ctypes.Structure):
                 ("parent", ctypes.c_void_p), ("tip_states", ctypes.c_void_p),
                 ("pattern_weights", ctypes.c_void_p), ("Q", ctypes.c_void_p),
                 ("branch_model", ctypes.c_void_p), ("root_freqs", ctypes.c_void_p),
-                ("cat_rates", ctypes.c_void_p), ("cat_weights", ctypes.c_void_p)]
+                ("cat_rates", ctypes.c_void_p), ("cat_weights", ctypes.c_void_p),
+                ("tip_stride", ctypes.c_int32)]
+
+
+class pg_server_options(ctypes.Structure):
+    _fields_ = [("max_inflight", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("arena_bytes", ctypes.c_uint64)]
+
+
+class pg_request(ctypes.Structure):
+    _fields_ = [("problem", ctypes.c_void_p), ("b", ctypes.c_void_p), ("logL", ctypes.c_void_p),
+                ("grad", ctypes.c_void_p), ("hess", ctypes.c_void_p)]
+
+
+class pg_request_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("reserved", ctypes.c_int32), ("submit_s", ctypes.c_double),
+                ("start_s", ctypes.c_double), ("done_s", ctypes.c_double)]
 
 
 class pg_handle_info(ctypes.Structure):
@@ -99,6 +116,10 @@ def load(path: str = LIB_PATH):
         "pg_backward_batch_async": ([vp, i32, vp, vp, vp, vp], i32),
         "pg_clock_lengths_async": ([vp, i32, vp, vp, vp, vp, vp], i32),
         "pg_clock_grad_async": ([vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp], i32),
+        "pg_server_create": ([vp, ctypes.POINTER(pg_server_options), ctypes.POINTER(vp)], i32),
+        "pg_server_submit": ([vp, ctypes.POINTER(pg_request), ctypes.POINTER(ctypes.c_uint64)], i32),
+        "pg_server_wait": ([vp, ctypes.c_uint64, ctypes.POINTER(pg_request_info)], i32),
+        "pg_server_destroy": ([vp], i32),
         "pg_status_string": ([i32], ctypes.c_char_p),
         "pg_last_error": ([], ctypes.c_char_p),
     }
@@ -144,6 +165,33 @@ def _dev_ptr(t):
     return t.data_ptr()
 
 
+def problem_struct(problem: dict, precision: str = "fp32"):
+    """The pg_problem of a problem dict and the arrays it points into (keep both alive while the
+    library may read them).  Tip rows may be a row-strided view (unit stride along patterns)."""
+    if precision not in PRECISIONS:
+        raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
+    parent = np.ascontiguousarray(problem["parent"], dtype=np.int32)
+    tips = np.asarray(problem["tip_states"])
+    if tips.dtype != np.uint8 or tips.ndim != 2 or tips.strides[1] != 1 or tips.strides[0] < tips.shape[1]:
+        tips = np.ascontiguousarray(tips, dtype=np.uint8)
+    stride = int(tips.strides[0]) if tips.ndim == 2 and tips.shape[0] > 1 else 0
+    w = np.ascontiguousarray(problem["weights"], dtype=np.float64)
+    Q = np.ascontiguousarray(problem["Q"], dtype=np.float64)
+    if Q.ndim == 2:
+        Q = Q[None]
+    bm = problem.get("branch_model")
+    bm = None if bm is None else np.ascontiguousarray(bm, dtype=np.int32)
+    pi = np.ascontiguousarray(problem["root_freqs"], dtype=np.float64)
+    rates = np.ascontiguousarray(problem["cat_rates"], dtype=np.float64)
+    cw = np.ascontiguousarray(problem["cat_weights"], dtype=np.float64)
+    n = parent.shape[0]
+    P = tips.shape[1] if tips.ndim == 2 else 0
+    pr = pg_problem((n + 1) // 2, Q.shape[1], P, rates.shape[0], Q.shape[0], PRECISIONS[precision],
+                    _np_ptr(parent), _np_ptr(tips), _np_ptr(w), _np_ptr(Q), _np_ptr(bm), _np_ptr(pi),
+                    _np_ptr(rates), _np_ptr(cw), stride if stride != P else 0)
+    return pr, (parent, tips, w, Q, bm, pi, rates, cw)
+
+
 class Context:
     """One CUDA device with an optional device-memory budget (pg_create / pg_destroy)."""
 
@@ -179,22 +227,8 @@ class Handle:
         if precision not in PRECISIONS:
             raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
         self.ctx = ctx
-        parent = np.ascontiguousarray(problem["parent"], dtype=np.int32)
-        tips = np.ascontiguousarray(problem["tip_states"], dtype=np.uint8)
-        w = np.ascontiguousarray(problem["weights"], dtype=np.float64)
-        Q = np.ascontiguousarray(problem["Q"], dtype=np.float64)
-        if Q.ndim == 2:
-            Q = Q[None]
-        bm = problem.get("branch_model")
-        bm = None if bm is None else np.ascontiguousarray(bm, dtype=np.int32)
-        pi = np.ascontiguousarray(problem["root_freqs"], dtype=np.float64)
-        rates = np.ascontiguousarray(problem["cat_rates"], dtype=np.float64)
-        cw = np.ascontiguousarray(problem["cat_weights"], dtype=np.float64)
-        n = parent.shape[0]
-        pr = pg_problem((n + 1) // 2, Q.shape[1], tips.shape[1] if tips.ndim == 2 else 0,
-                        rates.shape[0], Q.shape[0], PRECISIONS[precision], _np_ptr(parent), _np_ptr(tips),
-                        _np_ptr(w), _np_ptr(Q), _np_ptr(bm), _np_ptr(pi), _np_ptr(rates),
-                        _np_ptr(cw))
+        pr, _keep = problem_struct(problem, precision)
+        n = pr.n_tips * 2 - 1
         out = ctypes.c_void_p()
         check(lib.pg_upload(ctx._ptr, ctypes.byref(pr), ctypes.byref(out)))
         self._ptr = out
@@ -351,3 +385,52 @@ def eval_noalloc(problem: dict, b, precision: str = "fp32", grad=True, hess=Fals
     if st not in (PG_OK, PG_ERR_NUMERIC):
         raise PhyloGradError(st, lib.pg_status_string(st).decode())
     return out
+
+
+class Server:
+    """Continuous-batching request server (pg_server_*): submit(problem, b) queues a request and
+    returns a ticket; wait(ticket) blocks until it completes and returns its results and times."""
+
+    def __init__(self, ctx: Context, max_inflight: int = 4, arena_bytes: int = 0):
+        lib = load()
+        opt = pg_server_options(max_inflight, 0, arena_bytes)
+        out = ctypes.c_void_p()
+        check(lib.pg_server_create(ctx._ptr, ctypes.byref(opt), ctypes.byref(out)))
+        self._ptr = out
+        self.ctx = ctx
+        self._live = {}
+
+    def submit(self, problem: dict, b=None, grad=True, hess=False) -> int:
+        pr, keep = problem_struct(problem, problem.get("precision", "fp32"))
+        n = pr.n_tips * 2 - 1
+        b = np.ascontiguousarray(problem["b"] if b is None else b, dtype=np.float64)
+        if b.shape != (n,):
+            raise ValueError(f"b must have shape ({n},)")
+        out = {"logL": np.zeros(1), "grad": np.zeros(n) if grad else None, "hess": np.zeros(n) if hess else None}
+        rq = pg_request(ctypes.addressof(pr), _np_ptr(b), _np_ptr(out["logL"]), _np_ptr(out["grad"]),
+                        _np_ptr(out["hess"]))
+        ticket = ctypes.c_uint64()
+        check(load().pg_server_submit(self._ptr, ctypes.byref(rq), ctypes.byref(ticket)))
+        self._live[ticket.value] = (pr, keep, b, out, rq)
+        return ticket.value
+
+    def wait(self, ticket: int) -> dict:
+        info = pg_request_info()
+        st = load().pg_server_wait(self._ptr, ticket, ctypes.byref(info))
+        pr, keep, b, out, rq = self._live.pop(ticket)
+        if st not in (PG_OK, PG_ERR_NUMERIC):
+            check(st)
+        return {"logL": float(out["logL"][0]), "grad": out["grad"], "hess": out["hess"], "status": st,
+                "submit_s": info.submit_s, "start_s": info.start_s, "done_s": info.done_s}
+
+    def close(self):
+        if self._ptr:
+            load().pg_server_destroy(self._ptr)
+            self._ptr = None
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

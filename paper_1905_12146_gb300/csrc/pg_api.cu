@@ -16,8 +16,10 @@
 
 #include "phylograd.h"
 #include "pg_internal.cuh"
+#include "pg_host.h"
 
-namespace {
+namespace pg {
+namespace host {
 
 thread_local std::string g_err;
 
@@ -30,6 +32,14 @@ pg_status fail(pg_status s, const char *fmt, ...) {
     g_err = buf;
     return s;
 }
+
+}  // namespace host
+}  // namespace pg
+
+using pg::host::fail;
+using pg::host::Placement;
+
+namespace {
 
 #define PG_CUDA(call)                                                                          \
     do {                                                                                       \
@@ -54,39 +64,6 @@ struct DeviceGuard {
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 }  // namespace
-
-struct pg_ctx {
-    int device = 0;
-    int n_sm = 1;
-    int blocks_per_sm[2][pg::kMaxCat + 1] = {};   // tree kernel occupancy [precision][C]
-    int max_range = 0;                            // cap on patterns per block (0 = kMaxRange)
-    uint64_t budget = 0;
-    uint64_t used = 0;
-    uint32_t flags = 0;
-    std::vector<pg_handle *> handles;
-};
-
-struct pg_handle {
-    pg_ctx *ctx = nullptr;
-    pg::ProbDesc desc{};     // device pointers; b and outputs are set per evaluation
-    void *block = nullptr;   // one device allocation holding every array of the problem
-    size_t bytes = 0;
-    int max_tiles = 0;       // blocks one evaluation of this problem may use
-    int cut = 0;             // levels [0, cut) run as level kernels when evaluated alone
-    std::vector<int> level_off;   // host copy of the level offsets
-    std::vector<uint8_t> level_cherry;   // 1 when every node of the level has two tip children
-    bool timing = false;
-    std::vector<cudaEvent_t> events;   // 6 per timed evaluation
-    uint64_t post_levels_bytes = 0, fused_bytes = 0, pre_levels_bytes = 0;
-    double *io_b = nullptr, *io_logL = nullptr, *io_grad = nullptr, *io_hess = nullptr,
-           *io_site = nullptr;   // device staging for the host-pointer pg_eval
-    pg_handle_info info{};
-    cudaStream_t last_stream = nullptr;
-    bool have_post = false;   // an enqueued post-order left partials a backward pass can use
-    bool mstate = false;      // a general state space (pg_mstate.cu): md holds its layout
-    pg::MDesc md{};
-    alignas(64) CUtensorMap tm_post, tm_pre, tm_tab;   // TMA descriptors of the tensor-core kernels
-};
 
 // ------------------------------------------------------------------------------------------
 // validation and tree preparation
@@ -244,108 +221,72 @@ void set_tiling(pg::ProbDesc &d, int target, int max_range) {
 
 namespace {
 
-// Stationary distribution of a generator: pi Q = 0, sum pi = 1 (Gaussian elimination with partial
-// pivoting on Q^T, the last equation replaced by the normalisation).  False if singular.
-bool stationary(const double *Q, int m, std::vector<double> &pi) {
-    std::vector<double> A((size_t)m * (m + 1));
-    for (int i = 0; i < m; ++i) {
-        for (int j = 0; j < m; ++j) A[(size_t)i * (m + 1) + j] = (i == m - 1) ? 1.0 : Q[(size_t)j * m + i];
-        A[(size_t)i * (m + 1) + m] = (i == m - 1) ? 1.0 : 0.0;
-    }
-    for (int c = 0; c < m; ++c) {
-        int piv = c;
-        for (int r = c + 1; r < m; ++r)
-            if (std::fabs(A[(size_t)r * (m + 1) + c]) > std::fabs(A[(size_t)piv * (m + 1) + c])) piv = r;
-        if (std::fabs(A[(size_t)piv * (m + 1) + c]) < 1e-300) return false;
-        if (piv != c)
-            for (int j = 0; j <= m; ++j) std::swap(A[(size_t)c * (m + 1) + j], A[(size_t)piv * (m + 1) + j]);
-        for (int r = 0; r < m; ++r) {
-            if (r == c) continue;
-            const double f = A[(size_t)r * (m + 1) + c] / A[(size_t)c * (m + 1) + c];
-            if (f == 0.0) continue;
-            for (int j = c; j <= m; ++j) A[(size_t)r * (m + 1) + j] -= f * A[(size_t)c * (m + 1) + j];
-        }
-    }
-    pi.assign(m, 0.0);
-    for (int i = 0; i < m; ++i) pi[i] = A[(size_t)i * (m + 1) + m] / A[(size_t)i * (m + 1) + i];
-    return true;
-}
-
-// Cyclic Jacobi eigenvalue iteration for a symmetric matrix S (m x m, row-major, overwritten):
-// S = U diag(lam) U^T, U orthogonal (column k = eigenvector k).
-void jacobi_eigen(std::vector<double> &S, int m, std::vector<double> &U, std::vector<double> &lam) {
-    U.assign((size_t)m * m, 0.0);
-    for (int i = 0; i < m; ++i) U[(size_t)i * m + i] = 1.0;
-    double norm = 0.0;
-    for (double x : S) norm += x * x;
-    for (int sweep = 0; sweep < 100; ++sweep) {
-        double off = 0.0;
-        for (int p = 0; p < m; ++p)
-            for (int q = p + 1; q < m; ++q) off += S[(size_t)p * m + q] * S[(size_t)p * m + q];
-        if (off <= 1e-32 * norm) break;
-        for (int p = 0; p < m; ++p)
-            for (int q = p + 1; q < m; ++q) {
-                const double apq = S[(size_t)p * m + q];
-                if (apq == 0.0) continue;
-                const double theta = (S[(size_t)q * m + q] - S[(size_t)p * m + p]) / (2.0 * apq);
-                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
-                const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
-                for (int k = 0; k < m; ++k) {   // columns p, q
-                    const double skp = S[(size_t)k * m + p], skq = S[(size_t)k * m + q];
-                    S[(size_t)k * m + p] = c * skp - sn * skq;
-                    S[(size_t)k * m + q] = sn * skp + c * skq;
-                }
-                for (int k = 0; k < m; ++k) {   // rows p, q
-                    const double spk = S[(size_t)p * m + k], sqk = S[(size_t)q * m + k];
-                    S[(size_t)p * m + k] = c * spk - sn * sqk;
-                    S[(size_t)q * m + k] = sn * spk + c * sqk;
-                }
-                for (int k = 0; k < m; ++k) {
-                    const double ukp = U[(size_t)k * m + p], ukq = U[(size_t)k * m + q];
-                    U[(size_t)k * m + p] = c * ukp - sn * ukq;
-                    U[(size_t)k * m + q] = sn * ukp + c * ukq;
-                }
+// Uniformisation of one generator (m states): mu = max_i -Q_ii (1 for Q = 0), B = I + Q / mu
+// (entrywise non-negative for a generator), and B^k for k = 1 .. kUnifK in FP64, stored FP32 in
+// the padded kMP x kMP layout; QT the transposed generator in FP32.
+void uniformise(const double *Q, int m, float *Bpow, float *QT, double *mu_out) {
+    double mu = 0.0;
+    for (int i = 0; i < m; ++i) mu = std::max(mu, -Q[(size_t)i * m + i]);
+    if (!(mu > 0.0)) mu = 1.0;
+    std::vector<double> B((size_t)m * m), Bk((size_t)m * m), next((size_t)m * m);
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) B[(size_t)i * m + j] = (i == j ? 1.0 : 0.0) + Q[(size_t)i * m + j] / mu;
+    Bk = B;
+    const int KP = pg::kMP;
+    for (int k = 1; k <= pg::kUnifK; ++k) {
+        float *dst = Bpow + (size_t)(k - 1) * KP * KP;
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < m; ++j) dst[(size_t)i * KP + j] = (float)Bk[(size_t)i * m + j];
+        if (k == pg::kUnifK) break;
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < m; ++j) {
+                double acc = 0.0;
+                for (int t = 0; t < m; ++t) acc += Bk[(size_t)i * m + t] * B[(size_t)t * m + j];
+                next[(size_t)i * m + j] = acc;
             }
+        Bk.swap(next);
     }
-    lam.assign(m, 0.0);
-    for (int i = 0; i < m; ++i) lam[i] = S[(size_t)i * m + i];
+    for (int k = 0; k < m; ++k)
+        for (int s = 0; s < m; ++s) QT[(size_t)k * KP + s] = (float)Q[(size_t)s * m + k];
+    *mu_out = mu;
 }
 
-// The symmetrised eigensystem of a reversible Q (detailed balance pi*_i Q_ij = pi*_j Q_ji with
-// pi* > 0): S = Pi^{1/2} Q Pi^{-1/2} = U diag(lam) U^T.  Writes UT (FP32, kMP x kMP, UT[k][j] =
-// U[j][k]), lam, sqrt(pi*) and 1 / sqrt(pi*), pads zero.  False (with a message) otherwise.
-pg_status symmetric_eigensystem(const double *Q, int m, int md, float *UT, double *lam_out, float *sq_out,
-                                float *isq_out) {
-    std::vector<double> pi;
-    if (!stationary(Q, m, pi)) return fail(PG_ERR_UNSUPPORTED, "Q[%d] has no unique stationary distribution", md);
-    double scale = 0.0;
-    for (int i = 0; i < m; ++i) {
-        if (!(pi[i] > 0.0)) return fail(PG_ERR_UNSUPPORTED, "the stationary distribution of Q[%d] is not positive", md);
-        for (int j = 0; j < m; ++j) scale = std::max(scale, std::fabs(pi[i] * Q[(size_t)i * m + j]));
+pg_status acquire_block(pg_ctx *ctx, const Placement *pl, size_t bytes, void **block) {
+    *block = nullptr;
+    if (pl) {
+        *block = pl->alloc(pl->self, bytes);
+        return *block ? PG_OK : fail(PG_ERR_OOM, "no room for %zu bytes in the arena", bytes);
     }
-    for (int i = 0; i < m; ++i)
-        for (int j = i + 1; j < m; ++j)
-            if (std::fabs(pi[i] * Q[(size_t)i * m + j] - pi[j] * Q[(size_t)j * m + i]) > 1e-10 * scale)
-                return fail(PG_ERR_UNSUPPORTED,
-                            "Q[%d] is not reversible; general (non-reversible) generators are implemented for 4 states", md);
-    std::vector<double> S((size_t)m * m), U, lam;
-    for (int i = 0; i < m; ++i)
-        for (int j = 0; j < m; ++j) S[(size_t)i * m + j] = std::sqrt(pi[i] / pi[j]) * Q[(size_t)i * m + j];
-    for (int i = 0; i < m; ++i)
-        for (int j = i + 1; j < m; ++j) {
-            const double a = 0.5 * (S[(size_t)i * m + j] + S[(size_t)j * m + i]);
-            S[(size_t)i * m + j] = S[(size_t)j * m + i] = a;
-        }
-    jacobi_eigen(S, m, U, lam);
-    for (int k = 0; k < m; ++k) {
-        lam_out[k] = std::min(lam[k], 0.0);   // a generator's eigenvalues are <= 0
-        for (int j = 0; j < m; ++j) UT[(size_t)k * pg::kMP + j] = (float)U[(size_t)j * m + k];
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        if (ctx->budget && ctx->used + bytes > ctx->budget)
+            return fail(PG_ERR_OOM, "problem needs %zu bytes, %llu of %llu budget in use", bytes,
+                        (unsigned long long)ctx->used, (unsigned long long)ctx->budget);
     }
-    for (int j = 0; j < m; ++j) {
-        sq_out[j] = (float)std::sqrt(pi[j]);
-        isq_out[j] = (float)(1.0 / std::sqrt(pi[j]));
+    cudaError_t ce = cudaMalloc(block, bytes);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        *block = nullptr;
+        return fail(PG_ERR_OOM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(ce));
     }
     return PG_OK;
+}
+void release_block(const Placement *pl, void *block) {
+    if (!block) return;
+    if (pl) pl->release(pl->self, block);
+    else cudaFree(block);
+}
+cudaError_t h2d(const Placement *pl, void *dst, const void *src, size_t n) {
+    if (n == 0) return cudaSuccess;
+    return pl ? cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, pl->stream)
+              : cudaMemcpy(dst, src, n, cudaMemcpyHostToDevice);
+}
+cudaError_t h2d_rows(const Placement *pl, void *dst, size_t dpitch, const void *src, size_t spitch, size_t w, size_t h) {
+    return pl ? cudaMemcpy2DAsync(dst, dpitch, src, spitch, w, h, cudaMemcpyHostToDevice, pl->stream)
+              : cudaMemcpy2D(dst, dpitch, src, spitch, w, h, cudaMemcpyHostToDevice);
+}
+cudaError_t dzero(const Placement *pl, void *dst, size_t n) {
+    return pl ? cudaMemsetAsync(dst, 0, n, pl->stream) : cudaMemset(dst, 0, n);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -374,25 +315,22 @@ pg_status encode_map(CUtensorMap *m, void *base, int rank, const cuuint64_t *dim
 }
 
 // upload of a problem with 5..64 states (pg_mstate.cu kernels)
-pg_status upload_m(pg_ctx *ctx, const pg_problem *pr, const TreePlan &tp, pg_handle **out) {
+pg_status upload_m(pg_ctx *ctx, const pg_problem *pr, const TreePlan &tp, pg_handle **out, const Placement *pl) {
     const int N = pr->n_tips, m = pr->n_states, P = pr->n_patterns, C = pr->n_categories, M = pr->n_models;
     const int n = 2 * N - 1, H = (int)tp.level_off.size() - 1;
     const int KP = pg::kMP;
-    std::vector<float> UT((size_t)M * KP * KP, 0.f), sq((size_t)M * KP, 0.f), isq((size_t)M * KP, 0.f);
-    std::vector<double> lam((size_t)M * KP, 0.0);
-    for (int md = 0; md < M; ++md) {
-        pg_status st = symmetric_eigensystem(pr->Q + (size_t)md * m * m, m, md, UT.data() + (size_t)md * KP * KP,
-                                             lam.data() + (size_t)md * KP, sq.data() + (size_t)md * KP,
-                                             isq.data() + (size_t)md * KP);
-        if (st != PG_OK) return st;
-    }
+    std::vector<float> Bpow((size_t)M * pg::kUnifK * KP * KP, 0.f), QT((size_t)M * KP * KP, 0.f);
+    std::vector<double> mu(M, 1.0);
+    for (int md = 0; md < M; ++md)
+        uniformise(pr->Q + (size_t)md * m * m, m, Bpow.data() + (size_t)md * pg::kUnifK * KP * KP,
+                   QT.data() + (size_t)md * KP * KP, &mu[md]);
     const int Ps = (P + 15) / 16 * 16;
     const int n_pt = (P + pg::kMTile - 1) / pg::kMTile, n_lb = (P + 255) / 256;
     Carver cv;
     const size_t o_ops = cv.take<int4>(N - 1), o_lv = cv.take<int>(H + 1);
     const size_t o_tips = cv.take<uint8_t>((size_t)N * Ps), o_w = cv.take<double>(Ps);
-    const size_t o_UT = cv.take<float>(UT.size()), o_lam = cv.take<double>(lam.size());
-    const size_t o_sq = cv.take<float>(sq.size()), o_isq = cv.take<float>(isq.size());
+    const size_t o_Bp = cv.take<float>(Bpow.size()), o_QT = cv.take<float>(QT.size());
+    const size_t o_mu = cv.take<double>(mu.size());
     const size_t o_bm = pr->branch_model ? cv.take<int>(n) : 0;
     const bool tc = !(ctx->flags & PG_FLAG_SIMT_MSTATE);
     const size_t o_tab = cv.take<float>((size_t)n * C * (tc ? (size_t)pg::kTcKinds * KP * KP
@@ -407,42 +345,35 @@ pg_status upload_m(pg_ctx *ctx, const pg_problem *pr, const TreePlan &tp, pg_han
     const size_t o_ib = cv.take<double>(n), o_il = cv.take<double>(1), o_ig = cv.take<double>(n);
     const size_t o_ih = cv.take<double>(n), o_is = cv.take<double>(std::max(P, 1));
     const size_t bytes = align_up(cv.off, 256);
-    if (ctx->budget && ctx->used + bytes > ctx->budget)
-        return fail(PG_ERR_OOM, "problem needs %zu bytes, %llu of %llu budget in use", bytes,
-                    (unsigned long long)ctx->used, (unsigned long long)ctx->budget);
     DeviceGuard g(ctx->device);
     if (!g.ok) return fail(PG_ERR_CUDA, "cannot select device %d", ctx->device);
     void *block = nullptr;
-    cudaError_t ce = cudaMalloc(&block, bytes);
-    if (ce != cudaSuccess) {
-        cudaGetLastError();
-        return fail(PG_ERR_OOM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(ce));
-    }
+    if (pg_status st = acquire_block(ctx, pl, bytes, &block); st != PG_OK) return st;
     char *base = static_cast<char *>(block);
     pg_handle *h = new (std::nothrow) pg_handle;
-    if (!h) { cudaFree(block); return fail(PG_ERR_OOM, "host allocation failed"); }
+    if (!h) { release_block(pl, block); return fail(PG_ERR_OOM, "host allocation failed"); }
     h->ctx = ctx;
     h->block = block;
     h->bytes = bytes;
     h->mstate = true;
+    h->external = pl != nullptr;
     auto cp = [&](size_t off, const void *src, size_t nbytes) -> cudaError_t {
-        if (nbytes == 0) return cudaSuccess;
-        return cudaMemcpy(base + off, src, nbytes, cudaMemcpyHostToDevice);
+        return h2d(pl, base + off, src, nbytes);
     };
     cudaError_t e = cp(o_ops, tp.ops.data(), sizeof(int4) * tp.ops.size());
     if (e == cudaSuccess) e = cp(o_lv, tp.level_off.data(), sizeof(int) * tp.level_off.size());
-    if (e == cudaSuccess && P > 0) e = cudaMemcpy2D(base + o_tips, Ps, pr->tip_states, P, P, N, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && P > 0)
+        e = h2d_rows(pl, base + o_tips, Ps, pr->tip_states, pr->tip_stride ? pr->tip_stride : P, P, N);
     if (e == cudaSuccess && P > 0) e = cp(o_w, pr->pattern_weights, sizeof(double) * P);
-    if (e == cudaSuccess) e = cp(o_UT, UT.data(), sizeof(float) * UT.size());
-    if (e == cudaSuccess) e = cp(o_lam, lam.data(), sizeof(double) * lam.size());
-    if (e == cudaSuccess) e = cp(o_sq, sq.data(), sizeof(float) * sq.size());
-    if (e == cudaSuccess) e = cp(o_isq, isq.data(), sizeof(float) * isq.size());
+    if (e == cudaSuccess) e = cp(o_Bp, Bpow.data(), sizeof(float) * Bpow.size());
+    if (e == cudaSuccess) e = cp(o_QT, QT.data(), sizeof(float) * QT.size());
+    if (e == cudaSuccess) e = cp(o_mu, mu.data(), sizeof(double) * mu.size());
     if (e == cudaSuccess && pr->branch_model) e = cp(o_bm, pr->branch_model, sizeof(int) * n);
     if (e == cudaSuccess) e = cp(o_par, pr->parent, sizeof(int) * n);
-    if (e == cudaSuccess) e = cudaMemset(base + o_st, 0, sizeof(int));
+    if (e == cudaSuccess) e = dzero(pl, base + o_st, sizeof(int));
     // padded states of every partial stay zero: the kernels write whole columns, pads included
     if (e != cudaSuccess) {
-        cudaFree(block);
+        release_block(pl, block);
         delete h;
         return fail(PG_ERR_CUDA, "upload: %s", cudaGetErrorString(e));
     }
@@ -451,10 +382,9 @@ pg_status upload_m(pg_ctx *ctx, const pg_problem *pr, const TreePlan &tp, pg_han
     d.level_off = reinterpret_cast<const int *>(base + o_lv);
     d.tips = reinterpret_cast<const uint8_t *>(base + o_tips);
     d.weights = reinterpret_cast<const double *>(base + o_w);
-    d.UT = reinterpret_cast<const float *>(base + o_UT);
-    d.lam = reinterpret_cast<const double *>(base + o_lam);
-    d.sq = reinterpret_cast<const float *>(base + o_sq);
-    d.isq = reinterpret_cast<const float *>(base + o_isq);
+    d.Bpow = reinterpret_cast<const float *>(base + o_Bp);
+    d.QT = reinterpret_cast<const float *>(base + o_QT);
+    d.mu = reinterpret_cast<const double *>(base + o_mu);
     d.bmodel = pr->branch_model ? reinterpret_cast<const int *>(base + o_bm) : nullptr;
     d.tabs = reinterpret_cast<float *>(base + o_tab);
     d.post = reinterpret_cast<float *>(base + o_post);
@@ -490,7 +420,7 @@ pg_status upload_m(pg_ctx *ctx, const pg_problem *pr, const TreePlan &tp, pg_han
         if (st == PG_OK) st = encode_map(&h->tm_pre, d.pre, 3, pdims, pstr, pbox);
         if (st == PG_OK) st = encode_map(&h->tm_tab, d.tabs, 2, tdims, tstr, tbox);
         if (st != PG_OK) {
-            cudaFree(block);
+            release_block(pl, block);
             delete h;
             return st;
         }
@@ -538,8 +468,11 @@ pg_status upload_m(pg_ctx *ctx, const pg_problem *pr, const TreePlan &tp, pg_han
     I.stream_bytes = 5ull * (uint64_t)(N - 2) * node_stream + 2ull * (uint64_t)N * P;
     // post P x, pre P x, G x and P^T q per internal child branch and column (2 kMP^2 each)
     I.flops = (uint64_t)(N - 2) * P * C * 4ull * 2ull * KP * KP;
-    ctx->used += bytes;
-    ctx->handles.push_back(h);
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        if (!pl) ctx->used += bytes;
+        ctx->handles.push_back(h);
+    }
     *out = h;
     return PG_OK;
 }
@@ -596,7 +529,7 @@ const char *pg_status_string(pg_status s) {
     return "unknown status";
 }
 
-const char *pg_last_error(void) { return g_err.c_str(); }
+const char *pg_last_error(void) { return pg::host::g_err.c_str(); }
 
 pg_status pg_create(const pg_options *opt, pg_ctx **out) {
     if (!out) return fail(PG_ERR_INVALID, "out is NULL");
@@ -631,9 +564,12 @@ pg_status pg_free(pg_handle *h) {
     pg_ctx *c = h->ctx;
     DeviceGuard g(c->device);
     for (cudaEvent_t x : h->events) cudaEventDestroy(x);
-    if (h->block) cudaFree(h->block);
-    c->used -= h->bytes;
-    c->handles.erase(std::remove(c->handles.begin(), c->handles.end(), h), c->handles.end());
+    if (h->block && !h->external) cudaFree(h->block);
+    {
+        std::lock_guard<std::mutex> gl(c->mu);
+        if (h->block && !h->external) c->used -= h->bytes;
+        c->handles.erase(std::remove(c->handles.begin(), c->handles.end(), h), c->handles.end());
+    }
     delete h;
     return PG_OK;
 }
@@ -645,7 +581,11 @@ pg_status pg_destroy(pg_ctx *ctx) {
     return PG_OK;
 }
 
-pg_status pg_upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out) {
+pg_status pg_upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out) { return pg::host::upload(ctx, pr, out, nullptr); }
+
+}  // extern "C"
+
+pg_status pg::host::upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out, const Placement *pl) {
     if (!ctx || !pr || !out) return fail(PG_ERR_INVALID, "NULL argument");
     *out = nullptr;
     const int N = pr->n_tips, m = pr->n_states, P = pr->n_patterns, C = pr->n_categories;
@@ -664,13 +604,15 @@ pg_status pg_upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out) {
     if (!pr->parent) return fail(PG_ERR_INVALID, "parent is NULL");
     if (P > 0 && (!pr->tip_states || !pr->pattern_weights))
         return fail(PG_ERR_INVALID, "tip_states and pattern_weights are required when n_patterns > 0");
+    if (pr->tip_stride != 0 && pr->tip_stride < P)
+        return fail(PG_ERR_INVALID, "tip_stride = %d is smaller than n_patterns = %d", pr->tip_stride, P);
     if ((int64_t)N * 2 - 1 > (int64_t)1 << 30) return fail(PG_ERR_UNSUPPORTED, "tree too large");
     TreePlan tp;
     pg_status st = plan_tree(N, pr->parent, tp);
     if (st != PG_OK) return st;
     st = check_model(pr);
     if (st != PG_OK) return st;
-    if (m != pg::kStates) return upload_m(ctx, pr, tp, out);
+    if (m != pg::kStates) return upload_m(ctx, pr, tp, out, pl);
 
     const int n = 2 * N - 1;
     const int H = (int)tp.level_off.size() - 1;
@@ -744,24 +686,18 @@ pg_status pg_upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out) {
     const size_t o_ib = cv.take<double>(n), o_il = cv.take<double>(1), o_ig = cv.take<double>(n);
     const size_t o_ih = cv.take<double>(n), o_is = cv.take<double>(std::max(P, 1));
     const size_t bytes = align_up(cv.off, 256);
-    if (ctx->budget && ctx->used + bytes > ctx->budget)
-        return fail(PG_ERR_OOM, "problem needs %zu bytes, %llu of %llu budget in use", bytes,
-                    (unsigned long long)ctx->used, (unsigned long long)ctx->budget);
 
     DeviceGuard g(ctx->device);
     if (!g.ok) return fail(PG_ERR_CUDA, "cannot select device %d", ctx->device);
     void *block = nullptr;
-    cudaError_t ce = cudaMalloc(&block, bytes);
-    if (ce != cudaSuccess) {
-        cudaGetLastError();
-        return fail(PG_ERR_OOM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(ce));
-    }
+    if (pg_status st = acquire_block(ctx, pl, bytes, &block); st != PG_OK) return st;
     char *base = static_cast<char *>(block);
     pg_handle *h = new (std::nothrow) pg_handle;
-    if (!h) { cudaFree(block); return fail(PG_ERR_OOM, "host allocation failed"); }
+    if (!h) { release_block(pl, block); return fail(PG_ERR_OOM, "host allocation failed"); }
     h->ctx = ctx;
     h->block = block;
     h->bytes = bytes;
+    h->external = pl != nullptr;
     h->max_tiles = max_tiles;
 
     // Taylor coefficients Q^k / k! and ||Q||_1 per model (FP64, host, once per upload)
@@ -789,8 +725,7 @@ pg_status pg_upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out) {
             Qf[md * 4 + c] = make_float4((float)Q[c], (float)Q[4 + c], (float)Q[8 + c], (float)Q[12 + c]);
         }
     auto cp = [&](size_t off, const void *src, size_t nbytes) -> cudaError_t {
-        if (nbytes == 0) return cudaSuccess;
-        return cudaMemcpy(base + off, src, nbytes, cudaMemcpyHostToDevice);
+        return h2d(pl, base + off, src, nbytes);
     };
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cp(o_ops, tp.ops.data(), sizeof(int4) * tp.ops.size());
@@ -798,7 +733,7 @@ pg_status pg_upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out) {
     std::vector<float> wf(Ps, 0.f);
     for (int p = 0; p < P; ++p) wf[p] = (float)pr->pattern_weights[p];
     if (e == cudaSuccess && P > 0)
-        e = cudaMemcpy2D(base + o_tips, Ps, pr->tip_states, P, P, N, cudaMemcpyHostToDevice);
+        e = h2d_rows(pl, base + o_tips, Ps, pr->tip_states, pr->tip_stride ? pr->tip_stride : P, P, N);
     if (e == cudaSuccess && P > 0) e = cp(o_w, pr->pattern_weights, sizeof(double) * P);
     if (e == cudaSuccess && P > 0) e = cp(o_wf, wf.data(), sizeof(float) * Ps);
     if (e == cudaSuccess) e = cp(o_Qd, pr->Q, sizeof(double) * 16 * M);
@@ -810,9 +745,9 @@ pg_status pg_upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out) {
     if (e == cudaSuccess) e = cp(o_tc, top_code.data(), sizeof(int2) * top_code.size());
     if (e == cudaSuccess && n_bnd > 0) e = cp(o_bn, bnd_node.data(), sizeof(int) * n_bnd);
     if (e == cudaSuccess) e = cp(o_par, pr->parent, sizeof(int) * n);
-    if (e == cudaSuccess) e = cudaMemset(base + o_st, 0, sizeof(int));
+    if (e == cudaSuccess) e = dzero(pl, base + o_st, sizeof(int));
     if (e != cudaSuccess) {
-        cudaFree(block);
+        release_block(pl, block);
         delete h;
         return fail(PG_ERR_CUDA, "upload: %s", cudaGetErrorString(e));
     }
@@ -917,17 +852,24 @@ pg_status pg_upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out) {
     I.stream_bytes = 5ull * (uint64_t)(N - 2) * node_stream + 2ull * (uint64_t)N * P;
     I.flops = (uint64_t)(N - 1) * P * C * (68ull + 216ull);
 
-    ctx->used += bytes;
-    ctx->handles.push_back(h);
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        if (!pl) ctx->used += bytes;
+        ctx->handles.push_back(h);
+    }
     *out = h;
     return PG_OK;
 }
+
+extern "C" {
 
 pg_status pg_get_info(const pg_handle *h, pg_handle_info *out) {
     if (!h || !out) return fail(PG_ERR_INVALID, "NULL argument");
     *out = h->info;
     return PG_OK;
 }
+
+}  // extern "C"
 
 namespace {
 
@@ -1081,6 +1023,15 @@ pg_status check_batch(pg_handle *const *hs, int32_t k) {
 }
 
 }  // namespace
+
+pg_status pg::host::enqueue(pg_handle *h, int skip, const double *d_b, double *d_logL, double *d_grad,
+                           double *d_hess, double *d_site_logL, const double *d_gscale, cudaStream_t s) {
+    DeviceGuard g(h->ctx->device);
+    if (!g.ok) return fail(PG_ERR_CUDA, "cannot select device %d", h->ctx->device);
+    return enqueue_single(h, skip, d_b, d_logL, d_grad, d_hess, d_site_logL, d_gscale, s);
+}
+
+extern "C" {
 
 pg_status pg_eval_async(pg_handle *h, const double *d_b, double *d_logL, double *d_grad,
                         double *d_hess, double *d_site_logL, void *stream) {

@@ -132,9 +132,13 @@ struct ClockArgs {
 cudaError_t launch_clock(const ClockArgs<kMaxClock> &a, bool grad, cudaStream_t s);
 
 // ---- general state spaces (pg_mstate.cu): 5 <= m <= 64 states, padded to kMP ---------------------
-// A reversible Q with stationary distribution pi* > 0 is symmetrised, S = Pi^{1/2} Q Pi^{-1/2} =
-// U diag(lambda) U^T (host, FP64, once per upload); per branch and category the device forms
-//   D = P - I = Pi^{-1/2} U diag(expm1(lambda b r)) U^T Pi^{1/2},   G = r Q P,   H = r^2 Q^2 P.
+// Transition matrices by uniformisation: with mu = max_i -Q_ii and B = I + Q / mu (entrywise
+// non-negative), P(t) = e^{-mu t} sum_k (mu t)^k / k! B^k.  The host forms B^k, k = 1 .. kUnifK,
+// in FP64 once per upload; per branch and category the device forms (t = b r, halved s times until
+// mu t <= 4 and squared back in the D form D <- 2 D + D D)
+//   D = P - I = expm1(-mu t) I + e^{-mu t} sum_{k>=1} (mu t)^k / k! B^k,  G = r Q P,  H = r^2 Q^2 P,
+// where every off-diagonal term is positive: small transition probabilities keep their relative
+// accuracy and never turn negative.
 // Partials are FP32 [node - N][C][Ps][kMP] (a column = (pattern, category) holds kMP states, pads
 // zero) with one power-of-two exponent per column [node - N][C][Ps].
 constexpr int kMP = 64;                 // padded state count
@@ -142,6 +146,7 @@ constexpr int kMTile = 64;              // patterns per item of the m-state kern
 constexpr int kTabRows = kMP + 1;       // table rows: kMP, then the ambiguous-code row
 constexpr int kTabFloats = kTabRows * kMP;
 constexpr int kTabDT = 0, kTabD = 1, kTabGT = 2, kTabHT = 3, kTabKinds = 4;
+constexpr int kUnifK = 32;              // powers of B held per model (covers mu t <= 4 to ~1e-13)
 
 struct MDesc {
     const int4 *ops;
@@ -149,10 +154,9 @@ struct MDesc {
     const uint8_t *tips;           // [N][Ps] codes; >= m is the all-ones (missing/ambiguous) code
     const double *weights;         // [P]
     const double *b;               // [n] branch lengths of this evaluation
-    const float *UT;               // [n_models][kMP][kMP]: UT[k][j] = U[j][k] (eigenvector k), FP32
-    const double *lam;             // [n_models][kMP] eigenvalues (pads 0)
-    const float *sq;               // [n_models][kMP] sqrt(pi*) (pads 0)
-    const float *isq;              // [n_models][kMP] 1 / sqrt(pi*) (pads 0)
+    const float *Bpow;             // [n_models][kUnifK][kMP][kMP]: B^k (k = 1 ..), FP32, pads 0
+    const float *QT;               // [n_models][kMP][kMP]: QT[k][s] = Q[s][k], FP32, pads 0
+    const double *mu;              // [n_models] uniformisation rates
     const int *bmodel;
     float *tabs;                   // [n][C][kTabKinds][kTabRows][kMP]
     float *post, *pre;             // [n_int][C][Ps][kMP]

@@ -139,21 +139,88 @@ __device__ __forceinline__ void store_scaled(float *rows, int *exps, const MDesc
 }
 
 // ---- transition tables ------------------------------------------------------------------------
-// Block (branch c, category l): f_k = expm1(lambda_k t), g_k = r lambda_k e^{lambda_k t},
-// h_k = r^2 lambda_k^2 e^{lambda_k t} with t = b_c r (FP64), then for each
-//   M = U diag(f) U^T (FP32),  X[s][j] = M[s][j] sqrt(pi*_j) / sqrt(pi*_s)
-// stored transposed (DT, GT, HT: row j = column j of X) plus the row sums as the ambiguous-code
-// row (1 + row sums of D for P), and D row-major for the pre-order product P^T q.
-// With TC the tables take the tensor-core layout instead: row-major D, G, H and D^T, each with its
-// TF32 remainder W - trunc_tf32(W) (kTcKinds tables of kMP x kMP per branch and category).
+// Block (branch c, category l), thread (ts, tj) owns rows s = 4 ts + a and columns j = 4 tj + b of
+// the 64 x 64 tables.  D by uniformisation (see MDesc), then G = r (Q + Q D) and H = r Q G as
+// products from shared memory.  SIMT layout: DT, GT, HT transposed (row j = column j) with the row
+// sums as the ambiguous-code row (1 + row sums of D for P) and D row-major for P^T q.  With TC the
+// tensor-core layout instead: row-major D, G, H and D^T, each with its TF32 remainder
+// W - trunc_tf32(W) (kTcKinds tables of kMP x kMP per branch and category).
 __device__ __forceinline__ float tf32_rem(float x) { return x - __uint_as_float(__float_as_uint(x) & 0xffffe000u); }
+
+// acc[a][b] = sum_k A[k][4 ts + a] * Bm[k][4 tj + b]  (A = left operand transposed, Bm row-major)
+__device__ __forceinline__ void smem_product(const float *A, const float *Bm, int ts, int tj, float acc[4][4]) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+#pragma unroll 8
+    for (int k = 0; k < kMP; ++k) {
+        const float4 w = *reinterpret_cast<const float4 *>(A + k * kMP + 4 * ts);
+        const float4 u = *reinterpret_cast<const float4 *>(Bm + k * kMP + 4 * tj);
+        const float wa[4] = {w.x, w.y, w.z, w.w}, ub[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(wa[a], ub[b], acc[a][b]);
+    }
+}
+__device__ __forceinline__ void put_rowmajor(float *M, int ts, int tj, const float acc[4][4]) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+        *reinterpret_cast<float4 *>(M + (4 * ts + a) * kMP + 4 * tj) = f4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+}
+__device__ __forceinline__ void put_transposed(float *M, int ts, int tj, const float acc[4][4]) {
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+        *reinterpret_cast<float4 *>(M + (4 * tj + b) * kMP + 4 * ts) = f4(acc[0][b], acc[1][b], acc[2][b], acc[3][b]);
+}
+__device__ __forceinline__ void put_rem(float *M, const float acc[4][4], int ts, int tj, bool transposed) {
+    float r[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) r[a][b] = tf32_rem(acc[a][b]);
+    if (transposed) put_transposed(M, ts, tj, r);
+    else put_rowmajor(M, ts, tj, r);
+}
+
+// kind 0: D, 1: G, 2: H of (c, l) into the table layout
+template <bool TC>
+__device__ __forceinline__ void store_tables(const MDesc &d, int c, int l, int kind, const float acc[4][4], int ts, int tj) {
+    if (TC) {
+        float *base = d.tabs + (size_t)(c * d.C + l) * kTcKinds * kMP * kMP;
+        const int hk = kind == 0 ? kTcD : (kind == 1 ? kTcG : kTcH);
+        const int lk = kind == 0 ? kTcDlo : (kind == 1 ? kTcGlo : kTcHlo);
+        put_rowmajor(base + (size_t)hk * kMP * kMP, ts, tj, acc);
+        put_rem(base + (size_t)lk * kMP * kMP, acc, ts, tj, false);
+        if (kind == 0) {
+            put_transposed(base + (size_t)kTcDT * kMP * kMP, ts, tj, acc);
+            put_rem(base + (size_t)kTcDTlo * kMP * kMP, acc, ts, tj, true);
+        }
+        return;
+    }
+    float rs[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) rs[a] = sum16(acc[a][0] + acc[a][1] + acc[a][2] + acc[a][3]);
+    float *T = d.tabs + ((size_t)(c * d.C + l) * kTabKinds + (kind == 0 ? kTabDT : (kind == 1 ? kTabGT : kTabHT))) * kTabFloats;
+    put_transposed(T, ts, tj, acc);
+    if (tj == 0) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int s = 4 * ts + a;
+            T[kMP * kMP + s] = kind == 0 ? (s < d.m ? 1.f + rs[a] : 0.f) : rs[a];
+        }
+    }
+    if (kind == 0) put_rowmajor(d.tabs + ((size_t)(c * d.C + l) * kTabKinds + kTabD) * kTabFloats, ts, tj, acc);
+}
 
 template <bool TC>
 __global__ void __launch_bounds__(kMThreads) m_pmatrix_kernel(const __grid_constant__ MDesc d, int kinds) {
-    __shared__ __align__(16) float UT[kMP * kMP];
-    __shared__ __align__(16) float W[kMP * kMP];
-    __shared__ float fk[3][kMP];
-    __shared__ float sq[kMP], isq[kMP];
+    __shared__ __align__(16) float A[kMP * kMP];    // left operand, transposed
+    __shared__ __align__(16) float Bm[kMP * kMP];   // right operand, row-major
+    __shared__ float ck[kUnifK + 1];
+    __shared__ float e0;
+    __shared__ int nk, nsq;
     const int c = blockIdx.x / d.C, l = blockIdx.x - c * d.C;
     if (c == d.root) return;
     const double bl = d.b[c];
@@ -162,96 +229,87 @@ __global__ void __launch_bounds__(kMThreads) m_pmatrix_kernel(const __grid_const
         return;
     }
     const int md = d.bmodel ? d.bmodel[c] : 0;
-    const double r = d.rates[l], t = bl * r;
-    if (threadIdx.x < kMP) {
-        const int k = threadIdx.x;
-        const double lam = d.lam[md * kMP + k], x = lam * t, ex = exp(x);
-        fk[0][k] = (float)expm1(x);
-        fk[1][k] = (float)(r * lam * ex);
-        fk[2][k] = (float)(r * r * lam * lam * ex);
-        sq[k] = d.sq[md * kMP + k];
-        isq[k] = d.isq[md * kMP + k];
+    const float r = (float)d.rates[l];
+    if (threadIdx.x == 0) {   // Poisson weights of the (halved) interval, FP64
+        double x = d.mu[md] * bl * d.rates[l];
+        int s = 0;
+        while (x > 4.0 && s < 1000) {
+            x *= 0.5;
+            ++s;
+        }
+        const int K = min(kUnifK, (int)ceil(x + 6.0 * sqrt(x) + 10.0));
+        double w = exp(-x);
+        for (int k = 1; k <= K; ++k) {
+            w *= x / k;
+            ck[k] = (float)w;
+        }
+        e0 = (float)expm1(-x);
+        nk = K;
+        nsq = s;
     }
-    {
-        const float4 *src = reinterpret_cast<const float4 *>(d.UT + (size_t)md * kMP * kMP);
-        float4 *dst = reinterpret_cast<float4 *>(UT);
-        for (int i = threadIdx.x; i < kMP * kMP / 4; i += blockDim.x) dst[i] = __ldg(src + i);
+    __syncthreads();
+    const int ts = threadIdx.x >> 4, tj = threadIdx.x & 15;
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+    const float *Bp = d.Bpow + (size_t)md * kUnifK * kMP * kMP;
+    for (int k = 1; k <= nk; ++k) {
+        const float w = ck[k];
+        const float *Bk = Bp + (size_t)(k - 1) * kMP * kMP;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(Bk + (4 * ts + a) * kMP + 4 * tj));
+            acc[a][0] = fmaf(w, v.x, acc[a][0]);
+            acc[a][1] = fmaf(w, v.y, acc[a][1]);
+            acc[a][2] = fmaf(w, v.z, acc[a][2]);
+            acc[a][3] = fmaf(w, v.w, acc[a][3]);
+        }
     }
-    const int ts = threadIdx.x >> 4, tj = threadIdx.x & 15;   // rows s = 4 ts + a, columns j = 4 tj + b
-    for (int kind = 0; kind < kinds; ++kind) {
-        __syncthreads();   // fk, UT ready; the previous kind's readers of W done
-        for (int i = threadIdx.x; i < kMP * kMP; i += blockDim.x) W[i] = fk[kind][i / kMP] * UT[i];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+            if (4 * ts + a == 4 * tj + b && 4 * ts + a < d.m) acc[a][b] += e0;
+    for (int i = 0; i < nsq; ++i) {   // P(2t) = P(t)^2 in the D form: D <- 2 D + D D
+        put_transposed(A, ts, tj, acc);
+        put_rowmajor(Bm, ts, tj, acc);
         __syncthreads();
-        float acc[4][4];
+        float sq[4][4];
+        smem_product(A, Bm, ts, tj, sq);
+        __syncthreads();
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-#pragma unroll 8
-        for (int k = 0; k < kMP; ++k) {
-            const float4 w = *reinterpret_cast<const float4 *>(W + k * kMP + 4 * ts);
-            const float4 u = *reinterpret_cast<const float4 *>(UT + k * kMP + 4 * tj);
-            const float wa[4] = {w.x, w.y, w.z, w.w}, ub[4] = {u.x, u.y, u.z, u.w};
+            for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(2.f, acc[a][b], sq[a][b]);
+    }
+    store_tables<TC>(d, c, l, 0, acc, ts, tj);
+    // G = r (Q + Q D)
+    {
+        const float4 *src = reinterpret_cast<const float4 *>(d.QT + (size_t)md * kMP * kMP);
+        for (int i = threadIdx.x; i < kMP * kMP / 4; i += blockDim.x) reinterpret_cast<float4 *>(A)[i] = __ldg(src + i);
+    }
+    put_rowmajor(Bm, ts, tj, acc);
+    __syncthreads();
+    float g[4][4];
+    smem_product(A, Bm, ts, tj, g);
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(wa[a], ub[b], acc[a][b]);
-        }
-        float rs[4];
+        for (int b = 0; b < 4; ++b) g[a][b] = r * (g[a][b] + A[(4 * tj + b) * kMP + 4 * ts + a]);
+    store_tables<TC>(d, c, l, 1, g, ts, tj);
+    if (kinds > 2) {   // H = r Q G
+        __syncthreads();
+        put_rowmajor(Bm, ts, tj, g);
+        __syncthreads();
+        float h[4][4];
+        smem_product(A, Bm, ts, tj, h);
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            rs[a] = 0.f;
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                acc[a][b] *= isq[4 * ts + a] * sq[4 * tj + b];
-                rs[a] += acc[a][b];
-            }
-            rs[a] = sum16(rs[a]);
-        }
-        if (TC) {
-            float *base = d.tabs + (size_t)(c * d.C + l) * kTcKinds * kMP * kMP;
-            const int hk = kind == 0 ? kTcD : (kind == 1 ? kTcG : kTcH);
-            const int lk = kind == 0 ? kTcDlo : (kind == 1 ? kTcGlo : kTcHlo);
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {   // row-major
-                const int s = 4 * ts + a;
-                const float v[4] = {acc[a][0], acc[a][1], acc[a][2], acc[a][3]};
-                const size_t o = (size_t)s * kMP + 4 * tj;
-                *reinterpret_cast<float4 *>(base + (size_t)hk * kMP * kMP + o) = f4(v[0], v[1], v[2], v[3]);
-                *reinterpret_cast<float4 *>(base + (size_t)lk * kMP * kMP + o) =
-                    f4(tf32_rem(v[0]), tf32_rem(v[1]), tf32_rem(v[2]), tf32_rem(v[3]));
-            }
-            if (kind == 0) {
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {   // D^T: row j holds column j of D
-                    const int j = 4 * tj + b;
-                    const float v[4] = {acc[0][b], acc[1][b], acc[2][b], acc[3][b]};
-                    const size_t o = (size_t)j * kMP + 4 * ts;
-                    *reinterpret_cast<float4 *>(base + (size_t)kTcDT * kMP * kMP + o) = f4(v[0], v[1], v[2], v[3]);
-                    *reinterpret_cast<float4 *>(base + (size_t)kTcDTlo * kMP * kMP + o) =
-                        f4(tf32_rem(v[0]), tf32_rem(v[1]), tf32_rem(v[2]), tf32_rem(v[3]));
-                }
-            }
-            continue;
-        }
-        const int tk = kind == 0 ? kTabDT : (kind == 1 ? kTabGT : kTabHT);
-        float *T = d.tabs + ((size_t)(c * d.C + l) * kTabKinds + tk) * kTabFloats;
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-            *reinterpret_cast<float4 *>(T + (4 * tj + b) * kMP + 4 * ts) = f4(acc[0][b], acc[1][b], acc[2][b], acc[3][b]);
-        if (tj == 0) {
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                const int s = 4 * ts + a;
-                T[kMP * kMP + s] = kind == 0 ? (s < d.m ? 1.f + rs[a] : 0.f) : rs[a];
-            }
-        }
-        if (kind == 0) {
-            float *Dr = d.tabs + ((size_t)(c * d.C + l) * kTabKinds + kTabD) * kTabFloats;
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-                *reinterpret_cast<float4 *>(Dr + (4 * ts + a) * kMP + 4 * tj) = f4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
-        }
+            for (int b = 0; b < 4; ++b) h[a][b] *= r;
+        store_tables<TC>(d, c, l, 2, h, ts, tj);
     }
 }
 

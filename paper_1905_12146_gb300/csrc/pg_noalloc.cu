@@ -102,7 +102,7 @@ pg_status check_inputs(const pg_problem *pr) {
     if (pr->precision != PG_PRECISION_FP32 && pr->precision != PG_PRECISION_FP64)
         return noalloc_fail(PG_ERR_INVALID, "precision = %d", pr->precision);
     if (!pr->parent || !pr->Q || !pr->root_freqs || !pr->cat_rates || !pr->cat_weights ||
-        (P > 0 && (!pr->tip_states || !pr->pattern_weights)))
+        (P > 0 && (!pr->tip_states || !pr->pattern_weights)) || (pr->tip_stride != 0 && pr->tip_stride < P))
         return noalloc_fail(PG_ERR_INVALID, "a required input is NULL");
     for (int md = 0; md < M; ++md) {
         const double *Q = pr->Q + (size_t)md * 16;
@@ -234,7 +234,8 @@ extern "C" pg_status pg_eval_noalloc(const pg_problem *pr, const double *b, doub
     NOALLOC_CUDA(cudaMemcpyAsync(base + o_ops, g_ops, sizeof(int4) * (N - 1), cudaMemcpyHostToDevice, s));
     NOALLOC_CUDA(cudaMemcpyAsync(base + o_lv, g_level_off, sizeof(int) * (H + 1), cudaMemcpyHostToDevice, s));
     if (P > 0) {
-        NOALLOC_CUDA(cudaMemcpy2DAsync(base + o_tips, Ps, pr->tip_states, P, P, N, cudaMemcpyHostToDevice, s));
+        NOALLOC_CUDA(cudaMemcpy2DAsync(base + o_tips, Ps, pr->tip_states, pr->tip_stride > 0 ? pr->tip_stride : P, P, N,
+                                       cudaMemcpyHostToDevice, s));
         NOALLOC_CUDA(cudaMemcpyAsync(base + o_w, pr->pattern_weights, sizeof(double) * P, cudaMemcpyHostToDevice, s));
     }
     NOALLOC_CUDA(cudaMemcpyAsync(base + o_Qd, pr->Q, sizeof(double) * 16 * M, cudaMemcpyHostToDevice, s));

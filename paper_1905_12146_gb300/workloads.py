@@ -414,6 +414,41 @@ def serving_requests(n_requests: int, seed: int = 5, taxa=(50, 2000), patterns=(
     return reqs
 
 
+def serving_masters(max_taxa: int = 2000, max_patterns: int = 20000, seed: int = 6, ambiguous: float = 0.02):
+    """Seeded tip-state matrices [max_taxa, max_patterns] for 4 and 61 states (i.i.d. codes, a
+    fraction ``ambiguous`` set to the all-ones code).  A serving request takes a row-strided view
+    of its taxa x patterns block, so generating 2,000 requests of up to 2,000 x 20,000 cells costs
+    no per-request alignment simulation; the likelihood arithmetic does not depend on the codes'
+    correlation across taxa."""
+    rng = np.random.default_rng(seed)
+    out = {}
+    for m in (4, 61):
+        t = rng.integers(0, m, size=(max_taxa, max_patterns), dtype=np.uint8)
+        t[rng.random((max_taxa, max_patterns)) < ambiguous] = m
+        out[m] = t
+    return out
+
+
+def serving_problem(desc, masters):
+    """Problem of one serving request: a Yule tree of desc["n_tips"] taxa, branch lengths
+    Exp(mean 0.01), a general 4-state Q or a codon Q, desc["n_cat"] discrete-gamma categories
+    (shape 0.5) and a view of desc["n_patterns"] patterns of the master tip matrix."""
+    rng = np.random.default_rng(desc["seed"])
+    N, P, m, C = desc["n_tips"], desc["n_patterns"], desc["n_states"], desc["n_cat"]
+    parent, _ = yule_tree(N, rng)
+    b = branch_lengths(parent, 0.01, rng)
+    if m == 61:
+        Q, pi = codon_Q(rng)
+    else:
+        Q, pi = random_general_Q(4, rng), dirichlet_freqs(4, rng)
+    rates, cw = discrete_gamma(0.5, C)
+    master = masters[m]
+    off = int(rng.integers(0, master.shape[1] - P + 1))
+    pr = make_problem(parent, np.zeros((0, 0), dtype=np.uint8), np.ones(P), Q, pi, rates, cw, b)
+    pr["tip_states"] = master[:N, off:off + P]   # row-strided view, not copied
+    return pr
+
+
 def materialise_request(desc):
     return random_problem(desc["n_tips"], desc["n_patterns"], n_states=desc["n_states"],
                           n_cat=desc["n_cat"], seed=desc["seed"], b_mean=0.01)

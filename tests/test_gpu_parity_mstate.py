@@ -98,12 +98,24 @@ def test_other_state_counts(ctx, oracle_mod, m):
     _check(ctx, oracle_mod, pr, label=f"m={m}")
 
 
-def test_non_reversible_general_state_space_is_rejected(ctx):
-    from paper_1905_12146_gb300 import _native
-    pr = wl.random_problem(6, 20, n_states=20, seed=1)   # general (non-reversible) Q
-    with pytest.raises(_native.PhyloGradError) as e:
-        ctx.upload(pr)
-    assert e.value.status == _native.PG_ERR_UNSUPPORTED
+@pytest.mark.parametrize("m", [20, 61])
+def test_non_reversible_general_state_space(ctx, oracle_mod, m):
+    """A general (non-reversible) generator with a root distribution that is not stationary."""
+    rng = np.random.default_rng(40 + m)
+    pr = wl.random_problem(15, 180, n_states=m, n_cat=2, seed=40 + m, b_mean=0.1, ambiguous=0.03)
+    pr["Q"] = wl.random_general_Q(m, rng)[None]
+    pr["root_freqs"] = wl.dirichlet_freqs(m, rng)
+    _check(ctx, oracle_mod, pr, label=f"non-reversible m={m}")
+
+
+def test_short_branches_and_unlikely_sites(ctx, oracle_mod):
+    """Codon tips drawn independently of the tree on very short branches: the site likelihoods
+    rest on multi-step transition probabilities of order t^3, which must stay positive and
+    relatively accurate."""
+    rng = np.random.default_rng(77)
+    pr = wl.random_problem(40, 300, n_states=61, n_cat=4, seed=77, b_mean=0.002)
+    pr["tip_states"] = rng.integers(0, 61, size=pr["tip_states"].shape).astype(np.uint8)
+    _check(ctx, oracle_mod, pr, label="codon random tips, short branches")
 
 
 def test_codon_forward_backward_equals_eval(ctx):
