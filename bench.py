@@ -14,6 +14,11 @@ the blocking host-pointer call (branch lengths copied from pinned host memory, l
 copied back each step).  ``roofline`` is for the dominant kernel (the pre-order level kernels),
 ``cpu_baseline`` the FP64 CPU oracle on a bounded sample of the same workload.
 ``--impl reference`` times that oracle alone (there is no reference GPU implementation).
+
+Rank 0 then adds three measured objects (skipped with ``--no-extras``): ``codon`` (500 taxa x
+3,000 codon patterns x 4 categories on the tensor-core kernels), ``differentiation`` (the 64-tree
+clock batch through the torch.autograd.Functions) and ``serving`` (``--serving-requests`` Poisson
+requests through the continuous-batching server against the one-request-at-a-time plain path).
 """
 from __future__ import annotations
 
@@ -199,6 +204,135 @@ def run_reference(args):
     return 0
 
 
+SERVING = ("serving: Poisson arrivals of logL+gradient requests, taxa U{50..2000}, patterns "
+           "U{500..20000}, 4 states (80%) or 61 codon states (20%), 1-4 gamma categories, Yule trees, "
+           "b~Exp(0.01), tip rows drawn from seeded master matrices; admitted by device-arena budget")
+
+
+def _serving(n_requests: int, device: int):
+    """The serving configuration: saturated throughput of the plain path (one request at a time)
+    and of continuous batching, then Poisson arrivals at 0.5, 0.7 and 0.9 of the continuous path's
+    saturated throughput (and the plain path at 0.7 of it) with p50 / p99 latency (completion minus
+    submission)."""
+    import numpy as np
+
+    from paper_1905_12146_gb300 import _native, workloads
+
+    t0 = time.perf_counter()
+    masters = workloads.serving_masters()
+    descs = workloads.serving_requests(n_requests, seed=5)
+    probs = [workloads.serving_problem(d, masters) for d in descs]
+    gen_s = time.perf_counter() - t0
+    ctx = _native.Context(device)
+
+    def run(slots, rate=None, seed=7):
+        srv = _native.Server(ctx, max_inflight=slots)
+        gaps = np.random.default_rng(seed).exponential(1.0 / rate, size=len(probs)) if rate else np.zeros(len(probs))
+        t_next = time.perf_counter()
+        tickets = []
+        for p, g in zip(probs, gaps):
+            t_next += g
+            while True:
+                dt = t_next - time.perf_counter()
+                if dt <= 0:
+                    break
+                time.sleep(min(dt, 0.0005))
+            tickets.append(srv.submit(p))
+        res = [srv.wait(t) for t in tickets]
+        srv.close()
+        lat = np.array([r["done_s"] - r["submit_s"] for r in res]) * 1e3
+        span = max(r["done_s"] for r in res) - min(r["submit_s"] for r in res)
+        bad = sum(1 for r in res if r["status"] != 0)
+        return {"evals_per_s": len(res) / span, "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "failed": bad,
+                "offered_per_s": rate}
+
+    out = {"workload": SERVING, "requests": n_requests, "codon_requests": sum(d["n_states"] == 61 for d in descs),
+           "generation_s": gen_s, "unit": "evals/s, ms"}
+    out["saturated_plain"] = run(1)
+    out["saturated_continuous"] = run(8)
+    sat = out["saturated_continuous"]["evals_per_s"]
+    out["poisson"] = [dict(load=f, continuous=run(8, f * sat, seed=11 + i)) for i, f in enumerate((0.5, 0.7, 0.9))]
+    out["poisson"][1]["plain"] = run(1, 0.7 * sat, seed=12)
+    ctx.close()
+    return out
+
+
+def _differentiation(device: int, steps: int = 30):
+    """The differentiation batch: 64 trees x 300 taxa x 5,000 patterns, one category; one step is
+    the clock branch lengths, the batched forward (post-order) and the autograd backward (pre-order
+    gradient kernels and the clock chain rule)."""
+    import numpy as np
+    import torch
+
+    from paper_1905_12146_gb300 import _native, autograd, workloads
+
+    probs = workloads.config_clock_batch()
+    ctx = _native.Context(device)
+    hs = [ctx.upload(p) for p in probs]
+    dev = torch.device("cuda", device)
+    eps = torch.tensor(np.stack([p["eps"] for p in probs]), device=dev).requires_grad_(True)
+    mu = torch.tensor([p["mu"] for p in probs], dtype=torch.float64, device=dev).requires_grad_(True)
+    t = torch.tensor(np.stack([p["node_time"] for p in probs]), device=dev).requires_grad_(True)
+
+    def step():
+        eps.grad = mu.grad = t.grad = None
+        autograd.tree_loglik(autograd.clock_branch_lengths(eps, mu, t, hs), hs).sum().backward()
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize(dev)
+    autograd.check_status(hs)
+    ms = e0.elapsed_time(e1) / steps
+    nbytes = sum(h.info().stream_bytes for h in hs)
+    for h in hs:
+        h.close()
+    ctx.close()
+    return {"workload": "64 Yule trees x 300 taxa x 5,000 patterns, 1 category, clock b = mu eps dt",
+            "ms_per_step": ms, "evals_per_s": len(probs) / (ms * 1e-3), "unit": "tree evals/s",
+            "algorithmic_bytes_per_step": nbytes, "achieved_gbs": nbytes / (ms * 1e-3) / 1e9}
+
+
+def _codon(device: int, steps: int = 20):
+    """The codon configuration: 500 taxa x 3,000 patterns x 4 categories, 61 states, tensor-core
+    kernels (three-pass TF32, FP32 accumulation)."""
+    import torch
+
+    from paper_1905_12146_gb300 import _native, workloads
+
+    pr = workloads.config_codon()
+    ctx = _native.Context(device)
+    h = ctx.upload(pr)
+    dev = torch.device("cuda", device)
+    b = torch.tensor(pr["b"], device=dev)
+    lg = torch.zeros(1, dtype=torch.float64, device=dev)
+    g = torch.zeros_like(b)
+    for _ in range(3):
+        h.eval_async(b, lg, g)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        h.eval_async(b, lg, g)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    st = h.status()
+    ms = e0.elapsed_time(e1) / steps
+    info = h.info()
+    h.close()
+    ctx.close()
+    return {"workload": "codon: 500-taxon Yule tree, 61-state codon Q (omega 0.3), 4 categories, 3,000 patterns",
+            "ms_per_eval": ms, "evals_per_s": 1e3 / ms, "status": st,
+            "algorithmic_bytes": info.stream_bytes, "achieved_gbs": info.stream_bytes / (ms * 1e-3) / 1e9,
+            "useful_tflops": info.flops / (ms * 1e-3) / 1e12}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -315,6 +449,11 @@ def run_gpu(args):
         line["cpu_baseline"] = _cpu_baseline(pr)
     h.close()
     ctx.close()
+    if rank == 0 and not args.no_extras:
+        line["codon"] = _codon(local)
+        line["differentiation"] = _differentiation(local)
+        if args.serving_requests > 0:
+            line["serving"] = _serving(args.serving_requests, local)
     if dist is not None:
         dist.destroy_process_group()
     if rank == 0:
@@ -328,6 +467,10 @@ def main():
     ap.add_argument("--steps", type=int, default=800)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=("gpu", "reference"), default="gpu")
+    ap.add_argument("--serving-requests", type=int, default=2000,
+                    help="requests of the serving measurement (0 skips it)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="only the headline nucleotide measurement (no codon, differentiation, serving)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
