@@ -75,6 +75,17 @@ __device__ __forceinline__ void mma_tile(uint32_t acc, uint32_t a, uint32_t b, u
                  (accumulate || kk > 0) ? 1u : 0u);
     }
 }
+// the same with A[128 x 64] read from tensor memory (lane = row, one column per element)
+__device__ __forceinline__ void mma_tile_ta(uint32_t acc, uint32_t a_tmem, uint32_t b, uint32_t n, bool accumulate) {
+    const uint32_t id = idesc_tf32(kTcTile, n);
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+        const uint32_t kb = kk >> 2, ko = (kk & 3) * 32;
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n"
+                     ::"r"(acc), "r"(a_tmem + (uint32_t)(kk * 8)), "l"(umma_desc(b + kb * n * 128 + ko)), "r"(id),
+                       "r"((accumulate || kk > 0) ? 1u : 0u));
+    }
+}
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
     uint32_t r[16];
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
@@ -85,6 +96,17 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float v[16]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n"
+                 ::"r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                   "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+                   "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+                   "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+                   "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+                   "r"(__float_as_uint(v[15]))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
 
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *m, int x, int y, uint64_t *bar) {
     asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
@@ -242,7 +264,7 @@ m_post_tc_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
             if (!tip)
                 for (int kb = 0; kb < 2; ++kb) tma_load_3d(XA + kb * kRowKB, &tm_post, kb * 32, p0, (c - N) * C + l, &bar[0]);
         }
-        if (tip) tip_row(XA, d, c, p0, cnt, t);
+        if (tip) tip_row(XA, d, c, p0, cnt, t);   // exact one-hot rows: no remainder pass
         else if (t < cnt) E += __ldcg(d.pe + ((size_t)(c - N) * C + l) * d.Ps + p0 + t);
         load_pending = true;
         ok = wait_all(&bar[0], ph_load);
@@ -274,10 +296,12 @@ m_post_tc_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
 #pragma unroll
                 for (int j = 0; j < 16; ++j) a0[16 * ch + j] = a[j] + x[j];
             }
+            tc_before();
             __syncthreads();   // every row read before the next copies land in XA
         }
     }
     if (ok) {
+        unsigned char *stage = XA;
         tc_after();
         float mx = 0.f;
 #pragma unroll
@@ -298,13 +322,13 @@ m_post_tc_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
             tmem_wait_ld();
 #pragma unroll
             for (int j = 0; j < 16; ++j) a[j] = a0[16 * ch + j] * (a[j] + x[j]);
-            put16(XA, t, ch, a, e);   // the row's own slots: read above, by this thread only
+            put16(stage, t, ch, a, e);   // the row's own slots: read above, by this thread only
         }
         if (t < cnt) __stcg(d.pe + ((size_t)(k - N) * C + l) * d.Ps + p0 + t, E + e);
         fence_async_smem();
         __syncthreads();
         if (t == 0) {
-            for (int kb = 0; kb < 2; ++kb) tma_store_3d(&tm_post, XA + kb * kRowKB, kb * 32, p0, (k - N) * C + l);
+            for (int kb = 0; kb < 2; ++kb) tma_store_3d(&tm_post, stage + kb * kRowKB, kb * 32, p0, (k - N) * C + l);
             bulk_commit();
             bulk_wait_read0();
         }
@@ -570,6 +594,254 @@ m_pre_tc_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtenso
     if (warp == 0) tmem_dealloc(tmem, kCols);
 }
 
+// ---- pre-order level without the Hessian: two load rounds per category ----------------------------
+// Round A brings q_k, both children's rows and both children's [D; G] tables (hi | lo); the rows'
+// TF32 remainders go to tensor memory, and six MMA groups give A_c = x_c [D_c; G_c]^T (TMEM columns
+// 128 c .. +127).  Round B (both children's D^T tables) is issued at once and lands while the
+// epilogue forms qt_c = q_k o (x_other + D_other x_other), the branch terms qt_c . (G_c x_c), and
+// writes qt_c (columns 128 c .. +63) and its remainder (+64 .. +127) back into tensor memory in
+// place; the products D_c^T qt_c then read A from tensor memory into columns 256 + 64 c.
+__global__ void __launch_bounds__(kTcThreads, 1)
+m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtensorMap tm_post,
+                 const __grid_constant__ CUtensorMap tm_pre, const __grid_constant__ CUtensorMap tm_tab, int o0, int n_pt) {
+    extern __shared__ __align__(1024) unsigned char tc_raw[];
+    unsigned char *sm = align1024(tc_raw);
+    unsigned char *X[2] = {sm, sm + kRowTile};                 // children's rows
+    unsigned char *QK = sm + 2 * kRowTile;                      // q_k rows
+    unsigned char *T[2] = {sm + 3 * kRowTile, sm + 3 * kRowTile + 4 * kTab};   // [D; G] hi | lo per child
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ uint32_t tmem_slot;
+    __shared__ double red[2][kTcThreads / 32];
+    const int C = d.C, N = d.n_tips, t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int u = blockIdx.x / n_pt, pt = blockIdx.x - u * n_pt;
+    const int4 op = __ldg(d.ops + o0 + u);
+    const int k = op.x, p0 = pt * kTcTile, cnt = min(kTcTile, d.P - p0);
+    const bool root = k == d.root;
+    const int cs[2] = {op.y, op.z};
+    const bool tip[2] = {op.y < N, op.z < N};
+    if (warp == 0) tmem_alloc(&tmem_slot, 512);
+    if (t == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+    }
+    tc_before();
+    __syncthreads();
+    tc_after();
+    const uint32_t tmem = tmem_slot, lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    const bool on = t < cnt;
+    const float inv = on ? __ldcg(d.site_invL + p0 + t) : 0.f;
+    const int Er = on ? __ldcg(d.site_Er + p0 + t) : 0;
+    float dsum[2] = {0.f, 0.f};
+    uint32_t ph_load = 0, ph_mma = 0;
+    bool ok = true, load_pending = false, mma_pending = false;
+    for (int l = 0; l < C && ok; ++l) {
+        const int Eq = (on && !root) ? __ldcg(d.qe + ((size_t)(k - N) * C + l) * d.Ps + p0 + t) : 0;
+        int Ex[2];
+        for (int side = 0; side < 2; ++side)
+            Ex[side] = (on && !tip[side]) ? __ldcg(d.pe + ((size_t)(cs[side] - N) * C + l) * d.Ps + p0 + t) : 0;
+        // round A
+        if (t == 0) {
+            uint32_t bytes = 8 * kTab;
+            if (!root) bytes += kRowTile;
+            for (int side = 0; side < 2; ++side) bytes += tip[side] ? 0u : kRowTile;
+            mbar_arrive_expect(&bar[0], bytes);
+            if (!root)
+                for (int kb = 0; kb < 2; ++kb) tma_load_3d(QK + kb * kRowKB, &tm_pre, kb * 32, p0, (k - N) * C + l, &bar[0]);
+            for (int side = 0; side < 2; ++side) {
+                if (!tip[side])
+                    for (int kb = 0; kb < 2; ++kb)
+                        tma_load_3d(X[side] + kb * kRowKB, &tm_post, kb * 32, p0, (cs[side] - N) * C + l, &bar[0]);
+                load_tables(T[side], &tm_tab, d, cs[side], l, kTcD, 2, &bar[0]);
+                load_tables(T[side] + 2 * kTab, &tm_tab, d, cs[side], l, kTcDlo, 2, &bar[0]);
+            }
+        }
+        for (int side = 0; side < 2; ++side)   // a tip's exact one-hot rows: no remainder pass
+            if (tip[side]) tip_row(X[side], d, cs[side], p0, cnt, t);
+        load_pending = true;
+        ok = wait_all(&bar[0], ph_load);
+        load_pending = !ok;
+        if (!ok) break;
+        for (int side = 0; side < 2; ++side) {   // remainders of the internal children's rows
+            if (tip[side]) continue;
+#pragma unroll
+            for (int ch = 0; ch < 4; ++ch) {
+                float x[16];
+                row16(X[side], t, ch, x);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) x[j] = tf32_lo(x[j]);
+                tmem_st16(lane_base + 256 + 64 * side + ch * 16, x);
+            }
+        }
+        tmem_wait_st();
+        fence_async_smem();
+        tc_before();
+        __syncthreads();
+        if (t == 0) {
+            tc_after();
+            for (int side = 0; side < 2; ++side) {
+                const uint32_t acc = tmem + 128 * side, xa = smem_u32(X[side]), tb = smem_u32(T[side]);
+                mma_tile(acc, xa, tb, 2 * kMP, false);
+                mma_tile(acc, xa, tb + 2 * kTab, 2 * kMP, true);
+                if (!tip[side]) mma_tile_ta(acc, tmem + 256 + 64 * side, tb, 2 * kMP, true);
+            }
+            mma_commit(&bar[1]);
+        }
+        mma_pending = true;
+        ok = wait_all(&bar[1], ph_mma);
+        mma_pending = !ok;
+        if (!ok) break;
+        // round B: the D^T tables (hi | lo) of each internal child, into its own (now free) T buffer
+        const bool any_q = !tip[0] || !tip[1];
+        if (t == 0 && any_q) {
+            mbar_arrive_expect(&bar[0], (tip[0] ? 0u : 2 * kTab) + (tip[1] ? 0u : 2 * kTab));
+            for (int side = 0; side < 2; ++side) {
+                if (tip[side]) continue;
+                load_tables(T[side], &tm_tab, d, cs[side], l, kTcDT, 1, &bar[0]);
+                load_tables(T[side] + kTab, &tm_tab, d, cs[side], l, kTcDTlo, 1, &bar[0]);
+            }
+        }
+        // epilogue 1: qt and the branch terms; qt (and remainder) of internal children into TMEM
+        tc_after();
+        float dot[2] = {0.f, 0.f};
+#pragma unroll 1
+        for (int ch = 0; ch < 4; ++ch) {
+            float a0[16], u0[16], a1[16], u1[16], x0[16], x1[16], qk[16];
+            tmem_ld16(lane_base + ch * 16, a0);
+            tmem_ld16(lane_base + 64 + ch * 16, u0);
+            tmem_ld16(lane_base + 128 + ch * 16, a1);
+            tmem_ld16(lane_base + 192 + ch * 16, u1);
+            row16(X[0], t, ch, x0);
+            row16(X[1], t, ch, x1);
+            if (root) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) qk[j] = d.pif[16 * ch + j];
+            } else {
+                row16(QK, t, ch, qk);
+            }
+            tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {   // P x = x + D x
+                a0[j] += x0[j];
+                a1[j] += x1[j];
+            }
+            float q0[16], q1[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                q0[j] = qk[j] * a1[j];   // top of branch c0: q_k o P_1 x_1
+                q1[j] = qk[j] * a0[j];
+                dot[0] = fmaf(q0[j], u0[j], dot[0]);
+                dot[1] = fmaf(q1[j], u1[j], dot[1]);
+            }
+            if (!tip[0]) {
+                tmem_st16(lane_base + ch * 16, q0);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) q0[j] = tf32_lo(q0[j]);
+                tmem_st16(lane_base + 64 + ch * 16, q0);
+            }
+            if (!tip[1]) {
+                tmem_st16(lane_base + 128 + ch * 16, q1);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) q1[j] = tf32_lo(q1[j]);
+                tmem_st16(lane_base + 192 + ch * 16, q1);
+            }
+        }
+        tmem_wait_st();
+        {
+            const int dE = Eq + Ex[0] + Ex[1] - Er;
+            const float cw = (float)d.cw[l];
+            for (int side = 0; side < 2; ++side) dsum[side] += cw * ldexpf(dot[side], dE) * inv;
+        }
+        tc_before();
+        __syncthreads();
+        if (any_q) {
+            load_pending = true;
+            ok = wait_all(&bar[0], ph_load);
+            load_pending = !ok;
+            if (!ok) break;
+            if (t == 0) {
+                tc_after();
+                for (int side = 0; side < 2; ++side) {
+                    if (tip[side]) continue;
+                    const uint32_t acc = tmem + 256 + 64 * side, qa = tmem + 128 * side;
+                    const uint32_t tb = smem_u32(T[side]);
+                    mma_tile_ta(acc, qa, tb, kMP, false);
+                    mma_tile_ta(acc, qa, tb + kTab, kMP, true);
+                    mma_tile_ta(acc, qa + 64, tb, kMP, true);
+                }
+                mma_commit(&bar[1]);
+            }
+            mma_pending = true;
+            ok = wait_all(&bar[1], ph_mma);
+            mma_pending = !ok;
+            if (!ok) break;
+            tc_after();
+            // epilogue 2: q_c = qt_c + D_c^T qt_c, scaled, staged (child 0 in QK, child 1 in X[0])
+            for (int side = 0; side < 2; ++side) {
+                if (tip[side]) continue;
+                unsigned char *stage = side ? X[0] : QK;
+                const uint32_t qa = lane_base + 128 * side, acc = lane_base + 256 + 64 * side;
+                float mx = 0.f;
+#pragma unroll
+                for (int ch = 0; ch < 4; ++ch) {
+                    float a[16], q[16];
+                    tmem_ld16(acc + ch * 16, a);
+                    tmem_ld16(qa + ch * 16, q);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) mx = fmaxf(mx, a[j] + q[j]);
+                }
+                const int e = scale_exponent(mx);
+#pragma unroll
+                for (int ch = 0; ch < 4; ++ch) {
+                    float a[16], q[16];
+                    tmem_ld16(acc + ch * 16, a);
+                    tmem_ld16(qa + ch * 16, q);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) a[j] += q[j];
+                    put16(stage, t, ch, a, e);
+                }
+                if (on) __stcg(d.qe + ((size_t)(cs[side] - N) * C + l) * d.Ps + p0 + t, Eq + Ex[1 - side] + e);
+            }
+            fence_async_smem();
+            __syncthreads();
+            if (t == 0) {
+                for (int side = 0; side < 2; ++side) {
+                    if (tip[side]) continue;
+                    unsigned char *stage = side ? X[0] : QK;
+                    for (int kb = 0; kb < 2; ++kb)
+                        tma_store_3d(&tm_pre, stage + kb * kRowKB, kb * 32, p0, (cs[side] - N) * C + l);
+                }
+                bulk_commit();
+                bulk_wait_read0();   // the staging tiles are read before the next category's copies
+            }
+        }
+        tc_before();
+        __syncthreads();
+    }
+    if (ok) {
+        const double w = on ? d.weights[p0 + t] : 0.0;
+        for (int side = 0; side < 2; ++side) {
+            double g = w != 0.0 ? w * (double)dsum[side] : 0.0;
+            g = warp_sum(g);
+            if (lane == 0) red[side][warp] = g;
+        }
+        __syncthreads();
+        if (t < 2) {
+            double g = 0.0;
+            for (int j = 0; j < kTcThreads / 32; ++j) g += red[t][j];
+            d.gpart[(size_t)cs[t] * d.n_gslots + pt] = g;
+        }
+    } else if (t == 0) {
+        atomicOr(d.status, kStatusTimeout);
+        drain(bar, ph_load, ph_mma, load_pending, mma_pending);
+    }
+    tc_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
+constexpr size_t kPre2TcSmem = 1024 + 3 * kRowTile + 8 * kTab;
 constexpr size_t kPostTcSmem = 1024 + 2 * kRowTile + 2 * kTab;
 constexpr size_t kPreTcSmem = 1024 + 4 * kRowTile + 4 * kTab + kRowTile;
 
@@ -609,8 +881,17 @@ cudaError_t launch_m_pre_level_tc(const MDesc &d, const void *tm_post, const voi
                                   int o0, int nd, bool hess, cudaStream_t s) {
     const int n_pt = (d.P + kTcTile - 1) / kTcTile;
     if (nd <= 0 || n_pt <= 0) return cudaSuccess;
-    return hess ? launch_pre_tc<true>(d, tm_post, tm_pre, tm_tab, o0, nd, n_pt, s)
-                : launch_pre_tc<false>(d, tm_post, tm_pre, tm_tab, o0, nd, n_pt, s);
+    if (hess) return launch_pre_tc<true>(d, tm_post, tm_pre, tm_tab, o0, nd, n_pt, s);
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(m_pre_tc2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPre2TcSmem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    m_pre_tc2_kernel<<<nd * n_pt, kTcThreads, kPre2TcSmem, s>>>(
+        d, *static_cast<const CUtensorMap *>(tm_post), *static_cast<const CUtensorMap *>(tm_pre),
+        *static_cast<const CUtensorMap *>(tm_tab), o0, n_pt);
+    return cudaGetLastError();
 }
 
 }  // namespace pg

@@ -54,9 +54,15 @@ def _check(ctx, oracle_mod, pr, hess=True, label=""):
     h = ctx.upload(pr)
     try:
         got = h.eval(pr["b"], grad=True, hess=hess, site=True)
+        plain = h.eval(pr["b"], grad=True, hess=False, site=True) if hess else got
     finally:
         h.close()
     ref = oracle_mod.evaluate(pr, pr["b"])
+    # the evaluation without the Hessian runs its own pre-order kernel: same bounds
+    assert plain["status"] == 0
+    assert abs(plain["logL"] - ref.logL) <= _logl_atol(pr)
+    assert _maxrel(plain["grad"], ref.grad) <= M_GRAD_RTOL
+    print(f"{ctx.kind} {label} (no Hessian): grad {_maxrel(plain['grad'], ref.grad):.2e}")
     el = abs(got["logL"] - ref.logL) / abs(ref.logL)
     eg = _maxrel(got["grad"], ref.grad)
     es = np.abs(got["site_logL"] - ref.site_logL).max() if pr["weights"].shape[0] else 0.0
