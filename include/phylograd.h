@@ -144,9 +144,10 @@ pg_status pg_eval_async(pg_handle *h, const double *d_b, double *d_logL, double 
 /* Evaluate k problems in as few launches as possible (problems are grouped by category count;
  * each launch covers every tile of every problem in the group).  d_b[i], d_grad[i], d_hess[i]
  * are per-problem DEVICE pointers (d_grad/d_hess may be NULL, or have NULL entries);
- * d_logL[k] is one DEVICE array.  The patterns of a problem are split into blocks according to
- * the whole batch, so results agree with separate pg_eval_async calls to rounding order (the
- * per-block partial sums differ), and are identical for the same batch composition.
+ * d_logL[k] is one DEVICE array.  FP32 problems run every level below the root in level
+ * kernels shared by the group (one launch per level index) and the root's level in the fused
+ * kernel; FP64 problems run the fused kernel.  Results agree with separate pg_eval_async calls to
+ * FP32 rounding order (the same parity bounds hold) and are identical for the same batch.
  * Errors: PG_ERR_INVALID (k < 0, a NULL handle, handles from different contexts). */
 pg_status pg_eval_batch_async(pg_handle *const *hs, int32_t k, const double *const *d_b,
                               double *d_logL, double *const *d_grad, double *const *d_hess,

@@ -633,11 +633,11 @@ pg_status pg::host::upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out, c
         while (cut < H - 1 && (int64_t)(tp.level_off[cut + 1] - tp.level_off[cut]) * level_ranges >= 2 * ctx->n_sm)
             ++cut;
     }
-    std::vector<uint8_t> wide(n, 0);
-    for (int lv = 0; lv < cut; ++lv)
+    std::vector<int> plevel(n, -1);   // level index of each node's parent
+    for (int lv = 0; lv < H; ++lv)
         for (int o = tp.level_off[lv]; o < tp.level_off[lv + 1]; ++o) {
-            wide[tp.ops[o].y] = 1;
-            wide[tp.ops[o].z] = 1;
+            plevel[tp.ops[o].y] = lv;
+            plevel[tp.ops[o].z] = lv;
         }
     // the top part (levels >= cut) for the shared-memory top kernel: children of top nodes coded
     // as -1 - slot (a tip), their top index, or n_top + their boundary index
@@ -679,7 +679,8 @@ pg_status pg::host::upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out, c
     const size_t o_pe = cv.take<int>((size_t)(N - 1) * Ps), o_qe = cv.take<int>((size_t)(N - 1) * Ps);
     const size_t o_gp = cv.take<double>((size_t)n * slot_cap), o_hp = cv.take<double>((size_t)n * slot_cap);
     const size_t o_lp = cv.take<double>(slot_cap), o_st = cv.take<int>(1);
-    const size_t o_wide = cv.take<uint8_t>(n), o_sinv = cv.take<float>(std::max(Ps, 16));
+    const size_t o_plv = cv.take<int>(n), o_sinv = cv.take<float>(std::max(Ps, 16));
+    const size_t o_desc = cv.take<pg::ProbDesc>(1);
     const size_t o_ser = cv.take<int>(std::max(Ps, 16));
     const size_t o_tc = cv.take<int2>(top_code.size()), o_bn = cv.take<int>(std::max(n_bnd, 1));
     const size_t o_par = cv.take<int>(n);
@@ -741,7 +742,7 @@ pg_status pg::host::upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out, c
     if (e == cudaSuccess) e = cp(o_Mp, Mpow.data(), sizeof(double) * Mpow.size());
     if (e == cudaSuccess) e = cp(o_qn, qnorm.data(), sizeof(double) * M);
     if (e == cudaSuccess && pr->branch_model) e = cp(o_bm, pr->branch_model, sizeof(int) * n);
-    if (e == cudaSuccess) e = cp(o_wide, wide.data(), wide.size());
+    if (e == cudaSuccess) e = cp(o_plv, plevel.data(), sizeof(int) * plevel.size());
     if (e == cudaSuccess) e = cp(o_tc, top_code.data(), sizeof(int2) * top_code.size());
     if (e == cudaSuccess && n_bnd > 0) e = cp(o_bn, bnd_node.data(), sizeof(int) * n_bnd);
     if (e == cudaSuccess) e = cp(o_par, pr->parent, sizeof(int) * n);
@@ -773,7 +774,7 @@ pg_status pg::host::upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out, c
     d.hpart = reinterpret_cast<double *>(base + o_hp);
     d.lpart = reinterpret_cast<double *>(base + o_lp);
     d.status = reinterpret_cast<int *>(base + o_st);
-    d.wide = reinterpret_cast<const uint8_t *>(base + o_wide);
+    d.plevel = reinterpret_cast<const int *>(base + o_plv);
     d.site_invL = reinterpret_cast<float *>(base + o_sinv);
     d.site_Er = reinterpret_cast<int *>(base + o_ser);
     d.level_ranges = level_ranges;
@@ -852,6 +853,13 @@ pg_status pg::host::upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out, c
     I.stream_bytes = 5ull * (uint64_t)(N - 2) * node_stream + 2ull * (uint64_t)N * P;
     I.flops = (uint64_t)(N - 1) * P * C * (68ull + 216ull);
 
+    // the static descriptor in device memory, for launches that cover several problems
+    h->d_desc = reinterpret_cast<const pg::ProbDesc *>(base + o_desc);
+    if (h2d(pl, base + o_desc, &h->desc, sizeof(pg::ProbDesc)) != cudaSuccess) {
+        release_block(pl, block);
+        delete h;
+        return fail(PG_ERR_CUDA, "upload of the descriptor failed");
+    }
     {
         std::lock_guard<std::mutex> g(ctx->mu);
         if (!pl) ctx->used += bytes;
@@ -993,7 +1001,9 @@ pg_status enqueue_batch(pg_handle *const *hs, int32_t k, int skip, const double 
                 d.out_site = nullptr;
                 d.gscale = d_gscale ? d_gscale + i : nullptr;
                 d.skip = skip;
-                d.cut = 0;   // batched problems run every level in the fused kernel
+                // FP32: every level below the root's in batched level kernels, the root's level
+                // in the fused kernel; FP64: every level in the fused kernel
+                d.cut = (prec == PG_PRECISION_FP32 && d.P > 0) ? d.n_levels - 1 : 0;
                 hess = hess || d.out_hess;
                 a->d[j] = d;
                 a->tile_base[j + 1] = a->tile_base[j] + d.n_tiles;
@@ -1002,9 +1012,36 @@ pg_status enqueue_batch(pg_handle *const *hs, int32_t k, int skip, const double 
                 hs[i]->last_stream = s;
                 if (fwd) hs[i]->have_post = true;
             }
+            // one launch per level index across the group: problem j takes part while L < cut_j
+            int max_cut = 0;
+            for (int j = 0; j < cnt; ++j) max_cut = std::max(max_cut, a->d[j].cut);
+            auto level_batch = [&](int L, pg::LevelBatch &lb) {
+                lb.n = 0;
+                lb.base[0] = 0;
+                for (int j = 0; j < cnt; ++j) {
+                    if (L >= a->d[j].cut) continue;
+                    const pg_handle *hj = hs[idx[at + j]];
+                    const int o0 = hj->level_off[L], nd = hj->level_off[L + 1] - o0;
+                    lb.d[lb.n] = hj->d_desc;
+                    lb.o0[lb.n] = o0;
+                    lb.nr[lb.n] = a->d[j].level_ranges;
+                    lb.base[lb.n + 1] = lb.base[lb.n] + nd * a->d[j].level_ranges;
+                    ++lb.n;
+                }
+            };
+            const int n_sm = hs[0]->ctx->n_sm;
             cudaError_t e = cudaSuccess;
+            pg::LevelBatch lb;
             if (fwd) e = pg::launch_pmatrix<pg::kMaxBatch>(*a, s);
+            for (int L = 0; fwd && e == cudaSuccess && L < max_cut; ++L) {
+                level_batch(L, lb);
+                if (lb.n) e = pg::launch_post_level_batch(lb, C, n_sm, L == 0, s);
+            }
             if (e == cudaSuccess) e = pg::launch_tree<pg::kMaxBatch>(*a, hess, s);
+            for (int L = max_cut - 1; bwd && e == cudaSuccess && L >= 0; --L) {
+                level_batch(L, lb);
+                if (lb.n) e = pg::launch_pre_level_batch(lb, C, hess, n_sm, L == 0, s);
+            }
             if (e == cudaSuccess) e = pg::launch_reduce<pg::kMaxBatch>(*a, hess, s);
             if (e != cudaSuccess) { delete a; return fail(PG_ERR_CUDA, "launch: %s", cudaGetErrorString(e)); }
         }

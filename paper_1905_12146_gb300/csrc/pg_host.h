@@ -47,6 +47,7 @@ struct pg_handle {
     pg::MDesc md{};
     alignas(64) CUtensorMap tm_post, tm_pre, tm_tab;   // TMA descriptors of the tensor-core kernels
     bool external = false;    // the device block belongs to a caller's arena (not freed here)
+    const pg::ProbDesc *d_desc = nullptr;   // device copy of desc (batched level kernels read it)
 };
 
 namespace pg {

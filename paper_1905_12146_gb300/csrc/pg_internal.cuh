@@ -61,9 +61,8 @@ struct ProbDesc {
     double *lpart;                 // [slot_cap] per-(block, piece) log-likelihood sums
     int *status;
     // levels [0, cut) run as one launch per level (level kernels), [cut, n_levels) in the fused
-    // tree kernel; wide[i] = 1 when branch i's parent lies below the cut
+    // tree kernel
     int cut;
-    const uint8_t *wide;
     float *site_invL;              // [P] 1 / Lhat_p, written at the root for the level kernels
     int *site_Er;                  // [P] log2 scale of L_p
     int level_ranges;              // ceil(P / kLevelRange); a wide branch has 4 slots per range
@@ -82,6 +81,9 @@ struct ProbDesc {
     int skip;
     const double *gscale;
     const int *parent;             // [n] parent index, -1 at the root
+    // [n] level index of each node's parent (-1 at the root): a branch whose parent lies below
+    // the cut was summed in level-kernel slots, the others in fused-kernel slots
+    const int *plevel;
     // sizes
     int n_tips, n_nodes, root, n_levels;
     int P;                         // site patterns
@@ -211,6 +213,17 @@ int tree_blocks_per_sm(int C, bool f64);
 // (pg_top.cu); returns cudaErrorNotSupported when they do not fit
 cudaError_t launch_top(const BatchArgs<1> &args, bool hess, int n_sm, cudaStream_t s);
 size_t top_smem_bytes(const ProbDesc &d);
+// one level index of up to kMaxBatch problems in one launch: segment i covers problem
+// d[i]'s nodes [o0[i], o0[i] + nd) x nr[i] pattern ranges, items [base[i], base[i + 1]); d[i] is
+// the problem's descriptor in device memory
+struct LevelBatch {
+    int n;
+    int base[kMaxBatch + 1];
+    int o0[kMaxBatch], nr[kMaxBatch];
+    const ProbDesc *d[kMaxBatch];
+};
+cudaError_t launch_post_level_batch(const LevelBatch &lb, int C, int n_sm, bool cherry, cudaStream_t s);
+cudaError_t launch_pre_level_batch(const LevelBatch &lb, int C, bool hess, int n_sm, bool cherry, cudaStream_t s);
 // one post-order (pre-order) level [o0, o0 + nd) of a single FP32 problem (pg_levels.cu)
 // (cherry: every node of the level has two tip children)
 cudaError_t launch_post_level(const ProbDesc &d, int o0, int nd, int n_sm, bool cherry, cudaStream_t s);

@@ -64,12 +64,14 @@ struct Ring {
 __device__ __forceinline__ unsigned round16(unsigned b) { return (b + 15u) & ~15u; }
 
 struct Item {
+    const ProbDesc *pd;   // the item's problem
     int4 op;
     int rg, p0, cnt;
 };
 
 __device__ __forceinline__ Item item_of(const ProbDesc &d, int o0, int nr, int j) {
     Item it;
+    it.pd = &d;
     const int u = j / nr;
     it.rg = j - u * nr;
     it.op = __ldg(d.ops + o0 + u);
@@ -257,9 +259,9 @@ __device__ __forceinline__ void compute_pre(const ProbDesc &d, const Item &it, c
 // issues the item's bulk copies.  Consumer warps wait for the stage to be full, compute their 32
 // patterns and release it.  Every wait is bounded; a warp that gives up records PG_ERR_TIMEOUT and
 // leaves (the producer first lets the copies it issued land).
-template <class Stage, int STAGES, class Issue, class Compute>
-__device__ __forceinline__ void staged_walk(const ProbDesc &d, int o0, int nr, int n_items,
-                                            Ring<Stage, STAGES> &ring, Issue &&issue, Compute &&compute) {
+template <class Stage, int STAGES, class ItemFn, class Issue, class Compute>
+__device__ __forceinline__ void staged_walk(int n_items, Ring<Stage, STAGES> &ring, ItemFn &&item_at, Issue &&issue,
+                                            Compute &&compute) {
     const int G = gridDim.x, b = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -278,11 +280,12 @@ __device__ __forceinline__ void staged_walk(const ProbDesc &d, int o0, int nr, i
             const int j = b + i * G;
             if (j >= n_items) break;
             const int s = i % STAGES, use = i / STAGES;
+            const Item it = item_at(j);
             if (use > 0 && !mbar_wait_bounded(&ring.empty[s], (unsigned)(use - 1) & 1u, kWaitLimitCycles)) {
-                atomicOr(d.status, kStatusTimeout);
+                atomicOr(it.pd->status, kStatusTimeout);
                 break;
             }
-            issue(item_of(d, o0, nr, j), ring.st[s], &ring.full[s]);
+            issue(it, ring.st[s], &ring.full[s]);
         }
         // let every copy issued by this warp land before the block may leave
         for (int q = (i > STAGES ? i - STAGES : 0); q < i; ++q)
@@ -293,34 +296,71 @@ __device__ __forceinline__ void staged_walk(const ProbDesc &d, int o0, int nr, i
         const int j = b + i * G;
         if (j >= n_items) break;
         const int s = i % STAGES;
+        const Item it = item_at(j);
         if (!mbar_wait_bounded(&ring.full[s], (unsigned)(i / STAGES) & 1u, kWaitLimitCycles)) {
-            if (lane == 0) atomicOr(d.status, kStatusTimeout);
+            if (lane == 0) atomicOr(it.pd->status, kStatusTimeout);
             return;
         }
-        compute(item_of(d, o0, nr, j), ring.st[s], threadIdx.x);
+        compute(it, ring.st[s], threadIdx.x);
         __syncwarp();
         if (lane == 0) mbar_arrive(&ring.empty[s]);
     }
 }
 
-template <int C, int STAGES, bool CHERRY>
-__global__ void __launch_bounds__(kLevelThreads) post_level_kernel(const __grid_constant__ ProbDesc d, int o0, int nr, int n_items) {
+// the item source of one problem's level, or of one level index across a batch of problems
+struct OneLevel {
+    const ProbDesc &d;
+    int o0, nr;
+    __device__ Item operator()(int j) const { return item_of(d, o0, nr, j); }
+};
+struct BatchLevel {
+    const LevelBatch &lb;
+    __device__ Item operator()(int j) const {
+        int lo = 0, hi = lb.n - 1;   // the segment holding item j: base[lo] <= j < base[lo + 1]
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (lb.base[mid] <= j) lo = mid;
+            else hi = mid - 1;
+        }
+        return item_of(*lb.d[lo], lb.o0[lo], lb.nr[lo], j - lb.base[lo]);
+    }
+};
+
+template <int C, int STAGES, bool CHERRY, class Src>
+__device__ __forceinline__ void post_walk(int n_items, const Src &src) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using St = PostStage<C, CHERRY>;
     auto &ring = *reinterpret_cast<Ring<St, STAGES> *>(smem_raw);
-    staged_walk(d, o0, nr, n_items, ring,
-                [&](const Item &it, St &st, uint64_t *bar) { issue_post<C, CHERRY>(d, it, st, bar); },
-                [&](const Item &it, const St &st, int t) { compute_post<C, CHERRY>(d, it, st, t); });
+    staged_walk(n_items, ring, src,
+                [&](const Item &it, St &st, uint64_t *bar) { issue_post<C, CHERRY>(*it.pd, it, st, bar); },
+                [&](const Item &it, const St &st, int t) { compute_post<C, CHERRY>(*it.pd, it, st, t); });
 }
-
-template <int C, bool HESS, int STAGES, bool CHERRY>
-__global__ void __launch_bounds__(kLevelThreads) pre_level_kernel(const __grid_constant__ ProbDesc d, int o0, int nr, int n_items) {
+template <int C, bool HESS, int STAGES, bool CHERRY, class Src>
+__device__ __forceinline__ void pre_walk(int n_items, const Src &src) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using St = PreStage<C, CHERRY>;
     auto &ring = *reinterpret_cast<Ring<St, STAGES> *>(smem_raw);
-    staged_walk(d, o0, nr, n_items, ring,
-                [&](const Item &it, St &st, uint64_t *bar) { issue_pre<C, CHERRY>(d, it, st, bar); },
-                [&](const Item &it, const St &st, int t) { compute_pre<C, HESS, CHERRY>(d, it, st, t); });
+    staged_walk(n_items, ring, src,
+                [&](const Item &it, St &st, uint64_t *bar) { issue_pre<C, CHERRY>(*it.pd, it, st, bar); },
+                [&](const Item &it, const St &st, int t) { compute_pre<C, HESS, CHERRY>(*it.pd, it, st, t); });
+}
+
+template <int C, int STAGES, bool CHERRY>
+__global__ void __launch_bounds__(kLevelThreads) post_level_kernel(const __grid_constant__ ProbDesc d, int o0, int nr, int n_items) {
+    post_walk<C, STAGES, CHERRY>(n_items, OneLevel{d, o0, nr});
+}
+template <int C, bool HESS, int STAGES, bool CHERRY>
+__global__ void __launch_bounds__(kLevelThreads) pre_level_kernel(const __grid_constant__ ProbDesc d, int o0, int nr, int n_items) {
+    pre_walk<C, HESS, STAGES, CHERRY>(n_items, OneLevel{d, o0, nr});
+}
+// one level index of every problem of a batch (descriptors in device memory)
+template <int C, int STAGES, bool CHERRY>
+__global__ void __launch_bounds__(kLevelThreads) post_level_batch_kernel(const __grid_constant__ LevelBatch lb, int n_items) {
+    post_walk<C, STAGES, CHERRY>(n_items, BatchLevel{lb});
+}
+template <int C, bool HESS, int STAGES, bool CHERRY>
+__global__ void __launch_bounds__(kLevelThreads) pre_level_batch_kernel(const __grid_constant__ LevelBatch lb, int n_items) {
+    pre_walk<C, HESS, STAGES, CHERRY>(n_items, BatchLevel{lb});
 }
 
 constexpr int kPostStages = 2, kPreStages = 2, kCherryStages = 3;
@@ -352,6 +392,47 @@ cudaError_t launch_pdl(K kernel, int blocks, size_t smem, cudaStream_t s, const 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kernel, d, o0, nr, n_items);
+}
+
+template <class K, class A>
+cudaError_t launch_pdl_batch(K kernel, int blocks, size_t smem, cudaStream_t s, const A &lb, int n_items) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3(kLevelThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, lb, n_items);
+}
+
+template <int C, bool CHERRY>
+cudaError_t post_batch_c(const LevelBatch &lb, int n_sm, cudaStream_t s) {
+    static bool configured = false;
+    static int per_sm = 1;
+    constexpr int ST = CHERRY ? kCherryStages : kPostStages;
+    const int n_items = lb.base[lb.n];
+    if (n_items <= 0) return cudaSuccess;
+    const size_t smem = sizeof(Ring<PostStage<C, CHERRY>, ST>);
+    const int blocks = persistent_blocks(post_level_batch_kernel<C, ST, CHERRY>, smem, n_sm, n_items, configured, per_sm);
+    if (blocks < 0) return cudaErrorInvalidConfiguration;
+    return launch_pdl_batch(post_level_batch_kernel<C, ST, CHERRY>, blocks, smem, s, lb, n_items);
+}
+
+template <int C, bool HESS, bool CHERRY>
+cudaError_t pre_batch_c(const LevelBatch &lb, int n_sm, cudaStream_t s) {
+    static bool configured = false;
+    static int per_sm = 1;
+    constexpr int ST = CHERRY ? kCherryStages : kPreStages;
+    const int n_items = lb.base[lb.n];
+    if (n_items <= 0) return cudaSuccess;
+    const size_t smem = sizeof(Ring<PreStage<C, CHERRY>, ST>);
+    const int blocks = persistent_blocks(pre_level_batch_kernel<C, HESS, ST, CHERRY>, smem, n_sm, n_items, configured, per_sm);
+    if (blocks < 0) return cudaErrorInvalidConfiguration;
+    return launch_pdl_batch(pre_level_batch_kernel<C, HESS, ST, CHERRY>, blocks, smem, s, lb, n_items);
 }
 
 template <int C, bool CHERRY>
@@ -412,6 +493,42 @@ cudaError_t launch_pre_level(const ProbDesc &d, int o0, int nd, bool hess, int n
         case 17: return pre_c<4, false, true>(d, o0, nd, n_sm, s);
         case 18: return pre_c<4, true, false>(d, o0, nd, n_sm, s);
         case 19: return pre_c<4, true, true>(d, o0, nd, n_sm, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_post_level_batch(const LevelBatch &lb, int C, int n_sm, bool cherry, cudaStream_t s) {
+    switch (C * 2 + (cherry ? 1 : 0)) {
+        case 2: return post_batch_c<1, false>(lb, n_sm, s);
+        case 3: return post_batch_c<1, true>(lb, n_sm, s);
+        case 4: return post_batch_c<2, false>(lb, n_sm, s);
+        case 5: return post_batch_c<2, true>(lb, n_sm, s);
+        case 6: return post_batch_c<3, false>(lb, n_sm, s);
+        case 7: return post_batch_c<3, true>(lb, n_sm, s);
+        case 8: return post_batch_c<4, false>(lb, n_sm, s);
+        case 9: return post_batch_c<4, true>(lb, n_sm, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_pre_level_batch(const LevelBatch &lb, int C, bool hess, int n_sm, bool cherry, cudaStream_t s) {
+    switch (C * 4 + (hess ? 2 : 0) + (cherry ? 1 : 0)) {
+        case 4: return pre_batch_c<1, false, false>(lb, n_sm, s);
+        case 5: return pre_batch_c<1, false, true>(lb, n_sm, s);
+        case 6: return pre_batch_c<1, true, false>(lb, n_sm, s);
+        case 7: return pre_batch_c<1, true, true>(lb, n_sm, s);
+        case 8: return pre_batch_c<2, false, false>(lb, n_sm, s);
+        case 9: return pre_batch_c<2, false, true>(lb, n_sm, s);
+        case 10: return pre_batch_c<2, true, false>(lb, n_sm, s);
+        case 11: return pre_batch_c<2, true, true>(lb, n_sm, s);
+        case 12: return pre_batch_c<3, false, false>(lb, n_sm, s);
+        case 13: return pre_batch_c<3, false, true>(lb, n_sm, s);
+        case 14: return pre_batch_c<3, true, false>(lb, n_sm, s);
+        case 15: return pre_batch_c<3, true, true>(lb, n_sm, s);
+        case 16: return pre_batch_c<4, false, false>(lb, n_sm, s);
+        case 17: return pre_batch_c<4, false, true>(lb, n_sm, s);
+        case 18: return pre_batch_c<4, true, false>(lb, n_sm, s);
+        case 19: return pre_batch_c<4, true, true>(lb, n_sm, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -271,7 +271,7 @@ extern "C" pg_status pg_eval_noalloc(const pg_problem *pr, const double *b, doub
     d.lpart = reinterpret_cast<double *>(base + o_lp);
     d.status = reinterpret_cast<int *>(base + o_st);
     d.cut = 0;
-    d.wide = nullptr;
+    d.plevel = nullptr;
     d.site_invL = reinterpret_cast<float *>(base + o_sinv);
     d.site_Er = reinterpret_cast<int *>(base + o_ser);
     d.b = reinterpret_cast<const double *>(base + o_ib);

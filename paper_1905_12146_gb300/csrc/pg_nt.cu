@@ -758,7 +758,7 @@ __global__ void __launch_bounds__(256) reduce_kernel(const __grid_constant__ Bat
     double g = 0.0, h = 0.0;
     if (item != d.root) {
         // branches below the cut were reduced per level-kernel block, the others per fused slot
-        const int ns = (d.cut > 0 && d.wide[item]) ? d.level_ranges * (kLevelRange / 32) : d.n_tg;
+        const int ns = (d.cut > 0 && d.plevel[item] < d.cut) ? d.level_ranges * (kLevelRange / 32) : d.n_tg;
         const double *gp = d.gpart + (size_t)item * d.slot_cap;
         for (int j = lane; j < ns; j += 32) g += gp[j];
         g = warp_sum(g);

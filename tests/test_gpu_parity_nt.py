@@ -182,9 +182,11 @@ def test_nucleotide_configuration_full_size(ctx, oracle_mod):
     print(f"\nconfig nucleotide: logL rel err {rel:.3e}, grad max-norm rel err {gerr:.3e}")
 
 
-def test_batch_equals_single(ctx):
-    """Results alone and inside a batched launch agree to 1e-12 relative (a batch may split a
-    problem's patterns over a different number of blocks, which only regroups FP64 sums)."""
+def test_batch_equals_single(ctx, oracle_mod):
+    """A batched launch runs every level below the root in level kernels shared by the batch
+    (a problem alone runs its narrow levels in the top kernel), so batch and single results differ
+    by FP32 rounding order only: both meet the parity bounds against the oracle, and they agree
+    with each other within the same bounds."""
     torch = pytest.importorskip("torch")
     probs = [wl.random_problem(20 + 7 * i, 100 + 31 * i, n_states=4, n_cat=1 + i % 4, seed=200 + i,
                                ambiguous=0.02) for i in range(6)]
@@ -205,10 +207,15 @@ def test_batch_equals_single(ctx):
     hhs = [torch.zeros_like(b) for b in bs]
     _native.eval_batch_async(hs, bs, lgs, gs, hhs)
     torch.cuda.synchronize()
-    for i in range(len(hs)):
-        assert torch.allclose(lgs[i:i + 1], single[i][0], rtol=1e-12, atol=0)
-        for got, ref in ((gs[i], single[i][1]), (hhs[i], single[i][2])):
-            assert (got - ref).abs().max() <= 1e-12 * ref.abs().max()
+    for i, p in enumerate(probs):
+        ref = oracle_mod.evaluate(p, p["b"])
+        tol = _logl_tol(p, ref.logL, "fp32")
+        for lg, g, hh in ((lgs[i].item(), gs[i], hhs[i]), (single[i][0].item(), single[i][1], single[i][2])):
+            assert abs(lg - ref.logL) <= tol
+            assert np.abs(g.cpu().numpy() - ref.grad).max() <= GRAD_RTOL * np.abs(ref.grad).max()
+            assert np.abs(hh.cpu().numpy() - ref.hess).max() <= HESS_RTOL * np.abs(ref.hess).max()
+        assert abs(lgs[i].item() - single[i][0].item()) <= 2 * tol
+        assert (gs[i] - single[i][1]).abs().max().item() <= 2 * GRAD_RTOL * np.abs(ref.grad).max()
     for h in hs:
         h.close()
 
@@ -278,9 +285,11 @@ def test_host_validation(ctx):
         with pytest.raises(_native.PhyloGradError) as e:
             ctx.upload(broken)
         assert e.value.status == _native.PG_ERR_INVALID
-    with pytest.raises(_native.PhyloGradError) as e:
-        ctx.upload(wl.random_problem(5, 4, n_states=20, seed=1))
-    assert e.value.status == _native.PG_ERR_UNSUPPORTED
+    for unsupported, precision in ((wl.random_problem(5, 4, n_states=65, seed=1), "fp32"),   # > 64 states
+                                   (wl.random_problem(5, 4, n_states=20, seed=1), "fp64")):  # FP64: 4 states
+        with pytest.raises(_native.PhyloGradError) as e:
+            ctx.upload(unsupported, precision)
+        assert e.value.status == _native.PG_ERR_UNSUPPORTED
 
 
 def test_budget_admission():
