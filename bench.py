@@ -258,7 +258,7 @@ def _serving(n_requests: int, device: int):
     return out
 
 
-def _differentiation(device: int, steps: int = 30):
+def _differentiation(device: int, steps: int = 30, warmup: int = 3):
     """The differentiation batch: 64 trees x 300 taxa x 5,000 patterns, one category; one step is
     the clock branch lengths, the batched forward (post-order) and the autograd backward (pre-order
     gradient kernels and the clock chain rule)."""
@@ -279,7 +279,7 @@ def _differentiation(device: int, steps: int = 30):
         eps.grad = mu.grad = t.grad = None
         autograd.tree_loglik(autograd.clock_branch_lengths(eps, mu, t, hs), hs).sum().backward()
 
-    for _ in range(3):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -299,7 +299,42 @@ def _differentiation(device: int, steps: int = 30):
             "algorithmic_bytes_per_step": nbytes, "achieved_gbs": nbytes / (ms * 1e-3) / 1e9}
 
 
-def _codon(device: int, steps: int = 20):
+def _inference(device: int):
+    """The shape of the paper's Table 1: maximum-likelihood branch rates by L-BFGS with the
+    analytic gradient against central finite differences, on a 104-taxon Yule tree (206 rates, as
+    the paper's smallest example) with 1,000 simulated patterns.  FP64 partials (as the paper's
+    implementation): with FP32 partials a central difference at h = 1e-6 is dominated by rounding
+    (~1e-7 |logL| / 2h)."""
+    import numpy as np
+
+    from paper_1905_12146_gb300 import _native, inference, workloads
+
+    pr = workloads.config_clock_batch(seed=31, n_trees=1, n_tips=104, n_patterns=1000)[0]
+    ctx = _native.Context(device)
+    h = ctx.upload(pr, "fp64")
+    par = pr["parent"]
+    theta0 = np.zeros(par.shape[0])
+    theta0[par >= 0] = np.log(pr["mu"])
+    out = {"workload": "104-taxon Yule tree, 206 branch rates, 1,000 simulated patterns, 1 category, "
+                       "FP64 partials; L-BFGS (history 10, strong Wolfe) until |change| < 1e-9",
+           "rates": int((par >= 0).sum())}
+    # one-time set-up (CUDA module loading of the optimiser's and the library's kernels) outside
+    # the timings
+    inference.rate_mle(h, pr["node_time"], theta0, "analytic", max_iter=500, tolerance_change=1e-9)
+    inference.rate_mle(h, pr["node_time"], theta0, "numeric", max_iter=2)
+    for method in ("analytic", "numeric"):
+        r = inference.rate_mle(h, pr["node_time"], theta0, method, max_iter=500, tolerance_change=1e-9)
+        out[method] = {"seconds": r["seconds"], "iterations": r["iterations"], "logL": r["logL"],
+                       "objective_evaluations": r["objective_evaluations"], "forward_passes": r["forward_passes"]}
+    a, n = out["analytic"], out["numeric"]
+    out["speedup_per_iteration"] = (n["seconds"] / max(n["iterations"], 1)) / (a["seconds"] / max(a["iterations"], 1))
+    out["speedup_total"] = n["seconds"] / a["seconds"]
+    h.close()
+    ctx.close()
+    return out
+
+
+def _codon(device: int, steps: int = 20, warmup: int = 3):
     """The codon configuration: 500 taxa x 3,000 patterns x 4 categories, 61 states, tensor-core
     kernels (three-pass TF32, FP32 accumulation)."""
     import torch
@@ -313,7 +348,7 @@ def _codon(device: int, steps: int = 20):
     b = torch.tensor(pr["b"], device=dev)
     lg = torch.zeros(1, dtype=torch.float64, device=dev)
     g = torch.zeros_like(b)
-    for _ in range(3):
+    for _ in range(warmup):
         h.eval_async(b, lg, g)
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -452,6 +487,7 @@ def run_gpu(args):
     if rank == 0 and not args.no_extras:
         line["codon"] = _codon(local)
         line["differentiation"] = _differentiation(local)
+        line["inference"] = _inference(local)
         if args.serving_requests > 0:
             line["serving"] = _serving(args.serving_requests, local)
     if dist is not None:
@@ -471,6 +507,9 @@ def main():
                     help="requests of the serving measurement (0 skips it)")
     ap.add_argument("--no-extras", action="store_true",
                     help="only the headline nucleotide measurement (no codon, differentiation, serving)")
+    ap.add_argument("--case", choices=("all", "codon", "differentiation"), default="all",
+                    help="codon / differentiation: time that workload alone for --steps steps after "
+                         "--warmup (for profiling); all: the full measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -478,6 +517,11 @@ def main():
         return run_reference(args)
     from paper_1905_12146_gb300 import build
     build.build()
+    if args.case != "all":
+        _, _, local = _rank_env()
+        fn = _codon if args.case == "codon" else _differentiation
+        print(json.dumps({"case": args.case, **fn(local, steps=args.steps, warmup=args.warmup)}), flush=True)
+        return 0
     return run_gpu(args)
 
 

@@ -229,6 +229,7 @@ class Handle:
         self.ctx = ctx
         pr, _keep = problem_struct(problem, precision)
         n = pr.n_tips * 2 - 1
+        self.root = int(np.flatnonzero(_keep[0] < 0)[0])
         out = ctypes.c_void_p()
         check(lib.pg_upload(ctx._ptr, ctypes.byref(pr), ctypes.byref(out)))
         self._ptr = out
