@@ -45,6 +45,23 @@ def _rank_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def _max_over_ranks(seconds: float, dist, device):
+    """Slowest rank's time (the job takes as long as its slowest replica); identity alone."""
+    if dist is None:
+        return seconds
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_throughput(units_per_rank: int, seconds: float, world: int, dist, device):
+    """Whole-job throughput of replicas: every rank processed units_per_rank units of its own
+    (weak scaling, no data-path collective); value = all ranks' units / the slowest rank's time."""
+    slowest = _max_over_ranks(seconds, dist, device)
+    return world * units_per_rank / slowest, slowest
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -418,12 +435,8 @@ def run_gpu(args):
     pt = h.phase_times()
     h.set_phase_timing(False)
     status = h.status()
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    ms_per_step = ms / args.steps
-    value = world * args.steps / (ms / 1e3)
+    value, seconds = _job_throughput(args.steps, ms / 1e3, world, dist, dev)
+    ms_per_step = seconds * 1e3 / args.steps
 
     # end to end: the blocking host-pointer call, pinned host buffers, copies inside the region
     b_host = torch.tensor(pr["b"]).pin_memory()
@@ -438,13 +451,8 @@ def run_gpu(args):
         st = lib.pg_eval(h._ptr, b_host.data_ptr(), out_logL.data_ptr(), out_grad.data_ptr(), None, None)
         if st != 0:
             raise SystemExit(f"pg_eval failed with status {st}")
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
-           "d2h_bytes_per_step": 8 + 8 * n}
+    e2e_value, _ = _job_throughput(e2e_steps, time.perf_counter() - t0, world, dist, dev)
+    e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 + 8 * n}
 
     peak, peak_kind = _peaks()
     pre_ms = pt.pre_levels_ms / max(pt.evals, 1)
