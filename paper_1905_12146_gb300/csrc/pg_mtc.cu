@@ -594,124 +594,167 @@ m_pre_tc_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtenso
     if (warp == 0) tmem_dealloc(tmem, kCols);
 }
 
-// ---- pre-order level without the Hessian: two load rounds per category ----------------------------
-// Round A brings q_k, both children's rows and both children's [D; G] tables (hi | lo); the rows'
-// TF32 remainders go to tensor memory, and six MMA groups give A_c = x_c [D_c; G_c]^T (TMEM columns
-// 128 c .. +127).  Round B (both children's D^T tables) is issued at once and lands while the
-// epilogue forms qt_c = q_k o (x_other + D_other x_other), the branch terms qt_c . (G_c x_c), and
-// writes qt_c (columns 128 c .. +63) and its remainder (+64 .. +127) back into tensor memory in
-// place; the products D_c^T qt_c then read A from tensor memory into columns 256 + 64 c.
-__global__ void __launch_bounds__(kTcThreads, 1)
+// ---- pre-order level without the Hessian: loads of the next category overlap this one ----------------
+// Tensor memory holds, per category, A_c = x_c [D_c; G_c]^T (columns 128 c .. +127) and the
+// children's rows as MMA A operands: x_c (256 + 128 c .. +63) and its TF32 remainder (+64 .. +127);
+// the shared-memory row slots are only staging for TMA, so the next category's rows are copied
+// into them while this category's products and epilogues run.  Per category: rows -> TMEM,
+// products with both children's [D; G] tables, the epilogue forms qt_c = q_k o (x_other +
+// D_other x_other) and the branch terms and writes qt_c (and remainder) over x_c in tensor memory,
+// the D_c^T tables arrive meanwhile, the products D_c^T qt_c (columns 128 c .. +63 again) give
+// q_c = qt_c + D_c^T qt_c, stored straight from registers.  Tip children's one-hot rows are
+// written into tensor memory by the threads.
+__global__ void __launch_bounds__(2 * kTcThreads, 1)
 m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtensorMap tm_post,
                  const __grid_constant__ CUtensorMap tm_pre, const __grid_constant__ CUtensorMap tm_tab, int o0, int n_pt) {
     extern __shared__ __align__(1024) unsigned char tc_raw[];
-    unsigned char *sm = align1024(tc_raw);
-    unsigned char *X[2] = {sm, sm + kRowTile};                 // children's rows
+    if (smem_u32(tc_raw) & 1023u) {   // the layout needs a 1024-byte aligned base (see kPre2TcSmem)
+        if (threadIdx.x == 0) atomicOr(d.status, kStatusTimeout);
+        return;
+    }
+    unsigned char *sm = tc_raw;
+    unsigned char *X[2] = {sm, sm + kRowTile};                 // children's rows (staging)
     unsigned char *QK = sm + 2 * kRowTile;                      // q_k rows
-    unsigned char *T[2] = {sm + 3 * kRowTile, sm + 3 * kRowTile + 4 * kTab};   // [D; G] hi | lo per child
-    __shared__ __align__(8) uint64_t bar[2];
+    unsigned char *T[2] = {sm + 3 * kRowTile, sm + 3 * kRowTile + 4 * kTab};   // [D; G] or D^T, hi | lo
+    enum { BX = 0, BQ = 1, BT = 2, BD = 3, BM = 4, NB = 5 };    // rows, q_k, [D;G], D^T, products
+    __shared__ __align__(8) uint64_t bar[NB];
     __shared__ uint32_t tmem_slot;
     __shared__ double red[2][kTcThreads / 32];
-    const int C = d.C, N = d.n_tips, t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    __shared__ float half_part[2][2][kTcTile];   // per child, per half of the states, per row
+    // 8 warps: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its quadrant) = rows t, and half w / 4
+    // of the 64 states (chunks 2 hf, 2 hf + 1)
+    const int C = d.C, N = d.n_tips, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int hf = warp >> 2, t = 32 * (warp & 3) + lane, ch0 = 2 * hf;
     const int u = blockIdx.x / n_pt, pt = blockIdx.x - u * n_pt;
     const int4 op = __ldg(d.ops + o0 + u);
     const int k = op.x, p0 = pt * kTcTile, cnt = min(kTcTile, d.P - p0);
     const bool root = k == d.root;
     const int cs[2] = {op.y, op.z};
     const bool tip[2] = {op.y < N, op.z < N};
+    const bool any_int = !tip[0] || !tip[1];
     if (warp == 0) tmem_alloc(&tmem_slot, 512);
-    if (t == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-    }
+    if (threadIdx.x == 0)
+        for (int i = 0; i < NB; ++i) mbar_init(&bar[i], 1);
     tc_before();
     __syncthreads();
     tc_after();
-    const uint32_t tmem = tmem_slot, lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    const bool leader = threadIdx.x == 0;   // issues every copy and product
+    const uint32_t tmem = tmem_slot, lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
     const bool on = t < cnt;
     const float inv = on ? __ldcg(d.site_invL + p0 + t) : 0.f;
     const int Er = on ? __ldcg(d.site_Er + p0 + t) : 0;
     float dsum[2] = {0.f, 0.f};
-    uint32_t ph_load = 0, ph_mma = 0;
-    bool ok = true, load_pending = false, mma_pending = false;
+    uint32_t ph[NB] = {0, 0, 0, 0, 0};
+    bool pend[NB] = {false, false, false, false, false};
+    bool ok = true;
+    // copies (thread 0): rows of the internal children, q_k, tables
+    auto issue_rows = [&](int l) {
+        uint32_t bytes = 0;
+        for (int side = 0; side < 2; ++side) bytes += tip[side] ? 0u : kRowTile;
+        if (!bytes) return;
+        pend[BX] = true;
+        mbar_arrive_expect(&bar[BX], bytes);
+        for (int side = 0; side < 2; ++side)
+            if (!tip[side])
+                for (int kb = 0; kb < 2; ++kb)
+                    tma_load_3d(X[side] + kb * kRowKB, &tm_post, kb * 32, p0, (cs[side] - N) * C + l, &bar[BX]);
+    };
+    auto issue_qk = [&](int l) {
+        pend[BQ] = true;
+        mbar_arrive_expect(&bar[BQ], kRowTile);
+        for (int kb = 0; kb < 2; ++kb) tma_load_3d(QK + kb * kRowKB, &tm_pre, kb * 32, p0, (k - N) * C + l, &bar[BQ]);
+    };
+    auto issue_tables = [&](int l) {
+        pend[BT] = true;
+        mbar_arrive_expect(&bar[BT], 8 * kTab);
+        for (int side = 0; side < 2; ++side) {
+            load_tables(T[side], &tm_tab, d, cs[side], l, kTcD, 2, &bar[BT]);
+            load_tables(T[side] + 2 * kTab, &tm_tab, d, cs[side], l, kTcDlo, 2, &bar[BT]);
+        }
+    };
+    auto wait = [&](int i) {   // all threads, one phase of barrier i
+        ok = wait_all(&bar[i], ph[i]);
+        if (ok) pend[i] = false;
+        return ok;
+    };
+    if (leader) {
+        issue_rows(0);
+        if (!root) issue_qk(0);
+        issue_tables(0);
+    }
     for (int l = 0; l < C && ok; ++l) {
         const int Eq = (on && !root) ? __ldcg(d.qe + ((size_t)(k - N) * C + l) * d.Ps + p0 + t) : 0;
         int Ex[2];
         for (int side = 0; side < 2; ++side)
             Ex[side] = (on && !tip[side]) ? __ldcg(d.pe + ((size_t)(cs[side] - N) * C + l) * d.Ps + p0 + t) : 0;
-        // round A
-        if (t == 0) {
-            uint32_t bytes = 8 * kTab;
-            if (!root) bytes += kRowTile;
-            for (int side = 0; side < 2; ++side) bytes += tip[side] ? 0u : kRowTile;
-            mbar_arrive_expect(&bar[0], bytes);
-            if (!root)
-                for (int kb = 0; kb < 2; ++kb) tma_load_3d(QK + kb * kRowKB, &tm_pre, kb * 32, p0, (k - N) * C + l, &bar[0]);
-            for (int side = 0; side < 2; ++side) {
-                if (!tip[side])
-                    for (int kb = 0; kb < 2; ++kb)
-                        tma_load_3d(X[side] + kb * kRowKB, &tm_post, kb * 32, p0, (cs[side] - N) * C + l, &bar[0]);
-                load_tables(T[side], &tm_tab, d, cs[side], l, kTcD, 2, &bar[0]);
-                load_tables(T[side] + 2 * kTab, &tm_tab, d, cs[side], l, kTcDlo, 2, &bar[0]);
-            }
-        }
-        for (int side = 0; side < 2; ++side)   // a tip's exact one-hot rows: no remainder pass
-            if (tip[side]) tip_row(X[side], d, cs[side], p0, cnt, t);
-        load_pending = true;
-        ok = wait_all(&bar[0], ph_load);
-        load_pending = !ok;
-        if (!ok) break;
-        for (int side = 0; side < 2; ++side) {   // remainders of the internal children's rows
-            if (tip[side]) continue;
+        // the children's rows (and remainders) into tensor memory
+        if (any_int && !wait(BX)) break;
+        for (int side = 0; side < 2; ++side) {
+            const uint32_t xc = lane_base + 256 + 128 * side;
+            if (tip[side]) {   // one-hot (all-ones for a code >= m) rows
+                const int y = on ? (int)__ldg(d.tips + (size_t)cs[side] * d.Ps + p0 + t) : -1;
 #pragma unroll
-            for (int ch = 0; ch < 4; ++ch) {
+                for (int ch = ch0; ch < ch0 + 2; ++ch) {
+                    float x[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int st = 16 * ch + j;
+                        x[j] = (y >= 0 && (y >= d.m ? st < d.m : st == y)) ? 1.f : 0.f;
+                    }
+                    tmem_st16(xc + ch * 16, x);
+                }
+                continue;
+            }
+#pragma unroll
+            for (int ch = ch0; ch < ch0 + 2; ++ch) {
                 float x[16];
                 row16(X[side], t, ch, x);
+                tmem_st16(xc + ch * 16, x);
 #pragma unroll
                 for (int j = 0; j < 16; ++j) x[j] = tf32_lo(x[j]);
-                tmem_st16(lane_base + 256 + 64 * side + ch * 16, x);
+                tmem_st16(xc + 64 + ch * 16, x);
             }
         }
         tmem_wait_st();
-        fence_async_smem();
         tc_before();
-        __syncthreads();
-        if (t == 0) {
+        __syncthreads();   // rows read: the slots may take the next category's rows
+        if (leader && l + 1 < C) issue_rows(l + 1);
+        if (!wait(BT)) break;
+        if (leader) {
             tc_after();
             for (int side = 0; side < 2; ++side) {
-                const uint32_t acc = tmem + 128 * side, xa = smem_u32(X[side]), tb = smem_u32(T[side]);
-                mma_tile(acc, xa, tb, 2 * kMP, false);
-                mma_tile(acc, xa, tb + 2 * kTab, 2 * kMP, true);
-                if (!tip[side]) mma_tile_ta(acc, tmem + 256 + 64 * side, tb, 2 * kMP, true);
+                const uint32_t acc = tmem + 128 * side, xa = tmem + 256 + 128 * side, tb = smem_u32(T[side]);
+                mma_tile_ta(acc, xa, tb, 2 * kMP, false);
+                mma_tile_ta(acc, xa, tb + 2 * kTab, 2 * kMP, true);
+                if (!tip[side]) mma_tile_ta(acc, xa + 64, tb, 2 * kMP, true);
             }
-            mma_commit(&bar[1]);
+            pend[BM] = true;
+            mma_commit(&bar[BM]);
         }
-        mma_pending = true;
-        ok = wait_all(&bar[1], ph_mma);
-        mma_pending = !ok;
-        if (!ok) break;
-        // round B: the D^T tables (hi | lo) of each internal child, into its own (now free) T buffer
-        const bool any_q = !tip[0] || !tip[1];
-        if (t == 0 && any_q) {
-            mbar_arrive_expect(&bar[0], (tip[0] ? 0u : 2 * kTab) + (tip[1] ? 0u : 2 * kTab));
+        if (!wait(BM)) break;
+        // the D^T tables of the internal children into their (now free) table slots
+        if (leader && any_int) {
+            pend[BD] = true;
+            mbar_arrive_expect(&bar[BD], (tip[0] ? 0u : 2 * kTab) + (tip[1] ? 0u : 2 * kTab));
             for (int side = 0; side < 2; ++side) {
                 if (tip[side]) continue;
-                load_tables(T[side], &tm_tab, d, cs[side], l, kTcDT, 1, &bar[0]);
-                load_tables(T[side] + kTab, &tm_tab, d, cs[side], l, kTcDTlo, 1, &bar[0]);
+                load_tables(T[side], &tm_tab, d, cs[side], l, kTcDT, 1, &bar[BD]);
+                load_tables(T[side] + kTab, &tm_tab, d, cs[side], l, kTcDTlo, 1, &bar[BD]);
             }
         }
-        // epilogue 1: qt and the branch terms; qt (and remainder) of internal children into TMEM
+        if (!root && !wait(BQ)) break;
+        // epilogue 1: qt, the branch terms; qt of internal children over their rows in TMEM
         tc_after();
         float dot[2] = {0.f, 0.f};
 #pragma unroll 1
-        for (int ch = 0; ch < 4; ++ch) {
+        for (int ch = ch0; ch < ch0 + 2; ++ch) {
             float a0[16], u0[16], a1[16], u1[16], x0[16], x1[16], qk[16];
             tmem_ld16(lane_base + ch * 16, a0);
             tmem_ld16(lane_base + 64 + ch * 16, u0);
             tmem_ld16(lane_base + 128 + ch * 16, a1);
             tmem_ld16(lane_base + 192 + ch * 16, u1);
-            row16(X[0], t, ch, x0);
-            row16(X[1], t, ch, x1);
+            tmem_ld16(lane_base + 256 + ch * 16, x0);
+            tmem_ld16(lane_base + 384 + ch * 16, x1);
             if (root) {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) qk[j] = d.pif[16 * ch + j];
@@ -719,129 +762,139 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
                 row16(QK, t, ch, qk);
             }
             tmem_wait_ld();
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {   // P x = x + D x
-                a0[j] += x0[j];
-                a1[j] += x1[j];
-            }
             float q0[16], q1[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                q0[j] = qk[j] * a1[j];   // top of branch c0: q_k o P_1 x_1
-                q1[j] = qk[j] * a0[j];
+                q0[j] = qk[j] * (a1[j] + x1[j]);   // top of branch c0: q_k o P_1 x_1
+                q1[j] = qk[j] * (a0[j] + x0[j]);
                 dot[0] = fmaf(q0[j], u0[j], dot[0]);
                 dot[1] = fmaf(q1[j], u1[j], dot[1]);
             }
             if (!tip[0]) {
-                tmem_st16(lane_base + ch * 16, q0);
+                tmem_st16(lane_base + 256 + ch * 16, q0);
 #pragma unroll
                 for (int j = 0; j < 16; ++j) q0[j] = tf32_lo(q0[j]);
-                tmem_st16(lane_base + 64 + ch * 16, q0);
+                tmem_st16(lane_base + 320 + ch * 16, q0);
             }
             if (!tip[1]) {
-                tmem_st16(lane_base + 128 + ch * 16, q1);
+                tmem_st16(lane_base + 384 + ch * 16, q1);
 #pragma unroll
                 for (int j = 0; j < 16; ++j) q1[j] = tf32_lo(q1[j]);
-                tmem_st16(lane_base + 192 + ch * 16, q1);
+                tmem_st16(lane_base + 448 + ch * 16, q1);
             }
         }
         tmem_wait_st();
+        half_part[0][hf][t] = dot[0];
+        half_part[1][hf][t] = dot[1];
+        tc_before();
+        __syncthreads();   // q_k read: its slot may take the next category's
         {
             const int dE = Eq + Ex[0] + Ex[1] - Er;
             const float cw = (float)d.cw[l];
-            for (int side = 0; side < 2; ++side) dsum[side] += cw * ldexpf(dot[side], dE) * inv;
+            for (int side = 0; side < 2; ++side)
+                dsum[side] += cw * ldexpf(half_part[side][0][t] + half_part[side][1][t], dE) * inv;
         }
-        tc_before();
-        __syncthreads();
-        if (any_q) {
-            load_pending = true;
-            ok = wait_all(&bar[0], ph_load);
-            load_pending = !ok;
-            if (!ok) break;
-            if (t == 0) {
+        if (leader && !root && l + 1 < C) issue_qk(l + 1);
+        if (any_int) {
+            if (!wait(BD)) break;
+            if (leader) {
                 tc_after();
                 for (int side = 0; side < 2; ++side) {
                     if (tip[side]) continue;
-                    const uint32_t acc = tmem + 256 + 64 * side, qa = tmem + 128 * side;
+                    const uint32_t acc = tmem + 128 * side, qa = tmem + 256 + 128 * side;
                     const uint32_t tb = smem_u32(T[side]);
                     mma_tile_ta(acc, qa, tb, kMP, false);
                     mma_tile_ta(acc, qa, tb + kTab, kMP, true);
                     mma_tile_ta(acc, qa + 64, tb, kMP, true);
                 }
-                mma_commit(&bar[1]);
+                pend[BM] = true;
+            mma_commit(&bar[BM]);
             }
-            mma_pending = true;
-            ok = wait_all(&bar[1], ph_mma);
-            mma_pending = !ok;
-            if (!ok) break;
+            if (!wait(BM)) break;
+        }
+        if (any_int) {
+            // epilogue 2: q_c = qt_c + D_c^T qt_c, scaled, staged in the child's (now free) table
+            // slot and stored by TMA
             tc_after();
-            // epilogue 2: q_c = qt_c + D_c^T qt_c, scaled, staged (child 0 in QK, child 1 in X[0])
             for (int side = 0; side < 2; ++side) {
                 if (tip[side]) continue;
-                unsigned char *stage = side ? X[0] : QK;
-                const uint32_t qa = lane_base + 128 * side, acc = lane_base + 256 + 64 * side;
-                float mx = 0.f;
+                const uint32_t qa = lane_base + 256 + 128 * side, acc = lane_base + 128 * side;
+                float v[2][16];   // this half's 32 states of q_c, kept in registers
 #pragma unroll
-                for (int ch = 0; ch < 4; ++ch) {
-                    float a[16], q[16];
-                    tmem_ld16(acc + ch * 16, a);
-                    tmem_ld16(qa + ch * 16, q);
+                for (int i = 0; i < 2; ++i) {
+                    float q[16];
+                    tmem_ld16(acc + (ch0 + i) * 16, v[i]);
+                    tmem_ld16(qa + (ch0 + i) * 16, q);
                     tmem_wait_ld();
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) mx = fmaxf(mx, a[j] + q[j]);
+                    for (int j = 0; j < 16; ++j) v[i][j] += q[j];
                 }
-                const int e = scale_exponent(mx);
+                float mx = 0.f;
 #pragma unroll
-                for (int ch = 0; ch < 4; ++ch) {
+                for (int i = 0; i < 2; ++i)
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) mx = fmaxf(mx, v[i][j]);
+                half_part[side][hf][t] = mx;
+            }
+            __syncthreads();   // both halves' maxima
+            for (int side = 0; side < 2; ++side) {
+                if (tip[side]) continue;
+                const uint32_t qa = lane_base + 256 + 128 * side, acc = lane_base + 128 * side;
+                const int e = scale_exponent(fmaxf(half_part[side][0][t], half_part[side][1][t]));
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
                     float a[16], q[16];
-                    tmem_ld16(acc + ch * 16, a);
-                    tmem_ld16(qa + ch * 16, q);
+                    tmem_ld16(acc + (ch0 + i) * 16, a);
+                    tmem_ld16(qa + (ch0 + i) * 16, q);
                     tmem_wait_ld();
 #pragma unroll
                     for (int j = 0; j < 16; ++j) a[j] += q[j];
-                    put16(stage, t, ch, a, e);
+                    put16(T[side], t, ch0 + i, a, e);
                 }
-                if (on) __stcg(d.qe + ((size_t)(cs[side] - N) * C + l) * d.Ps + p0 + t, Eq + Ex[1 - side] + e);
+                if (on && hf == 0) __stcg(d.qe + ((size_t)(cs[side] - N) * C + l) * d.Ps + p0 + t, Eq + Ex[1 - side] + e);
             }
             fence_async_smem();
             __syncthreads();
-            if (t == 0) {
+            if (leader) {
                 for (int side = 0; side < 2; ++side) {
                     if (tip[side]) continue;
-                    unsigned char *stage = side ? X[0] : QK;
                     for (int kb = 0; kb < 2; ++kb)
-                        tma_store_3d(&tm_pre, stage + kb * kRowKB, kb * 32, p0, (cs[side] - N) * C + l);
+                        tma_store_3d(&tm_pre, T[side] + kb * kRowKB, kb * 32, p0, (cs[side] - N) * C + l);
                 }
                 bulk_commit();
-                bulk_wait_read0();   // the staging tiles are read before the next category's copies
+                bulk_wait_read0();   // the staged rows are read before the table slots refill
             }
         }
+        if (leader && l + 1 < C) issue_tables(l + 1);   // the table slots are free again
         tc_before();
-        __syncthreads();
+        __syncthreads();   // tensor memory read before the next category's rows overwrite it
     }
     if (ok) {
-        const double w = on ? d.weights[p0 + t] : 0.0;
+        const double w = (on && hf == 0) ? d.weights[p0 + t] : 0.0;   // each row once
         for (int side = 0; side < 2; ++side) {
             double g = w != 0.0 ? w * (double)dsum[side] : 0.0;
             g = warp_sum(g);
-            if (lane == 0) red[side][warp] = g;
+            if (lane == 0 && hf == 0) red[side][warp] = g;
         }
         __syncthreads();
-        if (t < 2) {
+        if (threadIdx.x < 2) {
             double g = 0.0;
-            for (int j = 0; j < kTcThreads / 32; ++j) g += red[t][j];
-            d.gpart[(size_t)cs[t] * d.n_gslots + pt] = g;
+            for (int j = 0; j < kTcThreads / 32; ++j) g += red[threadIdx.x][j];
+            d.gpart[(size_t)cs[threadIdx.x] * d.n_gslots + pt] = g;
         }
-    } else if (t == 0) {
+    } else if (leader) {
         atomicOr(d.status, kStatusTimeout);
-        drain(bar, ph_load, ph_mma, load_pending, mma_pending);
+        for (int i = 0; i < NB; ++i)   // let every copy and product in flight finish
+            if (pend[i]) mbar_wait_bounded(&bar[i], ph[i], kWaitLimitCycles);
     }
     tc_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
-constexpr size_t kPre2TcSmem = 1024 + 3 * kRowTile + 8 * kTab;
+// no alignment slack: the static shared memory is padded so that the dynamic region starts on a
+// 1024-byte boundary (checked in the kernel), and rows + tables + statics fill the 227 KB limit
+constexpr size_t kPre2TcSmem = 3 * kRowTile + 8 * kTab;
 constexpr size_t kPostTcSmem = 1024 + 2 * kRowTile + 2 * kTab;
 constexpr size_t kPreTcSmem = 1024 + 4 * kRowTile + 4 * kTab + kRowTile;
 
@@ -888,7 +941,7 @@ cudaError_t launch_m_pre_level_tc(const MDesc &d, const void *tm_post, const voi
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    m_pre_tc2_kernel<<<nd * n_pt, kTcThreads, kPre2TcSmem, s>>>(
+    m_pre_tc2_kernel<<<nd * n_pt, 2 * kTcThreads, kPre2TcSmem, s>>>(
         d, *static_cast<const CUtensorMap *>(tm_post), *static_cast<const CUtensorMap *>(tm_pre),
         *static_cast<const CUtensorMap *>(tm_tab), o0, n_pt);
     return cudaGetLastError();
