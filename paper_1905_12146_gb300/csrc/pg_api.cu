@@ -325,7 +325,7 @@ pg_status upload_m(pg_ctx *ctx, const pg_problem *pr, const TreePlan &tp, pg_han
         uniformise(pr->Q + (size_t)md * m * m, m, Bpow.data() + (size_t)md * pg::kUnifK * KP * KP,
                    QT.data() + (size_t)md * KP * KP, &mu[md]);
     const int Ps = (P + 15) / 16 * 16;
-    const int n_pt = (P + pg::kMTile - 1) / pg::kMTile, n_lb = (P + 255) / 256;
+    const int n_pt = (P + pg::kMTile - 1) / pg::kMTile, n_lb = (P + pg::kMRootPatterns - 1) / pg::kMRootPatterns;
     Carver cv;
     const size_t o_ops = cv.take<int4>(N - 1), o_lv = cv.take<int>(H + 1);
     const size_t o_tips = cv.take<uint8_t>((size_t)N * Ps), o_w = cv.take<double>(Ps);
@@ -338,7 +338,11 @@ pg_status upload_m(pg_ctx *ctx, const pg_problem *pr, const TreePlan &tp, pg_han
     const size_t part = (size_t)(N - 1) * C * Ps * KP;
     const size_t o_post = cv.take<float>(part), o_pre = cv.take<float>(part);
     const size_t o_pe = cv.take<int>((size_t)(N - 1) * C * Ps), o_qe = cv.take<int>((size_t)(N - 1) * C * Ps);
-    const size_t o_gp = cv.take<double>((size_t)n * std::max(n_pt, 1)), o_hp = cv.take<double>((size_t)n * std::max(n_pt, 1));
+    // gradient slots per branch: the SIMT kernel's pattern tiles, or the tensor-core kernel's
+    // 128-pattern tiles x category groups (at most one group per category)
+    const int n_gslots = tc ? ((P + pg::kTcTile - 1) / pg::kTcTile) * C : n_pt;
+    const size_t o_gp = cv.take<double>((size_t)n * std::max(n_gslots, 1));
+    const size_t o_hp = cv.take<double>((size_t)n * std::max(n_gslots, 1));
     const size_t o_lp = cv.take<double>(std::max(n_lb, 1)), o_st = cv.take<int>(1);
     const size_t o_sinv = cv.take<float>(std::max(Ps, 16)), o_ser = cv.take<int>(std::max(Ps, 16));
     const size_t o_par = cv.take<int>(n);
@@ -408,7 +412,7 @@ pg_status upload_m(pg_ctx *ctx, const pg_problem *pr, const TreePlan &tp, pg_han
     d.n_models = M;
     d.n_ptiles = n_pt;
     d.tc = tc ? 1 : 0;
-    d.n_gslots = tc ? (P + pg::kTcTile - 1) / pg::kTcTile : n_pt;
+    d.n_gslots = n_gslots;
     if (tc && P > 0) {
         const cuuint64_t pdims[3] = {(cuuint64_t)KP, (cuuint64_t)P, (cuuint64_t)(N - 1) * C};
         const cuuint64_t pstr[2] = {(cuuint64_t)KP * 4, (cuuint64_t)Ps * KP * 4};
@@ -502,7 +506,7 @@ pg_status enqueue_m(pg_handle *h, int skip, const double *d_b, double *d_logL, d
     }
     for (int lv = d.n_levels - 1; bwd && e == cudaSuccess && lv >= 0; --lv) {
         const int o0 = h->level_off[lv], nd = h->level_off[lv + 1] - o0;
-        e = d.tc ? pg::launch_m_pre_level_tc(d, &h->tm_post, &h->tm_pre, &h->tm_tab, o0, nd, hess, s)
+        e = d.tc ? pg::launch_m_pre_level_tc(d, &h->tm_post, &h->tm_pre, &h->tm_tab, o0, nd, hess, h->ctx->n_sm, s)
                  : pg::launch_m_pre_level(d, o0, nd, hess, s);
     }
     if (e == cudaSuccess) e = pg::launch_m_reduce(d, hess, s);

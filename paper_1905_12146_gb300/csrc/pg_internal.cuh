@@ -149,6 +149,7 @@ constexpr int kTabRows = kMP + 1;       // table rows: kMP, then the ambiguous-c
 constexpr int kTabFloats = kTabRows * kMP;
 constexpr int kTabDT = 0, kTabD = 1, kTabGT = 2, kTabHT = 3, kTabKinds = 4;
 constexpr int kUnifK = 32;              // powers of B held per model (covers mu t <= 4 to ~1e-13)
+constexpr int kMRootPatterns = 16;   // patterns per block of the general-state root kernel (16 lanes each)
 
 struct MDesc {
     const int4 *ops;
@@ -172,7 +173,7 @@ struct MDesc {
     const double *gscale;
     int skip;
     int n_tips, n_nodes, root, n_levels, P, Ps, m, C, n_models, n_ptiles;
-    int n_gslots;                  // per-branch gradient slots: pattern tiles of the pre-order kernel
+    int n_gslots;                  // per-branch gradient slots: pattern tiles (x categories, tensor-core path)
     int tc;                        // 1: tensor-core kernels and table layout, 0: SIMT
     double cw[kMaxCat], rates[kMaxCat];
     float pif[kMP];                // root frequencies, FP32 (pads 0)
@@ -196,7 +197,7 @@ cudaError_t launch_m_reduce(const MDesc &d, bool hess, cudaStream_t s);
 cudaError_t launch_m_post_level_tc(const MDesc &d, const void *tm_post, const void *tm_tab, int o0, int nd,
                                    cudaStream_t s);
 cudaError_t launch_m_pre_level_tc(const MDesc &d, const void *tm_post, const void *tm_pre, const void *tm_tab,
-                                  int o0, int nd, bool hess, cudaStream_t s);
+                                  int o0, int nd, bool hess, int n_sm, cudaStream_t s);
 
 // launchers (pg_nt.cu); every problem of one launch shares C and precision
 template <int MAXB>

@@ -355,28 +355,30 @@ __global__ void __launch_bounds__(kMThreads) m_post_kernel(const __grid_constant
     }
 }
 
-// ---- root: L_p = sum_l w_l 2^{E_l} pi . x_l (Section 2.5), one thread per pattern ---------------
+// ---- root: L_p = sum_l w_l 2^{E_l} pi . x_l (Section 2.5) ----------------------------------------
+// 16 lanes per pattern (4 states each, FP64 products and a fixed shuffle tree), kMRootPatterns
+// patterns per block: the FP64 work spreads over the SMs, and the block's weighted sum of log L_p is
+// one slot of lpart.
 __global__ void __launch_bounds__(kRootThreads) m_root_kernel(const __grid_constant__ MDesc d) {
     __shared__ double wsum[kRootThreads / 32];
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    double term = 0.0;
-    if (p < d.P) {
-        double s[kMaxCat];
-        int Ec[kMaxCat], Emax = -0x7fffffff;
-        for (int l = 0; l < d.C; ++l) {
-            const float4 *x = reinterpret_cast<const float4 *>(d.post + row_of(d, d.root, l, p));
-            double a = 0.0;
-            for (int q = 0; q < kMP / 4; ++q) {
-                const float4 v = __ldcg(x + q);
-                a = fma(d.pi[4 * q], (double)v.x, a);
-                a = fma(d.pi[4 * q + 1], (double)v.y, a);
-                a = fma(d.pi[4 * q + 2], (double)v.z, a);
-                a = fma(d.pi[4 * q + 3], (double)v.w, a);
-            }
-            s[l] = a;
-            Ec[l] = __ldcg(d.pe + col_of(d, d.root, l, p));
-            Emax = max(Emax, Ec[l]);
-        }
+    const int sub = threadIdx.x & 15, p = blockIdx.x * kMRootPatterns + (threadIdx.x >> 4);
+    const bool on = p < d.P;
+    double term = 0.0, s[kMaxCat];
+    int Ec[kMaxCat], Emax = -0x7fffffff;
+    for (int l = 0; l < d.C; ++l) {   // every lane takes part in the shuffles
+        const float4 v = on ? __ldcg(reinterpret_cast<const float4 *>(d.post + row_of(d, d.root, l, p)) + sub)
+                            : f4(0.f, 0.f, 0.f, 0.f);
+        double a = d.pi[4 * sub] * (double)v.x;
+        a = fma(d.pi[4 * sub + 1], (double)v.y, a);
+        a = fma(d.pi[4 * sub + 2], (double)v.z, a);
+        a = fma(d.pi[4 * sub + 3], (double)v.w, a);
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o, 16);
+        s[l] = a;
+        Ec[l] = on ? __ldcg(d.pe + col_of(d, d.root, l, p)) : 0;
+        Emax = max(Emax, Ec[l]);
+    }
+    if (on && sub == 0) {
         double S = 0.0;
         for (int l = 0; l < d.C; ++l) S = fma(d.cw[l], ldexp(s[l], Ec[l] - Emax), S);
         int e2 = 0;
@@ -593,7 +595,7 @@ cudaError_t launch_m_post_level(const MDesc &d, int o0, int nd, cudaStream_t s) 
 
 cudaError_t launch_m_root(const MDesc &d, cudaStream_t s) {
     if (d.P <= 0) return cudaSuccess;
-    m_root_kernel<<<(d.P + kRootThreads - 1) / kRootThreads, kRootThreads, 0, s>>>(d);
+    m_root_kernel<<<(d.P + kMRootPatterns - 1) / kMRootPatterns, kRootThreads, 0, s>>>(d);
     return cudaGetLastError();
 }
 
@@ -616,7 +618,7 @@ cudaError_t launch_m_pre_level(const MDesc &d, int o0, int nd, bool hess, cudaSt
 
 cudaError_t launch_m_reduce(const MDesc &d, bool hess, cudaStream_t s) {
     const int warps = d.n_nodes + 1;
-    const int n_lblocks = (d.P + kRootThreads - 1) / kRootThreads;
+    const int n_lblocks = (d.P + kMRootPatterns - 1) / kMRootPatterns;
     m_reduce_kernel<<<(warps + 7) / 8, 256, 0, s>>>(d, hess ? 1 : 0, n_lblocks);
     return cudaGetLastError();
 }

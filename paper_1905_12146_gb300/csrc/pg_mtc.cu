@@ -125,6 +125,7 @@ __device__ __forceinline__ void tma_store_3d(const CUtensorMap *m, const void *s
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all0() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
 
 // byte offset of 16-byte chunk cc (states 4 cc .. 4 cc + 3) of row r of a swizzled tile of `rows`
 // rows: two 32-state K blocks, rows 128 bytes apart, chunk index XOR (row mod 8)
@@ -227,13 +228,17 @@ __device__ __forceinline__ int store_sum_scaled(uint32_t ta, const unsigned char
     return e;
 }
 
-// ---- post-order level: item = (node, category, 128-pattern tile) ------------------------------------
-__global__ void __launch_bounds__(kTcThreads, 1)
+// ---- post-order level: item = (node, category, 128-pattern tile), three blocks per SM ----------------------
+// Per child: its D hi | D lo tables and rows (or one-hot tip rows) into shared memory, the rows'
+// TF32 remainders into tensor memory (columns 64 .. 127), D x into columns 0 .. 63 by three passes;
+// the first child's x + D x is kept in registers.  The result is scaled by its largest state,
+// written over the rows and stored by TMA.  64 KB of shared memory and 128 TMEM columns per block.
+__global__ void __launch_bounds__(kTcThreads, 3)
 m_post_tc_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtensorMap tm_post,
                  const __grid_constant__ CUtensorMap tm_tab, int o0, int n_pt) {
     extern __shared__ __align__(1024) unsigned char tc_raw[];
     unsigned char *sm = align1024(tc_raw);
-    unsigned char *XA = sm, *XL = sm + kRowTile, *TB = sm + 2 * kRowTile;   // rows, remainders, P hi|lo
+    unsigned char *XA = sm, *TB = sm + kRowTile;   // rows (then the result), D hi | D lo
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ uint32_t tmem_slot;
     const int C = d.C, N = d.n_tips, t = threadIdx.x, warp = t >> 5;
@@ -253,7 +258,7 @@ m_post_tc_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
     uint32_t ph_load = 0, ph_mma = 0;
     bool ok = true, load_pending = false, mma_pending = false;
     int E = 0;
-    float a0[kMP];   // P x of the first child: its D x (TMEM) plus its rows
+    float a0[kMP];   // x + D x of the first child
     for (int side = 0; side < 2 && ok; ++side) {
         const int c = side ? op.z : op.y;
         const bool tip = c < N;
@@ -270,22 +275,31 @@ m_post_tc_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
         ok = wait_all(&bar[0], ph_load);
         load_pending = !ok;
         if (!ok) break;
-        if (!tip) lo_row(XA, XL, t);
+        if (!tip) {
+#pragma unroll
+            for (int ch = 0; ch < 4; ++ch) {
+                float x[16];
+                row16(XA, t, ch, x);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) x[j] = tf32_lo(x[j]);
+                tmem_st16(lane_base + 64 + ch * 16, x);
+            }
+            tmem_wait_st();
+        }
         fence_async_smem();
         tc_before();
         __syncthreads();
         if (t == 0) {
             tc_after();
-            const uint32_t acc = tmem + side * 64;
-            mma_tile(acc, smem_u32(XA), smem_u32(TB), kMP, false);
-            mma_tile(acc, smem_u32(XA), smem_u32(TB + kTab), kMP, true);
-            if (!tip) mma_tile(acc, smem_u32(XL), smem_u32(TB), kMP, true);
+            mma_tile(tmem, smem_u32(XA), smem_u32(TB), kMP, false);
+            mma_tile(tmem, smem_u32(XA), smem_u32(TB + kTab), kMP, true);
+            if (!tip) mma_tile_ta(tmem, tmem + 64, smem_u32(TB), kMP, true);
             mma_commit(&bar[1]);
         }
         mma_pending = true;
         ok = wait_all(&bar[1], ph_mma);
         mma_pending = !ok;
-        if (ok && side == 0) {   // keep P x of the first child before its rows are replaced
+        if (ok && side == 0) {   // keep x + D x of the first child before its rows are replaced
             tc_after();
 #pragma unroll
             for (int ch = 0; ch < 4; ++ch) {
@@ -297,38 +311,32 @@ m_post_tc_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
                 for (int j = 0; j < 16; ++j) a0[16 * ch + j] = a[j] + x[j];
             }
             tc_before();
-            __syncthreads();   // every row read before the next copies land in XA
+            __syncthreads();   // every row and accumulator read before the next child's copies and products
         }
     }
     if (ok) {
-        unsigned char *stage = XA;
         tc_after();
         float mx = 0.f;
 #pragma unroll
         for (int ch = 0; ch < 4; ++ch) {
             float a[16], x[16];
-            tmem_ld16(lane_base + 64 + ch * 16, a);
+            tmem_ld16(lane_base + ch * 16, a);
             row16(XA, t, ch, x);
             tmem_wait_ld();
 #pragma unroll
-            for (int j = 0; j < 16; ++j) mx = fmaxf(mx, a0[16 * ch + j] * (a[j] + x[j]));
+            for (int j = 0; j < 16; ++j) {
+                a0[16 * ch + j] *= a[j] + x[j];
+                mx = fmaxf(mx, a0[16 * ch + j]);
+            }
         }
         const int e = scale_exponent(mx);
 #pragma unroll
-        for (int ch = 0; ch < 4; ++ch) {
-            float a[16], x[16];
-            tmem_ld16(lane_base + 64 + ch * 16, a);
-            row16(XA, t, ch, x);
-            tmem_wait_ld();
-#pragma unroll
-            for (int j = 0; j < 16; ++j) a[j] = a0[16 * ch + j] * (a[j] + x[j]);
-            put16(stage, t, ch, a, e);   // the row's own slots: read above, by this thread only
-        }
+        for (int ch = 0; ch < 4; ++ch) put16(XA, t, ch, a0 + 16 * ch, e);   // the row's own slots
         if (t < cnt) __stcg(d.pe + ((size_t)(k - N) * C + l) * d.Ps + p0 + t, E + e);
         fence_async_smem();
         __syncthreads();
         if (t == 0) {
-            for (int kb = 0; kb < 2; ++kb) tma_store_3d(&tm_post, stage + kb * kRowKB, kb * 32, p0, (k - N) * C + l);
+            for (int kb = 0; kb < 2; ++kb) tma_store_3d(&tm_post, XA + kb * kRowKB, kb * 32, p0, (k - N) * C + l);
             bulk_commit();
             bulk_wait_read0();
         }
@@ -584,6 +592,10 @@ m_pre_tc_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtenso
             }
             d.gpart[(size_t)cs[t] * d.n_gslots + pt] = g;
             if (HESS) d.hpart[(size_t)cs[t] * d.n_gslots + pt] = h;
+            for (int j = 1; j < C; ++j) {   // one category group: the other slots stay zero
+                d.gpart[(size_t)cs[t] * d.n_gslots + j * n_pt + pt] = 0.0;
+                if (HESS) d.hpart[(size_t)cs[t] * d.n_gslots + j * n_pt + pt] = 0.0;
+            }
         }
     } else if (t == 0) {
         atomicOr(d.status, kStatusTimeout);
@@ -606,7 +618,8 @@ m_pre_tc_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtenso
 // written into tensor memory by the threads.
 __global__ void __launch_bounds__(2 * kTcThreads, 1)
 m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtensorMap tm_post,
-                 const __grid_constant__ CUtensorMap tm_pre, const __grid_constant__ CUtensorMap tm_tab, int o0, int n_pt) {
+                 const __grid_constant__ CUtensorMap tm_pre, const __grid_constant__ CUtensorMap tm_tab, int o0, int n_pt,
+                 int n_cg) {
     extern __shared__ __align__(1024) unsigned char tc_raw[];
     if (smem_u32(tc_raw) & 1023u) {   // the layout needs a 1024-byte aligned base (see kPre2TcSmem)
         if (threadIdx.x == 0) atomicOr(d.status, kStatusTimeout);
@@ -625,7 +638,9 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
     // of the 64 states (chunks 2 hf, 2 hf + 1)
     const int C = d.C, N = d.n_tips, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int hf = warp >> 2, t = 32 * (warp & 3) + lane, ch0 = 2 * hf;
-    const int u = blockIdx.x / n_pt, pt = blockIdx.x - u * n_pt;
+    // item = (node, category group, tile): group g takes categories l0 .. l1 - 1
+    const int u = blockIdx.x / (n_cg * n_pt), rg = blockIdx.x - u * (n_cg * n_pt), g = rg / n_pt, pt = rg - g * n_pt;
+    const int G = (C + n_cg - 1) / n_cg, l0 = g * G, l1 = min(C, l0 + G);
     const int4 op = __ldg(d.ops + o0 + u);
     const int k = op.x, p0 = pt * kTcTile, cnt = min(kTcTile, d.P - p0);
     const bool root = k == d.root;
@@ -678,11 +693,11 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
         return ok;
     };
     if (leader) {
-        issue_rows(0);
-        if (!root) issue_qk(0);
-        issue_tables(0);
+        issue_rows(l0);
+        if (!root) issue_qk(l0);
+        issue_tables(l0);
     }
-    for (int l = 0; l < C && ok; ++l) {
+    for (int l = l0; l < l1 && ok; ++l) {
         const int Eq = (on && !root) ? __ldcg(d.qe + ((size_t)(k - N) * C + l) * d.Ps + p0 + t) : 0;
         int Ex[2];
         for (int side = 0; side < 2; ++side)
@@ -718,7 +733,7 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
         tmem_wait_st();
         tc_before();
         __syncthreads();   // rows read: the slots may take the next category's rows
-        if (leader && l + 1 < C) issue_rows(l + 1);
+        if (leader && l + 1 < l1) issue_rows(l + 1);
         if (!wait(BT)) break;
         if (leader) {
             tc_after();
@@ -794,7 +809,7 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
             for (int side = 0; side < 2; ++side)
                 dsum[side] += cw * ldexpf(half_part[side][0][t] + half_part[side][1][t], dE) * inv;
         }
-        if (leader && !root && l + 1 < C) issue_qk(l + 1);
+        if (leader && !root && l + 1 < l1) issue_qk(l + 1);
         if (any_int) {
             if (!wait(BD)) break;
             if (leader) {
@@ -865,22 +880,25 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
                 bulk_wait_read0();   // the staged rows are read before the table slots refill
             }
         }
-        if (leader && l + 1 < C) issue_tables(l + 1);   // the table slots are free again
+        if (leader && l + 1 < l1) issue_tables(l + 1);   // the table slots are free again
         tc_before();
         __syncthreads();   // tensor memory read before the next category's rows overwrite it
     }
     if (ok) {
         const double w = (on && hf == 0) ? d.weights[p0 + t] : 0.0;   // each row once
         for (int side = 0; side < 2; ++side) {
-            double g = w != 0.0 ? w * (double)dsum[side] : 0.0;
-            g = warp_sum(g);
-            if (lane == 0 && hf == 0) red[side][warp] = g;
+            double gs = w != 0.0 ? w * (double)dsum[side] : 0.0;
+            gs = warp_sum(gs);
+            if (lane == 0 && hf == 0) red[side][warp] = gs;
         }
         __syncthreads();
         if (threadIdx.x < 2) {
-            double g = 0.0;
-            for (int j = 0; j < kTcThreads / 32; ++j) g += red[threadIdx.x][j];
-            d.gpart[(size_t)cs[threadIdx.x] * d.n_gslots + pt] = g;
+            double v = 0.0;
+            for (int j = 0; j < kTcThreads / 32; ++j) v += red[threadIdx.x][j];
+            double *slots = d.gpart + (size_t)cs[threadIdx.x] * d.n_gslots;
+            slots[g * n_pt + pt] = v;
+            if (g == n_cg - 1)   // the slots of groups this launch does not have stay zero
+                for (int j = n_cg; j < C; ++j) slots[j * n_pt + pt] = 0.0;
         }
     } else if (leader) {
         atomicOr(d.status, kStatusTimeout);
@@ -895,7 +913,7 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
 // no alignment slack: the static shared memory is padded so that the dynamic region starts on a
 // 1024-byte boundary (checked in the kernel), and rows + tables + statics fill the 227 KB limit
 constexpr size_t kPre2TcSmem = 3 * kRowTile + 8 * kTab;
-constexpr size_t kPostTcSmem = 1024 + 2 * kRowTile + 2 * kTab;
+constexpr size_t kPostTcSmem = 1024 + kRowTile + 2 * kTab;
 constexpr size_t kPreTcSmem = 1024 + 4 * kRowTile + 4 * kTab + kRowTile;
 
 }  // namespace
@@ -930,20 +948,34 @@ cudaError_t launch_pre_tc(const MDesc &d, const void *tm_post, const void *tm_pr
     return cudaGetLastError();
 }
 
+// Categories per block: all of them (the next category's loads overlap this one's work) unless the
+// level has too few (node, tile) items to fill the SMs; then the categories split into the most
+// groups that still run in one wave, each group in its own block.  The gradient slots are per
+// (group, tile), so the result depends only on the problem and the SM count.
+int pre_category_groups(int C, int items, int n_sm) {
+    int best = 1;
+    for (int n_cg = 2; n_cg <= C; ++n_cg) {
+        const int G = (C + n_cg - 1) / n_cg;
+        if ((C + G - 1) / G == n_cg && (long)items * n_cg <= n_sm) best = n_cg;   // still one wave
+    }
+    return best;
+}
+
 cudaError_t launch_m_pre_level_tc(const MDesc &d, const void *tm_post, const void *tm_pre, const void *tm_tab,
-                                  int o0, int nd, bool hess, cudaStream_t s) {
+                                  int o0, int nd, bool hess, int n_sm, cudaStream_t s) {
     const int n_pt = (d.P + kTcTile - 1) / kTcTile;
     if (nd <= 0 || n_pt <= 0) return cudaSuccess;
     if (hess) return launch_pre_tc<true>(d, tm_post, tm_pre, tm_tab, o0, nd, n_pt, s);
+    const int n_cg = pre_category_groups(d.C, nd * n_pt, n_sm);
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(m_pre_tc2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPre2TcSmem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    m_pre_tc2_kernel<<<nd * n_pt, 2 * kTcThreads, kPre2TcSmem, s>>>(
+    m_pre_tc2_kernel<<<nd * n_cg * n_pt, 2 * kTcThreads, kPre2TcSmem, s>>>(
         d, *static_cast<const CUtensorMap *>(tm_post), *static_cast<const CUtensorMap *>(tm_pre),
-        *static_cast<const CUtensorMap *>(tm_tab), o0, n_pt);
+        *static_cast<const CUtensorMap *>(tm_tab), o0, n_pt, n_cg);
     return cudaGetLastError();
 }
 
