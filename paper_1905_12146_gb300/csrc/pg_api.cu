@@ -499,15 +499,18 @@ pg_status enqueue_m(pg_handle *h, int skip, const double *d_b, double *d_logL, d
         e = pg::launch_m_pmatrix(d, hess, s);
         for (int lv = 0; e == cudaSuccess && lv < d.n_levels; ++lv) {
             const int o0 = h->level_off[lv], nd = h->level_off[lv + 1] - o0;
-            e = d.tc ? pg::launch_m_post_level_tc(d, &h->tm_post, &h->tm_tab, o0, nd, s)
-                     : pg::launch_m_post_level(d, o0, nd, s);
+            // level 0 holds exactly the nodes whose children are both tips
+            e = !d.tc ? pg::launch_m_post_level(d, o0, nd, s)
+                : lv == 0 ? pg::launch_m_post_cherry(d, o0, nd, s)
+                          : pg::launch_m_post_level_tc(d, &h->tm_post, &h->tm_tab, o0, nd, s);
         }
         if (e == cudaSuccess) e = pg::launch_m_root(d, s);
     }
     for (int lv = d.n_levels - 1; bwd && e == cudaSuccess && lv >= 0; --lv) {
         const int o0 = h->level_off[lv], nd = h->level_off[lv + 1] - o0;
-        e = d.tc ? pg::launch_m_pre_level_tc(d, &h->tm_post, &h->tm_pre, &h->tm_tab, o0, nd, hess, h->ctx->n_sm, s)
-                 : pg::launch_m_pre_level(d, o0, nd, hess, s);
+        e = !d.tc ? pg::launch_m_pre_level(d, o0, nd, hess, s)
+            : (lv == 0 && !hess) ? pg::launch_m_pre_cherry(d, o0, nd, s)
+                                 : pg::launch_m_pre_level_tc(d, &h->tm_post, &h->tm_pre, &h->tm_tab, o0, nd, hess, h->ctx->n_sm, s);
     }
     if (e == cudaSuccess) e = pg::launch_m_reduce(d, hess, s);
     if (e != cudaSuccess) return fail(PG_ERR_CUDA, "launch: %s", cudaGetErrorString(e));

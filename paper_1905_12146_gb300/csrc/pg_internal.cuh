@@ -194,6 +194,9 @@ cudaError_t launch_m_pre_level(const MDesc &d, int o0, int nd, bool hess, cudaSt
 cudaError_t launch_m_reduce(const MDesc &d, bool hess, cudaStream_t s);
 // tensor-core level kernels; the maps describe d.post, d.pre (3-D: state, pattern, node * C +
 // category) and d.tabs (2-D: state, table row) with 128-byte swizzled 32-float boxes
+// level 0 of the tensor-core layout (both children tips): column lookups, no products
+cudaError_t launch_m_post_cherry(const MDesc &d, int o0, int nd, cudaStream_t s);
+cudaError_t launch_m_pre_cherry(const MDesc &d, int o0, int nd, cudaStream_t s);
 cudaError_t launch_m_post_level_tc(const MDesc &d, const void *tm_post, const void *tm_tab, int o0, int nd,
                                    cudaStream_t s);
 cudaError_t launch_m_pre_level_tc(const MDesc &d, const void *tm_post, const void *tm_pre, const void *tm_tab,
