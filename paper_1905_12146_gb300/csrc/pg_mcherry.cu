@@ -2,9 +2,9 @@
 // both tips.  A tip's state vector x is one-hot (or all-ones over the m states for an ambiguous
 // code), so P x is a column of P = I + D and G x a column of G: the post-order product (Section 2.3)
 // and the pre-order branch terms (Sections 2.4-2.5) are table lookups, done here in FP32 without
-// the tensor core.  The tables of one (node, category) are copied into shared memory once, with a
-// padding column that holds the row sums (the all-ones case), and a block then walks a chunk of
-// patterns: 16 lanes per pattern, 4 states per lane.
+// the tensor core.  The tables of one (node, category) are copied into shared memory once as
+// column tables, with the row sums (the all-ones case) as an extra column, and a block then walks a
+// chunk of patterns: 16 lanes per pattern, 4 states per lane.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -19,43 +19,53 @@ using namespace dev;
 
 constexpr int kChThreads = 256;            // 16 patterns x 16 lanes per step
 constexpr int kChChunk = 1024;             // patterns per block
-constexpr int kPad = kMP + 1;              // row stride of a table in shared memory; column kMP = row sum
-constexpr int kPadFloats = kMP * kPad;
+constexpr int kS = 68;                     // row stride (floats) of a column table in shared memory
+constexpr int kColFloats = (kMP + 1) * kS;
 
-// table `kind` of (branch c, category l) into T[s][k] (stride kPad) with T[s][kMP] = sum_k T[s][k]
-__device__ void load_padded(float *T, const MDesc &d, int c, int l, int kind) {
+// Column tables in shared memory: row k holds column k of the matrix (states contiguous, so a
+// lane reads its 4 states of a column as one float4), row kMP the row sums (the column of an
+// all-ones vector).
+// from a transposed table in global memory (row k = column k already)
+__device__ void columns_from_transposed(float *Cb, const MDesc &d, int c, int l, int kind) {
+    const float4 *src = reinterpret_cast<const float4 *>(d.tabs + ((size_t)(c * d.C + l) * kTcKinds + kind) * kMP * kMP);
+    for (int i = threadIdx.x; i < kMP * kMP / 4; i += blockDim.x)
+        *reinterpret_cast<float4 *>(Cb + (i / (kMP / 4)) * kS + 4 * (i % (kMP / 4))) = __ldg(src + i);
+}
+// from a row-major table in global memory (transposed on the way in)
+__device__ void columns_from_rows(float *Cb, const MDesc &d, int c, int l, int kind) {
     const float4 *src = reinterpret_cast<const float4 *>(d.tabs + ((size_t)(c * d.C + l) * kTcKinds + kind) * kMP * kMP);
     for (int i = threadIdx.x; i < kMP * kMP / 4; i += blockDim.x) {
         const float4 v = __ldg(src + i);
-        const int s = (4 * i) / kMP, k = (4 * i) % kMP;
-        float *row = T + s * kPad + k;
-        row[0] = v.x;
-        row[1] = v.y;
-        row[2] = v.z;
-        row[3] = v.w;
+        const int s = i / (kMP / 4), k = 4 * (i % (kMP / 4));
+        Cb[k * kS + s] = v.x;
+        Cb[(k + 1) * kS + s] = v.y;
+        Cb[(k + 2) * kS + s] = v.z;
+        Cb[(k + 3) * kS + s] = v.w;
     }
 }
-__device__ void row_sums(float *T, int s) {   // one thread per row, fixed order
+__device__ void row_sums(float *Cb, int s) {   // one thread per state, fixed order
     float a = 0.f;
-    for (int k = 0; k < kMP; ++k) a += T[s * kPad + k];
-    T[s * kPad + kMP] = a;
+    for (int k = 0; k < kMP; ++k) a += Cb[k * kS + s];
+    Cb[kMP * kS + s] = a;
 }
 
-// column y of P (or P 1 for an ambiguous code) at this lane's states 4 j .. 4 j + 3
-__device__ __forceinline__ void p_column(const float *D, int y, int m, int j, float a[4]) {
+// column y of P = I + D (or P 1 for an ambiguous code) at this lane's states 4 j .. 4 j + 3
+__device__ __forceinline__ void p_column(const float *Dc, int y, int m, int j, float a[4]) {
     const bool amb = y >= m;
-    const int col = amb ? kMP : y;
+    const float4 v = *reinterpret_cast<const float4 *>(Dc + (amb ? kMP : y) * kS + 4 * j);
+    const float dv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int s = 4 * j + i;
-        const float id = amb ? (s < m ? 1.f : 0.f) : (s == y ? 1.f : 0.f);
-        a[i] = id + D[s * kPad + col];
+        a[i] = (amb ? (s < m ? 1.f : 0.f) : (s == y ? 1.f : 0.f)) + dv[i];
     }
 }
-__device__ __forceinline__ void g_column(const float *G, int y, int m, int j, float u[4]) {
-    const int col = y >= m ? kMP : y;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) u[i] = G[(4 * j + i) * kPad + col];
+__device__ __forceinline__ void g_column(const float *Gc, int y, int m, int j, float u[4]) {
+    const float4 v = *reinterpret_cast<const float4 *>(Gc + (y >= m ? kMP : y) * kS + 4 * j);
+    u[0] = v.x;
+    u[1] = v.y;
+    u[2] = v.z;
+    u[3] = v.w;
 }
 __device__ __forceinline__ float sum16(float v) {
 #pragma unroll
@@ -77,13 +87,13 @@ __device__ __forceinline__ float max16(float v) {
 // ---- post-order: p_k = (P_0 x_0) o (P_1 x_1), scaled by its largest state -------------------------
 __global__ void __launch_bounds__(kChThreads) m_post_cherry_kernel(const __grid_constant__ MDesc d, int o0, int n_ch) {
     extern __shared__ float chs[];
-    float *D0 = chs, *D1 = chs + kPadFloats;
+    float *D0 = chs, *D1 = chs + kColFloats;
     const int item = blockIdx.x, pair = item / n_ch, ci = item - pair * n_ch;
     const int u = pair / d.C, l = pair - u * d.C;
     const int4 op = __ldg(d.ops + o0 + u);
     const int k = op.x, N = d.n_tips;
-    load_padded(D0, d, op.y, l, kTcD);
-    load_padded(D1, d, op.z, l, kTcD);
+    columns_from_transposed(D0, d, op.y, l, kTcDT);
+    columns_from_transposed(D1, d, op.z, l, kTcDT);
     __syncthreads();
     if (threadIdx.x < kMP) row_sums(D0, threadIdx.x);
     else if (threadIdx.x < 2 * kMP) row_sums(D1, threadIdx.x - kMP);
@@ -125,17 +135,17 @@ __global__ void __launch_bounds__(kChThreads) m_post_cherry_kernel(const __grid_
 __global__ void __launch_bounds__(kChThreads) m_pre_cherry_kernel(const __grid_constant__ MDesc d, int o0, int n_ch,
                                                                    int n_pt) {
     extern __shared__ float chs[];
-    float *D0 = chs, *D1 = chs + kPadFloats, *G0 = chs + 2 * kPadFloats, *G1 = chs + 3 * kPadFloats;
+    float *D0 = chs, *D1 = chs + kColFloats, *G0 = chs + 2 * kColFloats, *G1 = chs + 3 * kColFloats;
     __shared__ double red[2][kChThreads / 32];
     const int item = blockIdx.x, pair = item / n_ch, ci = item - pair * n_ch;
     const int u = pair / d.C, l = pair - u * d.C;
     const int4 op = __ldg(d.ops + o0 + u);
     const int k = op.x, N = d.n_tips;
     const bool root = k == d.root;
-    load_padded(D0, d, op.y, l, kTcD);
-    load_padded(D1, d, op.z, l, kTcD);
-    load_padded(G0, d, op.y, l, kTcG);
-    load_padded(G1, d, op.z, l, kTcG);
+    columns_from_transposed(D0, d, op.y, l, kTcDT);
+    columns_from_transposed(D1, d, op.z, l, kTcDT);
+    columns_from_rows(G0, d, op.y, l, kTcG);
+    columns_from_rows(G1, d, op.z, l, kTcG);
     __syncthreads();
     {
         const int r = threadIdx.x & (kMP - 1), which = threadIdx.x / kMP;   // 4 tables x 64 rows
@@ -212,8 +222,8 @@ __global__ void __launch_bounds__(kChThreads) m_pre_cherry_kernel(const __grid_c
     }
 }
 
-constexpr size_t kPostChSmem = 2 * kPadFloats * sizeof(float);
-constexpr size_t kPreChSmem = 4 * kPadFloats * sizeof(float);
+constexpr size_t kPostChSmem = 2 * kColFloats * sizeof(float);
+constexpr size_t kPreChSmem = 4 * kColFloats * sizeof(float);
 
 }  // namespace
 
