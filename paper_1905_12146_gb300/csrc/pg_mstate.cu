@@ -186,16 +186,27 @@ __device__ __forceinline__ void put_rem(float *M, const float acc[4][4], int ts,
 
 // kind 0: D, 1: G, 2: H of (c, l) into the table layout
 template <bool TC>
-__device__ __forceinline__ void store_tables(const MDesc &d, int c, int l, int kind, const float acc[4][4], int ts, int tj) {
+// (stage: a free kMP x kMP shared-memory tile, used by the tensor-core layout's transposed D; all
+// threads of the block call this)
+__device__ __forceinline__ void store_tables(const MDesc &d, int c, int l, int kind, const float acc[4][4], int ts, int tj,
+                                             float *stage) {
     if (TC) {
         float *base = d.tabs + (size_t)(c * d.C + l) * kTcKinds * kMP * kMP;
         const int hk = kind == 0 ? kTcD : (kind == 1 ? kTcG : kTcH);
         const int lk = kind == 0 ? kTcDlo : (kind == 1 ? kTcGlo : kTcHlo);
         put_rowmajor(base + (size_t)hk * kMP * kMP, ts, tj, acc);
         put_rem(base + (size_t)lk * kMP * kMP, acc, ts, tj, false);
-        if (kind == 0) {
-            put_transposed(base + (size_t)kTcDT * kMP * kMP, ts, tj, acc);
-            put_rem(base + (size_t)kTcDTlo * kMP * kMP, acc, ts, tj, true);
+        if (kind == 0) {   // D^T and its remainder through shared memory, so the rows go out whole
+            put_transposed(stage, ts, tj, acc);
+            __syncthreads();
+            float4 *dt = reinterpret_cast<float4 *>(base + (size_t)kTcDT * kMP * kMP);
+            float4 *dtlo = reinterpret_cast<float4 *>(base + (size_t)kTcDTlo * kMP * kMP);
+            for (int i = threadIdx.x; i < kMP * kMP / 4; i += blockDim.x) {
+                const float4 v = reinterpret_cast<const float4 *>(stage)[i];
+                dt[i] = v;
+                dtlo[i] = f4(tf32_rem(v.x), tf32_rem(v.y), tf32_rem(v.z), tf32_rem(v.w));
+            }
+            __syncthreads();
         }
         return;
     }
@@ -230,7 +241,9 @@ __global__ void __launch_bounds__(kMThreads) m_pmatrix_kernel(const __grid_const
     }
     const int md = d.bmodel ? d.bmodel[c] : 0;
     const float r = (float)d.rates[l];
-    if (threadIdx.x == 0) {   // Poisson weights of the (halved) interval, FP64
+    if (threadIdx.x < 32) {   // Poisson weights w_k = e^{-x} x^k / k! of the (halved) interval, FP64
+        static_assert(kUnifK <= 32, "one lane per power");
+        const int lane = threadIdx.x;
         double x = d.mu[md] * bl * d.rates[l];
         int s = 0;
         while (x > 4.0 && s < 1000) {
@@ -238,14 +251,19 @@ __global__ void __launch_bounds__(kMThreads) m_pmatrix_kernel(const __grid_const
             ++s;
         }
         const int K = min(kUnifK, (int)ceil(x + 6.0 * sqrt(x) + 10.0));
-        double w = exp(-x);
-        for (int k = 1; k <= K; ++k) {
-            w *= x / k;
-            ck[k] = (float)w;
+        // lane k - 1 holds x / k; an inclusive prefix product over the lanes gives x^k / k!
+        double f = x / (double)(lane + 1);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double g = __shfl_up_sync(0xffffffffu, f, o);
+            if (lane >= o) f *= g;
         }
-        e0 = (float)expm1(-x);
-        nk = K;
-        nsq = s;
+        if (lane < K) ck[lane + 1] = (float)(exp(-x) * f);
+        if (lane == 0) {
+            e0 = (float)expm1(-x);
+            nk = K;
+            nsq = s;
+        }
     }
     __syncthreads();
     const int ts = threadIdx.x >> 4, tj = threadIdx.x & 15;
@@ -284,7 +302,7 @@ __global__ void __launch_bounds__(kMThreads) m_pmatrix_kernel(const __grid_const
 #pragma unroll
             for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(2.f, acc[a][b], sq[a][b]);
     }
-    store_tables<TC>(d, c, l, 0, acc, ts, tj);
+    store_tables<TC>(d, c, l, 0, acc, ts, tj, A);
     // G = r (Q + Q D)
     {
         const float4 *src = reinterpret_cast<const float4 *>(d.QT + (size_t)md * kMP * kMP);
@@ -298,7 +316,7 @@ __global__ void __launch_bounds__(kMThreads) m_pmatrix_kernel(const __grid_const
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) g[a][b] = r * (g[a][b] + A[(4 * tj + b) * kMP + 4 * ts + a]);
-    store_tables<TC>(d, c, l, 1, g, ts, tj);
+    store_tables<TC>(d, c, l, 1, g, ts, tj, nullptr);
     if (kinds > 2) {   // H = r Q G
         __syncthreads();
         put_rowmajor(Bm, ts, tj, g);
@@ -309,7 +327,7 @@ __global__ void __launch_bounds__(kMThreads) m_pmatrix_kernel(const __grid_const
         for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b) h[a][b] *= r;
-        store_tables<TC>(d, c, l, 2, h, ts, tj);
+        store_tables<TC>(d, c, l, 2, h, ts, tj, nullptr);
     }
 }
 
