@@ -15,10 +15,13 @@ copied back each step).  ``roofline`` is for the dominant kernel (the pre-order 
 ``cpu_baseline`` the FP64 CPU oracle on a bounded sample of the same workload.
 ``--impl reference`` times that oracle alone (there is no reference GPU implementation).
 
-Rank 0 then adds three measured objects (skipped with ``--no-extras``): ``codon`` (500 taxa x
-3,000 codon patterns x 4 categories on the tensor-core kernels), ``differentiation`` (the 64-tree
-clock batch through the torch.autograd.Functions) and ``serving`` (``--serving-requests`` Poisson
-requests through the continuous-batching server against the one-request-at-a-time plain path).
+Rank 0 then adds measured objects (skipped with ``--no-extras``): ``codon`` (500 taxa x 3,000
+codon patterns x 4 categories on the tensor-core kernels), ``differentiation`` (the 64-tree clock
+batch through the torch.autograd.Functions), ``inference`` (L-BFGS branch rates, analytic gradient
+against finite differences), ``hmc`` (HMC over the branch rates, identity mass against the
+Hessian-adapted diagonal mass, effective samples per second) and ``serving``
+(``--serving-requests`` Poisson requests through the continuous-batching server against the
+one-request-at-a-time plain path).
 """
 from __future__ import annotations
 
@@ -351,6 +354,44 @@ def _inference(device: int):
     return out
 
 
+def _hmc(device: int, n_warm: int = 150, n_keep: int = 300, n_leapfrog: int = 10):
+    """HMC over the 206 branch rates of the 104-taxon clock problem (the inference object's
+    workload, FP64 partials), random-effects prior with psi = 0.5, from the prior mean: identity
+    mass against the diagonal mass adapted to the Hessian (Section 3.2.1).  Both chains adapt the
+    step size during the first n_warm iterations (discarded).  Reported: effective samples per
+    second (min and median over the rates) of the kept iterations, acceptance, gradient
+    evaluations."""
+    import numpy as np
+
+    from paper_1905_12146_gb300 import _native, hmc, workloads
+
+    pr = workloads.config_clock_batch(seed=31, n_trees=1, n_tips=104, n_patterns=1000)[0]
+    ctx = _native.Context(device)
+    h = ctx.upload(pr, "fp64")
+    out = {"workload": "104-taxon Yule tree, 206 branch rates, 1,000 simulated patterns, FP64 partials; "
+                       f"{n_warm} warm-up + {n_keep} kept iterations, {n_leapfrog} leapfrog steps"}
+    try:
+        for name, adapt in (("identity_mass", False), ("hessian_mass", True)):
+            tg = hmc.ClockTarget(h, pr["parent"], pr["node_time"], pr["mu"], 0.5)
+            theta0 = np.full(tg.dim, tg.m)
+            tg.logp_grad(theta0)   # one-time set-up outside the timing
+            r = hmc.hmc(tg, theta0, n_iter=n_warm + n_keep, eps=0.02, n_leapfrog=n_leapfrog, adapt_mass=adapt,
+                        k=10, adapt_eps_until=n_warm, seed=7)
+            x = r["samples"][n_warm:]
+            neff = np.array([hmc.ess(x[:, i]) for i in range(tg.dim)])
+            sec_keep = r["seconds"] * n_keep / (n_warm + n_keep)
+            out[name] = {"seconds": r["seconds"], "acceptance": float(r["accepted"][n_warm:].mean()),
+                         "eps": r["eps"], "gradient_evaluations": r["gradient_evaluations"],
+                         "ess_min": float(neff.min()), "ess_median": float(np.median(neff)),
+                         "ess_per_s_min": float(neff.min() / sec_keep),
+                         "ess_per_s_median": float(np.median(neff) / sec_keep)}
+    finally:
+        h.close()
+        ctx.close()
+    out["speedup_min_ess_per_s"] = out["hessian_mass"]["ess_per_s_min"] / max(out["identity_mass"]["ess_per_s_min"], 1e-30)
+    return out
+
+
 def _codon(device: int, steps: int = 20, warmup: int = 3):
     """The codon configuration: 500 taxa x 3,000 patterns x 4 categories, 61 states, tensor-core
     kernels (three-pass TF32, FP32 accumulation)."""
@@ -496,6 +537,7 @@ def run_gpu(args):
         line["codon"] = _codon(local)
         line["differentiation"] = _differentiation(local)
         line["inference"] = _inference(local)
+        line["hmc"] = _hmc(local)
         if args.serving_requests > 0:
             line["serving"] = _serving(args.serving_requests, local)
     if dist is not None:
@@ -515,9 +557,9 @@ def main():
                     help="requests of the serving measurement (0 skips it)")
     ap.add_argument("--no-extras", action="store_true",
                     help="only the headline nucleotide measurement (no codon, differentiation, serving)")
-    ap.add_argument("--case", choices=("all", "codon", "differentiation"), default="all",
+    ap.add_argument("--case", choices=("all", "codon", "differentiation", "hmc"), default="all",
                     help="codon / differentiation: time that workload alone for --steps steps after "
-                         "--warmup (for profiling); all: the full measurement")
+                         "--warmup (for profiling); hmc: the HMC object alone; all: the full measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -527,6 +569,9 @@ def main():
     build.build()
     if args.case != "all":
         _, _, local = _rank_env()
+        if args.case == "hmc":
+            print(json.dumps({"case": "hmc", **_hmc(local)}), flush=True)
+            return 0
         fn = _codon if args.case == "codon" else _differentiation
         print(json.dumps({"case": args.case, **fn(local, steps=args.steps, warmup=args.warmup)}), flush=True)
         return 0
