@@ -176,13 +176,55 @@ def _cpu_baseline(problem, seconds: float = 12.0):
     reps = max(1, min(20, int(seconds / max(per, 1e-3))))
     t0 = time.perf_counter()
     for _ in range(reps):
-        oracle.evaluate(problem, patterns=slice(0, sample))
+        ref = oracle.evaluate(problem, patterns=slice(0, sample))
     per = (time.perf_counter() - t0) / reps
     full = per * P / sample
     return {"value": 1.0 / full, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{sample} of {P} patterns, {reps} evaluations (single thread, FP64), "
                       f"time scaled by {P / sample:g} to the full alignment",
-            "seconds_per_full_eval": full}
+            "seconds_per_full_eval": full}, ref, sample
+
+
+def _stated_error(ctx, problem, ref, sample, device, steps: int = 10):
+    """Error against the FP64 oracle of the same call on the sampled patterns (weights of the
+    others set to zero), for the FP32 path that ``value`` times and for the library's FP64 path,
+    and the FP64 path's evaluations/s on the full workload (a floor: FP64 partials, every level in
+    the fused kernel)."""
+    import numpy as np
+    import torch
+
+    masked = dict(problem, weights=np.where(np.arange(problem["weights"].shape[0]) < sample, problem["weights"], 0.0))
+    gmax = float(np.abs(ref.grad).max())
+    out = {"reference": "FP64 oracle on the first %d patterns" % sample}
+    for prec in ("fp32", "fp64"):
+        h = ctx.upload(masked, prec)
+        try:
+            r = h.eval(problem["b"], grad=True)
+        finally:
+            h.close()
+        out[prec] = {"logL_rel": abs(r["logL"] - ref.logL) / abs(ref.logL),
+                     "grad_maxnorm_rel": float(np.abs(r["grad"] - ref.grad).max()) / gmax}
+    h = ctx.upload(problem, "fp64")
+    dev = torch.device("cuda", device)
+    n = problem["parent"].shape[0]
+    b = torch.tensor(problem["b"], device=dev)
+    lg = torch.zeros(1, dtype=torch.float64, device=dev)
+    g = torch.zeros(n, dtype=torch.float64, device=dev)
+    try:
+        for _ in range(3):
+            h.eval_async(b, lg, g)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            h.eval_async(b, lg, g)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        out["fp64_path"] = {"ms_per_eval": e0.elapsed_time(e1) / steps,
+                            "evals_per_s": 1e3 * steps / e0.elapsed_time(e1), "status": h.status()}
+    finally:
+        h.close()
+    return out
 
 
 def run_reference(args):
@@ -530,7 +572,8 @@ def run_gpu(args):
         "clocks": clocks.summary(),
     }
     if rank == 0 and world == 1:
-        line["cpu_baseline"] = _cpu_baseline(pr)
+        line["cpu_baseline"], ref, sample = _cpu_baseline(pr)
+        line["error"] = _stated_error(ctx, pr, ref, sample, local)
     h.close()
     ctx.close()
     if rank == 0 and not args.no_extras:
