@@ -628,8 +628,10 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
     unsigned char *sm = tc_raw;
     unsigned char *X[2] = {sm, sm + kRowTile};                 // children's rows (staging)
     unsigned char *QK = sm + 2 * kRowTile;                      // q_k rows
-    unsigned char *T[2] = {sm + 3 * kRowTile, sm + 3 * kRowTile + 4 * kTab};   // [D; G] or D^T, hi | lo
-    enum { BX = 0, BQ = 1, BT = 2, BD = 3, BM = 4, NB = 5 };    // rows, q_k, [D;G], D^T, products
+    // per child 64 KB: [D; G] hi in the lower half (then D^T hi | lo), [D; G] lo in the upper half
+    // (then the staged result q_c)
+    unsigned char *T[2] = {sm + 3 * kRowTile, sm + 3 * kRowTile + 4 * kTab};
+    enum { BX = 0, BQ = 1, BTH = 2, BTL = 3, BD = 4, BM = 5, NB = 6 };   // rows, q_k, [D;G] hi, lo, D^T, products
     __shared__ __align__(8) uint64_t bar[NB];
     __shared__ uint32_t tmem_slot;
     __shared__ double red[2][kTcThreads / 32];
@@ -659,9 +661,10 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
     const float inv = on ? __ldcg(d.site_invL + p0 + t) : 0.f;
     const int Er = on ? __ldcg(d.site_Er + p0 + t) : 0;
     float dsum[2] = {0.f, 0.f};
-    uint32_t ph[NB] = {0, 0, 0, 0, 0};
-    bool pend[NB] = {false, false, false, false, false};
+    uint32_t ph[NB] = {0, 0, 0, 0, 0, 0};
+    bool pend[NB] = {false, false, false, false, false, false};
     bool ok = true;
+    bool store_pending = false;   // (leader) results of the previous category still being read from the upper halves
     // copies (thread 0): rows of the internal children, q_k, tables
     auto issue_rows = [&](int l) {
         uint32_t bytes = 0;
@@ -679,13 +682,16 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
         mbar_arrive_expect(&bar[BQ], kRowTile);
         for (int kb = 0; kb < 2; ++kb) tma_load_3d(QK + kb * kRowKB, &tm_pre, kb * 32, p0, (k - N) * C + l, &bar[BQ]);
     };
-    auto issue_tables = [&](int l) {
-        pend[BT] = true;
-        mbar_arrive_expect(&bar[BT], 8 * kTab);
-        for (int side = 0; side < 2; ++side) {
-            load_tables(T[side], &tm_tab, d, cs[side], l, kTcD, 2, &bar[BT]);
-            load_tables(T[side] + 2 * kTab, &tm_tab, d, cs[side], l, kTcDlo, 2, &bar[BT]);
-        }
+    auto issue_tables_hi = [&](int l) {   // [D; G] hi into the lower halves
+        pend[BTH] = true;
+        mbar_arrive_expect(&bar[BTH], 4 * kTab);
+        for (int side = 0; side < 2; ++side) load_tables(T[side], &tm_tab, d, cs[side], l, kTcD, 2, &bar[BTH]);
+    };
+    auto issue_tables_lo = [&](int l) {   // [D; G] lo into the upper halves
+        pend[BTL] = true;
+        mbar_arrive_expect(&bar[BTL], 4 * kTab);
+        for (int side = 0; side < 2; ++side)
+            load_tables(T[side] + 2 * kTab, &tm_tab, d, cs[side], l, kTcDlo, 2, &bar[BTL]);
     };
     auto wait = [&](int i) {   // all threads, one phase of barrier i
         ok = wait_all(&bar[i], ph[i]);
@@ -695,7 +701,8 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
     if (leader) {
         issue_rows(l0);
         if (!root) issue_qk(l0);
-        issue_tables(l0);
+        issue_tables_hi(l0);
+        issue_tables_lo(l0);
     }
     for (int l = l0; l < l1 && ok; ++l) {
         const int Eq = (on && !root) ? __ldcg(d.qe + ((size_t)(k - N) * C + l) * d.Ps + p0 + t) : 0;
@@ -734,19 +741,35 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
         tc_before();
         __syncthreads();   // rows read: the slots may take the next category's rows
         if (leader && l + 1 < l1) issue_rows(l + 1);
-        if (!wait(BT)) break;
+        // the passes with the hi tables first (hi x hi, lo x hi); the lo tables may still be landing
+        if (!wait(BTH)) break;
         if (leader) {
             tc_after();
             for (int side = 0; side < 2; ++side) {
                 const uint32_t acc = tmem + 128 * side, xa = tmem + 256 + 128 * side, tb = smem_u32(T[side]);
                 mma_tile_ta(acc, xa, tb, 2 * kMP, false);
-                mma_tile_ta(acc, xa, tb + 2 * kTab, 2 * kMP, true);
                 if (!tip[side]) mma_tile_ta(acc, xa + 64, tb, 2 * kMP, true);
+            }
+            // while those run: the previous results leave the upper halves, this category's lo
+            // tables take their place
+            if (l > l0) {
+                if (store_pending) bulk_wait_read0();
+                store_pending = false;
+                issue_tables_lo(l);
+            }
+        }
+        if (!wait(BTL)) break;
+        if (leader) {
+            tc_after();
+            for (int side = 0; side < 2; ++side) {
+                const uint32_t acc = tmem + 128 * side, xa = tmem + 256 + 128 * side, tb = smem_u32(T[side]);
+                mma_tile_ta(acc, xa, tb + 2 * kTab, 2 * kMP, true);
             }
             pend[BM] = true;
             mma_commit(&bar[BM]);
         }
         if (!wait(BM)) break;
+        if (leader && !any_int && l + 1 < l1) issue_tables_hi(l + 1);   // no D^T products: the lower halves are free
         // the D^T tables of the internal children into their (now free) table slots
         if (leader && any_int) {
             pend[BD] = true;
@@ -823,13 +846,14 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
                     mma_tile_ta(acc, qa + 64, tb, kMP, true);
                 }
                 pend[BM] = true;
-            mma_commit(&bar[BM]);
+                mma_commit(&bar[BM]);
             }
             if (!wait(BM)) break;
+            if (leader && l + 1 < l1) issue_tables_hi(l + 1);   // the D^T tables have been read
         }
         if (any_int) {
-            // epilogue 2: q_c = qt_c + D_c^T qt_c, scaled, staged in the child's (now free) table
-            // slot and stored by TMA
+            // epilogue 2: q_c = qt_c + D_c^T qt_c, scaled, staged in the upper half of the child's
+            // table slot and stored by TMA
             tc_after();
             for (int side = 0; side < 2; ++side) {
                 if (tip[side]) continue;
@@ -864,7 +888,7 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
                     tmem_wait_ld();
 #pragma unroll
                     for (int j = 0; j < 16; ++j) a[j] += q[j];
-                    put16(T[side], t, ch0 + i, a, e);
+                    put16(T[side] + 2 * kTab, t, ch0 + i, a, e);
                 }
                 if (on && hf == 0) __stcg(d.qe + ((size_t)(cs[side] - N) * C + l) * d.Ps + p0 + t, Eq + Ex[1 - side] + e);
             }
@@ -874,13 +898,12 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
                 for (int side = 0; side < 2; ++side) {
                     if (tip[side]) continue;
                     for (int kb = 0; kb < 2; ++kb)
-                        tma_store_3d(&tm_pre, T[side] + kb * kRowKB, kb * 32, p0, (cs[side] - N) * C + l);
+                        tma_store_3d(&tm_pre, T[side] + 2 * kTab + kb * kRowKB, kb * 32, p0, (cs[side] - N) * C + l);
                 }
                 bulk_commit();
-                bulk_wait_read0();   // the staged rows are read before the table slots refill
+                store_pending = true;   // waited for before the next lo tables are copied over them
             }
         }
-        if (leader && l + 1 < l1) issue_tables(l + 1);   // the table slots are free again
         tc_before();
         __syncthreads();   // tensor memory read before the next category's rows overwrite it
     }
@@ -905,6 +928,7 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
         for (int i = 0; i < NB; ++i)   // let every copy and product in flight finish
             if (pend[i]) mbar_wait_bounded(&bar[i], ph[i], kWaitLimitCycles);
     }
+    if (leader) bulk_wait_read0();   // the staging smem is read before the block exits
     tc_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, 512);
