@@ -928,7 +928,7 @@ pg_status enqueue_single(pg_handle *h, int skip, const double *d_b, double *d_lo
     if (d.precision == PG_PRECISION_FP32 && d.P > 0) {
         for (int k = 2; k >= 1 && !use_top; --k) {
             set_tiling(d, k * h->ctx->n_sm, max_range);
-            use_top = (size_t)k * pg::top_smem_bytes(d) <= (size_t)220 * 1024;
+            use_top = (size_t)k * (pg::top_smem_bytes(d) + 1024) <= (size_t)228 * 1024;   // 1 KB reserved per block
         }
     }
     if (!use_top) set_tiling(d, single_target(h->ctx, d), max_range);

@@ -28,10 +28,16 @@ constexpr size_t kTopSmemLimit = 227 * 1024;
 // partial rows and scales of top and boundary nodes, site values, the top ops and codes, and the
 // tip codes of the top nodes' tip children (at most n_top + 1 of them)
 __host__ __device__ size_t top_bytes(int n_top, int n_bnd, int C, int L) {
-    const size_t rows = (size_t)(2 * n_top + n_bnd) * L * (16 * C + 4) + (size_t)L * 12;
+    const size_t tabs = (size_t)n_top * 2 * C * kPtabCols * 16;   // the top nodes' child-branch tables
+    const size_t rows = tabs + (size_t)(2 * n_top + n_bnd) * L * (16 * C + 4) + (size_t)L * 12;
     const size_t meta = (size_t)n_top * (sizeof(int4) + sizeof(int2));
     const size_t tipc = (size_t)(n_top + 1) * ((L + 15) / 16 * 16);
     return rows + meta + tipc + 64;
+}
+
+__device__ __forceinline__ void cols_from_smem(const float4 *p, float4 (&c)[4]) {   // load_cols for shared memory
+#pragma unroll
+    for (int t = 0; t < 4; ++t) c[t] = p[t];
 }
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
@@ -50,8 +56,10 @@ __global__ void __launch_bounds__(kBlock, 2) top_kernel(const __grid_constant__ 
     const int pieces = d.pieces, slot0 = tile * pieces;
     const int n_top = d.n_top, n_bnd = d.n_bnd;
     const int o_cut = d.level_off[d.cut];
-    // shared layout: float4 rows [node][C][L], then int scales [node][L], then site values [L]
-    float4 *Pt = dyn;                                   // post partials of top nodes
+    // shared layout: the top nodes' child-branch tables [node][side][C][kPtabCols], float4 rows
+    // [node][C][L], then int scales [node][L], then site values [L]
+    float4 *Tt = dyn;                                   // tables (each read many times per level)
+    float4 *Pt = Tt + (size_t)n_top * 2 * C * kPtabCols; // post partials of top nodes
     float4 *Qt = Pt + (size_t)n_top * C * L;            // pre partials of top nodes
     float4 *Bt = Qt + (size_t)n_top * C * L;            // post partials of boundary nodes
     int *EP = reinterpret_cast<int *>(Bt + (size_t)n_bnd * C * L);
@@ -72,11 +80,10 @@ __global__ void __launch_bounds__(kBlock, 2) top_kernel(const __grid_constant__ 
         ops_s[t] = __ldg(d.ops + o_cut + t);
         code_s[t] = __ldg(d.top_code + t);
     }
-    for (int t = threadIdx.x; t < n_top * 2 * ((C * kPtabCols * 16 + 127) / 128); t += blockDim.x) {
-        const int per = (C * kPtabCols * 16 + 127) / 128, nb = t / per, line = t - nb * per;
+    for (int t = threadIdx.x; t < n_top * 2 * C * kPtabCols; t += blockDim.x) {   // the tables, once
+        const int per = C * kPtabCols, nb = t / per, e = t - nb * per;
         const int4 op = __ldg(d.ops + o_cut + (nb >> 1));
-        const char *tab = reinterpret_cast<const char *>(d.Ptab + (size_t)((nb & 1) ? op.z : op.y) * C * kPtabCols);
-        asm volatile("prefetch.global.L1 [%0];\n" ::"l"(tab + line * 128));
+        cp_async16(Tt + (size_t)nb * per + e, d.Ptab + (size_t)((nb & 1) ? op.z : op.y) * per + e);
     }
     __syncthreads();
     // tip codes of the top nodes' tip children (code -1 - slot)
@@ -126,16 +133,16 @@ __global__ void __launch_bounds__(kBlock, 2) top_kernel(const __grid_constant__ 
 #pragma unroll
                 for (int side = 0; side < 2; ++side) {
                     const int c = side ? op.z : op.y, cc = side ? code.y : code.x;
-                    const float4 *T = d.Ptab + ((size_t)c * C + l) * kPtabCols;
+                    const float4 *T = Tt + ((size_t)(2 * ti + side) * C + l) * kPtabCols;
                     sm[side] = f4(0.f, 0.f, 0.f, 0.f);
                     if (cc < 0) {
                         const int y = tips_s[(size_t)(-1 - cc) * L16 + q];
-                        const float4 hi = __ldg(T + y), lo = __ldg(T + kColPlo + y);
+                        const float4 hi = T[y], lo = T[kColPlo + y];
                         x[side] = f4(fmaf(hi.x, r, lo.x * r), fmaf(hi.y, r, lo.y * r), fmaf(hi.z, r, lo.z * r),
                                      fmaf(hi.w, r, lo.w * r));
                     } else {
                         x[side] = cc < n_top ? Pt[((size_t)cc * C + l) * L + q] : Bt[((size_t)(cc - n_top) * C + l) * L + q];
-                        sm[side] = matvec_hilo(T + kColDhi, T + kColDlo, x[side]);
+                        sm[side] = matvec_hilo_v(T + kColDhi, T + kColDlo, x[side]);
                         if (l == 0) E += cc < n_top ? EP[cc * L + q] : EB[(cc - n_top) * L + q];
                     }
                 }
@@ -208,14 +215,14 @@ __global__ void __launch_bounds__(kBlock, 2) top_kernel(const __grid_constant__ 
                 else Ec[side] = cc < n_top ? EP[cc * L + q] : EB[(cc - n_top) * L + q];
 #pragma unroll
                 for (int l = 0; l < C; ++l) {
-                    const float4 *T = d.Ptab + ((size_t)c * C + l) * kPtabCols;
+                    const float4 *T = Tt + ((size_t)(2 * ti + side) * C + l) * kPtabCols;
                     if (cc < 0) {
-                        aa[side][l] = scal(__ldg(T + y[side]), r);
+                        aa[side][l] = scal(T[y[side]], r);
                     } else {
                         const float4 xv = cc < n_top ? Pt[((size_t)cc * C + l) * L + q]
                                                      : Bt[((size_t)(cc - n_top) * C + l) * L + q];
                         float4 H[4];
-                        load_cols(T, H);
+                        cols_from_smem(T, H);
                         aa[side][l] = matvec(H, xv);
                     }
                 }
@@ -239,7 +246,7 @@ __global__ void __launch_bounds__(kBlock, 2) top_kernel(const __grid_constant__ 
                     if (HESS) hs = fmaf(d.gw2[l], dot(qt, matvec(Qc, uu)), hs);
                     if (cc >= 0) {
                         float4 H[4];
-                        load_cols(d.Ptab + ((size_t)c * C + l) * kPtabCols, H);
+                        cols_from_smem(Tt + ((size_t)(2 * ti + side) * C + l) * kPtabCols, H);
                         qv[l] = matvec_t(H, qt);
                         mq = fmaxf(mq, hmax(qv[l]));
                     }
