@@ -5,15 +5,20 @@
 // in FP32 by the threads.  The tensor core's accumulation truncates, and P x sums positive terms
 // only, so keeping the O(1) identity out of it keeps that bias to the size of D x.
 //
-// One item is a tile of kTcTile = 128 patterns (the MMA's M) of one node; thread t of the 128-thread
-// block owns pattern row t, which is TMEM lane t of every accumulator, so per-pattern reductions
-// (the largest state of a column, q . G x) stay in one thread.  Operand tiles [128 x 64] FP32 and
-// tables [64 x 64] arrive by TMA with 128-byte swizzling (the canonical K-major layout); a tip
-// child's rows are written as one-hot (or all-ones) rows, so tips and internal children share the
-// product.  Each product runs three TF32 passes, hi x hi + hi x lo + lo x hi, where the tensor core
-// truncates an FP32 operand to its TF32 part (hi) and lo = x - trunc(x) is formed by the threads
-// for the rows and stored with the tables: about FP32 accuracy (error ~2^-21 relative per term).
-// Results leave through a swizzled staging tile and a TMA store; exponents with plain stores.
+// One item is a tile of kTcTile = 128 patterns (the MMA's M) of one node.  Pattern row t is TMEM
+// lane t of every accumulator.  A 128-thread block gives row t to thread t.  The 256-thread
+// pre-order kernel gives it to two threads, one per half of the states; they combine their partial
+// maxima and sums through shared memory.
+//
+// Operand tiles [128 x 64] FP32 and tables [64 x 64] arrive by TMA with 128-byte swizzling (the
+// canonical K-major layout).  A tip child's rows are written as one-hot (or all-ones) rows, so tips
+// and internal children share the product.
+//
+// Each product runs three TF32 passes, hi x hi + hi x lo + lo x hi.  The tensor core truncates an
+// FP32 operand to its TF32 part (hi); lo = x - trunc(x) is formed by the threads for the rows
+// (in shared or tensor memory) and stored with the tables.  This gives about FP32 accuracy (error
+// ~2^-21 relative per term).  Results leave through a swizzled staging tile and a TMA store;
+// exponents go out with plain stores.
 //
 // Every wait is bounded (kWaitLimitCycles); a block that gives up records PG_ERR_TIMEOUT, lets its
 // copies land, frees its tensor memory and returns.
