@@ -67,7 +67,11 @@ typedef struct pg_options {
 
 /*
  * A problem, as in Section 2.1 (all pointers are host pointers, read during pg_upload only).
- *   n_states m: 4 in this build (nucleotides); other m are rejected with PG_ERR_UNSUPPORTED.
+ *   n_states m: 4 (nucleotides: the CUDA-core path, FP32 or FP64 partials) or any other m in
+ *                          2..64 (amino acids, codons, ...: the general path, FP32 partials,
+ *                          tensor-core products unless PG_FLAG_SIMT_MSTATE).  m > 64, or FP64
+ *                          with m != 4, is rejected with PG_ERR_UNSUPPORTED; m < 2 with
+ *                          PG_ERR_INVALID.
  *   n_categories C: 1..4 discrete rate categories (Section 2.5).
  *   parent[2N-1]           parent node of each node, -1 for the root; every internal node must
  *                          have exactly two children (binary tree, Section 2.1).
