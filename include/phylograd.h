@@ -300,6 +300,15 @@ pg_status pg_set_phase_timing(pg_handle *h, int enable);
 pg_status pg_get_phase_times(pg_handle *h, pg_phase_times *out);
 
 /* Static text for a status code. */
+/* Failure-detection self-test.  Every kernel's device-side waits are bounded.  A wait that gives
+ * up records a status bit, lets its own copies land, frees its tensor memory and returns.  The
+ * host then reports PG_ERR_TIMEOUT instead of the GPU hanging.  This call runs that bounded wait
+ * on the context's device on an mbarrier that nothing arrives at.  limit_cycles is the wait's
+ * limit in SM clock cycles, in [1000, 2^32]; the library's own kernels use ~1 s.  Returns
+ * PG_ERR_TIMEOUT when the wait gave up as intended, and the context stays usable.  Errors:
+ * PG_ERR_INVALID (NULL context, limit out of range), PG_ERR_OOM, PG_ERR_CUDA. */
+pg_status pg_selftest_timeout(pg_ctx *ctx, uint64_t limit_cycles);
+
 const char *pg_status_string(pg_status s);
 
 /* Text of the last error raised on the calling thread ("" if none). */

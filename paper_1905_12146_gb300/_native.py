@@ -23,7 +23,8 @@ EXPORTED = ("pg_create", "pg_destroy", "pg_upload", "pg_free", "pg_eval", "pg_ev
             "pg_get_phase_times", "pg_eval_noalloc", "pg_status_string", "pg_last_error",
             "pg_forward_async", "pg_backward_async", "pg_forward_batch_async",
             "pg_backward_batch_async", "pg_clock_lengths_async", "pg_clock_grad_async",
-            "pg_server_create", "pg_server_submit", "pg_server_wait", "pg_server_destroy")
+            "pg_server_create", "pg_server_submit", "pg_server_wait", "pg_server_destroy",
+            "pg_selftest_timeout")
 
 
 class PhyloGradError(RuntimeError):
@@ -120,6 +121,7 @@ def load(path: str = LIB_PATH):
         "pg_server_submit": ([vp, ctypes.POINTER(pg_request), ctypes.POINTER(ctypes.c_uint64)], i32),
         "pg_server_wait": ([vp, ctypes.c_uint64, ctypes.POINTER(pg_request_info)], i32),
         "pg_server_destroy": ([vp], i32),
+        "pg_selftest_timeout": ([vp, ctypes.c_uint64], i32),
         "pg_status_string": ([i32], ctypes.c_char_p),
         "pg_last_error": ([], ctypes.c_char_p),
     }
@@ -202,6 +204,11 @@ class Context:
         check(lib.pg_create(ctypes.byref(opt), ctypes.byref(out)))
         self._ptr = out
         self.device = device
+
+    def selftest_timeout(self, limit_cycles: int = 2_000_000) -> int:
+        """Run the library's bounded device-side wait on a barrier nothing arrives at; returns the
+        status (PG_ERR_TIMEOUT when the wait gave up as intended)."""
+        return int(load().pg_selftest_timeout(self._ptr, int(limit_cycles)))
 
     def upload(self, problem: dict, precision: str | None = None) -> "Handle":
         return Handle(self, problem, precision)

@@ -16,6 +16,7 @@
 
 #include "phylograd.h"
 #include "pg_internal.cuh"
+#include <nvtx3/nvToolsExt.h>
 #include "pg_host.h"
 
 namespace pg {
@@ -481,6 +482,13 @@ pg_status upload_m(pg_ctx *ctx, const pg_problem *pr, const TreePlan &tp, pg_han
     return PG_OK;
 }
 
+// an NVTX range around the launches of one phase (host timeline; tools that follow NVTX attribute
+// the kernels launched inside it to the phase)
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
+
 pg_status enqueue_m(pg_handle *h, int skip, const double *d_b, double *d_logL, double *d_grad, double *d_hess,
                     double *d_site_logL, const double *d_gscale, cudaStream_t s) {
     pg::MDesc d = h->md;
@@ -495,6 +503,8 @@ pg_status enqueue_m(pg_handle *h, int skip, const double *d_b, double *d_logL, d
     const bool hess = bwd && d_hess != nullptr;
     if (hess && !fwd) return fail(PG_ERR_UNSUPPORTED, "the Hessian diagonal of a %d-state problem needs a full evaluation", d.m);
     cudaError_t e = cudaSuccess;
+    Range range(fwd && !(skip & pg::kSkipPre) ? "pg evaluation (general states)"
+                                               : (fwd ? "pg forward (general states)" : "pg backward (general states)"));
     if (fwd) {
         e = pg::launch_m_pmatrix(d, hess, s);
         for (int lv = 0; e == cudaSuccess && lv < d.n_levels; ++lv) {
@@ -942,6 +952,7 @@ pg_status enqueue_single(pg_handle *h, int skip, const double *d_b, double *d_lo
         h->events.insert(h->events.end(), ev, ev + 6);
     }
     auto mark = [&](int i) { if (timed) cudaEventRecord(ev[i], s); };
+    Range range(fwd && bwd ? "pg evaluation" : (fwd ? "pg forward" : "pg backward"));
     cudaError_t e = cudaSuccess;
     mark(0);
     if (fwd) e = pg::launch_pmatrix<1>(a, s);

@@ -49,3 +49,11 @@ def test_status_strings_are_host_only(lib_path):
         assert lib.pg_status_string(code)
     assert lib.pg_status_string(99) == b"unknown status"
 
+
+
+def test_selftest_rejects_a_null_context(lib_path):
+    """Argument checks come before any CUDA call, so this runs without a GPU."""
+    lib = ctypes.CDLL(lib_path)
+    lib.pg_selftest_timeout.argtypes = [ctypes.c_void_p, ctypes.c_uint64]
+    lib.pg_selftest_timeout.restype = ctypes.c_int32
+    assert lib.pg_selftest_timeout(None, 1_000_000) == 1   # PG_ERR_INVALID
