@@ -45,7 +45,7 @@ struct pg_handle {
     bool have_post = false;   // an enqueued post-order left partials a backward pass can use
     bool mstate = false;      // a general state space (pg_mstate.cu): md holds its layout
     pg::MDesc md{};
-    alignas(64) CUtensorMap tm_post, tm_pre, tm_tab;   // TMA descriptors of the tensor-core kernels
+    CUtensorMap tm_post, tm_pre, tm_tab;   // TMA descriptors of the tensor-core kernels (the type is 64-byte aligned)
     bool external = false;    // the device block belongs to a caller's arena (not freed here)
     const pg::ProbDesc *d_desc = nullptr;   // device copy of desc (batched level kernels read it)
 };

@@ -190,7 +190,7 @@ template <bool TC>
 // threads of the block call this)
 __device__ __forceinline__ void store_tables(const MDesc &d, int c, int l, int kind, const float acc[4][4], int ts, int tj,
                                              float *stage) {
-    if (TC) {
+    if constexpr (TC) {
         float *base = d.tabs + (size_t)(c * d.C + l) * kTcKinds * kMP * kMP;
         const int hk = kind == 0 ? kTcD : (kind == 1 ? kTcG : kTcH);
         const int lk = kind == 0 ? kTcDlo : (kind == 1 ? kTcGlo : kTcHlo);
@@ -208,21 +208,21 @@ __device__ __forceinline__ void store_tables(const MDesc &d, int c, int l, int k
             }
             __syncthreads();
         }
-        return;
-    }
-    float rs[4];
+    } else {
+        float rs[4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) rs[a] = sum16(acc[a][0] + acc[a][1] + acc[a][2] + acc[a][3]);
-    float *T = d.tabs + ((size_t)(c * d.C + l) * kTabKinds + (kind == 0 ? kTabDT : (kind == 1 ? kTabGT : kTabHT))) * kTabFloats;
-    put_transposed(T, ts, tj, acc);
-    if (tj == 0) {
+        for (int a = 0; a < 4; ++a) rs[a] = sum16(acc[a][0] + acc[a][1] + acc[a][2] + acc[a][3]);
+        float *T = d.tabs + ((size_t)(c * d.C + l) * kTabKinds + (kind == 0 ? kTabDT : (kind == 1 ? kTabGT : kTabHT))) * kTabFloats;
+        put_transposed(T, ts, tj, acc);
+        if (tj == 0) {
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            const int s = 4 * ts + a;
-            T[kMP * kMP + s] = kind == 0 ? (s < d.m ? 1.f + rs[a] : 0.f) : rs[a];
+            for (int a = 0; a < 4; ++a) {
+                const int s = 4 * ts + a;
+                T[kMP * kMP + s] = kind == 0 ? (s < d.m ? 1.f + rs[a] : 0.f) : rs[a];
+            }
         }
+        if (kind == 0) put_rowmajor(d.tabs + ((size_t)(c * d.C + l) * kTabKinds + kTabD) * kTabFloats, ts, tj, acc);
     }
-    if (kind == 0) put_rowmajor(d.tabs + ((size_t)(c * d.C + l) * kTabKinds + kTabD) * kTabFloats, ts, tj, acc);
 }
 
 template <bool TC>

@@ -130,7 +130,6 @@ __device__ __forceinline__ void tma_store_3d(const CUtensorMap *m, const void *s
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_all0() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
 
 // byte offset of 16-byte chunk cc (states 4 cc .. 4 cc + 3) of row r of a swizzled tile of `rows`
 // rows: two 32-state K blocks, rows 128 bytes apart, chunk index XOR (row mod 8)

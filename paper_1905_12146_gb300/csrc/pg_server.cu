@@ -60,7 +60,6 @@ class Arena {
             free_.erase(it);
             if (rest) free_[off + n] = rest;
             used_[off] = n;
-            in_use_ += n;
             return static_cast<char *>(base_) + off;
         }
         return nullptr;
@@ -70,7 +69,6 @@ class Arena {
         auto u = used_.find(off);
         if (u == used_.end()) return;
         size_t start = off, len = u->second;
-        in_use_ -= len;
         used_.erase(u);
         auto next = free_.lower_bound(start);
         if (next != free_.end() && next->first == start + len) {
@@ -89,12 +87,11 @@ class Arena {
         free_[start] = len;
     }
     size_t total() const { return total_; }
-    size_t in_use() const { return in_use_; }
     size_t last_request() const { return last_request_; }
 
   private:
     void *base_ = nullptr;
-    size_t total_ = 0, in_use_ = 0, last_request_ = 0;
+    size_t total_ = 0, last_request_ = 0;
     std::map<size_t, size_t> free_;               // offset -> bytes
     std::unordered_map<size_t, size_t> used_;     // offset -> bytes
 };

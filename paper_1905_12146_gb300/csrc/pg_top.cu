@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(kBlock, 2) top_kernel(const __grid_constant__ 
                 float4 x[2], sm[2];
 #pragma unroll
                 for (int side = 0; side < 2; ++side) {
-                    const int c = side ? op.z : op.y, cc = side ? code.y : code.x;
+                    const int cc = side ? code.y : code.x;
                     const float4 *T = Tt + ((size_t)(2 * ti + side) * C + l) * kPtabCols;
                     sm[side] = f4(0.f, 0.f, 0.f, 0.f);
                     if (cc < 0) {
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(kBlock, 2) top_kernel(const __grid_constant__ 
             float4 aa[2][C];
 #pragma unroll
             for (int side = 0; side < 2; ++side) {
-                const int c = side ? op.z : op.y, cc = side ? code.y : code.x;
+                const int cc = side ? code.y : code.x;
                 if (cc < 0) y[side] = tips_s[(size_t)(-1 - cc) * L16 + q];
                 else Ec[side] = cc < n_top ? EP[cc * L + q] : EB[(cc - n_top) * L + q];
 #pragma unroll

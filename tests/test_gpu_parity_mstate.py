@@ -97,7 +97,7 @@ def test_codon_caterpillar_and_models(ctx, oracle_mod):
     _check(ctx, oracle_mod, pr, hess=False, label="codon relabelled")
 
 
-@pytest.mark.parametrize("m", [5, 20, 33, 64])
+@pytest.mark.parametrize("m", [2, 3, 5, 20, 33, 64])
 def test_other_state_counts(ctx, oracle_mod, m):
     pr = wl.random_problem(20, 257, n_states=m, n_cat=2, seed=30 + m, reversible=True, b_mean=0.1,
                            ambiguous=0.05)
