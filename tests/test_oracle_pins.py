@@ -1,6 +1,7 @@
 """Pins of the FP64 oracle against things fixed by the paper and by mathematics, not by itself.
 
-* expm: scipy's independent implementation, the JC69 closed form, the semigroup property.
+* expm: scipy's independent implementation, the JC69 and 2-state closed forms, the semigroup
+  property.
 * likelihood: the definition Eq. 1 summed by brute force over internal states (with the rate
   mixture of Section 2.5), 2-taxon and zero-length closed forms, an underflow closed form.
 * gradient: term-by-term derivative of Eq. 1, the quadratic pruning gradient (Section 1),
@@ -8,7 +9,8 @@
 * pre-order partials: p_k' q_k = P(Y) at every node (Section 2.4).
 * invariances: root position for reversible stationary Q (Section 5), Q*c with b/c,
   identical rate categories, internal relabelling.
-* Hessian diagonal (Section 2.6): finite differences of the gradient.
+* Hessian diagonal (Section 2.6): finite differences of the gradient; the exact derivatives of
+  the closed-form 2-state transition matrices.
 """
 import numpy as np
 import pytest
@@ -173,6 +175,59 @@ def test_hessian_diagonal_central_differences(oracle_mod):
         bm[i] -= h
         fd = (oracle_mod.evaluate(pr, bp).grad[i] - oracle_mod.evaluate(pr, bm).grad[i]) / (2 * h)
         assert abs(fd - r.hess[i]) <= 1e-5 * max(1.0, abs(r.hess[i]))
+
+
+def test_two_state_closed_form_gradient_and_hessian(oracle_mod):
+    """A non-reversible 2-state chain Q = [[-a, a], [c, -c]] has, with s = a + c and E = e^-st,
+    P(t) = ([[c, a], [c, a]] + E [[a, -a], [-c, c]]) / s, so dP/dt = E Q and d2P/dt2 = -s E Q.
+    On a 3-taxon tree with a non-stationary root distribution and two unequally weighted rate
+    categories, Eq. 1 is summed over the internal states with these matrices; differentiating one
+    branch's factor once or twice gives the gradient and the Hessian diagonal exactly (Section
+    2.6, summed over sites with the per-site squared gradient)."""
+    a, c = 0.7, 1.9
+    s_ = a + c
+    Q = np.array([[-a, a], [c, -c]])
+
+    def P(t, k):
+        E = np.exp(-s_ * t)
+        if k == 0:
+            return (np.array([[c, a], [c, a]]) + E * np.array([[a, -a], [-c, c]])) / s_
+        return (E if k == 1 else -s_ * E) * Q
+
+    parent = np.array([3, 3, 4, 4, -1], dtype=np.int32)
+    tips = np.array([[0, 1, 0, 2, 1, 0, 2], [0, 0, 1, 1, 2, 1, 0], [1, 0, 0, 1, 0, 2, 1]], dtype=np.uint8)
+    wt = np.array([3.0, 1.0, 2.0, 1.0, 5.0, 1.0, 2.0])
+    pi = np.array([0.8, 0.2])
+    rates, cw = np.array([0.4, 1.9]), np.array([0.65, 0.35])
+    b = np.array([0.3, 0.05, 0.9, 0.2, 0.0])
+    pr = wl.make_problem(parent, tips, wt, Q, pi, rates, cw, b)
+
+    def tip(y):
+        return np.ones(2) if y >= 2 else np.eye(2)[y]
+
+    def L(p, branch=-1, k=0):
+        """L_p, or its k-th derivative in b_branch."""
+        tot = 0.0
+        for r, w in zip(rates, cw):
+            M = {i: P(r * b[i], 0) for i in range(4)}
+            if branch >= 0:
+                M[branch] = r ** k * P(r * b[branch], k)
+            v3 = (M[0] @ tip(tips[0, p])) * (M[1] @ tip(tips[1, p]))
+            tot += w * pi @ ((M[3] @ v3) * (M[2] @ tip(tips[2, p])))
+        return tot
+
+    n_pat = tips.shape[1]
+    logL = sum(wt[p] * np.log(L(p)) for p in range(n_pat))
+    grad, hess = np.zeros(5), np.zeros(5)
+    for i in range(4):
+        for p in range(n_pat):
+            g = L(p, i, 1) / L(p)
+            grad[i] += wt[p] * g
+            hess[i] += wt[p] * (L(p, i, 2) / L(p) - g * g)
+    r = oracle_mod.evaluate(pr)
+    assert abs(r.logL - logL) <= 1e-13 * abs(logL)
+    np.testing.assert_allclose(r.grad, grad, rtol=1e-11, atol=1e-13)
+    np.testing.assert_allclose(r.hess, hess, rtol=1e-11, atol=1e-13)
 
 
 # ------------------------------------------------------------------------------ partials
