@@ -3,8 +3,9 @@
  * linear-time branch-length gradient (Ji et al., "Gradients do grow on trees", arXiv 1905.12146).
  *
  * One evaluation runs, on the GPU:
- *   1. P_{i,l} = e^{Q_i b_i r_l} for every branch i and rate category l, in FP64
- *      (Section 2.1 transition matrices; Section 2.5 rate categories);
+ *   1. P_{i,l} = e^{Q_i b_i r_l} for every branch i and rate category l (Section 2.1
+ *      transition matrices; Section 2.5 rate categories): in FP64 for 4 states; for other state
+ *      counts by uniformisation, FP64 powers and Poisson weights summed in FP32;
  *   2. the post-order (pruning) pass p_k = (P_i p_i) o (P_j p_j)   (Section 2.3);
  *   3. the site likelihoods L_p = sum_l w_l pi' p_root,l and logL = sum_p wt_p log L_p
  *      (Section 2.3 root inner product, Section 2.5 mixture, sites i.i.d. per Section 2.1);
@@ -53,8 +54,8 @@ typedef struct pg_options {
     uint32_t flags;             /* PG_FLAG_* below; 0 = defaults                              */
 } pg_options;
 
-/* Problems with 5..64 states run their products on the tensor cores (three-pass TF32 with FP32
- * accumulation) unless this flag selects the CUDA-core (SIMT FP32) kernels. */
+/* Problems with any state count but 4 (2..64) run their products on the tensor cores (three-pass
+ * TF32 with FP32 accumulation) unless this flag selects the CUDA-core (SIMT FP32) kernels. */
 #define PG_FLAG_SIMT_MSTATE 1u
 
 /* Storage and arithmetic of the partial likelihood vectors.  FP32: partials in FP32 with FP64
@@ -123,7 +124,8 @@ pg_status pg_destroy(pg_ctx *ctx);
 
 /* Validate a problem and copy it to the device (tree levels, tip codes, weights, Q, pi, rates),
  * allocating the partial-likelihood buffers it needs.  Errors: PG_ERR_INVALID (the problem breaks
- * a rule above), PG_ERR_UNSUPPORTED (m != 4 or C > 4), PG_ERR_OOM (allocation or budget). */
+ * a rule above), PG_ERR_UNSUPPORTED (m > 64, FP64 with m != 4, C > 4, or more than 2^30 nodes),
+ * PG_ERR_OOM (allocation or budget). */
 pg_status pg_upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out);
 
 /* Release a handle's device memory. */
@@ -252,7 +254,8 @@ pg_status pg_server_wait(pg_server *s, uint64_t ticket, pg_request_info *info);
 pg_status pg_server_destroy(pg_server *s);
 
 /* Wait for the handle's last evaluation and return its device-side status (PG_OK,
- * PG_ERR_INVALID for a bad branch length, PG_ERR_NUMERIC for a failed site likelihood). */
+ * PG_ERR_INVALID for a bad branch length, PG_ERR_NUMERIC for a failed site likelihood,
+ * PG_ERR_TIMEOUT for a bounded wait that gave up). */
 pg_status pg_eval_status(pg_handle *h);
 
 /* Sizes and algorithmic traffic of a handle (for measurement). */
