@@ -40,6 +40,7 @@ def _load():
         lib.orc_expm.argtypes = [ctypes.c_int, dp, dp]
         lib.orc_expm.restype = ctypes.c_int
         lib.orc_eval.argtypes = [ctypes.c_int] * 5 + [ip, up, dp, dp, ip, dp, dp, dp, dp,
+                                                      ctypes.c_int, dp,
                                                       dp, dp, dp, dp, dp, dp, ip, ip]
         lib.orc_eval.restype = ctypes.c_int
         _lib = lib
@@ -70,6 +71,9 @@ def evaluate(problem: dict, b: np.ndarray | None = None, partials: bool = False,
              patterns: slice | None = None) -> OracleResult:
     """Run the oracle on ``problem`` (a dict from ``workloads``) at branch lengths ``b``.
 
+    An optional ``problem["tip_partials"]`` [K][m] holds the partial vectors of partially observed
+    tips: code m + k selects row k, codes from m + K on are missing data (all ones).
+
     ``patterns`` restricts the evaluation to a slice of the site patterns (the result is then the
     log-likelihood of that sub-alignment).  With ``partials=True`` the scaled post- and pre-order
     partials of every node are returned as ``post[n][P][C][m]``, ``pre[...]`` with their log2
@@ -92,9 +96,13 @@ def evaluate(problem: dict, b: np.ndarray | None = None, partials: bool = False,
     rates = np.ascontiguousarray(problem["cat_rates"], dtype=np.float64)
     cw = np.ascontiguousarray(problem["cat_weights"], dtype=np.float64)
     b = np.ascontiguousarray(problem["b"] if b is None else b, dtype=np.float64)
+    tv = problem.get("tip_partials")
+    tv = None if tv is None or len(tv) == 0 else np.ascontiguousarray(tv, dtype=np.float64)
     n = parent.shape[0]
     n_tips = (n + 1) // 2
     m = Q.shape[1]
+    if tv is not None and (tv.ndim != 2 or tv.shape[1] != m):
+        raise ValueError("tip_partials must be [K][m]")
     P = tips.shape[1]
     C = rates.shape[0]
     logL = np.zeros(1)
@@ -111,8 +119,8 @@ def evaluate(problem: dict, b: np.ndarray | None = None, partials: bool = False,
     rc = lib.orc_eval(n_tips, m, P, C, Q.shape[0], _ptr(parent, ctypes.c_int32),
                       _ptr(tips, ctypes.c_uint8), _ptr(w, dp), _ptr(Q, dp),
                       _ptr(bm, ctypes.c_int32), _ptr(pi, dp), _ptr(rates, dp), _ptr(cw, dp),
-                      _ptr(b, dp), _ptr(logL, dp), _ptr(grad, dp), _ptr(site, dp),
-                      _ptr(hess, dp), _ptr(post, dp), _ptr(pre, dp),
+                      _ptr(b, dp), 0 if tv is None else tv.shape[0], _ptr(tv, dp),
+                      _ptr(logL, dp), _ptr(grad, dp), _ptr(site, dp), _ptr(hess, dp), _ptr(post, dp), _ptr(pre, dp),
                       _ptr(pe, ctypes.c_int32), _ptr(qe, ctypes.c_int32))
     if rc != 0:
         raise ValueError(f"orc_eval rejected the problem (code {rc})")

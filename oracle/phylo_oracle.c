@@ -216,9 +216,12 @@ static int rescale(double *v, int len)
 
 /*
  * Inputs (host, FP64 unless stated):
- *   parent[2N-1] (int32), tips[N][P] (uint8; code >= m means all-ones, Section 2.1 missing data),
- *   weights[P], Q[n_models][m][m], branch_model[2N-1] (NULL = model 0), pi[m],
- *   rates[C], cat_w[C], b[2N-1] (root entry ignored).
+ *   parent[2N-1] (int32), tips[N][P] (uint8), weights[P], Q[n_models][m][m],
+ *   branch_model[2N-1] (NULL = model 0), pi[m], rates[C], cat_w[C], b[2N-1] (root entry ignored),
+ *   tip_vecs[K][m] (K = n_tip_vecs >= 0; NULL when K = 0).
+ * A tip's partial vector at a pattern (Section 2.1) follows its code y: the indicator of state y
+ * for y < m; row y - m of tip_vecs for m <= y < m + K (partially observed data: finite entries
+ * >= 0, at least one positive); the all-ones vector (missing data) for y >= m + K.
  * Outputs: logL (scalar), grad[2N-1] (root entry 0), site_logL[P], hess[2N-1] (each may be NULL).
  * Optional introspection (NULL to skip): post[n][P][C][m] and pre[n][P][C][m] scaled partials
  * with their integer log2 factors post_e[n][P], pre_e[n][P] (value = stored * 2^e).
@@ -227,10 +230,21 @@ int orc_eval(int n_tips, int m, int n_patterns, int n_cat, int n_models,
              const int32_t *parent, const uint8_t *tips, const double *weights,
              const double *Q, const int32_t *branch_model, const double *pi,
              const double *rates, const double *cat_w, const double *b,
+             int n_tip_vecs, const double *tip_vecs,
              double *logL, double *grad, double *site_logL, double *hess,
              double *post_out, double *pre_out, int32_t *post_e_out, int32_t *pre_e_out)
 {
     if (n_tips < 2 || m < 2 || n_patterns < 0 || n_cat < 1 || n_models < 1) return ORC_INVALID;
+    if (n_tip_vecs < 0 || (n_tip_vecs > 0 && !tip_vecs)) return ORC_INVALID;
+    for (int v = 0; v < n_tip_vecs; ++v) {
+        int positive = 0;
+        for (int s = 0; s < m; ++s) {
+            const double x = tip_vecs[(size_t)v * m + s];
+            if (!(x >= 0.0) || !isfinite(x)) return ORC_INVALID;
+            if (x > 0.0) positive = 1;
+        }
+        if (!positive) return ORC_INVALID;
+    }
     tree_t t;
     int rc = tree_build(n_tips, parent, &t);
     if (rc != ORC_OK) return rc;
@@ -266,7 +280,8 @@ int orc_eval(int n_tips, int m, int n_patterns, int n_cat, int n_models,
         }
     }
 
-    /* post-order: tips are indicator vectors, internal nodes by the pruning update */
+    /* post-order: tips are their partial vectors (indicator, given, or all-ones), internal nodes
+     * by the pruning update */
     for (int o = n - 1; o >= 0; --o) {
         int k = t.order[o];
         for (int p = 0; p < P; ++p) {
@@ -274,7 +289,13 @@ int orc_eval(int n_tips, int m, int n_patterns, int n_cat, int n_models,
             if (k < n_tips) {
                 int y = tips[(size_t)k * P + p];
                 for (int l = 0; l < C; ++l)
-                    for (int s = 0; s < m; ++s) pk[l * m + s] = (y >= m || y == s) ? 1.0 : 0.0;
+                    for (int s = 0; s < m; ++s) {
+                        double v;
+                        if (y < m) v = (y == s) ? 1.0 : 0.0;
+                        else if (y < m + n_tip_vecs) v = tip_vecs[(size_t)(y - m) * m + s];
+                        else v = 1.0;
+                        pk[l * m + s] = v;
+                    }
                 pe[(size_t)k * P + p] = 0;
                 continue;
             }

@@ -167,9 +167,19 @@ def _dev_ptr(t):
     return t.data_ptr()
 
 
+def _check_tip_codes(problem: dict):
+    """The library's tips are one observed state or missing data (code >= m, the all-ones
+    vector).  A problem with a table of partial tip vectors would have its codes m, m+1, ... read
+    as missing data, so it is refused."""
+    tv = problem.get("tip_partials")
+    if tv is not None and len(tv):
+        raise NotImplementedError("partially observed tips (tip_partials) are not implemented by the library")
+
+
 def problem_struct(problem: dict, precision: str = "fp32"):
     """The pg_problem of a problem dict and the arrays it points into (keep both alive while the
     library may read them).  Tip rows may be a row-strided view (unit stride along patterns)."""
+    _check_tip_codes(problem)
     if precision not in PRECISIONS:
         raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
     parent = np.ascontiguousarray(problem["parent"], dtype=np.int32)
@@ -362,6 +372,7 @@ def eval_noalloc(problem: dict, b, precision: str = "fp32", grad=True, hess=Fals
     """pg_eval_noalloc: one blocking evaluation with host arrays that allocates no device or host
     heap memory inside the library (its scratch is a fixed per-GPU device array).  For callers that
     cannot allocate at evaluation time; calls must not overlap.  Returns a dict like Handle.eval."""
+    _check_tip_codes(problem)
     lib = load()
     parent = np.ascontiguousarray(problem["parent"], dtype=np.int32)
     tips = np.ascontiguousarray(problem["tip_states"], dtype=np.uint8)

@@ -284,6 +284,37 @@ def make_ambiguous(tips: np.ndarray, frac: float, n_states: int, rng):
     return out
 
 
+MISSING = 255   # a tip code past every row of a tip-partial table: missing data (all ones)
+
+
+def iupac_nucleotide_partials(error: float = 0.0) -> np.ndarray:
+    """Partial vectors of the ten IUPAC ambiguity codes that name 2 or 3 of the states (A, C, G,
+    T) = (0, 1, 2, 3): R, Y, S, W, K, M, B, D, H, V as 0/1 vectors.  With ``error`` > 0, four rows
+    follow for a base call with that error probability spread over the other three states."""
+    sets = ["AG", "CT", "CG", "AT", "GT", "AC", "CGT", "AGT", "ACT", "ACG"]
+    rows = [[1.0 if c in s else 0.0 for c in "ACGT"] for s in sets]
+    if error > 0:
+        rows += [[1.0 - error if j == y else error / 3 for j in range(4)] for y in range(4)]
+    return np.array(rows)
+
+
+def make_partially_observed(tips: np.ndarray, frac: float, table: np.ndarray, rng):
+    """Recode a fraction of the observed cells (code < m) as partial observations: code m + k
+    for a row k of ``table`` [K][m] drawn among the rows that allow the cell's state.  Cells that
+    were missing (code >= m) become ``MISSING``, past the table's codes."""
+    K, m = table.shape
+    if m + K > MISSING:
+        raise ValueError("the table leaves no code for missing data")
+    out = tips.copy()
+    out[tips >= m] = MISSING
+    allow = [np.flatnonzero(table[:, y] > 0) for y in range(m)]
+    for idx in zip(*np.nonzero((tips < m) & (rng.random(tips.shape) < frac))):
+        rows = allow[tips[idx]]
+        if rows.size:
+            out[idx] = m + rows[rng.integers(rows.size)]
+    return out
+
+
 # --------------------------------------------------------------------------------------------
 # problems
 # --------------------------------------------------------------------------------------------

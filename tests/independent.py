@@ -19,6 +19,17 @@ def _model(problem, i):
     return 0 if bm is None else int(bm[i])
 
 
+def tip_vectors(problem, m):
+    """V[256][m]: the tip partial vector of every code (Section 2.1): the indicator of state y for
+    y < m, row y - m of problem["tip_partials"] for the next K codes, all ones after them."""
+    V = np.ones((256, m))
+    V[:m] = np.eye(m)
+    tv = problem.get("tip_partials")
+    if tv is not None and len(tv):
+        V[m:m + len(tv)] = tv
+    return V
+
+
 def transition_matrices(problem, b):
     """P[i][l] = expm(Q_i b_i r_l) and dP[i][l] = r_l Q_i P[i][l] (d/db_i) via scipy."""
     n = problem["parent"].shape[0]
@@ -56,6 +67,7 @@ def brute_force(problem, b=None):
     L = np.zeros(n_pat)
     dL = np.zeros((n, n_pat))
     branches = [i for i in range(n) if i != root]
+    V = tip_vectors(problem, m)
     for assign in itertools.product(range(m), repeat=len(internal)):
         y = dict(zip(internal, assign))
         for l in range(len(cw)):
@@ -63,12 +75,9 @@ def brute_force(problem, b=None):
             dfactors = {}
             for i in branches:
                 a = y[int(parent[i])]
-                if i < N:
-                    t = tips[i]
-                    amb = t >= m
-                    tc = np.where(amb, 0, t)
-                    factors[i] = np.where(amb, P[i, l][a].sum(), P[i, l][a, tc])
-                    dfactors[i] = np.where(amb, dP[i, l][a].sum(), dP[i, l][a, tc])
+                if i < N:   # sum over the tip's state, weighted by its partial vector
+                    factors[i] = V[tips[i]] @ P[i, l][a]
+                    dfactors[i] = V[tips[i]] @ dP[i, l][a]
                 else:
                     factors[i] = np.full(n_pat, P[i, l][a, y[i]])
                     dfactors[i] = np.full(n_pat, dP[i, l][a, y[i]])
@@ -107,12 +116,11 @@ def prune(problem, P, replace=None):
             return replace[1][l]
         return P[i, l]
 
+    V = tip_vectors(problem, m)
+
     def vec(k):  # [C][m][P]
         if k < N:
-            v = np.zeros((C, m, n_pat))
-            for s in range(m):
-                v[:, s, :] = ((tips[k] == s) | (tips[k] >= m))[None, :]
-            return v
+            return np.repeat(V[tips[k]].T[None], C, axis=0)
         out = np.ones((C, m, n_pat))
         for c in kids[k]:
             vc = vec(c)

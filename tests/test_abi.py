@@ -57,3 +57,21 @@ def test_selftest_rejects_a_null_context(lib_path):
     lib.pg_selftest_timeout.argtypes = [ctypes.c_void_p, ctypes.c_uint64]
     lib.pg_selftest_timeout.restype = ctypes.c_int32
     assert lib.pg_selftest_timeout(None, 1_000_000) == 1   # PG_ERR_INVALID
+
+
+def test_binding_refuses_partially_observed_tips():
+    """Tip-partial tables are an oracle-only input for now: the binding refuses them rather than
+    letting the library read their codes as missing data."""
+    import numpy as np
+
+    from paper_1905_12146_gb300 import _native
+    from paper_1905_12146_gb300 import workloads as wl
+    pr = wl.random_problem(6, 20, seed=3)
+    _native.problem_struct(pr)   # plain codes marshal
+    table = wl.iupac_nucleotide_partials()
+    pr = dict(pr, tip_partials=table,
+              tip_states=wl.make_partially_observed(pr["tip_states"], 0.3, table, np.random.default_rng(0)))
+    with pytest.raises(NotImplementedError):
+        _native.problem_struct(pr)
+    with pytest.raises(NotImplementedError):
+        _native.eval_noalloc(pr, pr["b"])
