@@ -76,8 +76,15 @@ typedef struct pg_options {
  *   n_categories C: 1..4 discrete rate categories (Section 2.5).
  *   parent[2N-1]           parent node of each node, -1 for the root; every internal node must
  *                          have exactly two children (binary tree, Section 2.1).
- *   tip_states[N][P]       observed state of tip t at pattern p; a code >= m means missing or
- *                          fully ambiguous, i.e. the all-ones partial vector (Section 2.1).
+ *   tip_states[N][P]       code of tip t at pattern p, selecting the tip's partial vector
+ *                          (Section 2.1): a code y < m is the observed state y (the indicator
+ *                          vector); m <= y < m + K selects row y - m of tip_partials (partially
+ *                          observed data); a larger code is missing data (the all-ones vector).
+ *   n_tip_partials K, tip_partials[K][m]
+ *                          partial vectors of partially observed tips, e.g. the sets of an
+ *                          ambiguity code or base-call likelihoods: finite, >= 0, each row with a
+ *                          positive entry; K >= 0 with m + K <= 256 (K = 0: tip_partials unused).
+ *                          A 4-state problem with K > 0 runs on the general path (FP32 only).
  *   pattern_weights[P]     multiplicity of each site pattern, finite and >= 0.
  *   Q[n_models][m][m]      CTMC generators: off-diagonals >= 0, rows summing to 0 (|row sum| <=
  *                          1e-10 * max|Q|); neither reversibility nor stationarity is required.
@@ -103,6 +110,8 @@ typedef struct pg_problem {
     const double *cat_rates;
     const double *cat_weights;
     int32_t tip_stride;         /* row pitch of tip_states in bytes (>= n_patterns); 0 = n_patterns */
+    int32_t n_tip_partials;     /* K: rows of tip_partials (0 = none)                              */
+    const double *tip_partials; /* [K][m]                                                          */
 } pg_problem;
 
 typedef struct pg_handle_info {
@@ -124,8 +133,8 @@ pg_status pg_destroy(pg_ctx *ctx);
 
 /* Validate a problem and copy it to the device (tree levels, tip codes, weights, Q, pi, rates),
  * allocating the partial-likelihood buffers it needs.  Errors: PG_ERR_INVALID (the problem breaks
- * a rule above), PG_ERR_UNSUPPORTED (m > 64, FP64 with m != 4, C > 4, or more than 2^30 nodes),
- * PG_ERR_OOM (allocation or budget). */
+ * a rule above), PG_ERR_UNSUPPORTED (m > 64, FP64 with m != 4 or with K > 0, C > 4, or more than
+ * 2^30 nodes), PG_ERR_OOM (allocation or budget). */
 pg_status pg_upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out);
 
 /* Release a handle's device memory. */
@@ -277,7 +286,8 @@ pg_status pg_get_info(const pg_handle *h, pg_handle_info *out);
  * before any stream capture.  All calls share the array and the static buffers: calls that
  * overlap, on the GPU or from several host threads, race and must be serialised by the caller.
  * Errors: PG_ERR_UNSUPPORTED when the problem needs more scratch than PG_NOALLOC_SCRATCH_BYTES, has
- * more than 8192 tips or 64 models, or m != 4 or C > 4; otherwise as pg_upload and pg_eval. */
+ * more than 8192 tips or 64 models, m != 4, C > 4 or tip partial vectors (K > 0); otherwise as
+ * pg_upload and pg_eval. */
 pg_status pg_eval_noalloc(const pg_problem *pr, const double *b, double *logL, double *grad,
                           double *hess, double *site_logL, void *stream);
 

@@ -49,7 +49,8 @@ class pg_problem(ctypes.Structure):
                 ("pattern_weights", ctypes.c_void_p), ("Q", ctypes.c_void_p),
                 ("branch_model", ctypes.c_void_p), ("root_freqs", ctypes.c_void_p),
                 ("cat_rates", ctypes.c_void_p), ("cat_weights", ctypes.c_void_p),
-                ("tip_stride", ctypes.c_int32)]
+                ("tip_stride", ctypes.c_int32), ("n_tip_partials", ctypes.c_int32),
+                ("tip_partials", ctypes.c_void_p)]
 
 
 class pg_server_options(ctypes.Structure):
@@ -167,19 +168,20 @@ def _dev_ptr(t):
     return t.data_ptr()
 
 
-def _check_tip_codes(problem: dict):
-    """The library's tips are one observed state or missing data (code >= m, the all-ones
-    vector).  A problem with a table of partial tip vectors would have its codes m, m+1, ... read
-    as missing data, so it is refused."""
+def _tip_partials(problem: dict):
+    """(K, [K][m] FP64 array or None) of the problem's optional tip partial vectors."""
     tv = problem.get("tip_partials")
-    if tv is not None and len(tv):
-        raise NotImplementedError("partially observed tips (tip_partials) are not implemented by the library")
+    if tv is None or len(tv) == 0:
+        return 0, None
+    tv = np.ascontiguousarray(tv, dtype=np.float64)
+    if tv.ndim != 2:
+        raise ValueError("tip_partials must be [K][n_states]")
+    return tv.shape[0], tv
 
 
 def problem_struct(problem: dict, precision: str = "fp32"):
     """The pg_problem of a problem dict and the arrays it points into (keep both alive while the
     library may read them).  Tip rows may be a row-strided view (unit stride along patterns)."""
-    _check_tip_codes(problem)
     if precision not in PRECISIONS:
         raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
     parent = np.ascontiguousarray(problem["parent"], dtype=np.int32)
@@ -198,10 +200,11 @@ def problem_struct(problem: dict, precision: str = "fp32"):
     cw = np.ascontiguousarray(problem["cat_weights"], dtype=np.float64)
     n = parent.shape[0]
     P = tips.shape[1] if tips.ndim == 2 else 0
+    K, tv = _tip_partials(problem)
     pr = pg_problem((n + 1) // 2, Q.shape[1], P, rates.shape[0], Q.shape[0], PRECISIONS[precision],
                     _np_ptr(parent), _np_ptr(tips), _np_ptr(w), _np_ptr(Q), _np_ptr(bm), _np_ptr(pi),
-                    _np_ptr(rates), _np_ptr(cw), stride if stride != P else 0)
-    return pr, (parent, tips, w, Q, bm, pi, rates, cw)
+                    _np_ptr(rates), _np_ptr(cw), stride if stride != P else 0, K, _np_ptr(tv))
+    return pr, (parent, tips, w, Q, bm, pi, rates, cw, tv)
 
 
 class Context:
@@ -372,7 +375,6 @@ def eval_noalloc(problem: dict, b, precision: str = "fp32", grad=True, hess=Fals
     """pg_eval_noalloc: one blocking evaluation with host arrays that allocates no device or host
     heap memory inside the library (its scratch is a fixed per-GPU device array).  For callers that
     cannot allocate at evaluation time; calls must not overlap.  Returns a dict like Handle.eval."""
-    _check_tip_codes(problem)
     lib = load()
     parent = np.ascontiguousarray(problem["parent"], dtype=np.int32)
     tips = np.ascontiguousarray(problem["tip_states"], dtype=np.uint8)
@@ -387,9 +389,10 @@ def eval_noalloc(problem: dict, b, precision: str = "fp32", grad=True, hess=Fals
     cw = np.ascontiguousarray(problem["cat_weights"], dtype=np.float64)
     n = parent.shape[0]
     P = tips.shape[1] if tips.ndim == 2 else 0
+    K, tv = _tip_partials(problem)
     pr = pg_problem((n + 1) // 2, Q.shape[1], P, rates.shape[0], Q.shape[0], PRECISIONS[precision],
                     _np_ptr(parent), _np_ptr(tips), _np_ptr(w), _np_ptr(Q), _np_ptr(bm),
-                    _np_ptr(pi), _np_ptr(rates), _np_ptr(cw))
+                    _np_ptr(pi), _np_ptr(rates), _np_ptr(cw), 0, K, _np_ptr(tv))
     b = np.ascontiguousarray(b, dtype=np.float64)
     logL = np.zeros(1)
     g = np.zeros(n) if grad else None

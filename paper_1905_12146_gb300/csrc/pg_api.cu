@@ -169,6 +169,19 @@ pg_status check_model(const pg_problem *pr) {
         s += pr->cat_weights[l];
     }
     if (std::fabs(s - 1.0) > 1e-10) return fail(PG_ERR_INVALID, "cat_weights sum to %.17g, not 1", s);
+    const int K = pr->n_tip_partials;
+    if (K < 0 || m + K > 256) return fail(PG_ERR_INVALID, "n_tip_partials = %d (0 .. %d)", K, 256 - m);
+    if (K > 0 && !pr->tip_partials) return fail(PG_ERR_INVALID, "tip_partials is NULL");
+    for (int v = 0; v < K; ++v) {
+        bool positive = false;
+        for (int i = 0; i < m; ++i) {
+            const double x = pr->tip_partials[(size_t)v * m + i];
+            if (!(x >= 0.0) || !std::isfinite(x))
+                return fail(PG_ERR_INVALID, "tip_partials[%d][%d] is negative or not finite", v, i);
+            positive = positive || x > 0.0;
+        }
+        if (!positive) return fail(PG_ERR_INVALID, "tip_partials[%d] has no positive entry", v);
+    }
     const int n = 2 * pr->n_tips - 1;
     if (pr->branch_model)
         for (int i = 0; i < n; ++i)
@@ -315,7 +328,8 @@ pg_status encode_map(CUtensorMap *m, void *base, int rank, const cuuint64_t *dim
     return PG_OK;
 }
 
-// upload of a problem with 5..64 states (pg_mstate.cu kernels)
+// upload of a problem on the general path (pg_mstate.cu, pg_mtc.cu, pg_mcherry.cu kernels): any
+// state count but 4, and 4-state problems with tip partial vectors
 pg_status upload_m(pg_ctx *ctx, const pg_problem *pr, const TreePlan &tp, pg_handle **out, const Placement *pl) {
     const int N = pr->n_tips, m = pr->n_states, P = pr->n_patterns, C = pr->n_categories, M = pr->n_models;
     const int n = 2 * N - 1, H = (int)tp.level_off.size() - 1;
@@ -330,6 +344,11 @@ pg_status upload_m(pg_ctx *ctx, const pg_problem *pr, const TreePlan &tp, pg_han
     Carver cv;
     const size_t o_ops = cv.take<int4>(N - 1), o_lv = cv.take<int>(H + 1);
     const size_t o_tips = cv.take<uint8_t>((size_t)N * Ps), o_w = cv.take<double>(Ps);
+    const int K = pr->n_tip_partials;
+    std::vector<float> tipv((size_t)std::max(K, 1) * KP, 0.f);   // FP32 rows, pads 0
+    for (int v = 0; v < K; ++v)
+        for (int i = 0; i < m; ++i) tipv[(size_t)v * KP + i] = (float)pr->tip_partials[(size_t)v * m + i];
+    const size_t o_tv = cv.take<float>(tipv.size());
     const size_t o_Bp = cv.take<float>(Bpow.size()), o_QT = cv.take<float>(QT.size());
     const size_t o_mu = cv.take<double>(mu.size());
     const size_t o_bm = pr->branch_model ? cv.take<int>(n) : 0;
@@ -370,6 +389,7 @@ pg_status upload_m(pg_ctx *ctx, const pg_problem *pr, const TreePlan &tp, pg_han
     if (e == cudaSuccess && P > 0)
         e = h2d_rows(pl, base + o_tips, Ps, pr->tip_states, pr->tip_stride ? pr->tip_stride : P, P, N);
     if (e == cudaSuccess && P > 0) e = cp(o_w, pr->pattern_weights, sizeof(double) * P);
+    if (e == cudaSuccess) e = cp(o_tv, tipv.data(), sizeof(float) * tipv.size());
     if (e == cudaSuccess) e = cp(o_Bp, Bpow.data(), sizeof(float) * Bpow.size());
     if (e == cudaSuccess) e = cp(o_QT, QT.data(), sizeof(float) * QT.size());
     if (e == cudaSuccess) e = cp(o_mu, mu.data(), sizeof(double) * mu.size());
@@ -386,6 +406,8 @@ pg_status upload_m(pg_ctx *ctx, const pg_problem *pr, const TreePlan &tp, pg_han
     d.ops = reinterpret_cast<const int4 *>(base + o_ops);
     d.level_off = reinterpret_cast<const int *>(base + o_lv);
     d.tips = reinterpret_cast<const uint8_t *>(base + o_tips);
+    d.tipv = reinterpret_cast<const float *>(base + o_tv);
+    d.n_tv = K;
     d.weights = reinterpret_cast<const double *>(base + o_w);
     d.Bpow = reinterpret_cast<const float *>(base + o_Bp);
     d.QT = reinterpret_cast<const float *>(base + o_QT);
@@ -617,6 +639,8 @@ pg_status pg::host::upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out, c
     if (m > pg::kMP) return fail(PG_ERR_UNSUPPORTED, "n_states = %d: at most %d", m, pg::kMP);
     if (m != pg::kStates && f64)
         return fail(PG_ERR_UNSUPPORTED, "FP64 partials are implemented for 4 states only");
+    if (pr->n_tip_partials > 0 && f64)
+        return fail(PG_ERR_UNSUPPORTED, "FP64 partials are implemented without tip partial vectors only");
     if (C > pg::kMaxCat) return fail(PG_ERR_UNSUPPORTED, "n_categories = %d: at most %d", C, pg::kMaxCat);
     if (!pr->parent) return fail(PG_ERR_INVALID, "parent is NULL");
     if (P > 0 && (!pr->tip_states || !pr->pattern_weights))
@@ -629,7 +653,9 @@ pg_status pg::host::upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out, c
     if (st != PG_OK) return st;
     st = check_model(pr);
     if (st != PG_OK) return st;
-    if (m != pg::kStates) return upload_m(ctx, pr, tp, out, pl);
+    // the 4-state kernels take state codes and missing data only; tip partial vectors run on the
+    // general path
+    if (m != pg::kStates || pr->n_tip_partials > 0) return upload_m(ctx, pr, tp, out, pl);
 
     const int n = 2 * N - 1;
     const int H = (int)tp.level_off.size() - 1;

@@ -154,7 +154,10 @@ constexpr int kMRootPatterns = 16;   // patterns per block of the general-state 
 struct MDesc {
     const int4 *ops;
     const int *level_off;
-    const uint8_t *tips;           // [N][Ps] codes; >= m is the all-ones (missing/ambiguous) code
+    const uint8_t *tips;           // [N][Ps] codes: < m a state, m .. m + n_tv - 1 a row of tipv,
+                                   // larger the all-ones (missing) code
+    const float *tipv;             // [n_tv][kMP] partial vectors of partially observed tips, pads 0
+    int n_tv;
     const double *weights;         // [P]
     const double *b;               // [n] branch lengths of this evaluation
     const float *Bpow;             // [n_models][kUnifK][kMP][kMP]: B^k (k = 1 ..), FP32, pads 0

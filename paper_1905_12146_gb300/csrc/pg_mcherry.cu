@@ -2,7 +2,8 @@
 // both tips.  A tip's state vector x is one-hot (or all-ones over the m states for an ambiguous
 // code), so P x is a column of P = I + D and G x a column of G: the post-order product (Section 2.3)
 // and the pre-order branch terms (Sections 2.4-2.5) are table lookups, done here in FP32 without
-// the tensor core.  The tables of one (node, category) are copied into shared memory once as
+// the tensor core.  The rare partially observed tip (a row of the problem's tip-vector table)
+// takes the sum of the columns weighted by its vector.  The tables of one (node, category) are copied into shared memory once as
 // column tables, with the row sums (the all-ones case) as an extra column, and a block then walks a
 // chunk of patterns: 16 lanes per pattern, 4 states per lane.
 #include <cuda_runtime.h>
@@ -49,8 +50,35 @@ __device__ void row_sums(float *Cb, int s) {   // one thread per state, fixed or
     Cb[kMP * kS + s] = a;
 }
 
-// column y of P = I + D (or P 1 for an ambiguous code) at this lane's states 4 j .. 4 j + 3
-__device__ __forceinline__ void p_column(const float *Dc, int y, int m, int j, float a[4]) {
+// W v at this lane's states 4 j .. 4 j + 3 for the partial vector v of a partially observed tip
+// (row y - m of d.tipv): the columns of W weighted by v, in state order
+__device__ __forceinline__ float4 weighted_columns(const float *Wc, const MDesc &d, int y, int j) {
+    const float *v = d.tipv + (size_t)(y - d.m) * kMP;
+    float4 a = f4(0.f, 0.f, 0.f, 0.f);
+    for (int k = 0; k < d.m; ++k) {
+        const float vk = __ldg(v + k);
+        if (vk == 0.f) continue;
+        const float4 c = *reinterpret_cast<const float4 *>(Wc + k * kS + 4 * j);
+        a = f4(fmaf(vk, c.x, a.x), fmaf(vk, c.y, a.y), fmaf(vk, c.z, a.z), fmaf(vk, c.w, a.w));
+    }
+    return a;
+}
+
+// P x = x + D x at this lane's states 4 j .. 4 j + 3 for the tip vector x of code y: column y of P
+// for a state, P 1 (the row sums) for missing data, x + D x for a partially observed tip (TV: the
+// problem has tip vectors)
+template <bool TV>
+__device__ __forceinline__ void p_column(const float *Dc, int y, const MDesc &d, int j, float a[4]) {
+    const int m = d.m;
+    if (TV && y >= m && y < m + d.n_tv) {
+        const float4 dv = weighted_columns(Dc, d, y, j);
+        const float4 x = __ldg(reinterpret_cast<const float4 *>(d.tipv + (size_t)(y - m) * kMP) + j);
+        a[0] = x.x + dv.x;
+        a[1] = x.y + dv.y;
+        a[2] = x.z + dv.z;
+        a[3] = x.w + dv.w;
+        return;
+    }
     const bool amb = y >= m;
     const float4 v = *reinterpret_cast<const float4 *>(Dc + (amb ? kMP : y) * kS + 4 * j);
     const float dv[4] = {v.x, v.y, v.z, v.w};
@@ -60,8 +88,10 @@ __device__ __forceinline__ void p_column(const float *Dc, int y, int m, int j, f
         a[i] = (amb ? (s < m ? 1.f : 0.f) : (s == y ? 1.f : 0.f)) + dv[i];
     }
 }
-__device__ __forceinline__ void g_column(const float *Gc, int y, int m, int j, float u[4]) {
-    const float4 v = *reinterpret_cast<const float4 *>(Gc + (y >= m ? kMP : y) * kS + 4 * j);
+template <bool TV>
+__device__ __forceinline__ void g_column(const float *Gc, int y, const MDesc &d, int j, float u[4]) {
+    const float4 v = (TV && y >= d.m && y < d.m + d.n_tv) ? weighted_columns(Gc, d, y, j)
+                                                          : *reinterpret_cast<const float4 *>(Gc + (y >= d.m ? kMP : y) * kS + 4 * j);
     u[0] = v.x;
     u[1] = v.y;
     u[2] = v.z;
@@ -85,6 +115,7 @@ __device__ __forceinline__ float max16(float v) {
 // result of pattern r.
 
 // ---- post-order: p_k = (P_0 x_0) o (P_1 x_1), scaled by its largest state -------------------------
+template <bool TV>
 __global__ void __launch_bounds__(kChThreads) m_post_cherry_kernel(const __grid_constant__ MDesc d, int o0, int n_ch) {
     extern __shared__ float chs[];
     float *D0 = chs, *D1 = chs + kColFloats;
@@ -112,8 +143,8 @@ __global__ void __launch_bounds__(kChThreads) m_post_cherry_kernel(const __grid_
         for (int r = 0; r < 16; ++r) {
             const int y0 = __shfl_sync(0xffffffffu, y0l, r, 16), y1 = __shfl_sync(0xffffffffu, y1l, r, 16);
             float a0[4], a1[4], v[4];
-            p_column(D0, y0, d.m, j, a0);
-            p_column(D1, y1, d.m, j, a1);
+            p_column<TV>(D0, y0, d, j, a0);
+            p_column<TV>(D1, y1, d, j, a1);
             float mx = 0.f;
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
@@ -132,6 +163,7 @@ __global__ void __launch_bounds__(kChThreads) m_post_cherry_kernel(const __grid_
 // ---- pre-order branch terms of both children: qt_c . (G_c x_c) 2^{E} / L_p per category ---------------
 // qt_0 = q_k o P_1 x_1, qt_1 = q_k o P_0 x_0 (q_root = pi); the block's weighted sum for category l
 // and chunk ci goes to gradient slot l * n_pt + ci of each child (slots ci >= n_ch are zeroed).
+template <bool TV>
 __global__ void __launch_bounds__(kChThreads) m_pre_cherry_kernel(const __grid_constant__ MDesc d, int o0, int n_ch,
                                                                    int n_pt) {
     extern __shared__ float chs[];
@@ -182,10 +214,10 @@ __global__ void __launch_bounds__(kChThreads) m_pre_cherry_kernel(const __grid_c
                 const int rr = 8 * h + r;
                 const int y0 = __shfl_sync(0xffffffffu, y0l, rr, 16), y1 = __shfl_sync(0xffffffffu, y1l, rr, 16);
                 float a0[4], a1[4], u0[4], u1[4];
-                p_column(D0, y0, d.m, j, a0);
-                p_column(D1, y1, d.m, j, a1);
-                g_column(G0, y0, d.m, j, u0);
-                g_column(G1, y1, d.m, j, u1);
+                p_column<TV>(D0, y0, d, j, a0);
+                p_column<TV>(D1, y1, d, j, a1);
+                g_column<TV>(G0, y0, d, j, u0);
+                g_column<TV>(G1, y1, d, j, u1);
                 const float q[4] = {qv[r].x, qv[r].y, qv[r].z, qv[r].w};
                 float dot0 = 0.f, dot1 = 0.f;
 #pragma unroll
@@ -225,26 +257,35 @@ __global__ void __launch_bounds__(kChThreads) m_pre_cherry_kernel(const __grid_c
 constexpr size_t kPostChSmem = 2 * kColFloats * sizeof(float);
 constexpr size_t kPreChSmem = 4 * kColFloats * sizeof(float);
 
+template <bool TV>
+cudaError_t launch_pre_cherry(const MDesc &d, int o0, int nd, int n_ch, int n_pt, cudaStream_t s) {
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(m_pre_cherry_kernel<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kPreChSmem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    m_pre_cherry_kernel<TV><<<nd * d.C * n_ch, kChThreads, kPreChSmem, s>>>(d, o0, n_ch, n_pt);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
+// problems with tip vectors take the instantiations that look them up; the others keep the plain
+// state and missing-data lookups
 cudaError_t launch_m_post_cherry(const MDesc &d, int o0, int nd, cudaStream_t s) {
     const int n_ch = (d.P + kChChunk - 1) / kChChunk;
     if (nd <= 0 || n_ch <= 0) return cudaSuccess;
-    m_post_cherry_kernel<<<nd * d.C * n_ch, kChThreads, kPostChSmem, s>>>(d, o0, n_ch);
+    if (d.n_tv > 0) m_post_cherry_kernel<true><<<nd * d.C * n_ch, kChThreads, kPostChSmem, s>>>(d, o0, n_ch);
+    else m_post_cherry_kernel<false><<<nd * d.C * n_ch, kChThreads, kPostChSmem, s>>>(d, o0, n_ch);
     return cudaGetLastError();
 }
 
 cudaError_t launch_m_pre_cherry(const MDesc &d, int o0, int nd, cudaStream_t s) {
     const int n_ch = (d.P + kChChunk - 1) / kChChunk, n_pt = (d.P + kTcTile - 1) / kTcTile;
     if (nd <= 0 || n_ch <= 0) return cudaSuccess;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(m_pre_cherry_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPreChSmem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    m_pre_cherry_kernel<<<nd * d.C * n_ch, kChThreads, kPreChSmem, s>>>(d, o0, n_ch, n_pt);
-    return cudaGetLastError();
+    return d.n_tv > 0 ? launch_pre_cherry<true>(d, o0, nd, n_ch, n_pt, s) : launch_pre_cherry<false>(d, o0, nd, n_ch, n_pt, s);
 }
 
 }  // namespace pg

@@ -84,11 +84,29 @@ __device__ __forceinline__ void add_tile(const float *X, int tp, int ts, float y
     }
 }
 
-// a tip child: y[i][.] = column code_i of the table (+1 on the diagonal for P = I + D), or the
-// table's ambiguous-code row (row sums) for codes >= m
-__device__ __forceinline__ void tip_tile(const float *T, const int code[4], int m, int ts, bool ident, float y[4][4]) {
+// a tip child: y[i][.] = column code_i of the table (+1 on the diagonal for P = I + D), the
+// table's ambiguous-code row (row sums) for missing data, or for a partially observed tip (a row v
+// of d.tipv) the columns weighted by v (+ v for P = I + D)
+__device__ __forceinline__ void tip_tile(const float *T, const int code[4], const MDesc &d, int ts, bool ident,
+                                         float y[4][4]) {
+    const int m = d.m;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
+        if (code[i] >= m && code[i] < m + d.n_tv) {
+            const float *v = d.tipv + (size_t)(code[i] - m) * kMP;
+            float4 a = ident ? __ldg(reinterpret_cast<const float4 *>(v) + ts) : f4(0.f, 0.f, 0.f, 0.f);
+            for (int k = 0; k < m; ++k) {
+                const float vk = __ldg(v + k);
+                if (vk == 0.f) continue;
+                const float4 c = *reinterpret_cast<const float4 *>(T + k * kMP + 4 * ts);
+                a = f4(fmaf(vk, c.x, a.x), fmaf(vk, c.y, a.y), fmaf(vk, c.z, a.z), fmaf(vk, c.w, a.w));
+            }
+            y[i][0] = a.x;
+            y[i][1] = a.y;
+            y[i][2] = a.z;
+            y[i][3] = a.w;
+            continue;
+        }
         const int r = code[i] < m ? code[i] : kMP;
         const float4 a = *reinterpret_cast<const float4 *>(T + r * kMP + 4 * ts);
         y[i][0] = a.x;
@@ -362,7 +380,7 @@ __global__ void __launch_bounds__(kMThreads) m_post_kernel(const __grid_constant
             } else {
                 int code[4];
                 tip_codes(d, c, p0, cnt, tp, code);
-                tip_tile(T, code, d.m, ts, true, y);
+                tip_tile(T, code, d, ts, true, y);
             }
 #pragma unroll
             for (int i = 0; i < 4; ++i)
@@ -476,7 +494,7 @@ __global__ void __launch_bounds__(kMThreads) m_pre_kernel(const __grid_constant_
                 gemm_tile(T, Xs[side], tp, ts, a[side]);
                 add_tile(Xs[side], tp, ts, a[side]);
             } else {
-                tip_tile(T, code[side], d.m, ts, true, a[side]);
+                tip_tile(T, code[side], d, ts, true, a[side]);
             }
         }
 #pragma unroll
@@ -498,7 +516,7 @@ __global__ void __launch_bounds__(kMThreads) m_pre_kernel(const __grid_constant_
                 __syncthreads();
                 float uu[4][4];
                 if (c >= N) gemm_tile(T, Xs[side], tp, ts, uu);
-                else tip_tile(T, code[side], d.m, ts, false, uu);
+                else tip_tile(T, code[side], d, ts, false, uu);
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     float t = qt[i][0] * uu[i][0];

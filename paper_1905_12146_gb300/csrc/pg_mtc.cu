@@ -11,8 +11,9 @@
 // maxima and sums through shared memory.
 //
 // Operand tiles [128 x 64] FP32 and tables [64 x 64] arrive by TMA with 128-byte swizzling (the
-// canonical K-major layout).  A tip child's rows are written as one-hot (or all-ones) rows, so tips
-// and internal children share the product.
+// canonical K-major layout).  A tip child's rows are written by the threads as the tips' partial
+// vectors (one-hot, all-ones, or a partially observed tip's row), so tips and internal children
+// share the product.
 //
 // Each product runs three TF32 passes, hi x hi + hi x lo + lo x hi.  The tensor core truncates an
 // FP32 operand to its TF32 part (hi); lo = x - trunc(x) is formed by the threads for the rows
@@ -143,7 +144,19 @@ __device__ __forceinline__ unsigned char *align1024(unsigned char *p) {
     return reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(p) + 1023) & ~(uintptr_t)1023);
 }
 
-// one-hot (or, for a code >= m, all-ones over the m states) row t of a tip child, zero past cnt
+// state s of the partial vector of tip code y (Section 2.1): the indicator of state y, the row of a
+// partially observed tip, or all ones over the m states (missing data); 0 for y < 0 (no pattern)
+__device__ __forceinline__ float tip_value(const MDesc &d, int y, int s) {
+    if (y < 0) return 0.f;
+    if (y < d.m) return s == y ? 1.f : 0.f;
+    if (y < d.m + d.n_tv) return __ldg(d.tipv + (size_t)(y - d.m) * kMP + s);
+    return s < d.m ? 1.f : 0.f;
+}
+
+// the partial vector of the tip code of row t of a tip child, zero past cnt.  Indicator and
+// all-ones rows are exact in TF32; rows of partially observed tips (TV: the problem has tip
+// vectors) need the remainder pass.
+template <bool TV>
 __device__ __forceinline__ void tip_row(unsigned char *X, const MDesc &d, int c, int p0, int cnt, int t) {
     const int y = t < cnt ? (int)__ldg(d.tips + (size_t)c * d.Ps + p0 + t) : -1;
     const bool amb = y >= d.m;
@@ -153,7 +166,8 @@ __device__ __forceinline__ void tip_row(unsigned char *X, const MDesc &d, int c,
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int s = 4 * cc + j;
-            v[j] = (y >= 0 && (amb ? s < d.m : s == y)) ? 1.f : 0.f;
+            if constexpr (TV) v[j] = tip_value(d, y, s);
+            else v[j] = (y >= 0 && (amb ? s < d.m : s == y)) ? 1.f : 0.f;
         }
         *reinterpret_cast<float4 *>(X + sw(t, cc, kTcTile)) = f4(v[0], v[1], v[2], v[3]);
     }
@@ -233,10 +247,11 @@ __device__ __forceinline__ int store_sum_scaled(uint32_t ta, const unsigned char
 }
 
 // ---- post-order level: item = (node, category, 128-pattern tile), three blocks per SM ----------------------
-// Per child: its D hi | D lo tables and rows (or one-hot tip rows) into shared memory, the rows'
+// Per child: its D hi | D lo tables and rows (or tip rows) into shared memory, the rows'
 // TF32 remainders into tensor memory (columns 64 .. 127), D x into columns 0 .. 63 by three passes;
 // the first child's x + D x is kept in registers.  The result is scaled by its largest state,
 // written over the rows and stored by TMA.  64 KB of shared memory and 128 TMEM columns per block.
+template <bool TV>
 __global__ void __launch_bounds__(kTcThreads, 3)
 m_post_tc_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtensorMap tm_post,
                  const __grid_constant__ CUtensorMap tm_tab, int o0, int n_pt) {
@@ -273,13 +288,15 @@ m_post_tc_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
             if (!tip)
                 for (int kb = 0; kb < 2; ++kb) tma_load_3d(XA + kb * kRowKB, &tm_post, kb * 32, p0, (c - N) * C + l, &bar[0]);
         }
-        if (tip) tip_row(XA, d, c, p0, cnt, t);   // exact one-hot rows: no remainder pass
+        // TF32 remainders: of internal rows, and of tip rows when some tip vectors are not exact
+        const bool lo_pass = !tip || TV;
+        if (tip) tip_row<TV>(XA, d, c, p0, cnt, t);
         else if (t < cnt) E += __ldcg(d.pe + ((size_t)(c - N) * C + l) * d.Ps + p0 + t);
         load_pending = true;
         ok = wait_all(&bar[0], ph_load);
         load_pending = !ok;
         if (!ok) break;
-        if (!tip) {
+        if (lo_pass) {
 #pragma unroll
             for (int ch = 0; ch < 4; ++ch) {
                 float x[16];
@@ -297,7 +314,7 @@ m_post_tc_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
             tc_after();
             mma_tile(tmem, smem_u32(XA), smem_u32(TB), kMP, false);
             mma_tile(tmem, smem_u32(XA), smem_u32(TB + kTab), kMP, true);
-            if (!tip) mma_tile_ta(tmem, tmem + 64, smem_u32(TB), kMP, true);
+            if (lo_pass) mma_tile_ta(tmem, tmem + 64, smem_u32(TB), kMP, true);
             mma_commit(&bar[1]);
         }
         mma_pending = true;
@@ -359,7 +376,7 @@ m_post_tc_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
 // optionally H_c x_c (columns 256 + 64 side); qt_c = q_k o a_other (q_root = pi), the branch terms
 // qt_c . u_c (and qt_c . H_c x_c) 2^{E} / L_p; for an internal child q_c = P_c^T qt_c (columns
 // 128 side .. +63 again: D_c^T qt_c, plus qt_c) scaled and stored.
-template <bool HESS>
+template <bool HESS, bool TV>
 __global__ void __launch_bounds__(kTcThreads, 1)
 m_pre_tc_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtensorMap tm_post,
                 const __grid_constant__ CUtensorMap tm_pre, const __grid_constant__ CUtensorMap tm_tab, int o0, int n_pt) {
@@ -415,13 +432,13 @@ m_pre_tc_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtenso
             load_tables(TB + 2 * kTab, &tm_tab, d, cs[0], l, kTcDlo, 2, &bar[0]);
         }
         for (int side = 0; side < 2; ++side)
-            if (tip[side]) tip_row(X[side], d, cs[side], p0, cnt, t);
+            if (tip[side]) tip_row<TV>(X[side], d, cs[side], p0, cnt, t);
         load_pending = true;
         ok = wait_all(&bar[0], ph_load);
         load_pending = !ok;
         if (!ok) break;
         for (int side = 0; side < 2; ++side)
-            if (!tip[side]) lo_row(X[side], X[side] + kRowTile, t);
+            if (!tip[side] || TV) lo_row(X[side], X[side] + kRowTile, t);
         fence_async_smem();
         // the products of both children: [P; G] (then H) tables of child `side`
         for (int side = 0; side < 2 && ok; ++side) {
@@ -452,7 +469,7 @@ m_pre_tc_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtenso
                     const uint32_t tl = tb + n * kMP * 4;
                     mma_tile(acc, xa, tb, n, false);
                     mma_tile(acc, xa, tl, n, true);
-                    if (!tip[side]) mma_tile(acc, xl, tb, n, true);
+                    if (!tip[side] || TV) mma_tile(acc, xl, tb, n, true);
                     mma_commit(&bar[1]);
                 }
                 mma_pending = true;
@@ -618,8 +635,9 @@ m_pre_tc_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtenso
 // products with both children's [D; G] tables, the epilogue forms qt_c = q_k o (x_other +
 // D_other x_other) and the branch terms and writes qt_c (and remainder) over x_c in tensor memory,
 // the D_c^T tables arrive meanwhile, the products D_c^T qt_c (columns 128 c .. +63 again) give
-// q_c = qt_c + D_c^T qt_c, stored straight from registers.  Tip children's one-hot rows are
-// written into tensor memory by the threads.
+// q_c = qt_c + D_c^T qt_c, stored straight from registers.  Tip children's rows (their partial
+// vectors) are written into tensor memory by the threads.
+template <bool TV>
 __global__ void __launch_bounds__(2 * kTcThreads, 1)
 m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtensorMap tm_post,
                  const __grid_constant__ CUtensorMap tm_pre, const __grid_constant__ CUtensorMap tm_tab, int o0, int n_pt,
@@ -717,17 +735,30 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
         if (any_int && !wait(BX)) break;
         for (int side = 0; side < 2; ++side) {
             const uint32_t xc = lane_base + 256 + 128 * side;
-            if (tip[side]) {   // one-hot (all-ones for a code >= m) rows
+            if (tip[side]) {   // the tips' partial vectors
                 const int y = on ? (int)__ldg(d.tips + (size_t)cs[side] * d.Ps + p0 + t) : -1;
+                if constexpr (!TV) {   // one-hot or all-ones rows: exact in TF32, no remainders
 #pragma unroll
-                for (int ch = ch0; ch < ch0 + 2; ++ch) {
-                    float x[16];
+                    for (int ch = ch0; ch < ch0 + 2; ++ch) {
+                        float x[16];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int st = 16 * ch + j;
-                        x[j] = (y >= 0 && (y >= d.m ? st < d.m : st == y)) ? 1.f : 0.f;
+                        for (int j = 0; j < 16; ++j) {
+                            const int st = 16 * ch + j;
+                            x[j] = (y >= 0 && (y >= d.m ? st < d.m : st == y)) ? 1.f : 0.f;
+                        }
+                        tmem_st16(xc + ch * 16, x);
                     }
-                    tmem_st16(xc + ch * 16, x);
+                } else {   // rows of partially observed tips may not be: remainders too
+#pragma unroll 1
+                    for (int ch = ch0; ch < ch0 + 2; ++ch) {
+                        float x[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) x[j] = tip_value(d, y, 16 * ch + j);
+                        tmem_st16(xc + ch * 16, x);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) x[j] = tf32_lo(x[j]);
+                        tmem_st16(xc + 64 + ch * 16, x);
+                    }
                 }
                 continue;
             }
@@ -752,7 +783,7 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
             for (int side = 0; side < 2; ++side) {
                 const uint32_t acc = tmem + 128 * side, xa = tmem + 256 + 128 * side, tb = smem_u32(T[side]);
                 mma_tile_ta(acc, xa, tb, 2 * kMP, false);
-                if (!tip[side]) mma_tile_ta(acc, xa + 64, tb, 2 * kMP, true);
+                if (!tip[side] || TV) mma_tile_ta(acc, xa + 64, tb, 2 * kMP, true);
             }
             // while those run: the previous results leave the upper halves, this category's lo
             // tables take their place
@@ -946,34 +977,65 @@ constexpr size_t kPreTcSmem = 1024 + 4 * kRowTile + 4 * kTab + kRowTile;
 
 }  // namespace
 
-cudaError_t launch_m_post_level_tc(const MDesc &d, const void *tm_post, const void *tm_tab, int o0, int nd,
-                                   cudaStream_t s) {
-    const int n_pt = (d.P + kTcTile - 1) / kTcTile;
-    if (nd <= 0 || n_pt <= 0) return cudaSuccess;
+namespace {
+
+// Each kernel has two instantiations: TV = true for problems with tip vectors (rows of partially
+// observed tips, with their remainder passes), TV = false with the plain one-hot / all-ones rows.
+template <bool TV>
+cudaError_t launch_post_tc(const MDesc &d, const void *tm_post, const void *tm_tab, int o0, int nd, int n_pt,
+                           cudaStream_t s) {
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(m_post_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPostTcSmem);
+        cudaError_t e = cudaFuncSetAttribute(m_post_tc_kernel<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kPostTcSmem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    m_post_tc_kernel<<<nd * d.C * n_pt, kTcThreads, kPostTcSmem, s>>>(
+    m_post_tc_kernel<TV><<<nd * d.C * n_pt, kTcThreads, kPostTcSmem, s>>>(
         d, *static_cast<const CUtensorMap *>(tm_post), *static_cast<const CUtensorMap *>(tm_tab), o0, n_pt);
     return cudaGetLastError();
 }
 
-template <bool HESS>
+template <bool HESS, bool TV>
 cudaError_t launch_pre_tc(const MDesc &d, const void *tm_post, const void *tm_pre, const void *tm_tab, int o0, int nd,
                           int n_pt, cudaStream_t s) {
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(m_pre_tc_kernel<HESS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPreTcSmem);
+        cudaError_t e = cudaFuncSetAttribute(m_pre_tc_kernel<HESS, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kPreTcSmem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    m_pre_tc_kernel<HESS><<<nd * n_pt, kTcThreads, kPreTcSmem, s>>>(
+    m_pre_tc_kernel<HESS, TV><<<nd * n_pt, kTcThreads, kPreTcSmem, s>>>(
         d, *static_cast<const CUtensorMap *>(tm_post), *static_cast<const CUtensorMap *>(tm_pre),
         *static_cast<const CUtensorMap *>(tm_tab), o0, n_pt);
     return cudaGetLastError();
+}
+
+template <bool TV>
+cudaError_t launch_pre_tc2(const MDesc &d, const void *tm_post, const void *tm_pre, const void *tm_tab, int o0,
+                           int nd, int n_pt, int n_cg, cudaStream_t s) {
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(m_pre_tc2_kernel<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kPre2TcSmem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    m_pre_tc2_kernel<TV><<<nd * n_cg * n_pt, 2 * kTcThreads, kPre2TcSmem, s>>>(
+        d, *static_cast<const CUtensorMap *>(tm_post), *static_cast<const CUtensorMap *>(tm_pre),
+        *static_cast<const CUtensorMap *>(tm_tab), o0, n_pt, n_cg);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_m_post_level_tc(const MDesc &d, const void *tm_post, const void *tm_tab, int o0, int nd,
+                                   cudaStream_t s) {
+    const int n_pt = (d.P + kTcTile - 1) / kTcTile;
+    if (nd <= 0 || n_pt <= 0) return cudaSuccess;
+    return d.n_tv > 0 ? launch_post_tc<true>(d, tm_post, tm_tab, o0, nd, n_pt, s)
+                      : launch_post_tc<false>(d, tm_post, tm_tab, o0, nd, n_pt, s);
 }
 
 // Categories per block: all of them (the next category's loads overlap this one's work) unless the
@@ -993,18 +1055,13 @@ cudaError_t launch_m_pre_level_tc(const MDesc &d, const void *tm_post, const voi
                                   int o0, int nd, bool hess, int n_sm, cudaStream_t s) {
     const int n_pt = (d.P + kTcTile - 1) / kTcTile;
     if (nd <= 0 || n_pt <= 0) return cudaSuccess;
-    if (hess) return launch_pre_tc<true>(d, tm_post, tm_pre, tm_tab, o0, nd, n_pt, s);
+    const bool tv = d.n_tv > 0;
+    if (hess)
+        return tv ? launch_pre_tc<true, true>(d, tm_post, tm_pre, tm_tab, o0, nd, n_pt, s)
+                  : launch_pre_tc<true, false>(d, tm_post, tm_pre, tm_tab, o0, nd, n_pt, s);
     const int n_cg = pre_category_groups(d.C, nd * n_pt, n_sm);
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(m_pre_tc2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPre2TcSmem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    m_pre_tc2_kernel<<<nd * n_cg * n_pt, 2 * kTcThreads, kPre2TcSmem, s>>>(
-        d, *static_cast<const CUtensorMap *>(tm_post), *static_cast<const CUtensorMap *>(tm_pre),
-        *static_cast<const CUtensorMap *>(tm_tab), o0, n_pt, n_cg);
-    return cudaGetLastError();
+    return tv ? launch_pre_tc2<true>(d, tm_post, tm_pre, tm_tab, o0, nd, n_pt, n_cg, s)
+              : launch_pre_tc2<false>(d, tm_post, tm_pre, tm_tab, o0, nd, n_pt, n_cg, s);
 }
 
 }  // namespace pg

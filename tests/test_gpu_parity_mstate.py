@@ -1,9 +1,9 @@
 """GPU parity of the general-state path (61 sense codons, 20 amino acids) against the FP64 oracle.
 
-Stated error (not the 4-state bounds): the transition tables are formed in FP32 from the FP64
-eigensystem of the symmetrised generator, D = P - I = Pi^{-1/2} U diag(expm1(lambda t)) U^T Pi^{1/2},
-so each entry carries an absolute error of about m 2^-24 max_k |expm1(lambda_k t)| sqrt(pi_j / pi_s)
-on top of the FP32 rounding of the partials.  Per site, every internal node adds at most about
+Stated error (not the 4-state bounds): the transition tables D = P - I are formed by
+uniformisation, FP64 powers of the uniformised chain and FP64 Poisson weights summed in FP32, so
+each entry carries an absolute error of about m 2^-24 on top of the FP32 rounding of the
+partials.  Per site, every internal node adds at most about
 m 2^-24 relative (an FP32 sum of m products, plus a table error of the same order), so the site
 logL bound is 2 n_internal m 2^-24 absolute and the logL bound the weighted sum of the site
 bounds.  The tensor-core kernels keep the identity part of P x out of the (truncating) tensor-core
@@ -184,3 +184,42 @@ def test_codon_full_size_sampled_sites(ctx, oracle_mod, codon_full):
     assert abs(part["logL"] - ref.logL) <= _logl_atol(pr, sub["weights"])
     assert eg <= M_GRAD_RTOL
     np.testing.assert_array_equal(part["site_logL"], full["site_logL"])
+
+
+def _with_partial_tips(pr, m, rng, frac=0.15):
+    """Partially observed tips (Section 2.1): the IUPAC ambiguity sets and base-call likelihoods
+    for nucleotides, random subsets with graded entries for larger state spaces."""
+    if m == 4:
+        table = wl.iupac_nucleotide_partials(error=0.03)
+    else:
+        table = np.where(rng.random((12, m)) < 0.3, rng.uniform(0.2, 1.0, (12, m)), 0.0)
+        table[np.arange(12), rng.integers(0, m, 12)] = 1.0
+    pr = dict(pr, tip_partials=table)
+    pr["tip_states"] = wl.make_partially_observed(pr["tip_states"], frac, table, rng)
+    return pr
+
+
+@pytest.mark.parametrize("m", [4, 20, 61])
+def test_partially_observed_tips(ctx, oracle_mod, m):
+    """Tip partial vectors, indicator codes and missing data mixed in every tile (a 4-state
+    problem with tip vectors runs on this path); 300 patterns = two full tiles and a ragged one."""
+    rng = np.random.default_rng(60 + m)
+    pr = wl.random_problem(24, 300, n_states=m, n_cat=2, seed=60 + m, b_mean=0.1, ambiguous=0.05)
+    pr = _with_partial_tips(pr, m, rng)
+    codes = pr["tip_states"]
+    assert ((codes >= m) & (codes < m + len(pr["tip_partials"]))).any() and (codes == wl.MISSING).any()
+    _check(ctx, oracle_mod, pr, label=f"partial tips m={m}")
+
+
+def test_partially_observed_tips_host_validation(ctx):
+    from paper_1905_12146_gb300 import _native
+    rng = np.random.default_rng(70)
+    pr = _with_partial_tips(wl.random_problem(8, 40, n_states=4, seed=70), 4, rng)
+    for table in (-pr["tip_partials"], np.zeros_like(pr["tip_partials"]),
+                  np.full_like(pr["tip_partials"], np.nan)):
+        with pytest.raises(_native.PhyloGradError) as e:
+            ctx.upload(dict(pr, tip_partials=table))
+        assert e.value.status == _native.PG_ERR_INVALID
+    with pytest.raises(_native.PhyloGradError) as e:   # FP64 partials: the 4-state path only
+        ctx.upload(pr, "fp64")
+    assert e.value.status == _native.PG_ERR_UNSUPPORTED
