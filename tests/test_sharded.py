@@ -76,3 +76,19 @@ def test_two_ranks_equal_the_whole_problem():
         assert abs(logL - ref.logL) <= 1e-12 * abs(ref.logL)
         np.testing.assert_allclose(grad, ref.grad, rtol=1e-10, atol=1e-10 * np.abs(ref.grad).max())
         np.testing.assert_allclose(hess, ref.hess, rtol=1e-9, atol=1e-9 * np.abs(ref.hess).max())
+
+
+def test_slices_keep_the_tip_vector_table():
+    """A slice keeps the problem's tip-vector table (partially observed tips), so the slices'
+    oracle results sum to the whole problem's."""
+    sys.path.insert(0, ROOT)
+    from oracle import oracle
+    pr = wl.random_problem(12, 90, n_states=4, n_cat=2, seed=81, b_mean=0.1, ambiguous=0.05)
+    table = wl.iupac_nucleotide_partials(error=0.02)
+    pr = dict(pr, tip_partials=table,
+              tip_states=wl.make_partially_observed(pr["tip_states"], 0.2, table, np.random.default_rng(81)))
+    ref = oracle.evaluate(pr)
+    parts = [oracle.evaluate(sharded.shard_problem(pr, r, 3)) for r in range(3)]
+    assert abs(sum(p.logL for p in parts) - ref.logL) <= 1e-12 * abs(ref.logL)
+    np.testing.assert_allclose(sum(p.grad for p in parts), ref.grad, rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(sum(p.hess for p in parts), ref.hess, rtol=1e-9, atol=1e-10)
