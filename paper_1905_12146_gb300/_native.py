@@ -224,6 +224,9 @@ class Context:
         return int(load().pg_selftest_timeout(self._ptr, int(limit_cycles)))
 
     def upload(self, problem: dict, precision: str | None = None) -> "Handle":
+        """pg_upload of a problem dict: parent, tip_states [N][P] (uint8 codes), weights, Q
+        ([models][m][m] or [m][m]), root_freqs, cat_rates, cat_weights; optional branch_model and
+        tip_partials [K][m] (codes m .. m+K-1 select its rows, partially observed tips)."""
         return Handle(self, problem, precision)
 
     def close(self):
