@@ -1,4 +1,4 @@
-// Tensor-core kernels of the general-state path (5..64 states): the products P x, G x, H x of the
+// Tensor-core kernels of the general-state path (2..64 states): the products P x, G x, H x of the
 // post-order (Section 2.3) and pre-order (Section 2.4) passes and P^T q of the pre-order, as
 // Y[p][s] = sum_k X[p][k] W[s][k] on tcgen05 (kind::tf32, FP32 accumulation in tensor memory).
 // With P = I + D only D x and D^T q go through the tensor core; the identity part (x, q) is added
