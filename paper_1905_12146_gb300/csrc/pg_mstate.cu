@@ -1,5 +1,5 @@
-// General state spaces (2..64 states other than the 4-state path's problems, e.g. the 61 sense
-// codons or 20 amino acids, and 4-state problems with tip partial vectors): the transition
+// General state spaces (any of 2..64 states but 4, e.g. the 61 sense codons or 20 amino acids;
+// also 4-state problems with tip partial vectors): the transition
 // tables, the post-order pass (Section 2.3), the root mixture (Section 2.5), the pre-order pass
 // (Section 2.4) with the branch gradient (Section 2.5) and Hessian diagonal (Section 2.6), and the
 // fixed-order reduction.  SIMT FP32 products; every column (pattern, category) carries its own
