@@ -168,14 +168,14 @@ def _dev_ptr(t):
     return t.data_ptr()
 
 
-def _tip_partials(problem: dict):
+def _tip_partials(problem: dict, m: int):
     """(K, [K][m] FP64 array or None) of the problem's optional tip partial vectors."""
     tv = problem.get("tip_partials")
     if tv is None or len(tv) == 0:
         return 0, None
     tv = np.ascontiguousarray(tv, dtype=np.float64)
-    if tv.ndim != 2:
-        raise ValueError("tip_partials must be [K][n_states]")
+    if tv.ndim != 2 or tv.shape[1] != m:
+        raise ValueError(f"tip_partials must be [K][{m}]")
     return tv.shape[0], tv
 
 
@@ -200,7 +200,7 @@ def problem_struct(problem: dict, precision: str = "fp32"):
     cw = np.ascontiguousarray(problem["cat_weights"], dtype=np.float64)
     n = parent.shape[0]
     P = tips.shape[1] if tips.ndim == 2 else 0
-    K, tv = _tip_partials(problem)
+    K, tv = _tip_partials(problem, Q.shape[1])
     pr = pg_problem((n + 1) // 2, Q.shape[1], P, rates.shape[0], Q.shape[0], PRECISIONS[precision],
                     _np_ptr(parent), _np_ptr(tips), _np_ptr(w), _np_ptr(Q), _np_ptr(bm), _np_ptr(pi),
                     _np_ptr(rates), _np_ptr(cw), stride if stride != P else 0, K, _np_ptr(tv))
@@ -392,7 +392,7 @@ def eval_noalloc(problem: dict, b, precision: str = "fp32", grad=True, hess=Fals
     cw = np.ascontiguousarray(problem["cat_weights"], dtype=np.float64)
     n = parent.shape[0]
     P = tips.shape[1] if tips.ndim == 2 else 0
-    K, tv = _tip_partials(problem)
+    K, tv = _tip_partials(problem, Q.shape[1])
     pr = pg_problem((n + 1) // 2, Q.shape[1], P, rates.shape[0], Q.shape[0], PRECISIONS[precision],
                     _np_ptr(parent), _np_ptr(tips), _np_ptr(w), _np_ptr(Q), _np_ptr(bm),
                     _np_ptr(pi), _np_ptr(rates), _np_ptr(cw), 0, K, _np_ptr(tv))

@@ -98,6 +98,8 @@ def test_binding_marshals_tip_partials():
     table = wl.iupac_nucleotide_partials()
     pr = dict(pr, tip_partials=table,
               tip_states=wl.make_partially_observed(pr["tip_states"], 0.3, table, np.random.default_rng(0)))
+    with pytest.raises(ValueError):   # rows must have one entry per state
+        _native.problem_struct(dict(pr, tip_partials=table[:, :3]))
     st, keep = _native.problem_struct(pr)
     assert st.n_tip_partials == table.shape[0]
     buf = (ctypes.c_double * table.size).from_address(st.tip_partials)
