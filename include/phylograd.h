@@ -82,8 +82,9 @@ typedef struct pg_options {
  *                          observed data); a larger code is missing data (the all-ones vector).
  *   n_tip_partials K, tip_partials[K][m]
  *                          partial vectors of partially observed tips, e.g. the sets of an
- *                          ambiguity code or base-call likelihoods: finite, >= 0, each row with a
- *                          positive entry; K >= 0 with m + K <= 256 (K = 0: tip_partials unused).
+ *                          ambiguity code or base-call likelihoods: >= 0 and within the FP32
+ *                          range (the device holds them in FP32), each row with a positive
+ *                          entry; K >= 0 with m + K <= 256 (K = 0: tip_partials unused).
  *                          A 4-state problem with K > 0 runs on the general path (FP32 only).
  *   pattern_weights[P]     multiplicity of each site pattern, finite and >= 0.
  *   Q[n_models][m][m]      CTMC generators: off-diagonals >= 0, rows summing to 0 (|row sum| <=

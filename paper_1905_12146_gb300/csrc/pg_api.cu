@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -176,8 +177,8 @@ pg_status check_model(const pg_problem *pr) {
         bool positive = false;
         for (int i = 0; i < m; ++i) {
             const double x = pr->tip_partials[(size_t)v * m + i];
-            if (!(x >= 0.0) || !std::isfinite(x))
-                return fail(PG_ERR_INVALID, "tip_partials[%d][%d] is negative or not finite", v, i);
+            if (!(x >= 0.0) || !(x <= (double)FLT_MAX))   // the device path holds them in FP32
+                return fail(PG_ERR_INVALID, "tip_partials[%d][%d] is negative, not finite or beyond FP32", v, i);
             positive = positive || x > 0.0;
         }
         if (!positive) return fail(PG_ERR_INVALID, "tip_partials[%d] has no positive entry", v);
