@@ -315,6 +315,26 @@ def make_partially_observed(tips: np.ndarray, frac: float, table: np.ndarray, rn
     return out
 
 
+def encode_tip_partials(partials: np.ndarray):
+    """Per-cell tip partial vectors [N][P][m] as (codes [N][P] uint8, table [K][m]): an indicator
+    vector becomes its state, an all-ones vector the missing code, every other distinct vector a
+    row of the table (code m + row).  Raises ValueError when more than 255 - m distinct vectors
+    remain."""
+    partials = np.asarray(partials, dtype=np.float64)
+    N, P, m = partials.shape
+    flat = partials.reshape(-1, m)
+    codes = np.full(flat.shape[0], MISSING, dtype=np.uint8)
+    ones = np.all(flat == 1.0, axis=1)
+    onehot = (np.sum(flat == 1.0, axis=1) == 1) & (np.sum(flat == 0.0, axis=1) == m - 1)
+    codes[onehot] = np.argmax(flat[onehot], axis=1)
+    rest = ~(ones | onehot)
+    table, inverse = np.unique(flat[rest], axis=0, return_inverse=True)
+    if m + table.shape[0] > MISSING:
+        raise ValueError(f"{table.shape[0]} distinct partial vectors leave no code for missing data")
+    codes[rest] = m + inverse.reshape(-1)
+    return codes.reshape(N, P), table
+
+
 # --------------------------------------------------------------------------------------------
 # problems
 # --------------------------------------------------------------------------------------------

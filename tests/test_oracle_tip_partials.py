@@ -131,3 +131,22 @@ def test_rejects_invalid_tip_vectors(oracle_mod, bad):
         table = table[:, :3]
     with pytest.raises(ValueError):
         oracle_mod.evaluate(dict(pr, tip_partials=table))
+
+
+def test_per_cell_partials_encode_to_codes_and_a_table(oracle_mod):
+    """Per-cell vectors [N][P][m] (one partial vector for every tip and pattern) reduce to codes and a
+    table that reproduce every cell; the oracle gives the same result on both encodings of a
+    problem whose per-cell form was built from codes."""
+    m = 4
+    pr = _partial_problem(9, 70, 91)
+    V = ind.tip_vectors(pr, m)
+    cells = V[pr["tip_states"]]                       # [N][P][m]
+    codes, table = wl.encode_tip_partials(cells)
+    np.testing.assert_array_equal(ind.tip_vectors(dict(tip_partials=table), m)[codes], cells)
+    assert table.shape[0] <= len(pr["tip_partials"])
+    r0 = oracle_mod.evaluate(pr)
+    r1 = oracle_mod.evaluate(dict(pr, tip_states=codes, tip_partials=table))
+    assert abs(r1.logL - r0.logL) <= 1e-13 * abs(r0.logL)
+    np.testing.assert_allclose(r1.grad, r0.grad, rtol=1e-12, atol=1e-14)
+    with pytest.raises(ValueError):   # too many distinct vectors for one-byte codes
+        wl.encode_tip_partials(np.random.default_rng(0).random((2, 300, m)))
