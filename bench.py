@@ -75,11 +75,21 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def _kernel_hash():
+def _kernel_hash(read=None):
+    """Hash of the source the pre-order level kernel is compiled from: pg_levels.cu,
+    pg_device.cuh and pg_internal.cuh without the general-path descriptor (struct MDesc), which
+    that kernel does not use.  ``read(name) -> bytes`` reads a source file (default: the tree)."""
+    if read is None:
+        def read(name):
+            with open(os.path.join(ROOT, "paper_1905_12146_gb300", "csrc", name), "rb") as f:
+                return f.read()
     h = hashlib.sha256()
     for name in ("pg_levels.cu", "pg_device.cuh", "pg_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_1905_12146_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        text = read(name)
+        if name == "pg_internal.cuh":
+            i = text.index(b"struct MDesc {")
+            text = text[:i] + text[text.index(b"\n};\n", i) + 4:]
+        h.update(text)
     return h.hexdigest()[:16]
 
 
