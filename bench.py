@@ -15,8 +15,9 @@ copied back each step).  ``roofline`` is for the dominant kernel (the pre-order 
 ``cpu_baseline`` the FP64 CPU oracle on a bounded sample of the same workload.
 ``--impl reference`` times that oracle alone (there is no reference GPU implementation).
 
-Rank 0 then adds measured objects (skipped with ``--no-extras``): ``codon`` (500 taxa x 3,000
-codon patterns x 4 categories on the tensor-core kernels), ``differentiation`` (the 64-tree clock
+Rank 0 then adds measured objects (skipped with ``--no-extras``): ``small`` (per-call latency of
+the 16-taxon, 500-pattern FP64 configuration, p50 / p99), ``codon`` (500 taxa x 3,000 codon
+patterns x 4 categories on the tensor-core kernels, with its error against the FP64 oracle), ``differentiation`` (the 64-tree clock
 batch through the torch.autograd.Functions), ``inference`` (L-BFGS branch rates, analytic gradient
 against finite differences), ``hmc`` (HMC over the branch rates, identity mass against the
 Hessian-adapted diagonal mass, effective samples per second) and ``serving``
@@ -76,20 +77,18 @@ def _peaks():
 
 
 def _kernel_hash(read=None):
-    """Hash of the source the pre-order level kernel is compiled from: pg_levels.cu,
-    pg_device.cuh and pg_internal.cuh without the general-path descriptor (struct MDesc), which
-    that kernel does not use.  ``read(name) -> bytes`` reads a source file (default: the tree)."""
+    """Hash of what the pre-order level kernel is built from: the whole of pg_levels.cu and the
+    headers it includes, and the nvcc architecture and code-generation flags.  ``read(name) ->
+    bytes`` reads a source file (default: the tree)."""
+    from paper_1905_12146_gb300 import build as _build
     if read is None:
         def read(name):
             with open(os.path.join(ROOT, "paper_1905_12146_gb300", "csrc", name), "rb") as f:
                 return f.read()
     h = hashlib.sha256()
     for name in ("pg_levels.cu", "pg_device.cuh", "pg_internal.cuh"):
-        text = read(name)
-        if name == "pg_internal.cuh":
-            i = text.index(b"struct MDesc {")
-            text = text[:i] + text[text.index(b"\n};\n", i) + 4:]
-        h.update(text)
+        h.update(read(name))
+    h.update(" ".join(_build.ARCH + _build.FLAGS).encode())
     return h.hexdigest()[:16]
 
 
@@ -465,7 +464,133 @@ def _hmc(device: int, n_warm: int = 150, n_keep: int = 300, n_leapfrog: int = 10
     return out
 
 
-def _codon(device: int, steps: int = 20, warmup: int = 3):
+SMALL = ("small FP64: 16-taxon Yule tree, b~Exp(0.05), non-reversible 4x4 Q, Dirichlet root "
+         "frequencies, 500 patterns with integer weights 1-5, 1 category; logL + 30 branch gradients")
+
+
+def _small(device: int, calls: int = 2000, warmup: int = 50):
+    """The small configuration (the plain FP64 method): per-call latency over ``calls`` calls of
+    pg_eval (host arrays, copies and synchronisation included), pg_eval_async (device arrays; the
+    device time between CUDA events on the stream around each call, and the host time from the
+    call to the stream's completion) and pg_eval_noalloc (host arrays, nothing allocated), with the
+    FP64 oracle's single-thread time for the same problem beside them.  Host times include the
+    Python/ctypes call overhead (about 1-3 us)."""
+    import numpy as np
+    import torch
+
+    from oracle import oracle
+    from paper_1905_12146_gb300 import _native, workloads
+
+    pr = workloads.config_small(seed=0)
+    n = pr["parent"].shape[0]
+    lib = _native.load()
+    ctx = _native.Context(device)
+    h = ctx.upload(pr, "fp64")
+    dev = torch.device("cuda", device)
+    b_host = np.ascontiguousarray(pr["b"])
+    out_l, out_g = np.zeros(1), np.zeros(n)
+
+    def pct(us):
+        us = np.asarray(us)
+        return {"p50_us": float(np.percentile(us, 50)), "p99_us": float(np.percentile(us, 99)),
+                "mean_us": float(us.mean()), "calls": int(us.size)}
+
+    res = {"workload": SMALL, "unit": "us per call"}
+    # pg_eval: host arrays
+    bp, lp, gp = b_host.ctypes.data, out_l.ctypes.data, out_g.ctypes.data
+    for _ in range(warmup):
+        lib.pg_eval(h._ptr, bp, lp, gp, None, None)
+    t = []
+    for _ in range(calls):
+        t0 = time.perf_counter_ns()
+        st = lib.pg_eval(h._ptr, bp, lp, gp, None, None)
+        t.append((time.perf_counter_ns() - t0) / 1e3)
+        if st != 0:
+            raise SystemExit(f"pg_eval failed with status {st}")
+    res["pg_eval"] = pct(t)
+    # pg_eval_async: device arrays, per-call events
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    b = torch.tensor(pr["b"], device=dev)
+    lg = torch.zeros(1, dtype=torch.float64, device=dev)
+    g = torch.zeros(n, dtype=torch.float64, device=dev)
+    args = (h._ptr, b.data_ptr(), lg.data_ptr(), g.data_ptr(), None, None, sp)
+    for _ in range(warmup):
+        lib.pg_eval_async(*args)
+    torch.cuda.synchronize(dev)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(calls)]
+    t = []
+    for e0, e1 in evs:
+        t0 = time.perf_counter_ns()
+        e0.record(stream)
+        lib.pg_eval_async(*args)
+        e1.record(stream)
+        stream.synchronize()
+        t.append((time.perf_counter_ns() - t0) / 1e3)
+    res["pg_eval_async_device"] = pct([1e3 * e0.elapsed_time(e1) for e0, e1 in evs])
+    res["pg_eval_async_host"] = pct(t)
+    res["async_status"] = h.status()
+    h.close()
+    ctx.close()
+    # pg_eval_noalloc: host arrays, fixed scratch (the problem's validation and level planning are
+    # part of every call)
+    import ctypes
+    pst, _keep = _native.problem_struct(pr, "fp64")
+    pref = ctypes.byref(pst)
+    for _ in range(warmup):
+        lib.pg_eval_noalloc(pref, bp, lp, gp, None, None, None)
+    t = []
+    for _ in range(calls):
+        t0 = time.perf_counter_ns()
+        st = lib.pg_eval_noalloc(pref, bp, lp, gp, None, None, None)
+        t.append((time.perf_counter_ns() - t0) / 1e3)
+        if st != 0:
+            raise SystemExit(f"pg_eval_noalloc failed with status {st}")
+    res["pg_eval_noalloc"] = pct(t)
+    # the oracle, single thread, the same problem
+    oracle.build()
+    reps = 20
+    oracle.evaluate(pr)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.evaluate(pr)
+    res["oracle_single_thread_us"] = (time.perf_counter() - t0) / reps * 1e6
+    return res
+
+
+def _codon_error(ctx, pr, n_sample: int = 24, seed: int = 0):
+    """Error of the codon evaluation against the FP64 oracle on sampled patterns: the per-site logL
+    of a full evaluation at the sampled patterns, and logL and gradient of an evaluation whose
+    weights are zero except at the sampled patterns, against the oracle on that sub-alignment."""
+    import numpy as np
+
+    from oracle import oracle
+    oracle.build()
+    P = pr["weights"].shape[0]
+    idx = np.sort(np.random.default_rng(seed).choice(P, n_sample, replace=False))
+    h = ctx.upload(pr)
+    try:
+        full = h.eval(pr["b"], grad=False, site=True)
+    finally:
+        h.close()
+    w = np.zeros(P)
+    w[idx] = pr["weights"][idx]
+    hm = ctx.upload(dict(pr, weights=w))
+    try:
+        part = hm.eval(pr["b"], grad=True)
+    finally:
+        hm.close()
+    t0 = time.perf_counter()
+    ref = oracle.evaluate(dict(pr, tip_states=pr["tip_states"][:, idx], weights=pr["weights"][idx]), pr["b"])
+    gmax = float(np.abs(ref.grad).max())
+    return {"reference": f"FP64 oracle on {n_sample} sampled patterns ({time.perf_counter() - t0:.1f} s)",
+            "site_logL_abs_max": float(np.abs(full["site_logL"][idx] - ref.site_logL).max()),
+            "logL_rel": abs(part["logL"] - ref.logL) / abs(ref.logL),
+            "grad_maxnorm_rel": float(np.abs(part["grad"] - ref.grad).max()) / gmax,
+            "status": [full["status"], part["status"]]}
+
+
+def _codon(device: int, steps: int = 20, warmup: int = 3, error: bool = True):
     """The codon configuration: 500 taxa x 3,000 patterns x 4 categories, 61 states, tensor-core
     kernels (three-pass TF32, FP32 accumulation)."""
     import torch
@@ -492,11 +617,16 @@ def _codon(device: int, steps: int = 20, warmup: int = 3):
     ms = e0.elapsed_time(e1) / steps
     info = h.info()
     h.close()
+    out = {"workload": "codon: 500-taxon Yule tree, 61-state codon Q (omega 0.3), 4 categories, 3,000 patterns",
+           "ms_per_eval": ms, "evals_per_s": 1e3 / ms, "status": st,
+           "algorithmic_bytes": info.stream_bytes, "achieved_gbs": info.stream_bytes / (ms * 1e-3) / 1e9,
+           "useful_tflops": info.flops / (ms * 1e-3) / 1e12,
+           "precision": "FP32 partials; three-pass TF32 tensor-core products with FP32 accumulation; "
+                        "transition tables by uniformisation: FP64 powers and Poisson weights, FP32 sums"}
+    if error:
+        out["error"] = _codon_error(ctx, pr)
     ctx.close()
-    return {"workload": "codon: 500-taxon Yule tree, 61-state codon Q (omega 0.3), 4 categories, 3,000 patterns",
-            "ms_per_eval": ms, "evals_per_s": 1e3 / ms, "status": st,
-            "algorithmic_bytes": info.stream_bytes, "achieved_gbs": info.stream_bytes / (ms * 1e-3) / 1e9,
-            "useful_tflops": info.flops / (ms * 1e-3) / 1e12}
+    return out
 
 
 def run_gpu(args):
@@ -608,6 +738,7 @@ def run_gpu(args):
     h.close()
     ctx.close()
     if rank == 0 and not args.no_extras:
+        line["small"] = _small(local)
         line["codon"] = _codon(local)
         line["differentiation"] = _differentiation(local)
         line["inference"] = _inference(local)
@@ -631,9 +762,9 @@ def main():
                     help="requests of the serving measurement (0 skips it)")
     ap.add_argument("--no-extras", action="store_true",
                     help="only the headline nucleotide measurement (no codon, differentiation, serving)")
-    ap.add_argument("--case", choices=("all", "codon", "differentiation", "hmc"), default="all",
+    ap.add_argument("--case", choices=("all", "codon", "differentiation", "hmc", "small"), default="all",
                     help="codon / differentiation: time that workload alone for --steps steps after "
-                         "--warmup (for profiling); hmc: the HMC object alone; all: the full measurement")
+                         "--warmup (for profiling); hmc, small: that object alone; all: the full measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -643,11 +774,15 @@ def main():
     build.build()
     if args.case != "all":
         _, _, local = _rank_env()
-        if args.case == "hmc":
-            print(json.dumps({"case": "hmc", **_hmc(local)}), flush=True)
+        if args.case in ("hmc", "small"):
+            fn = _hmc if args.case == "hmc" else _small
+            print(json.dumps({"case": args.case, **fn(local)}), flush=True)
             return 0
-        fn = _codon if args.case == "codon" else _differentiation
-        print(json.dumps({"case": args.case, **fn(local, steps=args.steps, warmup=args.warmup)}), flush=True)
+        if args.case == "codon":
+            out = _codon(local, steps=args.steps, warmup=args.warmup, error=False)
+        else:
+            out = _differentiation(local, steps=args.steps, warmup=args.warmup)
+        print(json.dumps({"case": args.case, **out}), flush=True)
         return 0
     return run_gpu(args)
 

@@ -82,9 +82,10 @@ typedef struct pg_options {
  *                          observed data); a larger code is missing data (the all-ones vector).
  *   n_tip_partials K, tip_partials[K][m]
  *                          partial vectors of partially observed tips, e.g. the sets of an
- *                          ambiguity code or base-call likelihoods: >= 0 and within the FP32
- *                          range (the device holds them in FP32), each row with a positive
- *                          entry; K >= 0 with m + K <= 256 (K = 0: tip_partials unused).
+ *                          ambiguity code or base-call likelihoods: finite and >= 0, each row
+ *                          with a positive entry; K >= 0 with m + K <= 256 (K = 0: tip_partials
+ *                          unused).  The device holds each row in FP32 scaled exactly by a power
+ *                          of two (largest entry in [1, 2)) and adds the scales back to logL.
  *                          A 4-state problem with K > 0 runs on the general path (FP32 only).
  *   pattern_weights[P]     multiplicity of each site pattern, finite and >= 0.
  *   Q[n_models][m][m]      CTMC generators: off-diagonals >= 0, rows summing to 0 (|row sum| <=

@@ -408,7 +408,7 @@ def eval_noalloc(problem: dict, b, precision: str = "fp32", grad=True, hess=Fals
                              _np_ptr(st_site), s)
     out = {"logL": float(logL[0]), "grad": g, "hess": h, "site_logL": st_site, "status": st}
     if st not in (PG_OK, PG_ERR_NUMERIC):
-        raise PhyloGradError(st, lib.pg_status_string(st).decode())
+        check(st)
     return out
 
 

@@ -19,6 +19,8 @@ INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libphylograd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# code-generation flags of every translation unit (explicit fmaf calls are the only contractions)
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false"]
 
 
 def _nvcc() -> str:
@@ -34,7 +36,7 @@ def _cuda_libdir(nvcc: str) -> str:
 
 def _compile(nvcc: str, src: str, extra: list[str]) -> str:
     obj = os.path.join(OBJDIR, os.path.basename(src) + ".o")
-    cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC,-O2",
+    cmd = [nvcc, *ARCH, *FLAGS, "-Xcompiler", "-fPIC,-O2",
            "-I", INCLUDE, "-I", CSRC, *extra, "-c", src, "-o", obj]
     subprocess.run(cmd, check=True)
     return obj

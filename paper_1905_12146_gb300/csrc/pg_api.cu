@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cfloat>
 #include <cmath>
 #include <cstdarg>
@@ -24,6 +25,19 @@ namespace pg {
 namespace host {
 
 thread_local std::string g_err;
+// Errors are ordered by one sequence: a thread's own last error (g_err, at g_err_at) or the static
+// message that pg_eval_noalloc published for it, whichever came later.
+std::atomic<uint64_t> g_err_seq{0};
+thread_local uint64_t g_err_at = 0;
+std::mutex g_static_mu;
+const char *g_static_msg = nullptr;
+pthread_t g_static_tid;
+uint64_t g_static_at = 0;
+
+void set_error(const std::string &msg) {
+    g_err = msg;
+    g_err_at = ++g_err_seq;
+}
 
 pg_status fail(pg_status s, const char *fmt, ...) {
     char buf[512];
@@ -31,8 +45,23 @@ pg_status fail(pg_status s, const char *fmt, ...) {
     va_start(ap, fmt);
     vsnprintf(buf, sizeof buf, fmt, ap);
     va_end(ap);
-    g_err = buf;
+    set_error(buf);
     return s;
+}
+
+void publish_static_error(const char *msg, pthread_t tid) {
+    std::lock_guard<std::mutex> g(g_static_mu);
+    g_static_msg = msg;
+    g_static_tid = tid;
+    g_static_at = ++g_err_seq;
+}
+
+const char *last_error() {
+    {
+        std::lock_guard<std::mutex> g(g_static_mu);
+        if (g_static_msg && pthread_equal(g_static_tid, pthread_self()) && g_static_at > g_err_at) return g_static_msg;
+    }
+    return g_err.c_str();
 }
 
 }  // namespace host
@@ -177,8 +206,8 @@ pg_status check_model(const pg_problem *pr) {
         bool positive = false;
         for (int i = 0; i < m; ++i) {
             const double x = pr->tip_partials[(size_t)v * m + i];
-            if (!(x >= 0.0) || !(x <= (double)FLT_MAX))   // the device path holds them in FP32
-                return fail(PG_ERR_INVALID, "tip_partials[%d][%d] is negative, not finite or beyond FP32", v, i);
+            if (!(x >= 0.0) || !std::isfinite(x))
+                return fail(PG_ERR_INVALID, "tip_partials[%d][%d] is negative or not finite", v, i);
             positive = positive || x > 0.0;
         }
         if (!positive) return fail(PG_ERR_INVALID, "tip_partials[%d] has no positive entry", v);
@@ -346,10 +375,36 @@ pg_status upload_m(pg_ctx *ctx, const pg_problem *pr, const TreePlan &tp, pg_han
     const size_t o_ops = cv.take<int4>(N - 1), o_lv = cv.take<int>(H + 1);
     const size_t o_tips = cv.take<uint8_t>((size_t)N * Ps), o_w = cv.take<double>(Ps);
     const int K = pr->n_tip_partials;
-    std::vector<float> tipv((size_t)std::max(K, 1) * KP, 0.f);   // FP32 rows, pads 0
-    for (int v = 0; v < K; ++v)
-        for (int i = 0; i < m; ++i) tipv[(size_t)v * KP + i] = (float)pr->tip_partials[(size_t)v * m + i];
+    // FP32 rows, pads 0, each scaled exactly by 2^-e_v so that its largest entry is 1 (any finite
+    // row then neither overflows nor underflows the FP32 products); a site's likelihood is the
+    // scaled one times 2^(sum of e over its tips), added back at the root
+    std::vector<float> tipv((size_t)std::max(K, 1) * KP, 0.f);
+    std::vector<int> tv_e(std::max(K, 1), 0);
+    for (int v = 0; v < K; ++v) {
+        double mx = 0.0;
+        for (int i = 0; i < m; ++i) mx = std::max(mx, pr->tip_partials[(size_t)v * m + i]);
+        int e = 0;
+        std::frexp(mx, &e);
+        tv_e[v] = e - 1;   // mx = f 2^e with f in [0.5, 1): mx 2^-(e-1) in [1, 2)
+        for (int i = 0; i < m; ++i)
+            tipv[(size_t)v * KP + i] = (float)std::ldexp(pr->tip_partials[(size_t)v * m + i], -tv_e[v]);
+    }
+    std::vector<int> tip_E;
+    bool any_scale = false;
+    for (int v = 0; v < K; ++v) any_scale = any_scale || tv_e[v] != 0;
+    if (any_scale && P > 0) {
+        tip_E.assign(Ps, 0);
+        const size_t stride = pr->tip_stride ? (size_t)pr->tip_stride : (size_t)P;
+        for (int t = 0; t < N; ++t) {
+            const uint8_t *row = pr->tip_states + (size_t)t * stride;
+            for (int p = 0; p < P; ++p) {
+                const int y = row[p];
+                if (y >= m && y < m + K) tip_E[p] += tv_e[y - m];
+            }
+        }
+    }
     const size_t o_tv = cv.take<float>(tipv.size());
+    const size_t o_tE = tip_E.empty() ? 0 : cv.take<int>(tip_E.size());
     const size_t o_Bp = cv.take<float>(Bpow.size()), o_QT = cv.take<float>(QT.size());
     const size_t o_mu = cv.take<double>(mu.size());
     const size_t o_bm = pr->branch_model ? cv.take<int>(n) : 0;
@@ -391,6 +446,7 @@ pg_status upload_m(pg_ctx *ctx, const pg_problem *pr, const TreePlan &tp, pg_han
         e = h2d_rows(pl, base + o_tips, Ps, pr->tip_states, pr->tip_stride ? pr->tip_stride : P, P, N);
     if (e == cudaSuccess && P > 0) e = cp(o_w, pr->pattern_weights, sizeof(double) * P);
     if (e == cudaSuccess) e = cp(o_tv, tipv.data(), sizeof(float) * tipv.size());
+    if (e == cudaSuccess && !tip_E.empty()) e = cp(o_tE, tip_E.data(), sizeof(int) * tip_E.size());
     if (e == cudaSuccess) e = cp(o_Bp, Bpow.data(), sizeof(float) * Bpow.size());
     if (e == cudaSuccess) e = cp(o_QT, QT.data(), sizeof(float) * QT.size());
     if (e == cudaSuccess) e = cp(o_mu, mu.data(), sizeof(double) * mu.size());
@@ -408,6 +464,7 @@ pg_status upload_m(pg_ctx *ctx, const pg_problem *pr, const TreePlan &tp, pg_han
     d.level_off = reinterpret_cast<const int *>(base + o_lv);
     d.tips = reinterpret_cast<const uint8_t *>(base + o_tips);
     d.tipv = reinterpret_cast<const float *>(base + o_tv);
+    d.tip_E = tip_E.empty() ? nullptr : reinterpret_cast<const int *>(base + o_tE);
     d.n_tv = K;
     d.weights = reinterpret_cast<const double *>(base + o_w);
     d.Bpow = reinterpret_cast<const float *>(base + o_Bp);
@@ -569,7 +626,7 @@ const char *pg_status_string(pg_status s) {
     return "unknown status";
 }
 
-const char *pg_last_error(void) { return pg::host::g_err.c_str(); }
+const char *pg_last_error(void) { return pg::host::last_error(); }
 
 pg_status pg_create(const pg_options *opt, pg_ctx **out) {
     if (!out) return fail(PG_ERR_INVALID, "out is NULL");
@@ -1281,6 +1338,9 @@ pg_status pg_eval_status(pg_handle *h) {
     if (st) PG_CUDA(cudaMemset(h->desc.status, 0, sizeof(int)));
     if (st & pg::kStatusBadLength) return fail(PG_ERR_INVALID, "a branch length was negative or not finite");
     if (st & pg::kStatusNumeric) return fail(PG_ERR_NUMERIC, "a site likelihood was zero or not finite");
+    if (st & pg::kStatusUnsettled)
+        return fail(PG_ERR_TIMEOUT, "a device-side wait gave up and a block left before the copies or products it "
+                                    "issued were confirmed complete: the device state is suspect, destroy the context");
     if (st & pg::kStatusTimeout) return fail(PG_ERR_TIMEOUT, "a device-side wait for staged data gave up");
     return PG_OK;
 }

@@ -5,6 +5,7 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <pthread.h>
 
 #include <cstdint>
 #include <mutex>
@@ -55,6 +56,11 @@ namespace host {
 
 extern thread_local std::string g_err;
 pg_status fail(pg_status s, const char *fmt, ...);
+// the calling thread's error text, as fail() records it (for messages built elsewhere)
+void set_error(const std::string &msg);
+// Records, without allocating, that `msg` (a static buffer that outlives the call) is the last error
+// of thread `tid`: pg_last_error on that thread returns it until the thread records another error.
+void publish_static_error(const char *msg, pthread_t tid);
 
 // Where an upload puts its one device block and how it copies into it: cudaMalloc under the
 // context's budget and blocking copies (pg_upload), or a caller's allocator (the serving arena)

@@ -4,10 +4,36 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <mutex>
 
 #include <cuda_runtime.h>
 
 namespace pg {
+
+// One-time set-up of a kernel on each device.  cudaFuncSetAttribute and the occupancy queries apply
+// to the device current at the call, so every device ordinal runs the set-up once (thread-safely:
+// a serving worker and the caller's thread may launch at the same time); later calls on that device
+// return the set-up's status and the value it produced (e.g. resident blocks per SM).
+constexpr int kMaxDevices = 64;
+struct DeviceOnce {
+    std::once_flag flag[kMaxDevices];
+    cudaError_t err[kMaxDevices] = {};
+    int value[kMaxDevices] = {};
+};
+template <class F>
+cudaError_t device_once(DeviceOnce &o, F &&setup, int *value = nullptr) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::call_once(o.flag[dev], [&] {
+        int v = 0;
+        o.err[dev] = setup(v);
+        o.value[dev] = v;
+    });
+    if (value) *value = o.value[dev];
+    return o.err[dev];
+}
 
 constexpr int kStates = 4;      // nucleotide state space handled by the kernels in pg_nt.cu
 constexpr int kMaxCat = 4;      // rate categories held in registers per pattern
@@ -30,6 +56,8 @@ constexpr int kPtab64Pairs = 10;
 constexpr int kStatusBadLength = 1;
 constexpr int kStatusNumeric = 2;
 constexpr int kStatusTimeout = 4;
+// a block that gave up left before every copy or product it issued was confirmed complete
+constexpr int kStatusUnsettled = 8;
 // bound on a block's wait for its own bulk copies (SM clocks, about one second)
 constexpr long long kWaitLimitCycles = 2000000000LL;
 
@@ -156,7 +184,11 @@ struct MDesc {
     const int *level_off;
     const uint8_t *tips;           // [N][Ps] codes: < m a state, m .. m + n_tv - 1 a row of tipv,
                                    // larger the all-ones (missing) code
-    const float *tipv;             // [n_tv][kMP] partial vectors of partially observed tips, pads 0
+    const float *tipv;             // [n_tv][kMP] partial vectors of partially observed tips, pads 0,
+                                   // each row scaled by a power of two so that its largest entry is 1
+    const int *tip_E;              // [Ps] or null: sum over the tips of pattern p of their rows' log2
+                                   // scales (added back to the site log-likelihoods only: the
+                                   // gradient and Hessian are ratios in which the scales cancel)
     int n_tv;
     const double *weights;         // [P]
     const double *b;               // [n] branch lengths of this evaluation

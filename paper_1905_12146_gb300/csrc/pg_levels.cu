@@ -289,7 +289,8 @@ __device__ __forceinline__ void staged_walk(int n_items, Ring<Stage, STAGES> &ri
         }
         // let every copy issued by this warp land before the block may leave
         for (int q = (i > STAGES ? i - STAGES : 0); q < i; ++q)
-            mbar_wait_bounded(&ring.full[q % STAGES], (unsigned)(q / STAGES) & 1u, kWaitLimitCycles);
+            if (!mbar_wait_bounded(&ring.full[q % STAGES], (unsigned)(q / STAGES) & 1u, kWaitLimitCycles))
+                atomicOr(item_at(b + q * G).pd->status, kStatusTimeout | kStatusUnsettled);
         return;
     }
     for (int i = 0;; ++i) {   // consumers
@@ -366,14 +367,17 @@ __global__ void __launch_bounds__(kLevelThreads) pre_level_batch_kernel(const __
 constexpr int kPostStages = 2, kPreStages = 2, kCherryStages = 3;
 
 // blocks of a persistent level launch: every resident slot, at most one per item
+// (the attribute and the occupancy are set up once per device and instantiation)
 template <class K>
-int persistent_blocks(K kernel, size_t smem, int n_sm, int n_items, bool &configured, int &per_sm) {
-    if (!configured) {
-        if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kLevelThreads, smem) != cudaSuccess) return -1;
-        if (per_sm < 1) per_sm = 1;
-        configured = true;
-    }
+int persistent_blocks(K kernel, size_t smem, int n_sm, int n_items, DeviceOnce &once) {
+    int per_sm = 1;
+    const cudaError_t e = device_once(once, [&](int &v) {
+        cudaError_t r = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (r == cudaSuccess) r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, kLevelThreads, smem);
+        if (v < 1) v = 1;
+        return r;
+    }, &per_sm);
+    if (e != cudaSuccess) return -1;
     return n_items < n_sm * per_sm ? n_items : n_sm * per_sm;
 }
 
@@ -411,50 +415,46 @@ cudaError_t launch_pdl_batch(K kernel, int blocks, size_t smem, cudaStream_t s, 
 
 template <int C, bool CHERRY>
 cudaError_t post_batch_c(const LevelBatch &lb, int n_sm, cudaStream_t s) {
-    static bool configured = false;
-    static int per_sm = 1;
+    static DeviceOnce once;
     constexpr int ST = CHERRY ? kCherryStages : kPostStages;
     const int n_items = lb.base[lb.n];
     if (n_items <= 0) return cudaSuccess;
     const size_t smem = sizeof(Ring<PostStage<C, CHERRY>, ST>);
-    const int blocks = persistent_blocks(post_level_batch_kernel<C, ST, CHERRY>, smem, n_sm, n_items, configured, per_sm);
+    const int blocks = persistent_blocks(post_level_batch_kernel<C, ST, CHERRY>, smem, n_sm, n_items, once);
     if (blocks < 0) return cudaErrorInvalidConfiguration;
     return launch_pdl_batch(post_level_batch_kernel<C, ST, CHERRY>, blocks, smem, s, lb, n_items);
 }
 
 template <int C, bool HESS, bool CHERRY>
 cudaError_t pre_batch_c(const LevelBatch &lb, int n_sm, cudaStream_t s) {
-    static bool configured = false;
-    static int per_sm = 1;
+    static DeviceOnce once;
     constexpr int ST = CHERRY ? kCherryStages : kPreStages;
     const int n_items = lb.base[lb.n];
     if (n_items <= 0) return cudaSuccess;
     const size_t smem = sizeof(Ring<PreStage<C, CHERRY>, ST>);
-    const int blocks = persistent_blocks(pre_level_batch_kernel<C, HESS, ST, CHERRY>, smem, n_sm, n_items, configured, per_sm);
+    const int blocks = persistent_blocks(pre_level_batch_kernel<C, HESS, ST, CHERRY>, smem, n_sm, n_items, once);
     if (blocks < 0) return cudaErrorInvalidConfiguration;
     return launch_pdl_batch(pre_level_batch_kernel<C, HESS, ST, CHERRY>, blocks, smem, s, lb, n_items);
 }
 
 template <int C, bool CHERRY>
 cudaError_t post_c(const ProbDesc &d, int o0, int nd, int n_sm, cudaStream_t s) {
-    static bool configured = false;   // attribute and occupancy, once per instantiation
-    static int per_sm = 1;
+    static DeviceOnce once;   // attribute and occupancy, once per device and instantiation
     constexpr int ST = CHERRY ? kCherryStages : kPostStages;
     const int nr = d.level_ranges, n_items = nd * nr;
     const size_t smem = sizeof(Ring<PostStage<C, CHERRY>, ST>);
-    const int blocks = persistent_blocks(post_level_kernel<C, ST, CHERRY>, smem, n_sm, n_items, configured, per_sm);
+    const int blocks = persistent_blocks(post_level_kernel<C, ST, CHERRY>, smem, n_sm, n_items, once);
     if (blocks < 0) return cudaErrorInvalidConfiguration;
     return launch_pdl(post_level_kernel<C, ST, CHERRY>, blocks, smem, s, d, o0, nr, n_items);
 }
 
 template <int C, bool HESS, bool CHERRY>
 cudaError_t pre_c(const ProbDesc &d, int o0, int nd, int n_sm, cudaStream_t s) {
-    static bool configured = false;
-    static int per_sm = 1;
+    static DeviceOnce once;
     constexpr int ST = CHERRY ? kCherryStages : kPreStages;
     const int nr = d.level_ranges, n_items = nd * nr;
     const size_t smem = sizeof(Ring<PreStage<C, CHERRY>, ST>);
-    const int blocks = persistent_blocks(pre_level_kernel<C, HESS, ST, CHERRY>, smem, n_sm, n_items, configured, per_sm);
+    const int blocks = persistent_blocks(pre_level_kernel<C, HESS, ST, CHERRY>, smem, n_sm, n_items, once);
     if (blocks < 0) return cudaErrorInvalidConfiguration;
     return launch_pdl(pre_level_kernel<C, HESS, ST, CHERRY>, blocks, smem, s, d, o0, nr, n_items);
 }

@@ -259,13 +259,9 @@ constexpr size_t kPreChSmem = 4 * kColFloats * sizeof(float);
 
 template <bool TV>
 cudaError_t launch_pre_cherry(const MDesc &d, int o0, int nd, int n_ch, int n_pt, cudaStream_t s) {
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(m_pre_cherry_kernel<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kPreChSmem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static DeviceOnce once;   // the shared-memory attribute, once per device
+    if (cudaError_t e = device_once(once, [](int &) { return cudaFuncSetAttribute(m_pre_cherry_kernel<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPreChSmem); }); e != cudaSuccess)
+        return e;
     m_pre_cherry_kernel<TV><<<nd * d.C * n_ch, kChThreads, kPreChSmem, s>>>(d, o0, n_ch, n_pt);
     return cudaGetLastError();
 }

@@ -421,7 +421,8 @@ __global__ void __launch_bounds__(kRootThreads) m_root_kernel(const __grid_const
         int e2 = 0;
         const double f = (S > 0.0 && isfinite(S)) ? frexp(S, &e2) : S;
         const int Er = Emax + e2;
-        const double lp = log(f) + (double)Er * 0.69314718055994530942;
+        const int Et = d.tip_E ? __ldg(d.tip_E + p) : 0;   // the tip rows' scales
+        const double lp = log(f) + (double)(Er + Et) * 0.69314718055994530942;
         d.site_invL[p] = (float)(1.0 / f);
         d.site_Er[p] = Er;
         if (!(f > 0.0) || !isfinite(lp)) atomicOr(d.status, kStatusNumeric);
@@ -620,12 +621,9 @@ cudaError_t launch_m_pmatrix(const MDesc &d, bool hess, cudaStream_t s) {
 
 cudaError_t launch_m_post_level(const MDesc &d, int o0, int nd, cudaStream_t s) {
     if (nd <= 0 || d.n_ptiles <= 0) return cudaSuccess;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(m_post_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPostSmem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static DeviceOnce once;   // the shared-memory attribute, once per device
+    if (cudaError_t e = device_once(once, [](int &) { return cudaFuncSetAttribute(m_post_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPostSmem); }); e != cudaSuccess)
+        return e;
     m_post_kernel<<<nd * d.n_ptiles, kMThreads, kPostSmem, s>>>(d, o0, d.n_ptiles);
     return cudaGetLastError();
 }
@@ -638,12 +636,9 @@ cudaError_t launch_m_root(const MDesc &d, cudaStream_t s) {
 
 template <bool HESS>
 cudaError_t launch_m_pre_h(const MDesc &d, int o0, int nd, cudaStream_t s) {
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(m_pre_kernel<HESS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPreSmem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static DeviceOnce once;   // the shared-memory attribute, once per device
+    if (cudaError_t e = device_once(once, [](int &) { return cudaFuncSetAttribute(m_pre_kernel<HESS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPreSmem); }); e != cudaSuccess)
+        return e;
     m_pre_kernel<HESS><<<nd * d.n_ptiles, kMThreads, kPreSmem, s>>>(d, o0, d.n_ptiles);
     return cudaGetLastError();
 }

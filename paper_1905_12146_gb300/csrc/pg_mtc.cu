@@ -194,11 +194,20 @@ __device__ __forceinline__ bool wait_all(uint64_t *bar, uint32_t &phase) {
     if (ok) phase ^= 1u;
     return ok;
 }
-// after a wait gave up: let the copies or products behind both barriers finish (bounded)
-__device__ __forceinline__ void drain(uint64_t *bar, uint32_t ph_load, uint32_t ph_mma, bool load_pending,
-                                      bool mma_pending) {
-    if (load_pending) mbar_wait_bounded(&bar[0], ph_load, kWaitLimitCycles);
-    if (mma_pending) mbar_wait_bounded(&bar[1], ph_mma, kWaitLimitCycles);
+// After a wait gave up (called by the thread that issued every copy and product): let the products
+// finish, tracked afresh by a new barrier and a commit of every tensor-core operation this thread
+// issued (complete whatever phase the earlier barriers were in), and the copies behind the pending
+// load barriers land; each wait bounded.  Returns false if something was still outstanding.  The
+// block releases its tensor memory in either case: a block that left holding it would make every
+// later allocation on that SM wait forever.  A false return is recorded as kStatusUnsettled.
+__device__ __forceinline__ bool drain_block(uint64_t *fresh, uint64_t *loads, const uint32_t *ph, const bool *pend,
+                                            int n_loads) {
+    mbar_init(fresh, 1);
+    mma_commit(fresh);
+    bool ok = mbar_wait_bounded(fresh, 0u, kWaitLimitCycles);
+    for (int i = 0; i < n_loads; ++i)
+        if (pend[i]) ok = mbar_wait_bounded(&loads[i], ph[i], kWaitLimitCycles) && ok;
+    return ok;
 }
 
 // row t of a tile (states 16 ch .. 16 ch + 15) from a swizzled [128 x 64] tile
@@ -258,7 +267,7 @@ m_post_tc_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
     extern __shared__ __align__(1024) unsigned char tc_raw[];
     unsigned char *sm = align1024(tc_raw);
     unsigned char *XA = sm, *TB = sm + kRowTile;   // rows (then the result), D hi | D lo
-    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ __align__(8) uint64_t bar[2], drain_bar;
     __shared__ uint32_t tmem_slot;
     const int C = d.C, N = d.n_tips, t = threadIdx.x, warp = t >> 5;
     const int per_node = C * n_pt;
@@ -363,7 +372,7 @@ m_post_tc_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
         }
     } else if (t == 0) {
         atomicOr(d.status, kStatusTimeout);
-        drain(bar, ph_load, ph_mma, load_pending, mma_pending);
+        if (!drain_block(&drain_bar, &bar[0], &ph_load, &load_pending, 1)) atomicOr(d.status, kStatusUnsettled);
     }
     tc_before();
     __syncthreads();
@@ -385,7 +394,7 @@ m_pre_tc_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtenso
     unsigned char *X[2] = {sm, sm + 2 * kRowTile};            // rows (hi) then remainders (lo) per child
     unsigned char *TB = sm + 4 * kRowTile;                     // tables: up to [128 x 64] hi | lo
     unsigned char *QK = sm + 4 * kRowTile + 2 * 2 * kTab;      // q_k rows
-    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ __align__(8) uint64_t bar[2], drain_bar;
     __shared__ uint32_t tmem_slot;
     __shared__ double red[2][2][kTcThreads / 32];
     constexpr uint32_t kCols = HESS ? 512 : 256;
@@ -620,7 +629,7 @@ m_pre_tc_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtenso
         }
     } else if (t == 0) {
         atomicOr(d.status, kStatusTimeout);
-        drain(bar, ph_load, ph_mma, load_pending, mma_pending);
+        if (!drain_block(&drain_bar, &bar[0], &ph_load, &load_pending, 1)) atomicOr(d.status, kStatusUnsettled);
     }
     tc_before();
     __syncthreads();
@@ -654,7 +663,7 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
     // (then the staged result q_c)
     unsigned char *T[2] = {sm + 3 * kRowTile, sm + 3 * kRowTile + 4 * kTab};
     enum { BX = 0, BQ = 1, BTH = 2, BTL = 3, BD = 4, BM = 5, NB = 6 };   // rows, q_k, [D;G] hi, lo, D^T, products
-    __shared__ __align__(8) uint64_t bar[NB];
+    __shared__ __align__(8) uint64_t bar[NB], drain_bar;
     __shared__ uint32_t tmem_slot;
     __shared__ double red[2][kTcThreads / 32];
     __shared__ float half_part[2][2][kTcTile];   // per child, per half of the states, per row
@@ -960,8 +969,8 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
         }
     } else if (leader) {
         atomicOr(d.status, kStatusTimeout);
-        for (int i = 0; i < NB; ++i)   // let every copy and product in flight finish
-            if (pend[i]) mbar_wait_bounded(&bar[i], ph[i], kWaitLimitCycles);
+        // let every copy (barriers BX .. BD) and product in flight finish
+        if (!drain_block(&drain_bar, bar, ph, pend, BM)) atomicOr(d.status, kStatusUnsettled);
     }
     if (leader) bulk_wait_read0();   // the staging smem is read before the block exits
     tc_before();
@@ -984,13 +993,9 @@ namespace {
 template <bool TV>
 cudaError_t launch_post_tc(const MDesc &d, const void *tm_post, const void *tm_tab, int o0, int nd, int n_pt,
                            cudaStream_t s) {
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(m_post_tc_kernel<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kPostTcSmem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static DeviceOnce once;   // the shared-memory attribute, once per device
+    if (cudaError_t e = device_once(once, [](int &) { return cudaFuncSetAttribute(m_post_tc_kernel<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPostTcSmem); }); e != cudaSuccess)
+        return e;
     m_post_tc_kernel<TV><<<nd * d.C * n_pt, kTcThreads, kPostTcSmem, s>>>(
         d, *static_cast<const CUtensorMap *>(tm_post), *static_cast<const CUtensorMap *>(tm_tab), o0, n_pt);
     return cudaGetLastError();
@@ -999,13 +1004,9 @@ cudaError_t launch_post_tc(const MDesc &d, const void *tm_post, const void *tm_t
 template <bool HESS, bool TV>
 cudaError_t launch_pre_tc(const MDesc &d, const void *tm_post, const void *tm_pre, const void *tm_tab, int o0, int nd,
                           int n_pt, cudaStream_t s) {
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(m_pre_tc_kernel<HESS, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kPreTcSmem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static DeviceOnce once;   // the shared-memory attribute, once per device
+    if (cudaError_t e = device_once(once, [](int &) { return cudaFuncSetAttribute(m_pre_tc_kernel<HESS, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPreTcSmem); }); e != cudaSuccess)
+        return e;
     m_pre_tc_kernel<HESS, TV><<<nd * n_pt, kTcThreads, kPreTcSmem, s>>>(
         d, *static_cast<const CUtensorMap *>(tm_post), *static_cast<const CUtensorMap *>(tm_pre),
         *static_cast<const CUtensorMap *>(tm_tab), o0, n_pt);
@@ -1015,13 +1016,9 @@ cudaError_t launch_pre_tc(const MDesc &d, const void *tm_post, const void *tm_pr
 template <bool TV>
 cudaError_t launch_pre_tc2(const MDesc &d, const void *tm_post, const void *tm_pre, const void *tm_tab, int o0,
                            int nd, int n_pt, int n_cg, cudaStream_t s) {
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(m_pre_tc2_kernel<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kPre2TcSmem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static DeviceOnce once;   // the shared-memory attribute, once per device
+    if (cudaError_t e = device_once(once, [](int &) { return cudaFuncSetAttribute(m_pre_tc2_kernel<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPre2TcSmem); }); e != cudaSuccess)
+        return e;
     m_pre_tc2_kernel<TV><<<nd * n_cg * n_pt, 2 * kTcThreads, kPre2TcSmem, s>>>(
         d, *static_cast<const CUtensorMap *>(tm_post), *static_cast<const CUtensorMap *>(tm_pre),
         *static_cast<const CUtensorMap *>(tm_tab), o0, n_pt, n_cg);

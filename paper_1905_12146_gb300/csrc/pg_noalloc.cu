@@ -11,29 +11,35 @@
 // __device__ variable it is created on every GPU that loads this library's code and stays there
 // until the process exits.  In host code its name is only a host-side stand-in, so its device
 // address is taken with cudaGetSymbolAddress, once per device, with that device current, on the
-// first call made on that device.  All calls share the array (and the static host buffers): calls
+// first call made on that device (thread-safely).  That cached address belongs to the device's
+// current CUDA context: after cudaDeviceReset on a device, do not call this entry point on that
+// device again in the same process.  All calls share the array (and the static host buffers): calls
 // that overlap -- on the GPU or from several host threads -- race and must be serialised by the
-// caller.  The array keeps the last call's contents; the only value that must start at zero, the
+// caller.  An error message is formatted into a fixed static buffer (no allocation) and is what
+// pg_last_error() returns on the failing call's thread until that thread records another error.  The array keeps the last call's contents; the only value that must start at zero, the
 // device status word, is cleared at the start of every call, and every partial and partial sum the
 // kernels read is written by the same call first.
 #include <cuda_runtime.h>
+#include <pthread.h>
 
 #include <cmath>
+#include <cstdarg>
+#include <cstdio>
 
 #include "phylograd.h"
+#include "pg_host.h"
 #include "pg_internal.cuh"
 
 namespace {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[PG_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
 constexpr int kMaxTips = 8192;                 // host planning buffers
 constexpr int kMaxNodes = 2 * kMaxTips - 1;
 constexpr int kMaxModels = 64;
 
-void *g_scratch_addr[kMaxDevices];
-bool g_scratch_ready[kMaxDevices];
+pg::DeviceOnce g_scratch_once;   // the array's device address, looked up once per device
+void *g_scratch_addr[pg::kMaxDevices];
 
 // static host buffers for validation and planning (no heap)
 int g_kid0[kMaxNodes], g_kid1[kMaxNodes], g_order[kMaxNodes], g_height[kMaxNodes], g_fill[kMaxNodes];
@@ -43,8 +49,17 @@ float4 g_qf[kMaxModels * 4];
 double g_mpow[kMaxModels * (pg::kTaylorDeg + 1) * 16];
 double g_qnorm[kMaxModels];
 
-// statuses only: formatting a message could allocate
-pg_status noalloc_fail(pg_status s, const char *, ...) { return s; }
+// the message of the last failure: a fixed buffer, formatted with vsnprintf (integer and string
+// conversions only, which allocate nothing), then published to pg_last_error
+char g_msg[256];
+pg_status noalloc_fail(pg_status s, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof g_msg, fmt, ap);
+    va_end(ap);
+    pg::host::publish_static_error(g_msg, pthread_self());
+    return s;
+}
 
 size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 
@@ -165,14 +180,12 @@ extern "C" pg_status pg_eval_noalloc(const pg_problem *pr, const double *b, doub
     const int Ps = (P + 15) / 16 * 16;
     int dev = 0, n_sm = 1;
     NOALLOC_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(PG_ERR_UNSUPPORTED, "device ordinal %d", dev);
+    if (dev < 0 || dev >= pg::kMaxDevices) return noalloc_fail(PG_ERR_UNSUPPORTED, "device ordinal %d", dev);
     NOALLOC_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
-    if (!g_scratch_ready[dev]) {   // set-up on this device's first call, with the device current
-        void *addr = nullptr;
-        NOALLOC_CUDA(cudaGetSymbolAddress(&addr, g_noalloc_scratch));
-        g_scratch_addr[dev] = addr;
-        g_scratch_ready[dev] = true;
-    }
+    // set-up on this device's first call, with the device current: the array's device address
+    NOALLOC_CUDA(pg::device_once(g_scratch_once, [dev](int &) {
+        return cudaGetSymbolAddress(&g_scratch_addr[dev], g_noalloc_scratch);
+    }));
     char *base = static_cast<char *>(g_scratch_addr[dev]);
 
     // tiling of the fused kernel over the patterns, as a single-problem evaluation
@@ -321,6 +334,8 @@ extern "C" pg_status pg_eval_noalloc(const pg_problem *pr, const double *b, doub
     NOALLOC_CUDA(cudaStreamSynchronize(s));
     if (status & pg::kStatusBadLength) return noalloc_fail(PG_ERR_INVALID, "a branch length was negative or not finite");
     if (status & pg::kStatusNumeric) return noalloc_fail(PG_ERR_NUMERIC, "a site likelihood was zero or not finite");
+    if (status & pg::kStatusUnsettled)
+        return noalloc_fail(PG_ERR_TIMEOUT, "a device-side wait gave up and a block left with copies unconfirmed");
     if (status & pg::kStatusTimeout) return noalloc_fail(PG_ERR_TIMEOUT, "a device-side wait gave up");
     return PG_OK;
 }

@@ -789,14 +789,9 @@ cudaError_t launch_tree_cc(const BatchArgs<MAXB> &args, bool f64, cudaStream_t s
         int rl = 0;
         for (int i = 0; i < args.n; ++i) rl = rl > args.d[i].range_len ? rl : args.d[i].range_len;
         const size_t smem = f32_dyn_smem<C>(rl);
-        static bool configured = false;   // one attribute call per instantiation
-        if (!configured) {
-            cudaError_t e = cudaFuncSetAttribute(tree4f_kernel<C, HESS, MAXB>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)f32_dyn_smem<C>(kMaxRange));
-            if (e != cudaSuccess) return e;
-            configured = true;
-        }
+        static DeviceOnce once;   // the shared-memory attribute, once per device
+        if (cudaError_t e = device_once(once, [](int &) { return cudaFuncSetAttribute(tree4f_kernel<C, HESS, MAXB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f32_dyn_smem<C>(kMaxRange)); }); e != cudaSuccess)
+            return e;
         tree4f_kernel<C, HESS, MAXB><<<blocks, kBlock, smem, s>>>(args);
     }
     return cudaGetLastError();
@@ -813,24 +808,30 @@ cudaError_t launch_tree_c(const BatchArgs<MAXB> &args, int C, bool f64, cudaStre
     }
 }
 
+// resident blocks per SM of the fused kernel, queried once per device
 template <int C, bool F64>
 int occupancy_of() {
-    int k = 0;
-    cudaError_t e;
-    if (F64) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, tree4d_kernel<C, true, kMaxBatch>, kBlock, 0);
-    } else {
-        const size_t smem = f32_dyn_smem<C>(64);
-        e = cudaFuncSetAttribute(tree4f_kernel<C, true, kMaxBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)f32_dyn_smem<C>(kMaxRange));
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, tree4f_kernel<C, true, kMaxBatch>, kBlock, smem);
-    }
+    static DeviceOnce once;
+    int k = 1;
+    const cudaError_t e = device_once(once, [](int &v) {
+        cudaError_t r;
+        if (F64) {
+            r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, tree4d_kernel<C, true, kMaxBatch>, kBlock, 0);
+        } else {
+            const size_t smem = f32_dyn_smem<C>(64);
+            r = cudaFuncSetAttribute(tree4f_kernel<C, true, kMaxBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)f32_dyn_smem<C>(kMaxRange));
+            if (r == cudaSuccess)
+                r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, tree4f_kernel<C, true, kMaxBatch>, kBlock, smem);
+        }
+        if (v < 1) v = 1;
+        return r;
+    }, &k);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
-    return k > 0 ? k : 1;
+    return k;
 }
 
 }  // namespace

@@ -383,7 +383,7 @@ pg_status pg_server_wait(pg_server *S, uint64_t ticket, pg_request_info *info) {
         info->start_s = r->t_start;
         info->done_s = r->t_done;
     }
-    if (st != PG_OK) pg::host::g_err = r->error;
+    if (st != PG_OK) pg::host::set_error(r->error);
     S->reqs.erase(it);
     delete r;
     return st;

@@ -287,13 +287,9 @@ __global__ void __launch_bounds__(kBlock, 2) top_kernel(const __grid_constant__ 
 
 template <int C, bool HESS>
 cudaError_t launch_top_c(const BatchArgs<1> &args, size_t smem, cudaStream_t s) {
-    static bool configured = false;   // one attribute call per instantiation
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(top_kernel<C, HESS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kTopSmemLimit);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static DeviceOnce once;   // the shared-memory attribute, once per device
+    if (cudaError_t e = device_once(once, [](int &) { return cudaFuncSetAttribute(top_kernel<C, HESS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTopSmemLimit); }); e != cudaSuccess)
+        return e;
     top_kernel<C, HESS><<<args.d[0].n_tiles, kBlock, smem, s>>>(args);
     return cudaGetLastError();
 }

@@ -216,10 +216,35 @@ def test_partially_observed_tips_host_validation(ctx):
     rng = np.random.default_rng(70)
     pr = _with_partial_tips(wl.random_problem(8, 40, n_states=4, seed=70), 4, rng)
     for table in (-pr["tip_partials"], np.zeros_like(pr["tip_partials"]),
-                  np.full_like(pr["tip_partials"], np.nan)):
+                  np.full_like(pr["tip_partials"], np.nan), np.full_like(pr["tip_partials"], np.inf)):
         with pytest.raises(_native.PhyloGradError) as e:
             ctx.upload(dict(pr, tip_partials=table))
         assert e.value.status == _native.PG_ERR_INVALID
     with pytest.raises(_native.PhyloGradError) as e:   # FP64 partials: the 4-state path only
         ctx.upload(pr, "fp64")
     assert e.value.status == _native.PG_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("m", [4, 61])
+def test_partially_observed_tips_beyond_fp32_range(ctx, oracle_mod, m):
+    """Tip partial vectors are only required to be finite: rows with entries beyond the FP32 range,
+    rows whose sum exceeds it and rows below its normal range are held scaled by exact powers of
+    two, whose exponents are added back to the site log-likelihoods (the gradient and Hessian
+    diagonal are ratios in which they cancel)."""
+    rng = np.random.default_rng(72 + m)
+    pr = _with_partial_tips(wl.random_problem(12, 160, n_states=m, n_cat=2, seed=72 + m, b_mean=0.1), m, rng,
+                            frac=0.3)
+    table = pr["tip_partials"].copy()
+    scale = np.ones(table.shape[0])
+    scale[0::4] = 1e39                       # entries beyond FLT_MAX
+    scale[1::4] = 3.0e38 / table.max(1)[1::4]   # largest entry near FLT_MAX, row sum beyond it
+    scale[2::4] = 1e-41                      # every entry below the FP32 normal range
+    pr["tip_partials"] = table * scale[:, None]
+    _check(ctx, oracle_mod, pr, label=f"scaled tip rows m={m}")
+    # the same problem with the unscaled rows differs in logL by the scales' logs alone
+    plain = oracle_mod.evaluate(dict(pr, tip_partials=table), pr["b"])
+    scaled = oracle_mod.evaluate(pr, pr["b"])
+    codes = pr["tip_states"].astype(np.int64)
+    sel = (codes >= m) & (codes < m + table.shape[0])
+    shift = np.where(sel, np.log(scale[np.clip(codes - m, 0, table.shape[0] - 1)]), 0.0).sum(0)
+    np.testing.assert_allclose(scaled.site_logL - plain.site_logL, shift, rtol=1e-12, atol=1e-9)
