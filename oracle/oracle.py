@@ -39,10 +39,10 @@ def _load():
         up = ctypes.POINTER(ctypes.c_uint8)
         lib.orc_expm.argtypes = [ctypes.c_int, dp, dp]
         lib.orc_expm.restype = ctypes.c_int
-        lib.orc_eval.argtypes = [ctypes.c_int] * 5 + [ip, up, dp, dp, ip, dp, dp, dp, dp,
-                                                      ctypes.c_int, dp,
-                                                      dp, dp, dp, dp, dp, dp, ip, ip]
-        lib.orc_eval.restype = ctypes.c_int
+        lib.orc_eval_tree.argtypes = [ctypes.c_int] * 6 + [ip, up, dp, dp, ip, dp, dp, dp, dp,
+                                                           ctypes.c_int, dp,
+                                                           dp, dp, dp, dp, dp, dp, ip, ip]
+        lib.orc_eval_tree.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -70,6 +70,9 @@ class OracleResult(dict):
 def evaluate(problem: dict, b: np.ndarray | None = None, partials: bool = False,
              patterns: slice | None = None) -> OracleResult:
     """Run the oracle on ``problem`` (a dict from ``workloads``) at branch lengths ``b``.
+
+    The tree has ``problem["n_tips"]`` tips (nodes 0..N-1) and ``len(parent)`` nodes: 2N-1 for a
+    binary tree, fewer when some internal nodes have more than two children.
 
     An optional ``problem["tip_partials"]`` [K][m] holds the partial vectors of partially observed
     tips: code m + k selects row k, codes from m + K on are missing data (all ones).
@@ -99,7 +102,7 @@ def evaluate(problem: dict, b: np.ndarray | None = None, partials: bool = False,
     tv = problem.get("tip_partials")
     tv = None if tv is None or len(tv) == 0 else np.ascontiguousarray(tv, dtype=np.float64)
     n = parent.shape[0]
-    n_tips = (n + 1) // 2
+    n_tips = int(problem.get("n_tips", (n + 1) // 2))   # fewer than n = 2N-1 nodes: multifurcations
     m = Q.shape[1]
     if tv is not None and (tv.ndim != 2 or tv.shape[1] != m):
         raise ValueError("tip_partials must be [K][m]")
@@ -116,7 +119,7 @@ def evaluate(problem: dict, b: np.ndarray | None = None, partials: bool = False,
         pe = np.zeros((n, P), dtype=np.int32)
         qe = np.zeros((n, P), dtype=np.int32)
     dp = ctypes.c_double
-    rc = lib.orc_eval(n_tips, m, P, C, Q.shape[0], _ptr(parent, ctypes.c_int32),
+    rc = lib.orc_eval_tree(n_tips, n, m, P, C, Q.shape[0], _ptr(parent, ctypes.c_int32),
                       _ptr(tips, ctypes.c_uint8), _ptr(w, dp), _ptr(Q, dp),
                       _ptr(bm, ctypes.c_int32), _ptr(pi, dp), _ptr(rates, dp), _ptr(cw, dp),
                       _ptr(b, dp), 0 if tv is None else tv.shape[0], _ptr(tv, dp),

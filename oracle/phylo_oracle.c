@@ -5,13 +5,16 @@
  * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the benchmark's CPU
  * baseline load this file.  It shares no code, header, table or helper with the CUDA library.
  *
- * What it computes, for one rooted binary tree with N tips (nodes 0..N-1) and N-1 internal nodes
+ * What it computes, for one rooted tree with N tips (nodes 0..N-1) and internal nodes N..n-1
  * (root = the node whose parent is -1), m states, C discrete rate categories and P site patterns:
  *   P_{i,l}  = e^{Q_i b_i r_l}                                   (Section 2.1; Section 2.5)
  *   p_k      = (P_{i,l} p_i) o (P_{j,l} p_j)   post-order        (Section 2.3, post-order update)
  *   L_p      = sum_l w_l pi' p_root,l                            (Section 2.3 root inner product;
  *                                                                 Section 2.5 mixture)
  *   q_root   = pi;  q_i = P_{i,l}' [q_k o (P_{j,l} p_j)]   pre-order (Section 2.4)
+ * The paper's tree is binary (n = 2N-1, Section 2.1).  A node with more than two children
+ * (a multifurcation) takes the same updates with the sibling set widened: p_k is the product of
+ * P_c p_c over all its children c, and q_i multiplies q_k by P_s p_s for every sibling s of i.
  *   dlogL/db_i = sum_p wt_p sum_l r_l w_l p_i,l' Q_i' q_i,l / L_p      (Section 2.5 gradient with
  *                                                                 rate categories)
  *   d2logL/db_i^2 = sum_p wt_p [ sum_l r_l^2 w_l p' (Q_i^2)' q / L_p - (per-site gradient)^2 ]
@@ -148,24 +151,27 @@ int orc_expm(int m, const double *A, double *out)
 
 typedef struct {
     int n_nodes, n_tips, root;
-    int *kid0, *kid1;   /* children of each node, -1 for tips */
+    int *kid_off;       /* children of node k: kids[kid_off[k] .. kid_off[k+1]-1] (none for tips) */
+    int *kids;          /* in increasing node order */
     int *order;         /* pre-order (parents before children); reversed = post-order */
 } tree_t;
 
 static void tree_free(tree_t *t)
 {
-    free(t->kid0); free(t->kid1); free(t->order);
+    free(t->kid_off); free(t->kids); free(t->order);
 }
 
-static int tree_build(int n_tips, const int32_t *parent, tree_t *t)
+/* Nodes 0..n_tips-1 are the tips, n_tips..n_nodes-1 internal; every internal node has at least two
+ * children, tips none; one root; every node reachable from it. */
+static int tree_build(int n_tips, int n_nodes, const int32_t *parent, tree_t *t)
 {
-    int n = 2 * n_tips - 1;
+    int n = n_nodes;
     memset(t, 0, sizeof(*t));
+    if (n_tips < 2 || n < n_tips + 1 || n > 2 * n_tips - 1) return ORC_INVALID;
     t->n_nodes = n; t->n_tips = n_tips; t->root = -1;
-    t->kid0 = malloc(n * sizeof(int)); t->kid1 = malloc(n * sizeof(int));
-    t->order = malloc(n * sizeof(int));
-    if (!t->kid0 || !t->kid1 || !t->order) { tree_free(t); return ORC_NOMEM; }
-    for (int i = 0; i < n; ++i) { t->kid0[i] = -1; t->kid1[i] = -1; }
+    t->kid_off = calloc((size_t)n + 1, sizeof(int)); t->kids = malloc((size_t)n * sizeof(int));
+    t->order = malloc((size_t)n * sizeof(int));
+    if (!t->kid_off || !t->kids || !t->order) { tree_free(t); return ORC_NOMEM; }
     for (int i = 0; i < n; ++i) {
         int p = parent[i];
         if (p < 0) {
@@ -173,26 +179,33 @@ static int tree_build(int n_tips, const int32_t *parent, tree_t *t)
             t->root = i;
             continue;
         }
-        if (p >= n || p < n_tips) { tree_free(t); return ORC_INVALID; }
-        if (t->kid0[p] < 0) t->kid0[p] = i;
-        else if (t->kid1[p] < 0) t->kid1[p] = i;
-        else { tree_free(t); return ORC_INVALID; }
+        if (p >= n || p < n_tips || p == i) { tree_free(t); return ORC_INVALID; }
+        t->kid_off[p + 1]++;
     }
-    if (t->root < n_tips && n_tips > 1) { tree_free(t); return ORC_INVALID; }
-    for (int i = n_tips; i < n; ++i)
-        if (t->kid0[i] < 0 || t->kid1[i] < 0) { tree_free(t); return ORC_INVALID; }
+    if (t->root < n_tips) { tree_free(t); return ORC_INVALID; }
+    for (int k = 0; k < n; ++k) {
+        int deg = t->kid_off[k + 1];
+        if (k >= n_tips && deg < 2) { tree_free(t); return ORC_INVALID; }
+        t->kid_off[k + 1] += t->kid_off[k];
+    }
+    int *fill = malloc((size_t)n * sizeof(int));
+    if (!fill) { tree_free(t); return ORC_NOMEM; }
+    for (int k = 0; k < n; ++k) fill[k] = t->kid_off[k];
+    for (int i = 0; i < n; ++i)
+        if (parent[i] >= 0) t->kids[fill[parent[i]]++] = i;
     /* depth-first pre-order from the root */
-    int *stack = malloc(n * sizeof(int));
-    if (!stack) { tree_free(t); return ORC_NOMEM; }
     int top = 0, cnt = 0;
-    stack[top++] = t->root;
+    fill[top++] = t->root;   /* fill doubles as the stack */
     while (top > 0) {
-        int k = stack[--top];
-        if (cnt >= n) { free(stack); tree_free(t); return ORC_INVALID; }
+        int k = fill[--top];
+        if (cnt >= n) { free(fill); tree_free(t); return ORC_INVALID; }
         t->order[cnt++] = k;
-        if (t->kid0[k] >= 0) { stack[top++] = t->kid1[k]; stack[top++] = t->kid0[k]; }
+        for (int c = t->kid_off[k + 1] - 1; c >= t->kid_off[k]; --c) {
+            if (top >= n) { free(fill); tree_free(t); return ORC_INVALID; }
+            fill[top++] = t->kids[c];
+        }
     }
-    free(stack);
+    free(fill);
     if (cnt != n) { tree_free(t); return ORC_INVALID; }   /* unreachable nodes: a cycle */
     return ORC_OK;
 }
@@ -215,24 +228,25 @@ static int rescale(double *v, int len)
 }
 
 /*
- * Inputs (host, FP64 unless stated):
- *   parent[2N-1] (int32), tips[N][P] (uint8), weights[P], Q[n_models][m][m],
- *   branch_model[2N-1] (NULL = model 0), pi[m], rates[C], cat_w[C], b[2N-1] (root entry ignored),
+ * Inputs (host, FP64 unless stated), n = n_nodes (2N-1 for a binary tree, fewer with
+ * multifurcations; tips are nodes 0..N-1, every internal node has at least two children):
+ *   parent[n] (int32), tips[N][P] (uint8), weights[P], Q[n_models][m][m],
+ *   branch_model[n] (NULL = model 0), pi[m], rates[C], cat_w[C], b[n] (root entry ignored),
  *   tip_vecs[K][m] (K = n_tip_vecs >= 0; NULL when K = 0).
  * A tip's partial vector at a pattern (Section 2.1) follows its code y: the indicator of state y
  * for y < m; row y - m of tip_vecs for m <= y < m + K (partially observed data: finite entries
  * >= 0, at least one positive); the all-ones vector (missing data) for y >= m + K.
- * Outputs: logL (scalar), grad[2N-1] (root entry 0), site_logL[P], hess[2N-1] (each may be NULL).
+ * Outputs: logL (scalar), grad[n] (root entry 0), site_logL[P], hess[n] (each may be NULL).
  * Optional introspection (NULL to skip): post[n][P][C][m] and pre[n][P][C][m] scaled partials
  * with their integer log2 factors post_e[n][P], pre_e[n][P] (value = stored * 2^e).
  */
-int orc_eval(int n_tips, int m, int n_patterns, int n_cat, int n_models,
-             const int32_t *parent, const uint8_t *tips, const double *weights,
-             const double *Q, const int32_t *branch_model, const double *pi,
-             const double *rates, const double *cat_w, const double *b,
-             int n_tip_vecs, const double *tip_vecs,
-             double *logL, double *grad, double *site_logL, double *hess,
-             double *post_out, double *pre_out, int32_t *post_e_out, int32_t *pre_e_out)
+int orc_eval_tree(int n_tips, int n_nodes, int m, int n_patterns, int n_cat, int n_models,
+                  const int32_t *parent, const uint8_t *tips, const double *weights,
+                  const double *Q, const int32_t *branch_model, const double *pi,
+                  const double *rates, const double *cat_w, const double *b,
+                  int n_tip_vecs, const double *tip_vecs,
+                  double *logL, double *grad, double *site_logL, double *hess,
+                  double *post_out, double *pre_out, int32_t *post_e_out, int32_t *pre_e_out)
 {
     if (n_tips < 2 || m < 2 || n_patterns < 0 || n_cat < 1 || n_models < 1) return ORC_INVALID;
     if (n_tip_vecs < 0 || (n_tip_vecs > 0 && !tip_vecs)) return ORC_INVALID;
@@ -246,7 +260,7 @@ int orc_eval(int n_tips, int m, int n_patterns, int n_cat, int n_models,
         if (!positive) return ORC_INVALID;
     }
     tree_t t;
-    int rc = tree_build(n_tips, parent, &t);
+    int rc = tree_build(n_tips, n_nodes, parent, &t);
     if (rc != ORC_OK) return rc;
     const int n = t.n_nodes, P = n_patterns, C = n_cat;
     const size_t mm = (size_t)m * m, row = (size_t)C * m;   /* row = one pattern of one node */
@@ -299,23 +313,24 @@ int orc_eval(int n_tips, int m, int n_patterns, int n_cat, int n_models,
                 pe[(size_t)k * P + p] = 0;
                 continue;
             }
-            int ci = t.kid0[k], cj = t.kid1[k];
-            const double *pi_ = post + ((size_t)ci * P + p) * row;
-            const double *pj_ = post + ((size_t)cj * P + p) * row;
-            for (int l = 0; l < C; ++l) {
-                const double *Pi = Pm + ((size_t)ci * C + l) * mm;
-                const double *Pj = Pm + ((size_t)cj * C + l) * mm;
-                for (int s = 0; s < m; ++s) {
-                    double a = 0.0, c2 = 0.0;
-                    for (int x = 0; x < m; ++x) {
-                        a += Pi[s * m + x] * pi_[l * m + x];
-                        c2 += Pj[s * m + x] * pj_[l * m + x];
+            /* p_k = product over the children c of P_c p_c (two children in the paper's
+             * binary tree) */
+            int ek = 0;
+            for (size_t x = 0; x < row; ++x) pk[x] = 1.0;
+            for (int o2 = t.kid_off[k]; o2 < t.kid_off[k + 1]; ++o2) {
+                int c = t.kids[o2];
+                const double *pc = post + ((size_t)c * P + p) * row;
+                for (int l = 0; l < C; ++l) {
+                    const double *Pc = Pm + ((size_t)c * C + l) * mm;
+                    for (int s2 = 0; s2 < m; ++s2) {
+                        double a = 0.0;
+                        for (int x = 0; x < m; ++x) a += Pc[s2 * m + x] * pc[l * m + x];
+                        pk[l * m + s2] *= a;
                     }
-                    pk[l * m + s] = a * c2;
                 }
+                ek += pe[(size_t)c * P + p];
             }
-            pe[(size_t)k * P + p] = pe[(size_t)ci * P + p] + pe[(size_t)cj * P + p]
-                                    + rescale(pk, (int)row);
+            pe[(size_t)k * P + p] = ek + rescale(pk, (int)row);
         }
     }
 
@@ -343,29 +358,36 @@ int orc_eval(int n_tips, int m, int n_patterns, int n_cat, int n_models,
     for (int o = 0; o < n; ++o) {
         int k = t.order[o];
         if (k < n_tips) continue;
-        for (int side = 0; side < 2; ++side) {
-            int ci = side == 0 ? t.kid0[k] : t.kid1[k];   /* child being updated */
-            int cj = side == 0 ? t.kid1[k] : t.kid0[k];   /* its sibling         */
+        for (int oi = t.kid_off[k]; oi < t.kid_off[k + 1]; ++oi) {
+            int ci = t.kids[oi];   /* child being updated; every other child of k is a sibling */
             for (int p = 0; p < P; ++p) {
                 const double *qk = pre + ((size_t)k * P + p) * row;
-                const double *pj_ = post + ((size_t)cj * P + p) * row;
                 double *qi = pre + ((size_t)ci * P + p) * row;
+                int es = 0;
                 for (int l = 0; l < C; ++l) {
-                    const double *Pi = Pm + ((size_t)ci * C + l) * mm;
-                    const double *Pj = Pm + ((size_t)cj * C + l) * mm;
-                    for (int s = 0; s < m; ++s) {
-                        double a = 0.0;
-                        for (int x = 0; x < m; ++x) a += Pj[s * m + x] * pj_[l * m + x];
-                        u[s] = qk[l * m + s] * a;
+                    /* u = q_k o (product over the siblings s of P_s p_s) */
+                    for (int s2 = 0; s2 < m; ++s2) u[s2] = qk[l * m + s2];
+                    for (int oj = t.kid_off[k]; oj < t.kid_off[k + 1]; ++oj) {
+                        int cj = t.kids[oj];
+                        if (cj == ci) continue;
+                        const double *pj_ = post + ((size_t)cj * P + p) * row;
+                        const double *Pj = Pm + ((size_t)cj * C + l) * mm;
+                        for (int s2 = 0; s2 < m; ++s2) {
+                            double a = 0.0;
+                            for (int x = 0; x < m; ++x) a += Pj[s2 * m + x] * pj_[l * m + x];
+                            u[s2] *= a;
+                        }
                     }
+                    const double *Pi = Pm + ((size_t)ci * C + l) * mm;
                     for (int x = 0; x < m; ++x) {
                         double a = 0.0;
-                        for (int s = 0; s < m; ++s) a += Pi[s * m + x] * u[s];
+                        for (int s2 = 0; s2 < m; ++s2) a += Pi[s2 * m + x] * u[s2];
                         qi[l * m + x] = a;
                     }
                 }
-                qe[(size_t)ci * P + p] = qe[(size_t)k * P + p] + pe[(size_t)cj * P + p]
-                                         + rescale(qi, (int)row);
+                for (int oj = t.kid_off[k]; oj < t.kid_off[k + 1]; ++oj)
+                    if (t.kids[oj] != ci) es += pe[(size_t)t.kids[oj] * P + p];
+                qe[(size_t)ci * P + p] = qe[(size_t)k * P + p] + es + rescale(qi, (int)row);
             }
         }
     }
@@ -412,4 +434,18 @@ done:
     free(A); free(Q2); free(u);
     tree_free(&t);
     return rc;
+}
+
+/* The paper's binary tree: n_nodes = 2 n_tips - 1. */
+int orc_eval(int n_tips, int m, int n_patterns, int n_cat, int n_models,
+             const int32_t *parent, const uint8_t *tips, const double *weights,
+             const double *Q, const int32_t *branch_model, const double *pi,
+             const double *rates, const double *cat_w, const double *b,
+             int n_tip_vecs, const double *tip_vecs,
+             double *logL, double *grad, double *site_logL, double *hess,
+             double *post_out, double *pre_out, int32_t *post_e_out, int32_t *pre_e_out)
+{
+    return orc_eval_tree(n_tips, 2 * n_tips - 1, m, n_patterns, n_cat, n_models, parent, tips, weights, Q,
+                         branch_model, pi, rates, cat_w, b, n_tip_vecs, tip_vecs, logL, grad, site_logL, hess,
+                         post_out, pre_out, post_e_out, pre_e_out);
 }

@@ -105,6 +105,50 @@ def root_of(parent: np.ndarray) -> int:
     return int(roots[0])
 
 
+def collapse_edges(parent: np.ndarray, n_tips: int, nodes, b: np.ndarray | None = None):
+    """A tree with multifurcations: every internal non-root node in ``nodes`` is removed and its
+    children are attached to its parent (its branch disappears).  The remaining internal nodes are
+    renumbered in order to stay contiguous after the tips.  Returns ``(parent, b, old)`` with
+    ``old[new_id]`` the node's id in the input tree (``b`` follows the kept nodes; None if not given)."""
+    parent = np.asarray(parent, dtype=np.int64)
+    n = parent.shape[0]
+    drop = set(int(x) for x in nodes)
+    for x in drop:
+        if x < n_tips or parent[x] < 0:
+            raise ValueError(f"node {x} is a tip or the root")
+    keep = [i for i in range(n) if i not in drop]
+    new_id = {old: new for new, old in enumerate(keep)}
+
+    def kept_ancestor(i):
+        p = int(parent[i])
+        while p in drop:
+            p = int(parent[p])
+        return p
+
+    out = np.full(len(keep), -1, dtype=np.int32)
+    for new, old in enumerate(keep):
+        if parent[old] >= 0:
+            out[new] = new_id[kept_ancestor(old)]
+    old_arr = np.array(keep, dtype=np.int64)
+    return out, (None if b is None else np.asarray(b, dtype=np.float64)[old_arr]), old_arr
+
+
+def multifurcating_problem(n_tips, n_patterns, n_collapse, n_states=4, n_cat=1, seed=0, **kw):
+    """random_problem on a Yule tree, then ``n_collapse`` random internal branches collapsed
+    (collapse_edges): nodes of degree 3 and more, the data simulated on the binary tree."""
+    pr = random_problem(n_tips, n_patterns, n_states=n_states, n_cat=n_cat, seed=seed, **kw)
+    rng = np.random.default_rng(seed + 1000)
+    root = root_of(pr["parent"])
+    cand = [i for i in range(n_tips, pr["parent"].shape[0]) if i != root]
+    nodes = rng.choice(cand, size=min(n_collapse, len(cand)), replace=False)
+    parent, b, old = collapse_edges(pr["parent"], n_tips, nodes, pr["b"])
+    out = dict(pr, parent=parent, b=b, n_tips=n_tips)
+    if pr.get("branch_model") is not None:
+        out["branch_model"] = np.ascontiguousarray(pr["branch_model"][old], dtype=np.int32)
+    out["node_time"] = None
+    return out
+
+
 def branch_lengths(parent: np.ndarray, mean: float, rng: np.random.Generator):
     """b_i ~ Exp(mean) for every non-root node; the root entry is 0."""
     b = rng.exponential(mean, size=parent.shape[0])

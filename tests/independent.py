@@ -55,7 +55,7 @@ def brute_force(problem, b=None):
     b = problem["b"] if b is None else b
     parent = problem["parent"]
     n = parent.shape[0]
-    N = (n + 1) // 2
+    N = int(problem.get("n_tips", (n + 1) // 2))
     m = problem["Q"].shape[1]
     tips = problem["tip_states"].astype(np.int64)
     n_pat = tips.shape[1]
@@ -100,7 +100,7 @@ def prune(problem, P, replace=None):
     ``replace`` = (branch, {l: matrix}).  Returns the site likelihoods."""
     parent = problem["parent"]
     n = parent.shape[0]
-    N = (n + 1) // 2
+    N = int(problem.get("n_tips", (n + 1) // 2))
     m = problem["Q"].shape[1]
     C = len(problem["cat_weights"])
     tips = problem["tip_states"]
@@ -189,3 +189,40 @@ def reroot(parent, b, edge_child, frac):
             new_b[v] = lv
             stack.append(v)
     return new_parent, new_b
+
+
+def resolve_zero_length(problem):
+    """A tree with multifurcations as a binary tree: a node with d > 2 children keeps its last child
+    and an added node, which keeps the next-to-last child and another added node, and so on; the
+    last added node takes the first two children.  The d - 2 added branches have length 0 (their
+    transition matrices are the identity).  The original nodes keep their ids; the added ones come
+    after them.  Returns the binary problem (b included) and the number of original nodes."""
+    parent = np.asarray(problem["parent"], dtype=np.int64)
+    n = parent.shape[0]
+    N = int(problem["n_tips"])
+    kids = [[] for _ in range(n)]
+    for i, p in enumerate(parent):
+        if p >= 0:
+            kids[int(p)].append(i)
+    new_parent = list(int(p) for p in parent)
+    b = list(problem["b"])
+    for k in range(n):
+        ch = kids[k]
+        if len(ch) <= 2:
+            continue
+        at = k
+        for j in range(len(ch) - 1, 1, -1):
+            new_parent[ch[j]] = at
+            x = len(new_parent)
+            new_parent.append(at)
+            b.append(0.0)
+            at = x
+        new_parent[ch[0]] = at
+        new_parent[ch[1]] = at
+    assert len(new_parent) == 2 * N - 1
+    out = dict(problem, parent=np.array(new_parent, dtype=np.int32), b=np.array(b), n_tips=N)
+    bm = problem.get("branch_model")
+    if bm is not None:
+        out["branch_model"] = np.concatenate([np.asarray(bm, dtype=np.int32),
+                                              np.zeros(len(new_parent) - n, dtype=np.int32)])
+    return out, n

@@ -314,7 +314,7 @@ def test_rejects_malformed_trees(oracle_mod):
     with pytest.raises(ValueError):
         oracle_mod.evaluate(dict(pr, parent=bad))
     bad = pr["parent"].copy()
-    bad[0] = bad[1] = bad[2] = bad[3]  # a node with too many children
+    bad[0] = bad[1] = bad[2] = bad[3]  # 2N-1 nodes with a node of degree > 2: another has < 2 children
     with pytest.raises(ValueError):
         oracle_mod.evaluate(dict(pr, parent=bad))
     with pytest.raises(ValueError):
