@@ -15,10 +15,11 @@
  *      which equals the paper's q_i' Q_i p_i because e^{Qb} and Q commute)  and optionally the
  *      diagonal of the Hessian (Section 2.6, applied site by site).
  *
- * Conventions.  A problem has N >= 2 tips and 2N-1 nodes.  Tips are nodes 0..N-1, internal
- * nodes N..2N-2 in any order, the root is the one node with parent -1 (the paper numbers tips
- * 1..N and fixes the root at 2N-1, Section 2.1).  A branch is named by its child node, so
- * per-branch arrays have 2N-1 entries and the root entry is ignored (input) or 0 (output).
+ * Conventions.  A problem has N >= 2 tips and n nodes, n = 2N-1 for a binary tree (fewer with
+ * multifurcations, see pg_problem).  Tips are nodes 0..N-1, internal nodes N..n-1 in any order,
+ * the root is the one node with parent -1 (the paper numbers tips 1..N and fixes the root at
+ * 2N-1, Section 2.1).  A branch is named by its child node, so per-branch arrays have n entries
+ * and the root entry is ignored (input) or 0 (output).  Below, "[2N-1]" reads "[n]".
  * All matrices are row-major doubles.  Every call returns a pg_status; no C++ exception crosses
  * this boundary.  The library owns all device memory it allocates; pointers passed in are
  * borrowed for the duration of the call (synchronous calls) or until the stream reaches the
@@ -74,8 +75,17 @@ typedef struct pg_options {
  *                          with m != 4, is rejected with PG_ERR_UNSUPPORTED; m < 2 with
  *                          PG_ERR_INVALID.
  *   n_categories C: 1..4 discrete rate categories (Section 2.5).
- *   parent[2N-1]           parent node of each node, -1 for the root; every internal node must
- *                          have exactly two children (binary tree, Section 2.1).
+ *   n_nodes n              nodes of the tree: 2N-1 for the paper's binary tree (Section 2.1;
+ *                          0 also means 2N-1), fewer when internal nodes have more than two
+ *                          children (a multifurcation), at least N+1.  Tips are nodes 0..N-1,
+ *                          internal nodes N..n-1.  Every per-node array of this problem, of b and
+ *                          of the outputs then has n entries.
+ *   parent[n]              parent node of each node, -1 for the root; every internal node has at
+ *                          least two children.  A node with d > 2 children is evaluated as a
+ *                          chain of d-2 added internal nodes joined by branches of length 0
+ *                          (P = I, so likelihoods and the derivatives in every original branch
+ *                          are those of the multifurcating tree); the added nodes are internal and
+ *                          invisible to the caller.
  *   tip_states[N][P]       code of tip t at pattern p, selecting the tip's partial vector
  *                          (Section 2.1): a code y < m is the observed state y (the indicator
  *                          vector); m <= y < m + K selects row y - m of tip_partials (partially
@@ -90,7 +100,7 @@ typedef struct pg_options {
  *   pattern_weights[P]     multiplicity of each site pattern, finite and >= 0.
  *   Q[n_models][m][m]      CTMC generators: off-diagonals >= 0, rows summing to 0 (|row sum| <=
  *                          1e-10 * max|Q|); neither reversibility nor stationarity is required.
- *   branch_model[2N-1]     generator used on each branch (NULL: model 0 everywhere).
+ *   branch_model[n]        generator used on each branch (NULL: model 0 everywhere).
  *   root_freqs[m]          root state distribution pi (>= 0, sums to 1 within 1e-10), not
  *                          necessarily stationary.
  *   cat_rates[C]           rate multipliers r_l >= 0; cat_weights[C] probabilities (sum 1).
@@ -114,6 +124,7 @@ typedef struct pg_problem {
     int32_t tip_stride;         /* row pitch of tip_states in bytes (>= n_patterns); 0 = n_patterns */
     int32_t n_tip_partials;     /* K: rows of tip_partials (0 = none)                              */
     const double *tip_partials; /* [K][m]                                                          */
+    int32_t n_nodes;            /* n: nodes of the tree, 0 = 2N-1 (binary); fewer: multifurcations */
 } pg_problem;
 
 typedef struct pg_handle_info {

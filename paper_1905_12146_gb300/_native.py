@@ -50,7 +50,7 @@ class pg_problem(ctypes.Structure):
                 ("branch_model", ctypes.c_void_p), ("root_freqs", ctypes.c_void_p),
                 ("cat_rates", ctypes.c_void_p), ("cat_weights", ctypes.c_void_p),
                 ("tip_stride", ctypes.c_int32), ("n_tip_partials", ctypes.c_int32),
-                ("tip_partials", ctypes.c_void_p)]
+                ("tip_partials", ctypes.c_void_p), ("n_nodes", ctypes.c_int32)]
 
 
 class pg_server_options(ctypes.Structure):
@@ -201,10 +201,15 @@ def problem_struct(problem: dict, precision: str = "fp32"):
     n = parent.shape[0]
     P = tips.shape[1] if tips.ndim == 2 else 0
     K, tv = _tip_partials(problem, Q.shape[1])
-    pr = pg_problem((n + 1) // 2, Q.shape[1], P, rates.shape[0], Q.shape[0], PRECISIONS[precision],
+    pr = pg_problem(_n_tips(problem, n), Q.shape[1], P, rates.shape[0], Q.shape[0], PRECISIONS[precision],
                     _np_ptr(parent), _np_ptr(tips), _np_ptr(w), _np_ptr(Q), _np_ptr(bm), _np_ptr(pi),
-                    _np_ptr(rates), _np_ptr(cw), stride if stride != P else 0, K, _np_ptr(tv))
+                    _np_ptr(rates), _np_ptr(cw), stride if stride != P else 0, K, _np_ptr(tv), n)
     return pr, (parent, tips, w, Q, bm, pi, rates, cw, tv)
+
+
+def _n_tips(problem: dict, n: int) -> int:
+    """Tips of a problem with n nodes: problem["n_tips"], else those of a binary tree."""
+    return int(problem.get("n_tips", (n + 1) // 2))
 
 
 class Context:
@@ -251,7 +256,7 @@ class Handle:
             raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
         self.ctx = ctx
         pr, _keep = problem_struct(problem, precision)
-        n = pr.n_tips * 2 - 1
+        n = pr.n_nodes
         self.root = int(np.flatnonzero(_keep[0] < 0)[0])
         out = ctypes.c_void_p()
         check(lib.pg_upload(ctx._ptr, ctypes.byref(pr), ctypes.byref(out)))
@@ -393,9 +398,9 @@ def eval_noalloc(problem: dict, b, precision: str = "fp32", grad=True, hess=Fals
     n = parent.shape[0]
     P = tips.shape[1] if tips.ndim == 2 else 0
     K, tv = _tip_partials(problem, Q.shape[1])
-    pr = pg_problem((n + 1) // 2, Q.shape[1], P, rates.shape[0], Q.shape[0], PRECISIONS[precision],
+    pr = pg_problem(_n_tips(problem, n), Q.shape[1], P, rates.shape[0], Q.shape[0], PRECISIONS[precision],
                     _np_ptr(parent), _np_ptr(tips), _np_ptr(w), _np_ptr(Q), _np_ptr(bm),
-                    _np_ptr(pi), _np_ptr(rates), _np_ptr(cw), 0, K, _np_ptr(tv))
+                    _np_ptr(pi), _np_ptr(rates), _np_ptr(cw), 0, K, _np_ptr(tv), n)
     b = np.ascontiguousarray(b, dtype=np.float64)
     logL = np.zeros(1)
     g = np.zeros(n) if grad else None
@@ -427,7 +432,7 @@ class Server:
 
     def submit(self, problem: dict, b=None, grad=True, hess=False) -> int:
         pr, keep = problem_struct(problem, problem.get("precision", "fp32"))
-        n = pr.n_tips * 2 - 1
+        n = pr.n_nodes
         b = np.ascontiguousarray(problem["b"] if b is None else b, dtype=np.float64)
         if b.shape != (n,):
             raise ValueError(f"b must have shape ({n},)")

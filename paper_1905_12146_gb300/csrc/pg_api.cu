@@ -682,7 +682,8 @@ pg_status pg_upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out) { return
 
 }  // extern "C"
 
-pg_status pg::host::upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out, const Placement *pl) {
+// upload of a binary tree (n = 2N-1 nodes); pg::host::upload resolves multifurcations first
+static pg_status upload_binary(pg_ctx *ctx, const pg_problem *pr, pg_handle **out, const Placement *pl) {
     if (!ctx || !pr || !out) return fail(PG_ERR_INVALID, "NULL argument");
     *out = nullptr;
     const int N = pr->n_tips, m = pr->n_states, P = pr->n_patterns, C = pr->n_categories;
@@ -970,6 +971,94 @@ pg_status pg::host::upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out, c
     return PG_OK;
 }
 
+namespace {
+
+// A tree with multifurcations as a binary tree.  The caller's nodes keep their ids 0..n_user-1; a
+// node k with children c_0 < c_1 < ... < c_{d-1}, d > 2, keeps c_0 and gets the added node x_1, x_1
+// takes c_1 and x_2, ..., x_{d-2} takes c_{d-2} and c_{d-1}.  The added nodes get ids n_user ..
+// 2N-2, model 0 and (at evaluation) branch length 0, so that P = I on their branches: every site
+// likelihood, and the gradient and Hessian entries of every original branch, are those of the
+// multifurcating tree (a branch of length 0 multiplies the partial vector below it by I).
+pg_status resolve_multifurcations(const pg_problem *pr, int n_user, std::vector<int32_t> &par,
+                                  std::vector<int32_t> &bm) {
+    const int N = pr->n_tips, n = 2 * N - 1;
+    if (n_user < N + 1 || n_user > n)
+        return fail(PG_ERR_INVALID, "n_nodes = %d: between n_tips + 1 = %d and 2 n_tips - 1 = %d", n_user, N + 1, n);
+    if (!pr->parent) return fail(PG_ERR_INVALID, "parent is NULL");
+    std::vector<std::vector<int>> kids(n_user);
+    int root = -1;
+    for (int i = 0; i < n_user; ++i) {
+        const int p = pr->parent[i];
+        if (p == -1) {
+            if (root >= 0) return fail(PG_ERR_INVALID, "more than one root (nodes %d and %d)", root, i);
+            root = i;
+            continue;
+        }
+        if (p < N || p >= n_user || p == i)
+            return fail(PG_ERR_INVALID, "parent[%d] = %d is not an internal node", i, p);
+        kids[p].push_back(i);
+    }
+    if (root < 0) return fail(PG_ERR_INVALID, "no root (no node with parent -1)");
+    for (int k = N; k < n_user; ++k)
+        if (kids[k].size() < 2) return fail(PG_ERR_INVALID, "internal node %d has fewer than two children", k);
+    par.assign(n, -1);
+    for (int i = 0; i < n_user; ++i) par[i] = pr->parent[i];
+    int next = n_user;
+    for (int k = N; k < n_user; ++k) {
+        const int d = (int)kids[k].size();
+        int host = k;
+        for (int j = 1; j < d - 1; ++j) {
+            const int x = next++;
+            par[x] = host;
+            par[kids[k][j]] = x;
+            host = x;
+        }
+        par[kids[k][d - 1]] = host;
+    }
+    if (next != n) return fail(PG_ERR_INVALID, "the parent array does not describe a tree");
+    if (pr->branch_model) {
+        bm.assign(n, 0);
+        for (int i = 0; i < n_user; ++i) bm[i] = pr->branch_model[i];
+    }
+    return PG_OK;
+}
+
+}  // namespace
+
+pg_status pg::host::upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out, const Placement *pl) {
+    if (!ctx || !pr || !out) return fail(PG_ERR_INVALID, "NULL argument");
+    *out = nullptr;
+    const int N = pr->n_tips;
+    if (N < 2) return fail(PG_ERR_INVALID, "n_tips = %d (at least 2 required)", N);
+    const int n = 2 * N - 1, n_user = pr->n_nodes ? pr->n_nodes : n;
+    if (n_user == n) {
+        pg_status st = upload_binary(ctx, pr, out, pl);
+        if (st == PG_OK) (*out)->n_user = n;
+        return st;
+    }
+    std::vector<int32_t> par, bm;
+    pg_status st = resolve_multifurcations(pr, n_user, par, bm);
+    if (st != PG_OK) return st;
+    pg_problem rb = *pr;
+    rb.parent = par.data();
+    rb.branch_model = pr->branch_model ? bm.data() : nullptr;
+    rb.n_nodes = n;
+    st = upload_binary(ctx, &rb, out, pl);
+    if (st != PG_OK) return st;
+    pg_handle *h = *out;
+    h->n_user = n_user;
+    h->info.n_nodes = n_user;
+    // the added nodes' branch lengths stay 0: the caller's lengths fill entries 0 .. n_user-1
+    DeviceGuard g(ctx->device);
+    cudaError_t e = dzero(pl, h->io_b, sizeof(double) * n);
+    if (e != cudaSuccess) {
+        pg_free(h);
+        *out = nullptr;
+        return fail(PG_ERR_CUDA, "upload: %s", cudaGetErrorString(e));
+    }
+    return PG_OK;
+}
+
 extern "C" {
 
 pg_status pg_get_info(const pg_handle *h, pg_handle_info *out) {
@@ -1161,6 +1250,59 @@ pg_status check_batch(pg_handle *const *hs, int32_t k) {
     return PG_OK;
 }
 
+// The public entry points take per-node arrays of the caller's n_user nodes.  A handle that holds a
+// resolved multifurcating tree evaluates on its full-size buffers: the branch lengths are copied
+// into io_b (whose added entries stay 0), the gradient and Hessian diagonal are written to io_grad
+// and io_hess and their first n_user entries (the caller's nodes) copied out.
+pg_status enqueue_user(pg_handle *h, int skip, const double *d_b, double *d_logL, double *d_grad, double *d_hess,
+                       double *d_site_logL, const double *d_gscale, cudaStream_t s) {
+    const int nu = h->n_user;
+    if (nu == h->desc.n_nodes)
+        return enqueue_single(h, skip, d_b, d_logL, d_grad, d_hess, d_site_logL, d_gscale, s);
+    const size_t bytes = sizeof(double) * nu;
+    if (d_b) PG_CUDA(cudaMemcpyAsync(h->io_b, d_b, bytes, cudaMemcpyDeviceToDevice, s));
+    pg_status st = enqueue_single(h, skip, d_b ? h->io_b : nullptr, d_logL, d_grad ? h->io_grad : nullptr,
+                                  d_hess ? h->io_hess : nullptr, d_site_logL, d_gscale, s);
+    if (st != PG_OK) return st;
+    if (d_grad) PG_CUDA(cudaMemcpyAsync(d_grad, h->io_grad, bytes, cudaMemcpyDeviceToDevice, s));
+    if (d_hess) PG_CUDA(cudaMemcpyAsync(d_hess, h->io_hess, bytes, cudaMemcpyDeviceToDevice, s));
+    return PG_OK;
+}
+
+// The same for a batch: per-problem pointer arrays with the resolved handles' entries replaced by
+// their full-size buffers (remap_in), and the caller's entries copied out afterwards (remap_out).
+struct BatchPtrs {
+    std::vector<const double *> b;
+    std::vector<double *> g, h;
+};
+pg_status remap_in(pg_handle *const *hs, int32_t k, const double *const *d_b, double *const *d_grad,
+                   double *const *d_hess, cudaStream_t s, BatchPtrs &bp) {
+    if (d_b) bp.b.assign(d_b, d_b + k);
+    if (d_grad) bp.g.assign(d_grad, d_grad + k);
+    if (d_hess) bp.h.assign(d_hess, d_hess + k);
+    for (int i = 0; i < k; ++i) {
+        pg_handle *h = hs[i];
+        if (h->n_user == h->desc.n_nodes) continue;
+        if (d_b && d_b[i]) {
+            PG_CUDA(cudaMemcpyAsync(h->io_b, d_b[i], sizeof(double) * h->n_user, cudaMemcpyDeviceToDevice, s));
+            bp.b[i] = h->io_b;
+        }
+        if (d_grad && d_grad[i]) bp.g[i] = h->io_grad;
+        if (d_hess && d_hess[i]) bp.h[i] = h->io_hess;
+    }
+    return PG_OK;
+}
+pg_status remap_out(pg_handle *const *hs, int32_t k, double *const *d_grad, double *const *d_hess, cudaStream_t s) {
+    for (int i = 0; i < k; ++i) {
+        pg_handle *h = hs[i];
+        if (h->n_user == h->desc.n_nodes) continue;
+        const size_t bytes = sizeof(double) * h->n_user;
+        if (d_grad && d_grad[i]) PG_CUDA(cudaMemcpyAsync(d_grad[i], h->io_grad, bytes, cudaMemcpyDeviceToDevice, s));
+        if (d_hess && d_hess[i]) PG_CUDA(cudaMemcpyAsync(d_hess[i], h->io_hess, bytes, cudaMemcpyDeviceToDevice, s));
+    }
+    return PG_OK;
+}
+
 }  // namespace
 
 pg_status pg::host::enqueue(pg_handle *h, int skip, const double *d_b, double *d_logL, double *d_grad,
@@ -1177,15 +1319,15 @@ pg_status pg_eval_async(pg_handle *h, const double *d_b, double *d_logL, double 
     if (!h || !d_b) return fail(PG_ERR_INVALID, "NULL handle or branch lengths");
     DeviceGuard g(h->ctx->device);
     if (!g.ok) return fail(PG_ERR_CUDA, "cannot select device %d", h->ctx->device);
-    return enqueue_single(h, 0, d_b, d_logL, d_grad, d_hess, d_site_logL, nullptr, static_cast<cudaStream_t>(stream));
+    return enqueue_user(h, 0, d_b, d_logL, d_grad, d_hess, d_site_logL, nullptr, static_cast<cudaStream_t>(stream));
 }
 
 pg_status pg_forward_async(pg_handle *h, const double *d_b, double *d_logL, double *d_site_logL, void *stream) {
     if (!h || !d_b) return fail(PG_ERR_INVALID, "NULL handle or branch lengths");
     DeviceGuard g(h->ctx->device);
     if (!g.ok) return fail(PG_ERR_CUDA, "cannot select device %d", h->ctx->device);
-    return enqueue_single(h, pg::kSkipPre, d_b, d_logL, nullptr, nullptr, d_site_logL, nullptr,
-                          static_cast<cudaStream_t>(stream));
+    return enqueue_user(h, pg::kSkipPre, d_b, d_logL, nullptr, nullptr, d_site_logL, nullptr,
+                        static_cast<cudaStream_t>(stream));
 }
 
 pg_status pg_backward_async(pg_handle *h, const double *d_gscale, double *d_grad, double *d_hess, void *stream) {
@@ -1193,8 +1335,8 @@ pg_status pg_backward_async(pg_handle *h, const double *d_gscale, double *d_grad
     if (!h->have_post) return fail(PG_ERR_INVALID, "no forward pass has been enqueued on this handle");
     DeviceGuard g(h->ctx->device);
     if (!g.ok) return fail(PG_ERR_CUDA, "cannot select device %d", h->ctx->device);
-    return enqueue_single(h, pg::kSkipPost, nullptr, nullptr, d_grad, d_hess, nullptr, d_gscale,
-                          static_cast<cudaStream_t>(stream));
+    return enqueue_user(h, pg::kSkipPost, nullptr, nullptr, d_grad, d_hess, nullptr, d_gscale,
+                        static_cast<cudaStream_t>(stream));
 }
 
 pg_status pg_eval_batch_async(pg_handle *const *hs, int32_t k, const double *const *d_b,
@@ -1205,7 +1347,13 @@ pg_status pg_eval_batch_async(pg_handle *const *hs, int32_t k, const double *con
     for (int i = 0; i < k; ++i)
         if (!d_b[i]) return fail(PG_ERR_INVALID, "batch entry %d is NULL", i);
     if (k == 0) return PG_OK;
-    return enqueue_batch(hs, k, 0, d_b, d_logL, d_grad, d_hess, nullptr, static_cast<cudaStream_t>(stream));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DeviceGuard g(hs[0]->ctx->device);
+    BatchPtrs bp;
+    if (pg_status st = remap_in(hs, k, d_b, d_grad, d_hess, s, bp); st != PG_OK) return st;
+    pg_status st = enqueue_batch(hs, k, 0, bp.b.data(), d_logL, d_grad ? bp.g.data() : nullptr,
+                                 d_hess ? bp.h.data() : nullptr, nullptr, s);
+    return st != PG_OK ? st : remap_out(hs, k, d_grad, d_hess, s);
 }
 
 pg_status pg_forward_batch_async(pg_handle *const *hs, int32_t k, const double *const *d_b, double *d_logL,
@@ -1215,8 +1363,11 @@ pg_status pg_forward_batch_async(pg_handle *const *hs, int32_t k, const double *
     for (int i = 0; i < k; ++i)
         if (!d_b[i]) return fail(PG_ERR_INVALID, "batch entry %d is NULL", i);
     if (k == 0) return PG_OK;
-    return enqueue_batch(hs, k, pg::kSkipPre, d_b, d_logL, nullptr, nullptr, nullptr,
-                         static_cast<cudaStream_t>(stream));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DeviceGuard g(hs[0]->ctx->device);
+    BatchPtrs bp;
+    if (pg_status st = remap_in(hs, k, d_b, nullptr, nullptr, s, bp); st != PG_OK) return st;
+    return enqueue_batch(hs, k, pg::kSkipPre, bp.b.data(), d_logL, nullptr, nullptr, nullptr, s);
 }
 
 pg_status pg_backward_batch_async(pg_handle *const *hs, int32_t k, const double *d_gscale,
@@ -1225,8 +1376,13 @@ pg_status pg_backward_batch_async(pg_handle *const *hs, int32_t k, const double 
     for (int i = 0; i < k; ++i)
         if (!hs[i]->have_post) return fail(PG_ERR_INVALID, "batch entry %d has no forward pass", i);
     if (k == 0) return PG_OK;
-    return enqueue_batch(hs, k, pg::kSkipPost, nullptr, nullptr, d_grad, d_hess, d_gscale,
-                         static_cast<cudaStream_t>(stream));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DeviceGuard g(hs[0]->ctx->device);
+    BatchPtrs bp;
+    if (pg_status st = remap_in(hs, k, nullptr, d_grad, d_hess, s, bp); st != PG_OK) return st;
+    pg_status st = enqueue_batch(hs, k, pg::kSkipPost, nullptr, nullptr, d_grad ? bp.g.data() : nullptr,
+                                 d_hess ? bp.h.data() : nullptr, d_gscale, s);
+    return st != PG_OK ? st : remap_out(hs, k, d_grad, d_hess, s);
 }
 
 namespace {
@@ -1242,6 +1398,9 @@ pg_status enqueue_clock(pg_handle *const *hs, int32_t k, bool grad, const double
         if (!d_eps[i] || !d_t[i] || (grad ? !d_grad_b[i] : !d_b[i]))
             return fail(PG_ERR_INVALID, "clock entry %d has a NULL array", i);
     if (k == 0) return PG_OK;
+    for (int i = 0; i < k; ++i)
+        if (hs[i]->n_user != hs[i]->desc.n_nodes)
+            return fail(PG_ERR_UNSUPPORTED, "clock entry %d: the clock parameterisation takes binary trees only", i);
     DeviceGuard g(hs[0]->ctx->device);
     if (!g.ok) return fail(PG_ERR_CUDA, "cannot select device %d", hs[0]->ctx->device);
     auto *a = new (std::nothrow) pg::ClockArgs<pg::kMaxClock>;
@@ -1350,10 +1509,10 @@ pg_status pg_eval(pg_handle *h, const double *b, double *logL, double *grad, dou
     if (!h || !b) return fail(PG_ERR_INVALID, "NULL handle or branch lengths");
     DeviceGuard g(h->ctx->device);
     if (!g.ok) return fail(PG_ERR_CUDA, "cannot select device %d", h->ctx->device);
-    const int n = h->desc.n_nodes, P = h->desc.P;
+    const int n = h->n_user, P = h->desc.P;   // the caller's nodes; added nodes keep b = 0 in io_b
     PG_CUDA(cudaMemcpy(h->io_b, b, sizeof(double) * n, cudaMemcpyHostToDevice));
-    pg_status st = pg_eval_async(h, h->io_b, h->io_logL, grad ? h->io_grad : nullptr,
-                                 hess ? h->io_hess : nullptr, site_logL ? h->io_site : nullptr, nullptr);
+    pg_status st = enqueue_single(h, 0, h->io_b, h->io_logL, grad ? h->io_grad : nullptr, hess ? h->io_hess : nullptr,
+                                  site_logL ? h->io_site : nullptr, nullptr, nullptr);
     if (st != PG_OK) return st;
     PG_CUDA(cudaStreamSynchronize(nullptr));
     if (logL) PG_CUDA(cudaMemcpy(logL, h->io_logL, sizeof(double), cudaMemcpyDeviceToHost));

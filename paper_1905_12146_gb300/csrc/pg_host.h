@@ -48,6 +48,9 @@ struct pg_handle {
     pg::MDesc md{};
     CUtensorMap tm_post, tm_pre, tm_tab;   // TMA descriptors of the tensor-core kernels (the type is 64-byte aligned)
     bool external = false;    // the device block belongs to a caller's arena (not freed here)
+    // nodes as the caller numbers them: 2N-1, or fewer for a tree with multifurcations, which the
+    // handle holds resolved into a binary tree with added nodes n_user .. 2N-2 (branches of length 0)
+    int n_user = 0;
     const pg::ProbDesc *d_desc = nullptr;   // device copy of desc (batched level kernels read it)
 };
 

@@ -113,6 +113,8 @@ pg_status check_inputs(const pg_problem *pr) {
     if (N < 2 || m < 2 || P < 0 || C < 1 || M < 1) return noalloc_fail(PG_ERR_INVALID, "bad problem sizes");
     if (m != pg::kStates || C > pg::kMaxCat) return noalloc_fail(PG_ERR_UNSUPPORTED, "4 states and at most 4 categories");
     if (pr->n_tip_partials != 0) return noalloc_fail(PG_ERR_UNSUPPORTED, "tip partial vectors need pg_upload");
+    if (pr->n_nodes != 0 && pr->n_nodes != 2 * N - 1)
+        return noalloc_fail(PG_ERR_UNSUPPORTED, "multifurcating trees (n_nodes = %d) need pg_upload", pr->n_nodes);
     if (N > kMaxTips || M > kMaxModels)
         return noalloc_fail(PG_ERR_UNSUPPORTED, "at most %d tips and %d models without allocation", kMaxTips, kMaxModels);
     if (pr->precision != PG_PRECISION_FP32 && pr->precision != PG_PRECISION_FP64)

@@ -164,7 +164,7 @@ pg_status admit(pg_server *S, Request *r, int si) {
         S->arena.release(block);
         return why;
     };
-    const int n = h->desc.n_nodes;
+    const int n = h->n_user;   // the caller's nodes (a multifurcating tree's added nodes stay internal)
     if (sl.cap < result_bytes(n)) {   // grow the slot's pinned buffer (rare)
         cudaStreamSynchronize(sl.stream);
         if (sl.pinned) cudaFreeHost(sl.pinned);
