@@ -258,7 +258,9 @@ def test_codon_transition_tables_against_expm(ctx):
     entry by entry against scipy's expm, for the codon generator over b r from 1e-4 to 5.  A 2-taxon
     tree whose second branch has length 0 (P = I) has site likelihood pi_y2 P(b)[y2, y1], so the 61^2
     patterns (y2, y1) expose every entry of P(b) through the site log-likelihoods.  Off the diagonal
-    P = D; the diagonal is 1 + D."""
+    P = D, small probabilities stay relatively accurate (bound 1e-5; measured 2.5e-6 at b r = 5).  The
+    diagonal is 1 + D in FP32, whose rounding is absolute: about 2^-24 of 1, however small P_ii is at
+    long branches (bound 16 2^-24; measured 1.5e-7 at b r = 5, where the smallest P_ii is 4e-3)."""
     import scipy.linalg as sla
     rng = np.random.default_rng(91)
     m = 61
@@ -269,7 +271,6 @@ def test_codon_transition_tables_against_expm(ctx):
     pr = wl.make_problem(np.array([2, 2, -1], dtype=np.int32), tips, np.ones(m * m), Q, pi,
                          np.array([1.0]), np.array([1.0]), np.array([0.1, 0.0, 0.0]))
     h = ctx.upload(pr)
-    worst = 0.0
     try:
         for t in (1e-4, 1e-3, 1e-2, 0.1, 0.5, 1.0, 2.0, 5.0):
             got = h.eval(np.array([t, 0.0, 0.0]), grad=False, site=True)
@@ -278,11 +279,10 @@ def test_codon_transition_tables_against_expm(ctx):
             Pe = sla.expm(Q * t)
             off = ~np.eye(m, dtype=bool)
             rel_off = np.abs(Pd[off] - Pe[off]) / Pe[off]
-            rel_diag = np.abs(np.diag(Pd) - np.diag(Pe)) / np.diag(Pe)
-            worst = max(worst, rel_off.max(), rel_diag.max())
-            print(f"{ctx.kind} t={t:g}: max rel error off-diagonal {rel_off.max():.2e}, diagonal {rel_diag.max():.2e}, "
+            abs_diag = np.abs(np.diag(Pd) - np.diag(Pe))
+            print(f"{ctx.kind} t={t:g}: max rel error off-diagonal {rel_off.max():.2e}, abs diagonal {abs_diag.max():.2e}, "
                   f"smallest entry {Pe[off].min():.1e}")
             assert (Pd > 0).all()
-            assert rel_off.max() <= 2e-5 and rel_diag.max() <= 2e-5
+            assert rel_off.max() <= 1e-5 and abs_diag.max() <= 16 * 2.0 ** -24
     finally:
         h.close()
