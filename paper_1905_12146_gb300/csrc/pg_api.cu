@@ -725,7 +725,7 @@ static pg_status upload_binary(pg_ctx *ctx, const pg_problem *pr, pg_handle **ou
     if ((int64_t)max_tiles * max_range < (int64_t)P)
         return fail(PG_ERR_UNSUPPORTED, "n_patterns = %d exceeds %d on this device", P, max_tiles * max_range);
     const int Ps = (P + 15) / 16 * 16;   // row stride of per-pattern arrays (16-byte rows for TMA)
-    const int level_ranges = (P + pg::kLevelRange - 1) / pg::kLevelRange;
+    const int level_ranges = (P + pg::level_range(C) - 1) / pg::level_range(C);
     // wide branches use one slot per (range, consumer warp) of the level kernels
     const int slot_cap = std::max((P + 31) / 32 + 3 * max_tiles + 2, level_ranges * (pg::kLevelRange / 32));
     // FP32 problems evaluated alone run every level with at least two blocks per SM of
@@ -1162,18 +1162,29 @@ pg_status enqueue_batch(pg_handle *const *hs, int32_t k, int skip, const double 
                                  nullptr, d_gscale ? d_gscale + i : nullptr, s);
         if (st != PG_OK) return st;
     }
-    auto *a = new (std::nothrow) pg::BatchArgs<pg::kMaxBatch>;
-    if (!a) return fail(PG_ERR_OOM, "host allocation failed");
     for (int key = 0; key < 2 * pg::kMaxCat; ++key) {
         const int C = 1 + key / 2, prec = key % 2;
         std::vector<int> idx;
         for (int i = 0; i < k; ++i)
             if (!hs[i]->mstate && hs[i]->desc.C == C && hs[i]->desc.precision == prec) idx.push_back(i);
-        for (size_t at = 0; at < idx.size(); at += pg::kMaxBatch) {
+        if (idx.empty()) continue;
+        // the fused-kernel, P-build and reduction launches take groups of up to kMaxBatch problems
+        // (descriptors by value); the level launches cover every problem of the key at once
+        const size_t n_groups = (idx.size() + pg::kMaxBatch - 1) / pg::kMaxBatch;
+        std::vector<pg::BatchArgs<pg::kMaxBatch>> groups;
+        try {
+            groups.resize(n_groups);
+        } catch (...) {
+            return fail(PG_ERR_OOM, "host allocation failed");
+        }
+        std::vector<int> cut_of(idx.size());
+        bool hess = false;
+        for (size_t gi = 0; gi < n_groups; ++gi) {
+            pg::BatchArgs<pg::kMaxBatch> &a = groups[gi];
+            const size_t at = gi * pg::kMaxBatch;
             const int cnt = (int)std::min<size_t>(pg::kMaxBatch, idx.size() - at);
-            a->n = cnt;
-            a->tile_base[0] = a->mat_base[0] = a->red_base[0] = 0;
-            bool hess = false;
+            a.n = cnt;
+            a.tile_base[0] = a.mat_base[0] = a.red_base[0] = 0;
             // blocks in proportion to each problem's partial-stream work, one wave in total
             double work = 0.0;
             for (int j = 0; j < cnt; ++j) work += (double)hs[idx[at + j]]->info.stream_bytes + 1.0;
@@ -1195,49 +1206,54 @@ pg_status enqueue_batch(pg_handle *const *hs, int32_t k, int skip, const double 
                 // FP32: every level below the root's in batched level kernels, the root's level
                 // in the fused kernel; FP64: every level in the fused kernel
                 d.cut = (prec == PG_PRECISION_FP32 && d.P > 0) ? d.n_levels - 1 : 0;
+                cut_of[at + j] = d.cut;
                 hess = hess || d.out_hess;
-                a->d[j] = d;
-                a->tile_base[j + 1] = a->tile_base[j] + d.n_tiles;
-                a->mat_base[j + 1] = a->mat_base[j] + d.n_nodes * d.C;
-                a->red_base[j + 1] = a->red_base[j] + d.n_nodes + 1;
+                a.d[j] = d;
+                a.tile_base[j + 1] = a.tile_base[j] + d.n_tiles;
+                a.mat_base[j + 1] = a.mat_base[j] + d.n_nodes * d.C;
+                a.red_base[j + 1] = a.red_base[j] + d.n_nodes + 1;
                 hs[i]->last_stream = s;
                 if (fwd) hs[i]->have_post = true;
             }
-            // one launch per level index across the group: problem j takes part while L < cut_j
-            int max_cut = 0;
-            for (int j = 0; j < cnt; ++j) max_cut = std::max(max_cut, a->d[j].cut);
-            auto level_batch = [&](int L, pg::LevelBatch &lb) {
-                lb.n = 0;
-                lb.base[0] = 0;
-                for (int j = 0; j < cnt; ++j) {
-                    if (L >= a->d[j].cut) continue;
-                    const pg_handle *hj = hs[idx[at + j]];
-                    const int o0 = hj->level_off[L], nd = hj->level_off[L + 1] - o0;
-                    lb.d[lb.n] = hj->d_desc;
-                    lb.o0[lb.n] = o0;
-                    lb.nr[lb.n] = a->d[j].level_ranges;
-                    lb.base[lb.n + 1] = lb.base[lb.n] + nd * a->d[j].level_ranges;
-                    ++lb.n;
-                }
-            };
-            const int n_sm = hs[0]->ctx->n_sm;
-            cudaError_t e = cudaSuccess;
-            pg::LevelBatch lb;
-            if (fwd) e = pg::launch_pmatrix<pg::kMaxBatch>(*a, s);
-            for (int L = 0; fwd && e == cudaSuccess && L < max_cut; ++L) {
-                level_batch(L, lb);
-                if (lb.n) e = pg::launch_post_level_batch(lb, C, n_sm, L == 0, s);
-            }
-            if (e == cudaSuccess) e = pg::launch_tree<pg::kMaxBatch>(*a, hess, s);
-            for (int L = max_cut - 1; bwd && e == cudaSuccess && L >= 0; --L) {
-                level_batch(L, lb);
-                if (lb.n) e = pg::launch_pre_level_batch(lb, C, hess, n_sm, L == 0, s);
-            }
-            if (e == cudaSuccess) e = pg::launch_reduce<pg::kMaxBatch>(*a, hess, s);
-            if (e != cudaSuccess) { delete a; return fail(PG_ERR_CUDA, "launch: %s", cudaGetErrorString(e)); }
         }
+        int max_cut = 0;
+        for (int cu : cut_of) max_cut = std::max(max_cut, cu);
+        const int n_sm = hs[0]->ctx->n_sm;
+        // one launch per level index over every problem that takes part (L < its cut), up to
+        // kMaxLevelBatch problems per launch
+        auto levels = [&](int L, bool post) -> cudaError_t {
+            pg::LevelBatch lb;
+            lb.n = 0;
+            lb.base[0] = 0;
+            for (size_t j = 0; j <= idx.size(); ++j) {
+                if (j == idx.size() || lb.n == pg::kMaxLevelBatch) {
+                    if (lb.n) {
+                        cudaError_t e = post ? pg::launch_post_level_batch(lb, C, n_sm, L == 0, s)
+                                             : pg::launch_pre_level_batch(lb, C, hess, n_sm, L == 0, s);
+                        if (e != cudaSuccess) return e;
+                    }
+                    lb.n = 0;
+                    if (j == idx.size()) break;
+                }
+                if (L >= cut_of[j]) continue;
+                const pg_handle *hj = hs[idx[j]];
+                const int o0 = hj->level_off[L], nd = hj->level_off[L + 1] - o0;
+                lb.d[lb.n] = hj->d_desc;
+                lb.o0[lb.n] = o0;
+                lb.nr[lb.n] = hj->desc.level_ranges;
+                lb.base[lb.n + 1] = lb.base[lb.n] + nd * hj->desc.level_ranges;
+                ++lb.n;
+            }
+            return cudaSuccess;
+        };
+        cudaError_t e = cudaSuccess;
+        for (size_t gi = 0; fwd && e == cudaSuccess && gi < n_groups; ++gi) e = pg::launch_pmatrix<pg::kMaxBatch>(groups[gi], s);
+        for (int L = 0; fwd && e == cudaSuccess && L < max_cut; ++L) e = levels(L, true);
+        for (size_t gi = 0; e == cudaSuccess && gi < n_groups; ++gi) e = pg::launch_tree<pg::kMaxBatch>(groups[gi], hess, s);
+        for (int L = max_cut - 1; bwd && e == cudaSuccess && L >= 0; --L) e = levels(L, false);
+        for (size_t gi = 0; e == cudaSuccess && gi < n_groups; ++gi) e = pg::launch_reduce<pg::kMaxBatch>(groups[gi], hess, s);
+        if (e != cudaSuccess) return fail(PG_ERR_CUDA, "launch: %s", cudaGetErrorString(e));
     }
-    delete a;
     return PG_OK;
 }
 

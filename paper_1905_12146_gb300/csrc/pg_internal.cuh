@@ -40,7 +40,11 @@ constexpr int kMaxCat = 4;      // rate categories held in registers per pattern
 constexpr int kMaxBatch = 32;   // problems per batched launch (kernel-parameter descriptors)
 constexpr int kMaxRange = 1024;  // patterns per thread block of the tree kernel (shared arrays)
 constexpr int kBlock = 256;      // threads per block of the tree kernel
-constexpr int kLevelRange = 128; // patterns per item (and threads per block) of the level kernels
+constexpr int kLevelRange = 128; // consumer threads per block of the level kernels (4 warps)
+// patterns per item of the level kernels for C rate categories: an item's copies and barrier round
+// trips cost the same whatever its size, so with fewer categories (smaller rows) an item takes more
+// patterns (each consumer thread kLevelRange apart), keeping items at several KB
+__host__ __device__ constexpr int level_range(int C) { return C == 1 ? 4 * kLevelRange : (C == 2 ? 2 * kLevelRange : kLevelRange); }
 constexpr int kTaylorDeg = 12;   // degree of the Taylor polynomial of e^{Q t} (||Q t||_1 <= 1/4)
 // FP32 transition table per (branch, category), float4 columns of the 4x4 matrices:
 //   [0..4]   P hi (columns 0..3, then the row sums = P applied to the all-ones vector)
@@ -93,7 +97,7 @@ struct ProbDesc {
     int cut;
     float *site_invL;              // [P] 1 / Lhat_p, written at the root for the level kernels
     int *site_Er;                  // [P] log2 scale of L_p
-    int level_ranges;              // ceil(P / kLevelRange); a wide branch has 4 slots per range
+    int level_ranges;              // ceil(P / level_range(C)); a wide branch has 4 slots per range
     // shared-memory-resident top part (levels >= cut) for the top kernel (pg_top.cu): n_top nodes
     // ops[level_off[cut] ..], children coded per top node: -1 - s for the s-th tip child,
     // [0, n_top) a top node, n_top + b the b-th boundary node (internal, below the cut;
@@ -255,11 +259,12 @@ size_t top_smem_bytes(const ProbDesc &d);
 // one level index of up to kMaxBatch problems in one launch: segment i covers problem
 // d[i]'s nodes [o0[i], o0[i] + nd) x nr[i] pattern ranges, items [base[i], base[i + 1]); d[i] is
 // the problem's descriptor in device memory
+constexpr int kMaxLevelBatch = 128;   // problems per batched level launch (device descriptors)
 struct LevelBatch {
     int n;
-    int base[kMaxBatch + 1];
-    int o0[kMaxBatch], nr[kMaxBatch];
-    const ProbDesc *d[kMaxBatch];
+    int base[kMaxLevelBatch + 1];
+    int o0[kMaxLevelBatch], nr[kMaxLevelBatch];
+    const ProbDesc *d[kMaxLevelBatch];
 };
 cudaError_t launch_post_level_batch(const LevelBatch &lb, int C, int n_sm, bool cherry, cudaStream_t s);
 cudaError_t launch_pre_level_batch(const LevelBatch &lb, int C, bool hess, int n_sm, bool cherry, cudaStream_t s);

@@ -27,12 +27,11 @@ namespace {
 
 using namespace dev;
 
-constexpr int R = kLevelRange;
-
 // CHERRY: every node of the level has two tip children (height-1 nodes), so a stage carries no
-// child partial rows
+// child partial rows.  A stage holds one item of R = level_range(C) patterns.
 template <int C, bool CHERRY = false>
 struct PostStage {
+    static constexpr int R = level_range(C);
     float4 x0[C][CHERRY ? 1 : R], x1[C][CHERRY ? 1 : R];   // children's partial rows
     int e0[R], e1[R];            // children's log2 scales
     uint8_t y0[R], y1[R];        // tip codes
@@ -41,6 +40,7 @@ struct PostStage {
 
 template <int C, bool CHERRY = false>
 struct PreStage {
+    static constexpr int R = level_range(C);
     float4 qk[C][R], x0[C][CHERRY ? 1 : R], x1[C][CHERRY ? 1 : R];
     int eq[R], e0[R], e1[R];
     int er[R];                   // log2 scale of L_p
@@ -51,8 +51,8 @@ struct PreStage {
     float4 qtab[2][4];           // Q columns of both children's models
 };
 
-constexpr int kConsumerWarps = R / 32;
-constexpr int kLevelThreads = R + 32;   // consumers + one producer warp
+constexpr int kConsumerWarps = kLevelRange / 32;
+constexpr int kLevelThreads = kLevelRange + 32;   // consumers + one producer warp
 
 template <class Stage, int STAGES>
 struct Ring {
@@ -75,8 +75,9 @@ __device__ __forceinline__ Item item_of(const ProbDesc &d, int o0, int nr, int j
     const int u = j / nr;
     it.rg = j - u * nr;
     it.op = __ldg(d.ops + o0 + u);
-    it.p0 = it.rg * R;
-    it.cnt = min(R, d.P - it.p0);
+    const int RL = level_range(d.C);
+    it.p0 = it.rg * RL;
+    it.cnt = min(RL, d.P - it.p0);
     return it;
 }
 
@@ -137,9 +138,9 @@ __device__ void issue_pre(const ProbDesc &d, const Item &it, PreStage<C, CHERRY>
     }
 }
 
-// post-order update (Section 2.3) of one item from its stage
+// post-order update (Section 2.3) of pattern t of one item from its stage
 template <int C, bool CHERRY>
-__device__ __forceinline__ void compute_post(const ProbDesc &d, const Item &it, const PostStage<C, CHERRY> &sm, int t) {
+__device__ __forceinline__ void compute_post_one(const ProbDesc &d, const Item &it, const PostStage<C, CHERRY> &sm, int t) {
     if (t >= it.cnt) return;
     const int N = d.n_tips, Ps = d.Ps, k = it.op.x, c0 = it.op.y, c1 = it.op.z;
     const bool t0 = CHERRY || c0 < N, t1 = CHERRY || c1 < N;
@@ -188,12 +189,18 @@ __device__ __forceinline__ void compute_post(const ProbDesc &d, const Item &it, 
     for (int l = 0; l < C; ++l) __stcg(out + ((size_t)(k - N) * C + l) * Ps + p, scale4(v[l], e));
     __stcg(d.pe + (size_t)(k - N) * Ps + p, E + e);
 }
+// the item's patterns t, t + kLevelRange, ... of consumer thread t
+template <int C, bool CHERRY>
+__device__ __forceinline__ void compute_post(const ProbDesc &d, const Item &it, const PostStage<C, CHERRY> &sm, int t) {
+#pragma unroll 1
+    for (int tt = t; tt < PostStage<C, CHERRY>::R; tt += kLevelRange) compute_post_one<C, CHERRY>(d, it, sm, tt);
+}
 
-// pre-order step (Section 2.4) with the branch gradient (2.5) and Hessian diagonal (2.6) for the
-// calling warp's 32 patterns of one item; the warp's sums go to its own slot of both child branches
-// (slot = 4 * range + warp; the reduction adds the slots in a fixed order)
+// pre-order step (Section 2.4) with the branch gradient (2.5) and Hessian diagonal (2.6) of pattern
+// t of one item: writes q of internal children, returns the pattern's weighted branch terms
 template <int C, bool HESS, bool CHERRY>
-__device__ __forceinline__ void compute_pre(const ProbDesc &d, const Item &it, const PreStage<C, CHERRY> &sm, int t) {
+__device__ __forceinline__ void compute_pre_one(const ProbDesc &d, const Item &it, const PreStage<C, CHERRY> &sm, int t,
+                                                float (&sums)[4]) {
     const int N = d.n_tips, Ps = d.Ps, c0 = it.op.y, c1 = it.op.z;
     const bool t0 = CHERRY || c0 < N, t1 = CHERRY || c1 < N;
     const bool active = t < it.cnt;
@@ -238,18 +245,30 @@ __device__ __forceinline__ void compute_pre(const ProbDesc &d, const Item &it, c
         __stcg(d.qe + (size_t)(c1 - N) * Ps + p, Eq + E0 + e);
     }
     const float d0 = ldexpf(g0, dE) * inv, d1 = ldexpf(g1, dE) * inv;
-    float sums[4];
-    sums[0] = wt * d0;
-    sums[1] = wt * d1;
-    sums[2] = HESS ? wt * (ldexpf(h0, dE) * inv - d0 * d0) : 0.f;
-    sums[3] = HESS ? wt * (ldexpf(h1, dE) * inv - d1 * d1) : 0.f;
-    const int lane = t & 31, slot = it.rg * kConsumerWarps + (t >> 5);
+    sums[0] = wt != 0.f ? wt * d0 : 0.f;
+    sums[1] = wt != 0.f ? wt * d1 : 0.f;
+    sums[2] = (HESS && wt != 0.f) ? wt * (ldexpf(h0, dE) * inv - d0 * d0) : 0.f;
+    sums[3] = (HESS && wt != 0.f) ? wt * (ldexpf(h1, dE) * inv - d1 * d1) : 0.f;
+}
+// the item's patterns t, t + kLevelRange, ... of consumer thread t; the warp's sums (32 patterns at a
+// time in FP32, those added in FP64) go to its own slot of both child branches (slot = 4 * range +
+// warp; the reduction adds the slots in a fixed order)
+template <int C, bool HESS, bool CHERRY>
+__device__ __forceinline__ void compute_pre(const ProbDesc &d, const Item &it, const PreStage<C, CHERRY> &sm, int t) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 1
+    for (int tt = t; tt < PreStage<C, CHERRY>::R; tt += kLevelRange) {
+        float sums[4];
+        compute_pre_one<C, HESS, CHERRY>(d, it, sm, tt, sums);
 #pragma unroll
-    for (int s = 0; s < (HESS ? 4 : 2); ++s) {   // 32 patterns summed in FP32
-        const float v = warp_sum_f(wt != 0.f ? sums[s] : 0.f);
-        if (lane == 0) {
+        for (int s = 0; s < (HESS ? 4 : 2); ++s) acc[s] += (double)warp_sum_f(sums[s]);
+    }
+    const int lane = t & 31, slot = it.rg * kConsumerWarps + (t >> 5);
+    if (lane == 0) {
+#pragma unroll
+        for (int s = 0; s < (HESS ? 4 : 2); ++s) {
             double *dst = (s < 2) ? d.gpart : d.hpart;
-            dst[(size_t)((s & 1) ? c1 : c0) * d.slot_cap + slot] = (double)v;
+            dst[(size_t)((s & 1) ? it.op.z : it.op.y) * d.slot_cap + slot] = acc[s];
         }
     }
 }

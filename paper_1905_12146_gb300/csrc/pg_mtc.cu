@@ -132,57 +132,6 @@ __device__ __forceinline__ void tma_store_3d(const CUtensorMap *m, const void *s
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
 
-// ---- clusters and distributed shared memory -------------------------------------------------------
-__device__ __forceinline__ uint32_t cluster_rank() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
-    return r;
-}
-// the shared::cluster address of the same byte in CTA `rank` of the cluster
-__device__ __forceinline__ uint32_t peer_addr(const void *p, uint32_t rank) {
-    uint32_t r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
-    return r;
-}
-__device__ __forceinline__ void st_cluster4(uint32_t addr, float4 v) {
-    asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"r"(addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
-                 : "memory");
-}
-__device__ __forceinline__ void st_cluster_u32(uint32_t addr, uint32_t v) {
-    asm volatile("st.shared::cluster.u32 [%0], %1;\n" ::"r"(addr), "r"(v) : "memory");
-}
-// an arrival on a barrier of another CTA of the cluster, releasing this thread's prior writes
-__device__ __forceinline__ void mbar_arrive_remote(uint32_t addr) {
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];\n" ::"r"(addr) : "memory");
-}
-// a wait that acquires at cluster scope (data written by the other CTA through shared::cluster)
-__device__ __forceinline__ bool mbar_try_wait_cl(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ void cluster_sync_all() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
-}
-// a barrier among the `n` threads (a multiple of 32) that name barrier `id`
-__device__ __forceinline__ void named_sync(uint32_t id, uint32_t n) {
-    asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(n) : "memory");
-}
-
-// the same with a vote: true iff `pred` holds in every one of the n threads
-__device__ __forceinline__ bool named_sync_and(uint32_t id, uint32_t n, bool pred) {
-    uint32_t r;
-    asm volatile("{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n barrier.red.and.pred p, %2, %3, q;\n selp.u32 %0, 1, 0, p;\n}\n"
-                 : "=r"(r)
-                 : "r"((uint32_t)pred), "r"(id), "r"(n)
-                 : "memory");
-    return r != 0;
-}
-
 // byte offset of 16-byte chunk cc (states 4 cc .. 4 cc + 3) of row r of a swizzled tile of `rows`
 // rows: two 32-state K blocks, rows 128 bytes apart, chunk index XOR (row mod 8)
 __device__ __forceinline__ uint32_t sw(int r, int cc, int rows) {
@@ -711,7 +660,6 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
     unsigned char *X[2] = {sm, sm + kRowTile};                 // children's rows (staging)
     unsigned char *QK = sm + 2 * kRowTile;                      // q_k rows
     // per child 64 KB: [D; G] hi in the lower half (then D^T hi | lo), [D; G] lo in the upper half
-    // (then the staged result q_c)
     unsigned char *T[2] = {sm + 3 * kRowTile, sm + 3 * kRowTile + 4 * kTab};
     enum { BX = 0, BQ = 1, BTH = 2, BTL = 3, BD = 4, BM = 5, NB = 6 };   // rows, q_k, [D;G] hi, lo, D^T, products
     __shared__ __align__(8) uint64_t bar[NB], drain_bar;
@@ -746,7 +694,6 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
     uint32_t ph[NB] = {0, 0, 0, 0, 0, 0};
     bool pend[NB] = {false, false, false, false, false, false};
     bool ok = true;
-    bool store_pending = false;   // (leader) results of the previous category still being read from the upper halves
     // copies (thread 0): rows of the internal children, q_k, tables
     auto issue_rows = [&](int l) {
         uint32_t bytes = 0;
@@ -845,13 +792,6 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
                 mma_tile_ta(acc, xa, tb, 2 * kMP, false);
                 if (!tip[side] || TV) mma_tile_ta(acc, xa + 64, tb, 2 * kMP, true);
             }
-            // while those run: the previous results leave the upper halves, this category's lo
-            // tables take their place
-            if (l > l0) {
-                if (store_pending) bulk_wait_read0();
-                store_pending = false;
-                issue_tables_lo(l);
-            }
         }
         if (!wait(BTL)) break;
         if (leader) {
@@ -864,6 +804,7 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
             mma_commit(&bar[BM]);
         }
         if (!wait(BM)) break;
+        if (leader && l + 1 < l1) issue_tables_lo(l + 1);   // the upper halves have been read
         if (leader && !any_int && l + 1 < l1) issue_tables_hi(l + 1);   // no D^T products: the lower halves are free
         // the D^T tables of the internal children into their (now free) table slots
         if (leader && any_int) {
@@ -947,8 +888,8 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
             if (leader && l + 1 < l1) issue_tables_hi(l + 1);   // the D^T tables have been read
         }
         if (any_int) {
-            // epilogue 2: q_c = qt_c + D_c^T qt_c, scaled, staged in the upper half of the child's
-            // table slot and stored by TMA
+            // epilogue 2: q_c = qt_c + D_c^T qt_c, scaled by its largest state and stored from
+            // registers (each thread writes its half row, 128 contiguous bytes of the column)
             tc_after();
             for (int side = 0; side < 2; ++side) {
                 if (tip[side]) continue;
@@ -975,6 +916,7 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
                 if (tip[side]) continue;
                 const uint32_t qa = lane_base + 256 + 128 * side, acc = lane_base + 128 * side;
                 const int e = scale_exponent(fmaxf(half_part[side][0][t], half_part[side][1][t]));
+                float4 *dst = reinterpret_cast<float4 *>(d.pre + (((size_t)(cs[side] - N) * C + l) * d.Ps + p0 + t) * kMP);
 #pragma unroll
                 for (int i = 0; i < 2; ++i) {
                     float a[16], q[16];
@@ -983,20 +925,13 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
                     tmem_wait_ld();
 #pragma unroll
                     for (int j = 0; j < 16; ++j) a[j] += q[j];
-                    put16(T[side] + 2 * kTab, t, ch0 + i, a, e);
+                    if (on) {
+#pragma unroll
+                        for (int q4 = 0; q4 < 4; ++q4)
+                            __stcg(dst + 4 * (ch0 + i) + q4, scale4(f4(a[4 * q4], a[4 * q4 + 1], a[4 * q4 + 2], a[4 * q4 + 3]), e));
+                    }
                 }
                 if (on && hf == 0) __stcg(d.qe + ((size_t)(cs[side] - N) * C + l) * d.Ps + p0 + t, Eq + Ex[1 - side] + e);
-            }
-            fence_async_smem();
-            __syncthreads();
-            if (leader) {
-                for (int side = 0; side < 2; ++side) {
-                    if (tip[side]) continue;
-                    for (int kb = 0; kb < 2; ++kb)
-                        tma_store_3d(&tm_pre, T[side] + 2 * kTab + kb * kRowKB, kb * 32, p0, (cs[side] - N) * C + l);
-                }
-                bulk_commit();
-                store_pending = true;   // waited for before the next lo tables are copied over them
             }
         }
         tc_before();
@@ -1023,420 +958,13 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
         // let every copy (barriers BX .. BD) and product in flight finish
         if (!drain_block(&drain_bar, bar, ph, pend, BM)) atomicOr(d.status, kStatusUnsettled);
     }
-    if (leader) bulk_wait_read0();   // the staging smem is read before the block exits
     tc_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
-// ---- pre-order level without the Hessian, one child per block: two-block clusters -------------------
-// A cluster of two blocks takes one item (node k, category group, 128-pattern tile); block r takes
-// child c = c_r of k (its sibling is s = c_{1-r}).  Per category it forms A = x_c [D_c; G_c]^T (D_c x_c
-// and u = G_c x_c), sends a_c = x_c + D_c x_c to the sibling's block through distributed shared
-// memory, receives a_s, forms the top-of-branch vector qt_c = q_k o a_s (q_root = pi), the branch
-// term qt_c . u (Section 2.5) and, for an internal child, q_c = qt_c + D_c^T qt_c (Section 2.4),
-// scaled and stored by TMA.
-// Warp roles: warp 0 lane 0 issues the TMA copies, warp 1 owns the tensor memory and its lane 0
-// issues the products, warps 2..9 are the epilogue (two warps per TMEM lane quadrant, each half of
-// the 64 states of its 32 rows).  Tensor memory holds two categories in buffers of 256 columns
-// ([D;G] accumulator 0..127, the rows' FP32 values 128..191 read by the MMA as TF32, their TF32
-// remainders 192..255; after the first epilogue qt takes the rows' place and D^T qt the first 64
-// accumulator columns), so the products of one category run while the epilogues of another do.
-// The epilogue runs, per category i: epilogue 1 of i, epilogue 2 of i - 1, the rows of i + 1; the
-// products run D^T of i, then [D; G] of i + 1.
-// Every wait is bounded and also ends when either block of the cluster has given up (a flag each
-// block sets in both blocks' shared memory); then every copy and product in flight is waited for
-// (bounded), tensor memory is released, and the two blocks leave together.
-constexpr int kClThreads = 320;
-constexpr int kClEpi = 256;   // epilogue threads (warps 2 .. 9)
-constexpr uint32_t kClXS = 0, kClQK = kRowTile, kClTDG = 2 * kRowTile, kClTDT = 2 * kRowTile + 4 * kTab;
-constexpr uint32_t kClXA = 2 * kRowTile + 6 * kTab, kClST = 3 * kRowTile + 6 * kTab;
-constexpr size_t kPreClSmem = 4 * kRowTile + 6 * kTab;   // 224 KB; the statics below bring it to 227 KB
-
-struct __align__(1024) PreClShared {
-    // copies: rows of the child, q_k, [D;G] hi|lo, D^T hi|lo ("full" by TMA bytes, "free" when read)
-    uint64_t rows_full, rows_free, qk_full, qk_free, tdg_full, tdg_free, tdt_full, tdt_free;
-    // per tensor-memory buffer: rows written, [D;G] products done, qt written, D^T products done
-    uint64_t rows_tmem[2], dg_done[2], qt_ready[2], dt_done[2];
-    // the exchange of a = x + D x: xa_full when the sibling's block has written this block's XA,
-    // xa_free when the sibling's block has read what this block wrote into its XA
-    uint64_t xa_full, xa_free, drain;
-    uint32_t tmem_slot;
-    volatile int abort;
-    double red[kClEpi / 32];
-    float half[2][kTcTile];        // the two half-row partial dot products / maxima of each row
-    unsigned char pad[3072 - 19 * 8 - 8 - 8 * 8 - 2 * kTcTile * 4];
-};
-static_assert(sizeof(PreClShared) == 3072, "the statics must keep the dynamic region 1024-byte aligned");
-
-// waits for phase `parity` of own barrier `bar` (cluster-scope acquire), bounded, and gives up early
-// when either block of the cluster has given up
-__device__ __forceinline__ bool wait_cl(uint64_t *bar, uint32_t parity, const volatile int *abort) {
-    const long long t0 = clock64();
-    while (!mbar_try_wait_cl(bar, parity)) {
-        if (*abort) return false;
-        if (clock64() - t0 > kWaitLimitCycles) return false;
-    }
-    return true;
-}
-
-template <bool TV>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kClThreads, 1)
-m_pre_cl_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtensorMap tm_post,
-                const __grid_constant__ CUtensorMap tm_pre, const __grid_constant__ CUtensorMap tm_tab, int o0, int n_pt,
-                int n_cg) {
-    extern __shared__ __align__(1024) unsigned char tc_raw[];
-    __shared__ PreClShared S;
-    if (smem_u32(tc_raw) & 1023u) {   // the same in both blocks of the cluster: both leave here
-        if (threadIdx.x == 0) atomicOr(d.status, kStatusTimeout);
-        return;
-    }
-    unsigned char *sm = tc_raw;
-    unsigned char *XS = sm + kClXS, *QK = sm + kClQK, *TDG = sm + kClTDG, *TDT = sm + kClTDT, *XA = sm + kClXA,
-                  *ST = sm + kClST;
-    const uint32_t rank = cluster_rank(), peer = rank ^ 1u;
-    const int C = d.C, N = d.n_tips, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // item = (node, category group, tile); the cluster's two blocks share it
-    const int item = blockIdx.x >> 1;
-    const int u = item / (n_cg * n_pt), rg = item - u * (n_cg * n_pt), g = rg / n_pt, pt = rg - g * n_pt;
-    const int G = (C + n_cg - 1) / n_cg, l0 = g * G, l1 = min(C, l0 + G), n_l = l1 - l0;
-    const int4 op = __ldg(d.ops + o0 + u);
-    const int k = op.x, p0 = pt * kTcTile, cnt = min(kTcTile, d.P - p0);
-    const bool root = k == d.root;
-    const int c = rank ? op.z : op.y, s = rank ? op.y : op.z;   // this block's child and its sibling
-    const bool tip = c < N, stip = s < N;
-    if (threadIdx.x == 0) {
-        mbar_init(&S.rows_full, 1);
-        mbar_init(&S.rows_free, 8);
-        mbar_init(&S.qk_full, 1);
-        mbar_init(&S.qk_free, 8);
-        mbar_init(&S.tdg_full, 1);
-        mbar_init(&S.tdg_free, 1);
-        mbar_init(&S.tdt_full, 1);
-        mbar_init(&S.tdt_free, 1);
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(&S.rows_tmem[b], 8);
-            mbar_init(&S.dg_done[b], 1);
-            mbar_init(&S.qt_ready[b], 8);
-            mbar_init(&S.dt_done[b], 1);
-        }
-        mbar_init(&S.xa_full, kClEpi);
-        mbar_init(&S.xa_free, kClEpi);
-        S.abort = 0;
-    }
-    if (warp == 1) tmem_alloc(&S.tmem_slot, 512);
-    tc_before();
-    cluster_sync_all();   // barriers initialised in both blocks before any remote arrival
-    tc_after();
-    const uint32_t tmem = S.tmem_slot;
-    const uint32_t abort_peer = peer_addr((const void *)&S.abort, peer);
-    auto give_up = [&]() {   // this block gives up: both blocks' waits end
-        atomicOr(d.status, kStatusTimeout);
-        S.abort = 1;
-        st_cluster_u32(abort_peer, 1u);
-    };
-    bool ok = true;
-    // the last phase of each copy barrier the producer started (drained below if a role gave up)
-    bool pend_rows = false, pend_qk = false, pend_tdg = false, pend_tdt = false;
-    uint32_t ph_rows = 0, ph_qk = 0, ph_tdg = 0, ph_tdt = 0;
-
-    if (warp == 0) {
-        // ---- copies (lane 0): per category the child's rows, q_k, [D;G] hi|lo, D^T hi|lo ----
-        if (lane == 0) {
-            for (int i = 0; i < n_l && ok; ++i) {
-                const int l = l0 + i;
-                if (!tip) {   // into XS once the previous category's rows are in tensor memory
-                    if (i > 0 && !(ok = wait_cl(&S.rows_free, (uint32_t)(i - 1) & 1u, &S.abort))) break;
-                    mbar_arrive_expect(&S.rows_full, kRowTile);
-                    for (int kb = 0; kb < 2; ++kb)
-                        tma_load_3d(XS + kb * kRowKB, &tm_post, kb * 32, p0, (c - N) * C + l, &S.rows_full);
-                    pend_rows = true;
-                    ph_rows = (uint32_t)i & 1u;
-                }
-                if (i > 0 && !(ok = wait_cl(&S.tdg_free, (uint32_t)(i - 1) & 1u, &S.abort))) break;
-                mbar_arrive_expect(&S.tdg_full, 4 * kTab);
-                load_tables(TDG, &tm_tab, d, c, l, kTcD, 2, &S.tdg_full);
-                load_tables(TDG + 2 * kTab, &tm_tab, d, c, l, kTcDlo, 2, &S.tdg_full);
-                pend_tdg = true;
-                ph_tdg = (uint32_t)i & 1u;
-                if (!root) {
-                    if (i > 0 && !(ok = wait_cl(&S.qk_free, (uint32_t)(i - 1) & 1u, &S.abort))) break;
-                    mbar_arrive_expect(&S.qk_full, kRowTile);
-                    for (int kb = 0; kb < 2; ++kb)
-                        tma_load_3d(QK + kb * kRowKB, &tm_pre, kb * 32, p0, (k - N) * C + l, &S.qk_full);
-                    pend_qk = true;
-                    ph_qk = (uint32_t)i & 1u;
-                }
-                if (!tip) {
-                    if (i > 0 && !(ok = wait_cl(&S.tdt_free, (uint32_t)(i - 1) & 1u, &S.abort))) break;
-                    mbar_arrive_expect(&S.tdt_full, 2 * kTab);
-                    load_tables(TDT, &tm_tab, d, c, l, kTcDT, 1, &S.tdt_full);
-                    load_tables(TDT + kTab, &tm_tab, d, c, l, kTcDTlo, 1, &S.tdt_full);
-                    pend_tdt = true;
-                    ph_tdt = (uint32_t)i & 1u;
-                }
-            }
-            if (!ok) give_up();
-        }
-    } else if (warp == 1) {
-        // ---- products (lane 0): [D;G] of category 0, then per category i: D^T of i, [D;G] of i+1 ----
-        if (lane == 0) {
-            auto dg = [&](int i) -> bool {
-                const uint32_t b = (uint32_t)i & 1u, base = tmem + 256u * b;
-                if (!wait_cl(&S.rows_tmem[b], (uint32_t)(i >> 1) & 1u, &S.abort)) return false;
-                if (!wait_cl(&S.tdg_full, (uint32_t)i & 1u, &S.abort)) return false;
-                tc_after();
-                const uint32_t tb = smem_u32(TDG);
-                mma_tile_ta(base, base + 128, tb, 2 * kMP, false);
-                mma_tile_ta(base, base + 128, tb + 2 * kTab, 2 * kMP, true);
-                if (!tip || TV) mma_tile_ta(base, base + 192, tb, 2 * kMP, true);
-                mma_commit(&S.dg_done[b]);
-                mma_commit(&S.tdg_free);
-                return true;
-            };
-            auto dt = [&](int i) -> bool {
-                const uint32_t b = (uint32_t)i & 1u, base = tmem + 256u * b;
-                if (!wait_cl(&S.qt_ready[b], (uint32_t)(i >> 1) & 1u, &S.abort)) return false;
-                if (!wait_cl(&S.tdt_full, (uint32_t)i & 1u, &S.abort)) return false;
-                tc_after();
-                const uint32_t tb = smem_u32(TDT);
-                mma_tile_ta(base, base + 128, tb, kMP, false);
-                mma_tile_ta(base, base + 128, tb + kTab, kMP, true);
-                mma_tile_ta(base, base + 192, tb, kMP, true);
-                mma_commit(&S.dt_done[b]);
-                mma_commit(&S.tdt_free);
-                return true;
-            };
-            ok = n_l > 0 ? dg(0) : true;
-            for (int i = 0; i < n_l && ok; ++i) {
-                if (!tip) ok = dt(i);
-                if (ok && i + 1 < n_l) ok = dg(i + 1);
-            }
-            if (!ok) give_up();
-            // every product issued (and, after a failure, any still running) completes before the
-            // tensor memory is released: a fresh barrier tracks them all
-            mbar_init(&S.drain, 1);
-            mma_commit(&S.drain);
-            if (!mbar_wait_bounded(&S.drain, 0u, kWaitLimitCycles)) atomicOr(d.status, kStatusUnsettled);
-        }
-    } else {
-        // ---- epilogue: warps 2..9.  Warp w reads TMEM lanes 32 (w % 4) .. + 31 = rows t and half
-        // (w - 2) / 4 of the states (chunks 2 hf, 2 hf + 1).  A wait that fails ends this warp's
-        // data work (eok, warp-uniform) but no barrier is skipped; results are written only when
-        // every epilogue thread succeeded. ----
-        const int ew = warp - 2, q4 = warp & 3, hf = ew >> 2;
-        const int t = 32 * q4 + lane, ch0 = 2 * hf;
-        const uint32_t lane_off = (uint32_t)(32 * q4) << 16;
-        const bool on = t < cnt;
-        const bool elected = ew == 0 && lane == 0;   // issues the TMA stores of q_c
-        const float inv = on ? __ldcg(d.site_invL + p0 + t) : 0.f;
-        const int Er = on ? __ldcg(d.site_Er + p0 + t) : 0;
-        const int y = (tip && on) ? (int)__ldg(d.tips + (size_t)c * d.Ps + p0 + t) : -1;
-        const uint32_t xa_peer = peer_addr(XA, peer);
-        const uint32_t xa_full_peer = peer_addr(&S.xa_full, peer), xa_free_peer = peer_addr(&S.xa_free, peer);
-        bool eok = true, store_pending = false;
-        float dsum = 0.f;
-        auto wait_e = [&](uint64_t *bar, uint32_t ph) {
-            const bool r = eok && wait_cl(bar, ph, &S.abort);
-            eok = __all_sync(0xffffffffu, r) != 0;
-            if (!eok && lane == 0) give_up();
-            return eok;
-        };
-        auto arrive_warp = [&](uint64_t *bar) {
-            __syncwarp();
-            if (lane == 0) mbar_arrive(bar);
-        };
-        // the child's rows of category i into tensor-memory buffer i & 1 (FP32 values and TF32 remainders)
-        auto rows = [&](int i) {
-            const uint32_t col = tmem + lane_off + 256u * ((uint32_t)i & 1u) + 128u;
-            if (tip) {
-#pragma unroll 1
-                for (int ch = ch0; ch < ch0 + 2; ++ch) {
-                    float x[16];
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int st = 16 * ch + j;
-                        if constexpr (TV) x[j] = tip_value(d, y, st);
-                        else x[j] = (y >= 0 && (y >= d.m ? st < d.m : st == y)) ? 1.f : 0.f;
-                    }
-                    tmem_st16(col + ch * 16, x);
-                    if constexpr (TV) {   // rows of partially observed tips need their remainders
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) x[j] = tf32_lo(x[j]);
-                        tmem_st16(col + 64 + ch * 16, x);
-                    }
-                }
-            } else if (wait_e(&S.rows_full, (uint32_t)i & 1u)) {
-#pragma unroll 1
-                for (int ch = ch0; ch < ch0 + 2; ++ch) {
-                    float x[16];
-                    row16(XS, t, ch, x);
-                    tmem_st16(col + ch * 16, x);
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) x[j] = tf32_lo(x[j]);
-                    tmem_st16(col + 64 + ch * 16, x);
-                }
-            }
-            tmem_wait_st();
-            tc_before();
-            if (!tip) arrive_warp(&S.rows_free);
-            arrive_warp(&S.rows_tmem[(uint32_t)i & 1u]);
-        };
-        // epilogue 1 of category i: a_c to the sibling's block, qt_c = q_k o a_s, the branch term,
-        // qt_c (and remainder) over the rows in tensor memory; returns E_q + E_s of its exponents
-        auto epi1 = [&](int i) -> int {
-            const int l = l0 + i;
-            const uint32_t base = tmem + lane_off + 256u * ((uint32_t)i & 1u);
-            float uu[32];
-            if (wait_e(&S.dg_done[(uint32_t)i & 1u], (uint32_t)(i >> 1) & 1u) &&
-                (i == 0 || wait_e(&S.xa_free, (uint32_t)(i - 1) & 1u))) {
-                tc_after();
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int ch = ch0 + h;
-                    float a[16], x[16];
-                    tmem_ld16(base + ch * 16, a);
-                    tmem_ld16(base + 128 + ch * 16, x);
-                    tmem_ld16(base + 64 + ch * 16, uu + 16 * h);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        st_cluster4(xa_peer + sw(t, ch * 4 + q, kTcTile),
-                                    f4(a[4 * q] + x[4 * q], a[4 * q + 1] + x[4 * q + 1], a[4 * q + 2] + x[4 * q + 2],
-                                       a[4 * q + 3] + x[4 * q + 3]));
-                }
-            }
-            mbar_arrive_remote(xa_full_peer);   // every thread, once per category
-            const int Eq = (on && !root) ? __ldcg(d.qe + ((size_t)(k - N) * C + l) * d.Ps + p0 + t) : 0;
-            const int Ec = (on && !tip) ? __ldcg(d.pe + ((size_t)(c - N) * C + l) * d.Ps + p0 + t) : 0;
-            const int Es = (on && !stip) ? __ldcg(d.pe + ((size_t)(s - N) * C + l) * d.Ps + p0 + t) : 0;
-            float dot = 0.f;
-            if (wait_e(&S.xa_full, (uint32_t)i & 1u) && (root || wait_e(&S.qk_full, (uint32_t)i & 1u))) {
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int ch = ch0 + h;
-                    float as[16], qk[16], qt[16];
-                    row16(XA, t, ch, as);
-                    if (root) {
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) qk[j] = d.pif[16 * ch + j];
-                    } else {
-                        row16(QK, t, ch, qk);
-                    }
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        qt[j] = qk[j] * as[j];
-                        dot = fmaf(qt[j], uu[16 * h + j], dot);
-                    }
-                    if (!tip) {
-                        tmem_st16(base + 128 + ch * 16, qt);
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) qt[j] = tf32_lo(qt[j]);
-                        tmem_st16(base + 192 + ch * 16, qt);
-                    }
-                }
-            }
-            mbar_arrive_remote(xa_free_peer);   // this block's XA has been read
-            if (!root) arrive_warp(&S.qk_free);
-            if (!tip) {
-                tmem_wait_st();
-                tc_before();
-                arrive_warp(&S.qt_ready[(uint32_t)i & 1u]);
-            }
-            S.half[hf][t] = dot;
-            named_sync(1, kClEpi);
-            if (eok && hf == 0) dsum += (float)d.cw[l] * ldexpf(S.half[0][t] + S.half[1][t], Eq + Ec + Es - Er) * inv;
-            named_sync(1, kClEpi);   // half[] read before it is written again
-            return Eq + Es;
-        };
-        // epilogue 2 of category i (internal child): q_c = qt_c + D_c^T qt_c, scaled by its largest
-        // state, staged and stored by TMA, with its exponent qb + e
-        auto epi2 = [&](int i, int qb) {
-            const int l = l0 + i;
-            const uint32_t base = tmem + lane_off + 256u * ((uint32_t)i & 1u);
-            float v[2][16];
-            float mx = 0.f;
-            if (wait_e(&S.dt_done[(uint32_t)i & 1u], (uint32_t)(i >> 1) & 1u)) {
-                tc_after();
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    float qq[16];
-                    tmem_ld16(base + (ch0 + h) * 16, v[h]);
-                    tmem_ld16(base + 128 + (ch0 + h) * 16, qq);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        v[h][j] += qq[j];
-                        mx = fmaxf(mx, v[h][j]);
-                    }
-                }
-                tc_before();
-            }
-            S.half[hf][t] = mx;
-            if (elected && store_pending) bulk_wait_read0();   // the previous store has read the staging tile
-            store_pending = false;
-            named_sync(1, kClEpi);
-            const int e = scale_exponent(fmaxf(S.half[0][t], S.half[1][t]));
-            if (eok) {
-#pragma unroll
-                for (int h = 0; h < 2; ++h) put16(ST, t, ch0 + h, v[h], e);
-                if (on && hf == 0) __stcg(d.qe + ((size_t)(c - N) * C + l) * d.Ps + p0 + t, qb + e);
-            }
-            fence_async_smem();
-            const bool all_ok = named_sync_and(1, kClEpi, eok);
-            if (elected && all_ok) {
-                for (int kb = 0; kb < 2; ++kb)
-                    tma_store_3d(&tm_pre, ST + kb * kRowKB, kb * 32, p0, (c - N) * C + l);
-                bulk_commit();
-                store_pending = true;
-            }
-        };
-        // per category i: epilogue 1 of i, epilogue 2 of i - 1, the rows of i + 1
-        if (n_l > 0) rows(0);
-        int qb_prev = 0;
-        for (int i = 0; i < n_l; ++i) {
-            const int qb = epi1(i);
-            if (!tip && i > 0) epi2(i - 1, qb_prev);
-            if (i + 1 < n_l) rows(i + 1);
-            qb_prev = qb;
-        }
-        if (!tip && n_l > 0) epi2(n_l - 1, qb_prev);
-        if (elected) bulk_wait_read0();   // the staging tile is read before the block leaves
-        // this block's branch: sum over the tile's patterns of w_p d_p (each row once)
-        const double w = (on && hf == 0) ? d.weights[p0 + t] : 0.0;
-        double gs = (eok && w != 0.0) ? w * (double)dsum : 0.0;
-        gs = warp_sum(gs);
-        if (lane == 0) S.red[ew] = gs;
-        const bool all_ok = named_sync_and(1, kClEpi, eok);
-        if (elected && all_ok) {
-            double v = 0.0;
-            for (int j = 0; j < kClEpi / 32; ++j) v += S.red[j];
-            double *slots = d.gpart + (size_t)c * d.n_gslots;
-            slots[g * n_pt + pt] = v;
-            if (g == n_cg - 1)   // the slots of groups this launch does not have stay zero
-                for (int j = n_cg; j < C; ++j) slots[j * n_pt + pt] = 0.0;
-        }
-        if (!all_ok && elected) atomicOr(d.status, kStatusTimeout);
-    }
-
-    tc_before();
-    __syncthreads();
-    // When every role finished, each copy was waited for by its consumer.  After a give-up the
-    // copies issued last may still be landing: the producer waits for each (bounded) before the
-    // block's shared memory is released.
-    if (warp == 0 && lane == 0 && S.abort) {
-        bool settled = true;
-        if (pend_rows) settled = mbar_wait_bounded(&S.rows_full, ph_rows, kWaitLimitCycles) && settled;
-        if (pend_qk) settled = mbar_wait_bounded(&S.qk_full, ph_qk, kWaitLimitCycles) && settled;
-        if (pend_tdg) settled = mbar_wait_bounded(&S.tdg_full, ph_tdg, kWaitLimitCycles) && settled;
-        if (pend_tdt) settled = mbar_wait_bounded(&S.tdt_full, ph_tdt, kWaitLimitCycles) && settled;
-        if (!settled) atomicOr(d.status, kStatusUnsettled);
-    }
-    __syncthreads();
-    if (warp == 1) tmem_dealloc(tmem, 512);
-    cluster_sync_all();   // neither block leaves while the other may still write into its memory
-}
-
+// no alignment slack: the static shared memory is padded so that the dynamic region starts on a
+// 1024-byte boundary (checked in the kernel), and rows + tables + statics fill the 227 KB limit
 constexpr size_t kPre2TcSmem = 3 * kRowTile + 8 * kTab;
 constexpr size_t kPostTcSmem = 1024 + kRowTile + 2 * kTab;
 constexpr size_t kPreTcSmem = 1024 + 4 * kRowTile + 4 * kTab + kRowTile;
@@ -1482,19 +1010,6 @@ cudaError_t launch_pre_tc2(const MDesc &d, const void *tm_post, const void *tm_p
     return cudaGetLastError();
 }
 
-template <bool TV>
-cudaError_t launch_pre_cl(const MDesc &d, const void *tm_post, const void *tm_pre, const void *tm_tab, int o0, int nd,
-                          int n_pt, int n_cg, cudaStream_t s) {
-    static DeviceOnce once;   // the shared-memory attribute, once per device
-    if (cudaError_t e = device_once(once, [](int &) { return cudaFuncSetAttribute(m_pre_cl_kernel<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPreClSmem); }); e != cudaSuccess)
-        return e;
-    // two blocks (a cluster) per item
-    m_pre_cl_kernel<TV><<<2 * nd * n_cg * n_pt, kClThreads, kPreClSmem, s>>>(
-        d, *static_cast<const CUtensorMap *>(tm_post), *static_cast<const CUtensorMap *>(tm_pre),
-        *static_cast<const CUtensorMap *>(tm_tab), o0, n_pt, n_cg);
-    return cudaGetLastError();
-}
-
 }  // namespace
 
 cudaError_t launch_m_post_level_tc(const MDesc &d, const void *tm_post, const void *tm_tab, int o0, int nd,
@@ -1526,9 +1041,9 @@ cudaError_t launch_m_pre_level_tc(const MDesc &d, const void *tm_post, const voi
     if (hess)
         return tv ? launch_pre_tc<true, true>(d, tm_post, tm_pre, tm_tab, o0, nd, n_pt, s)
                   : launch_pre_tc<true, false>(d, tm_post, tm_pre, tm_tab, o0, nd, n_pt, s);
-    const int n_cg = pre_category_groups(d.C, nd * n_pt, n_sm / 2);   // a cluster of two blocks per item
-    return tv ? launch_pre_cl<true>(d, tm_post, tm_pre, tm_tab, o0, nd, n_pt, n_cg, s)
-              : launch_pre_cl<false>(d, tm_post, tm_pre, tm_tab, o0, nd, n_pt, n_cg, s);
+    const int n_cg = pre_category_groups(d.C, nd * n_pt, n_sm);
+    return tv ? launch_pre_tc2<true>(d, tm_post, tm_pre, tm_tab, o0, nd, n_pt, n_cg, s)
+              : launch_pre_tc2<false>(d, tm_post, tm_pre, tm_tab, o0, nd, n_pt, n_cg, s);
 }
 
 }  // namespace pg
