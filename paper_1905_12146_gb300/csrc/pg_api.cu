@@ -239,6 +239,14 @@ struct Carver {
     }
 };
 
+// The per-evaluation arrays of a problem (partials, their exponents, per-branch slot sums, per-site
+// values): in the problem's own block, or in an external region shared by the pattern chunks of a
+// problem that is evaluated chunk by chunk (the chunks run one after another on one stream).
+struct Scratch {
+    char *base = nullptr;
+    size_t bytes = 0;
+};
+
 // Splits the P patterns of a problem into `target` blocks of contiguous ranges (fewer when the
 // ranges would otherwise hold less than one pattern or more than max_range).
 void set_tiling(pg::ProbDesc &d, int target, int max_range) {
@@ -360,7 +368,8 @@ pg_status encode_map(CUtensorMap *m, void *base, int rank, const cuuint64_t *dim
 
 // upload of a problem on the general path (pg_mstate.cu, pg_mtc.cu, pg_mcherry.cu kernels): any
 // state count but 4, and 4-state problems with tip partial vectors
-pg_status upload_m(pg_ctx *ctx, const pg_problem *pr, const TreePlan &tp, pg_handle **out, const Placement *pl) {
+pg_status upload_m(pg_ctx *ctx, const pg_problem *pr, const TreePlan &tp, pg_handle **out, const Placement *pl,
+                   const Scratch *ext, size_t *scratch_need) {
     const int N = pr->n_tips, m = pr->n_states, P = pr->n_patterns, C = pr->n_categories, M = pr->n_models;
     const int n = 2 * N - 1, H = (int)tp.level_off.size() - 1;
     const int KP = pg::kMP;
@@ -409,18 +418,26 @@ pg_status upload_m(pg_ctx *ctx, const pg_problem *pr, const TreePlan &tp, pg_han
     const size_t o_mu = cv.take<double>(mu.size());
     const size_t o_bm = pr->branch_model ? cv.take<int>(n) : 0;
     const bool tc = !(ctx->flags & PG_FLAG_SIMT_MSTATE);
-    const size_t o_tab = cv.take<float>((size_t)n * C * (tc ? (size_t)pg::kTcKinds * KP * KP
+    Carver sc;   // per-evaluation arrays (see Scratch)
+    const size_t o_tab = sc.take<float>((size_t)n * C * (tc ? (size_t)pg::kTcKinds * KP * KP
                                                               : (size_t)pg::kTabKinds * pg::kTabFloats));
     const size_t part = (size_t)(N - 1) * C * Ps * KP;
-    const size_t o_post = cv.take<float>(part), o_pre = cv.take<float>(part);
-    const size_t o_pe = cv.take<int>((size_t)(N - 1) * C * Ps), o_qe = cv.take<int>((size_t)(N - 1) * C * Ps);
+    const size_t o_post = sc.take<float>(part), o_pre = sc.take<float>(part);
+    const size_t o_pe = sc.take<int>((size_t)(N - 1) * C * Ps), o_qe = sc.take<int>((size_t)(N - 1) * C * Ps);
     // gradient slots per branch: the SIMT kernel's pattern tiles, or the tensor-core kernel's
     // 128-pattern tiles x category groups (at most one group per category)
     const int n_gslots = tc ? ((P + pg::kTcTile - 1) / pg::kTcTile) * C : n_pt;
-    const size_t o_gp = cv.take<double>((size_t)n * std::max(n_gslots, 1));
-    const size_t o_hp = cv.take<double>((size_t)n * std::max(n_gslots, 1));
-    const size_t o_lp = cv.take<double>(std::max(n_lb, 1)), o_st = cv.take<int>(1);
-    const size_t o_sinv = cv.take<float>(std::max(Ps, 16)), o_ser = cv.take<int>(std::max(Ps, 16));
+    const size_t o_gp = sc.take<double>((size_t)n * std::max(n_gslots, 1));
+    const size_t o_hp = sc.take<double>((size_t)n * std::max(n_gslots, 1));
+    const size_t o_lp = sc.take<double>(std::max(n_lb, 1)), o_st = cv.take<int>(1);
+    const size_t o_sinv = sc.take<float>(std::max(Ps, 16)), o_ser = sc.take<int>(std::max(Ps, 16));
+    const size_t scratch_bytes = align_up(sc.off, 256);
+    if (ext && ext->bytes < scratch_bytes) return fail(PG_ERR_INVALID, "shared scratch too small");
+    const size_t o_scr = ext ? 0 : cv.take<char>(scratch_bytes);
+    if (scratch_need) {
+        *scratch_need = scratch_bytes;
+        return PG_OK;
+    }
     const size_t o_par = cv.take<int>(n);
     const size_t o_ib = cv.take<double>(n), o_il = cv.take<double>(1), o_ig = cv.take<double>(n);
     const size_t o_ih = cv.take<double>(n), o_is = cv.take<double>(std::max(P, 1));
@@ -460,6 +477,7 @@ pg_status upload_m(pg_ctx *ctx, const pg_problem *pr, const TreePlan &tp, pg_han
         return fail(PG_ERR_CUDA, "upload: %s", cudaGetErrorString(e));
     }
     pg::MDesc &d = h->md;
+    char *scr = ext ? ext->base : base + o_scr;
     d.ops = reinterpret_cast<const int4 *>(base + o_ops);
     d.level_off = reinterpret_cast<const int *>(base + o_lv);
     d.tips = reinterpret_cast<const uint8_t *>(base + o_tips);
@@ -471,17 +489,17 @@ pg_status upload_m(pg_ctx *ctx, const pg_problem *pr, const TreePlan &tp, pg_han
     d.QT = reinterpret_cast<const float *>(base + o_QT);
     d.mu = reinterpret_cast<const double *>(base + o_mu);
     d.bmodel = pr->branch_model ? reinterpret_cast<const int *>(base + o_bm) : nullptr;
-    d.tabs = reinterpret_cast<float *>(base + o_tab);
-    d.post = reinterpret_cast<float *>(base + o_post);
-    d.pre = reinterpret_cast<float *>(base + o_pre);
-    d.pe = reinterpret_cast<int *>(base + o_pe);
-    d.qe = reinterpret_cast<int *>(base + o_qe);
-    d.gpart = reinterpret_cast<double *>(base + o_gp);
-    d.hpart = reinterpret_cast<double *>(base + o_hp);
-    d.lpart = reinterpret_cast<double *>(base + o_lp);
+    d.tabs = reinterpret_cast<float *>(scr + o_tab);
+    d.post = reinterpret_cast<float *>(scr + o_post);
+    d.pre = reinterpret_cast<float *>(scr + o_pre);
+    d.pe = reinterpret_cast<int *>(scr + o_pe);
+    d.qe = reinterpret_cast<int *>(scr + o_qe);
+    d.gpart = reinterpret_cast<double *>(scr + o_gp);
+    d.hpart = reinterpret_cast<double *>(scr + o_hp);
+    d.lpart = reinterpret_cast<double *>(scr + o_lp);
     d.status = reinterpret_cast<int *>(base + o_st);
-    d.site_invL = reinterpret_cast<float *>(base + o_sinv);
-    d.site_Er = reinterpret_cast<int *>(base + o_ser);
+    d.site_invL = reinterpret_cast<float *>(scr + o_sinv);
+    d.site_Er = reinterpret_cast<int *>(scr + o_ser);
     d.n_tips = N;
     d.n_nodes = n;
     d.root = tp.root;
@@ -660,6 +678,12 @@ pg_status pg_free(pg_handle *h) {
     if (!h) return PG_OK;
     pg_ctx *c = h->ctx;
     DeviceGuard g(c->device);
+    for (pg_handle *ch : h->chunks) pg_free(ch);   // a problem evaluated in pattern chunks
+    if (h->scratch_block) {
+        cudaFree(h->scratch_block);
+        std::lock_guard<std::mutex> gl(c->mu);
+        c->used -= h->scratch_bytes;
+    }
     for (cudaEvent_t x : h->events) cudaEventDestroy(x);
     if (h->block && !h->external) cudaFree(h->block);
     {
@@ -683,7 +707,9 @@ pg_status pg_upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out) { return
 }  // extern "C"
 
 // upload of a binary tree (n = 2N-1 nodes); pg::host::upload resolves multifurcations first
-static pg_status upload_binary(pg_ctx *ctx, const pg_problem *pr, pg_handle **out, const Placement *pl) {
+// (scratch_need: only compute the bytes of the per-evaluation arrays, allocate nothing)
+static pg_status upload_binary(pg_ctx *ctx, const pg_problem *pr, pg_handle **out, const Placement *pl,
+                               const Scratch *ext = nullptr, size_t *scratch_need = nullptr) {
     if (!ctx || !pr || !out) return fail(PG_ERR_INVALID, "NULL argument");
     *out = nullptr;
     const int N = pr->n_tips, m = pr->n_states, P = pr->n_patterns, C = pr->n_categories;
@@ -714,7 +740,7 @@ static pg_status upload_binary(pg_ctx *ctx, const pg_problem *pr, pg_handle **ou
     if (st != PG_OK) return st;
     // the 4-state kernels take state codes and missing data only; tip partial vectors run on the
     // general path
-    if (m != pg::kStates || pr->n_tip_partials > 0) return upload_m(ctx, pr, tp, out, pl);
+    if (m != pg::kStates || pr->n_tip_partials > 0) return upload_m(ctx, pr, tp, out, pl, ext, scratch_need);
 
     const int n = 2 * N - 1;
     const int H = (int)tp.level_off.size() - 1;
@@ -773,17 +799,25 @@ static pg_status upload_binary(pg_ctx *ctx, const pg_problem *pr, pg_handle **ou
     const size_t o_Qd = cv.take<double>((size_t)M * 16), o_Qf = cv.take<float4>((size_t)M * 4);
     const size_t o_Mp = cv.take<double>((size_t)M * (pg::kTaylorDeg + 1) * 16), o_qn = cv.take<double>(M);
     const size_t o_bm = pr->branch_model ? cv.take<int>(n) : 0;
-    const size_t o_P = f64 ? cv.take<double2>((size_t)n * C * pg::kPtab64Pairs)
-                           : cv.take<float4>((size_t)n * C * pg::kPtabCols);
+    Carver sc;   // per-evaluation arrays (see Scratch)
+    const size_t o_P = f64 ? sc.take<double2>((size_t)n * C * pg::kPtab64Pairs)
+                           : sc.take<float4>((size_t)n * C * pg::kPtabCols);
     const size_t part = (size_t)(N - 1) * C * Ps * (f64 ? 2 : 1);   // float4 or 2 x double2
-    const size_t o_post = f64 ? cv.take<double2>(part) : cv.take<float4>(part);
-    const size_t o_pre = f64 ? cv.take<double2>(part) : cv.take<float4>(part);
-    const size_t o_pe = cv.take<int>((size_t)(N - 1) * Ps), o_qe = cv.take<int>((size_t)(N - 1) * Ps);
-    const size_t o_gp = cv.take<double>((size_t)n * slot_cap), o_hp = cv.take<double>((size_t)n * slot_cap);
-    const size_t o_lp = cv.take<double>(slot_cap), o_st = cv.take<int>(1);
-    const size_t o_plv = cv.take<int>(n), o_sinv = cv.take<float>(std::max(Ps, 16));
+    const size_t o_post = f64 ? sc.take<double2>(part) : sc.take<float4>(part);
+    const size_t o_pre = f64 ? sc.take<double2>(part) : sc.take<float4>(part);
+    const size_t o_pe = sc.take<int>((size_t)(N - 1) * Ps), o_qe = sc.take<int>((size_t)(N - 1) * Ps);
+    const size_t o_gp = sc.take<double>((size_t)n * slot_cap), o_hp = sc.take<double>((size_t)n * slot_cap);
+    const size_t o_lp = sc.take<double>(slot_cap), o_st = cv.take<int>(1);
+    const size_t o_plv = cv.take<int>(n), o_sinv = sc.take<float>(std::max(Ps, 16));
     const size_t o_desc = cv.take<pg::ProbDesc>(1);
-    const size_t o_ser = cv.take<int>(std::max(Ps, 16));
+    const size_t o_ser = sc.take<int>(std::max(Ps, 16));
+    const size_t scratch_bytes = align_up(sc.off, 256);
+    if (ext && ext->bytes < scratch_bytes) return fail(PG_ERR_INVALID, "shared scratch too small");
+    const size_t o_scr = ext ? 0 : cv.take<char>(scratch_bytes);
+    if (scratch_need) {
+        *scratch_need = scratch_bytes;
+        return PG_OK;
+    }
     const size_t o_tc = cv.take<int2>(top_code.size()), o_bn = cv.take<int>(std::max(n_bnd, 1));
     const size_t o_par = cv.take<int>(n);
     const size_t o_ib = cv.take<double>(n), o_il = cv.take<double>(1), o_ig = cv.take<double>(n);
@@ -866,19 +900,20 @@ static pg_status upload_binary(pg_ctx *ctx, const pg_problem *pr, pg_handle **ou
     d.Mpow = reinterpret_cast<const double *>(base + o_Mp);
     d.qnorm = reinterpret_cast<const double *>(base + o_qn);
     d.bmodel = pr->branch_model ? reinterpret_cast<const int *>(base + o_bm) : nullptr;
-    d.Ptab = f64 ? nullptr : reinterpret_cast<float4 *>(base + o_P);
-    d.Ptab64 = f64 ? reinterpret_cast<double2 *>(base + o_P) : nullptr;
-    d.post = base + o_post;
-    d.pre = base + o_pre;
-    d.pe = reinterpret_cast<int *>(base + o_pe);
-    d.qe = reinterpret_cast<int *>(base + o_qe);
-    d.gpart = reinterpret_cast<double *>(base + o_gp);
-    d.hpart = reinterpret_cast<double *>(base + o_hp);
-    d.lpart = reinterpret_cast<double *>(base + o_lp);
+    char *scr = ext ? ext->base : base + o_scr;
+    d.Ptab = f64 ? nullptr : reinterpret_cast<float4 *>(scr + o_P);
+    d.Ptab64 = f64 ? reinterpret_cast<double2 *>(scr + o_P) : nullptr;
+    d.post = scr + o_post;
+    d.pre = scr + o_pre;
+    d.pe = reinterpret_cast<int *>(scr + o_pe);
+    d.qe = reinterpret_cast<int *>(scr + o_qe);
+    d.gpart = reinterpret_cast<double *>(scr + o_gp);
+    d.hpart = reinterpret_cast<double *>(scr + o_hp);
+    d.lpart = reinterpret_cast<double *>(scr + o_lp);
     d.status = reinterpret_cast<int *>(base + o_st);
     d.plevel = reinterpret_cast<const int *>(base + o_plv);
-    d.site_invL = reinterpret_cast<float *>(base + o_sinv);
-    d.site_Er = reinterpret_cast<int *>(base + o_ser);
+    d.site_invL = reinterpret_cast<float *>(scr + o_sinv);
+    d.site_Er = reinterpret_cast<int *>(scr + o_ser);
     d.level_ranges = level_ranges;
     d.n_top = n_top;
     d.n_bnd = n_bnd;
@@ -1025,6 +1060,151 @@ pg_status resolve_multifurcations(const pg_problem *pr, int n_user, std::vector<
 
 }  // namespace
 
+namespace {
+
+// A problem whose arrays do not fit the context's budget (or the device) as a whole.  Sites are
+// i.i.d. (Section 2.1): the log-likelihood, gradient and Hessian diagonal of the alignment are the
+// sums of those of contiguous pattern slices.  The problem is uploaded as K chunks of Pc patterns (a
+// multiple of 128, K doubling until it fits) whose per-evaluation arrays (partials, exponents, slot
+// sums) share one region sized for one chunk, so the device holds one chunk's partials at a time;
+// the parent handle runs the chunks one after another and sums their results in a fixed order.
+pg_status upload_chunked(pg_ctx *ctx, const pg_problem *pr, pg_handle **out) {
+    const int P = pr->n_patterns, n = 2 * pr->n_tips - 1;
+    const size_t stride = pr->tip_stride ? (size_t)pr->tip_stride : (size_t)P;
+    const std::string whole = pg::host::g_err;   // why the whole problem did not fit
+    auto add_used = [&](long long bytes) {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        ctx->used += bytes;
+    };
+    for (int K = 2;; K *= 2) {
+        const int Pc = ((P + K - 1) / K + 127) / 128 * 128;
+        if (Pc >= P) {
+            if (Pc <= 128) break;
+            continue;
+        }
+        const int nk = (P + Pc - 1) / Pc;
+        pg_problem c0 = *pr;
+        c0.n_patterns = Pc;
+        c0.tip_stride = (int32_t)stride;
+        size_t need = 0;
+        pg_handle *unused = nullptr;
+        pg_status st = upload_binary(ctx, &c0, &unused, nullptr, nullptr, &need);
+        if (st != PG_OK) return st;
+        // the shared scratch, then the parent's block: io arrays, b of the last forward, parts
+        DeviceGuard g(ctx->device);
+        void *scratch = nullptr, *pblock = nullptr;
+        if (acquire_block(ctx, nullptr, need, &scratch) != PG_OK) {
+            if (Pc <= 128) break;
+            continue;
+        }
+        add_used((long long)need);
+        Carver cv;
+        const size_t o_ib = cv.take<double>(n), o_il = cv.take<double>(1), o_ig = cv.take<double>(n);
+        const size_t o_ih = cv.take<double>(n), o_is = cv.take<double>(std::max(P, 1)), o_bf = cv.take<double>(n);
+        const size_t o_pt = cv.take<double>((size_t)nk * (1 + 2 * (size_t)n));
+        const size_t pbytes = align_up(cv.off, 256);
+        std::vector<pg_handle *> chunks;
+        auto undo = [&]() {
+            for (pg_handle *c : chunks) pg_free(c);
+            if (pblock) {
+                cudaFree(pblock);
+                add_used(-(long long)pbytes);
+            }
+            cudaFree(scratch);
+            add_used(-(long long)need);
+        };
+        if (acquire_block(ctx, nullptr, pbytes, &pblock) != PG_OK) {
+            pblock = nullptr;
+            undo();
+            if (Pc <= 128) break;
+            continue;
+        }
+        add_used((long long)pbytes);
+        Scratch ext;
+        ext.base = static_cast<char *>(scratch);
+        ext.bytes = need;
+        bool room = true;
+        for (int j = 0; j < nk; ++j) {
+            pg_problem cj = *pr;
+            cj.n_patterns = std::min(Pc, P - j * Pc);
+            cj.tip_stride = (int32_t)stride;
+            cj.tip_states = pr->tip_states + (size_t)j * Pc;
+            cj.pattern_weights = pr->pattern_weights + (size_t)j * Pc;
+            pg_handle *ch = nullptr;
+            st = upload_binary(ctx, &cj, &ch, nullptr, &ext);
+            if (st == PG_ERR_OOM) {
+                room = false;
+                break;
+            }
+            if (st != PG_OK) {
+                undo();
+                return st;
+            }
+            ch->n_user = n;
+            chunks.push_back(ch);
+        }
+        if (!room) {
+            undo();
+            if (Pc <= 128) break;
+            continue;
+        }
+        pg_handle *h = new (std::nothrow) pg_handle;
+        if (!h) {
+            undo();
+            return fail(PG_ERR_OOM, "host allocation failed");
+        }
+        {
+            std::lock_guard<std::mutex> gl(ctx->mu);   // the parent owns its chunks
+            for (pg_handle *c : chunks)
+                ctx->handles.erase(std::remove(ctx->handles.begin(), ctx->handles.end(), c), ctx->handles.end());
+            ctx->handles.push_back(h);
+        }
+        pg_handle *c0h = chunks[0];
+        h->ctx = ctx;
+        h->block = pblock;
+        h->bytes = pbytes;
+        h->desc = c0h->desc;   // tree, sizes and model of the problem (pointers of chunk 0)
+        h->desc.P = P;
+        h->mstate = c0h->mstate;
+        h->md = c0h->md;
+        h->n_user = n;
+        h->chunks = chunks;
+        for (int j = 0; j < nk; ++j) h->chunk_p0.push_back(j * Pc);
+        h->scratch_block = scratch;
+        h->scratch_bytes = need;
+        char *base = static_cast<char *>(pblock);
+        h->io_b = reinterpret_cast<double *>(base + o_ib);
+        h->io_logL = reinterpret_cast<double *>(base + o_il);
+        h->io_grad = reinterpret_cast<double *>(base + o_ig);
+        h->io_hess = reinterpret_cast<double *>(base + o_ih);
+        h->io_site = reinterpret_cast<double *>(base + o_is);
+        h->b_fwd = reinterpret_cast<double *>(base + o_bf);
+        h->part_out = reinterpret_cast<double *>(base + o_pt);
+        h->info = c0h->info;
+        h->info.n_patterns = P;
+        h->info.device_bytes = pbytes + need;
+        h->info.stream_bytes = 0;
+        h->info.flops = 0;
+        for (pg_handle *c : chunks) {
+            h->info.device_bytes += c->bytes;
+            h->info.stream_bytes += c->info.stream_bytes;
+            h->info.flops += c->info.flops;
+        }
+        *out = h;
+        return PG_OK;
+    }
+    return fail(PG_ERR_OOM, "%s; not even in pattern chunks of 128 patterns", whole.c_str());
+}
+
+// upload_binary, and in pattern chunks when the whole problem does not fit (not for a caller's arena)
+pg_status upload_fit(pg_ctx *ctx, const pg_problem *pr, pg_handle **out, const Placement *pl) {
+    pg_status st = upload_binary(ctx, pr, out, pl);
+    if (st == PG_ERR_OOM && !pl && pr->n_patterns > 128) st = upload_chunked(ctx, pr, out);
+    return st;
+}
+
+}  // namespace
+
 pg_status pg::host::upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out, const Placement *pl) {
     if (!ctx || !pr || !out) return fail(PG_ERR_INVALID, "NULL argument");
     *out = nullptr;
@@ -1032,7 +1212,7 @@ pg_status pg::host::upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out, c
     if (N < 2) return fail(PG_ERR_INVALID, "n_tips = %d (at least 2 required)", N);
     const int n = 2 * N - 1, n_user = pr->n_nodes ? pr->n_nodes : n;
     if (n_user == n) {
-        pg_status st = upload_binary(ctx, pr, out, pl);
+        pg_status st = upload_fit(ctx, pr, out, pl);
         if (st == PG_OK) (*out)->n_user = n;
         return st;
     }
@@ -1043,7 +1223,7 @@ pg_status pg::host::upload(pg_ctx *ctx, const pg_problem *pr, pg_handle **out, c
     rb.parent = par.data();
     rb.branch_model = pr->branch_model ? bm.data() : nullptr;
     rb.n_nodes = n;
-    st = upload_binary(ctx, &rb, out, pl);
+    st = upload_fit(ctx, &rb, out, pl);
     if (st != PG_OK) return st;
     pg_handle *h = *out;
     h->n_user = n_user;
@@ -1090,8 +1270,12 @@ namespace {
 // the cut up in the shared-memory top kernel (or the fused kernel), the pre-order levels, the
 // fixed-order reduction.  skip = kSkipPre enqueues the forward part (logL), kSkipPost the backward
 // part (gradient, Hessian diagonal) on the partials the last forward part left in the handle.
+pg_status enqueue_chunked(pg_handle *h, int skip, const double *d_b, double *d_logL, double *d_grad,
+                          double *d_hess, double *d_site_logL, const double *d_gscale, cudaStream_t s);
+
 pg_status enqueue_single(pg_handle *h, int skip, const double *d_b, double *d_logL, double *d_grad,
                          double *d_hess, double *d_site_logL, const double *d_gscale, cudaStream_t s) {
+    if (!h->chunks.empty()) return enqueue_chunked(h, skip, d_b, d_logL, d_grad, d_hess, d_site_logL, d_gscale, s);
     if (h->mstate) return enqueue_m(h, skip, d_b, d_logL, d_grad, d_hess, d_site_logL, d_gscale, s);
     pg::BatchArgs<1> a;
     pg::ProbDesc d = h->desc;
@@ -1148,6 +1332,39 @@ pg_status enqueue_single(pg_handle *h, int skip, const double *d_b, double *d_lo
     return PG_OK;
 }
 
+// A problem evaluated in pattern chunks (see upload_chunked): the chunks run one after another on
+// stream s, each writing its logL, gradient and Hessian diagonal to its slot of part_out (its site
+// log-likelihoods straight to its slice of d_site_logL), then fixed-order sums give the outputs.
+// The forward part keeps no partials (the next chunk overwrites them): it stores b for the backward
+// part, which runs each chunk's whole evaluation again -- the post-order partials of the chunk are
+// recomputed before its pre-order pass.
+pg_status enqueue_chunked(pg_handle *h, int skip, const double *d_b, double *d_logL, double *d_grad,
+                          double *d_hess, double *d_site_logL, const double *d_gscale, cudaStream_t s) {
+    const int K = (int)h->chunks.size(), n = h->desc.n_nodes;
+    const bool fwd = !(skip & pg::kSkipPost), bwd = !(skip & pg::kSkipPre);
+    double *p_l = h->part_out, *p_g = p_l + K, *p_h = p_g + (size_t)K * n;
+    const double *b = d_b;
+    if (fwd && !bwd) PG_CUDA(cudaMemcpyAsync(h->b_fwd, d_b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    if (!fwd) b = h->b_fwd;
+    for (int j = 0; j < K; ++j) {
+        pg_handle *c = h->chunks[j];
+        const int sk = (fwd && !bwd) ? pg::kSkipPre : 0;
+        pg_status st = enqueue_single(c, sk, b, p_l + j, (bwd && d_grad) ? p_g + (size_t)j * n : nullptr,
+                                      (bwd && d_hess) ? p_h + (size_t)j * n : nullptr,
+                                      (fwd && d_site_logL) ? d_site_logL + h->chunk_p0[j] : nullptr,
+                                      bwd ? d_gscale : nullptr, s);
+        if (st != PG_OK) return st;
+    }
+    cudaError_t e = cudaSuccess;
+    if (fwd && d_logL) e = pg::launch_chunk_sum(p_l, K, 1, d_logL, s);
+    if (e == cudaSuccess && bwd && d_grad) e = pg::launch_chunk_sum(p_g, K, n, d_grad, s);
+    if (e == cudaSuccess && bwd && d_hess) e = pg::launch_chunk_sum(p_h, K, n, d_hess, s);
+    if (e != cudaSuccess) return fail(PG_ERR_CUDA, "launch: %s", cudaGetErrorString(e));
+    h->last_stream = s;
+    if (fwd) h->have_post = true;
+    return PG_OK;
+}
+
 // k problems in as few launches as possible: grouped by category count and precision, each
 // launch covers every tile of every problem of the group, every level in the fused kernel
 pg_status enqueue_batch(pg_handle *const *hs, int32_t k, int skip, const double *const *d_b, double *d_logL,
@@ -1155,8 +1372,15 @@ pg_status enqueue_batch(pg_handle *const *hs, int32_t k, int skip, const double 
     const bool fwd = !(skip & pg::kSkipPost), bwd = !(skip & pg::kSkipPre);
     DeviceGuard g(hs[0]->ctx->device);
     if (!g.ok) return fail(PG_ERR_CUDA, "cannot select device %d", hs[0]->ctx->device);
-    for (int i = 0; i < k; ++i) {   // general state spaces: each problem's own level launches
-        if (!hs[i]->mstate) continue;
+    for (int i = 0; i < k; ++i) {   // general state spaces and chunked problems: their own launches
+        if (!hs[i]->mstate && hs[i]->chunks.empty()) continue;
+        if (!hs[i]->chunks.empty()) {
+            pg_status st = enqueue_chunked(hs[i], skip, d_b ? d_b[i] : nullptr, d_logL ? d_logL + i : nullptr,
+                                           (bwd && d_grad) ? d_grad[i] : nullptr, (bwd && d_hess) ? d_hess[i] : nullptr,
+                                           nullptr, d_gscale ? d_gscale + i : nullptr, s);
+            if (st != PG_OK) return st;
+            continue;
+        }
         pg_status st = enqueue_m(hs[i], skip, d_b ? d_b[i] : nullptr, d_logL ? d_logL + i : nullptr,
                                  (bwd && d_grad) ? d_grad[i] : nullptr, (bwd && d_hess) ? d_hess[i] : nullptr,
                                  nullptr, d_gscale ? d_gscale + i : nullptr, s);
@@ -1166,7 +1390,8 @@ pg_status enqueue_batch(pg_handle *const *hs, int32_t k, int skip, const double 
         const int C = 1 + key / 2, prec = key % 2;
         std::vector<int> idx;
         for (int i = 0; i < k; ++i)
-            if (!hs[i]->mstate && hs[i]->desc.C == C && hs[i]->desc.precision == prec) idx.push_back(i);
+            if (!hs[i]->mstate && hs[i]->chunks.empty() && hs[i]->desc.C == C && hs[i]->desc.precision == prec)
+                idx.push_back(i);
         if (idx.empty()) continue;
         // the fused-kernel, P-build and reduction launches take groups of up to kMaxBatch problems
         // (descriptors by value); the level launches cover every problem of the key at once
@@ -1472,6 +1697,7 @@ pg_status pg_clock_grad_async(pg_handle *const *hs, int32_t k, const double *con
 
 pg_status pg_set_phase_timing(pg_handle *h, int enable) {
     if (!h) return fail(PG_ERR_INVALID, "NULL handle");
+    if (!h->chunks.empty()) return fail(PG_ERR_UNSUPPORTED, "phase timing of a problem evaluated in pattern chunks");
     DeviceGuard g(h->ctx->device);
     for (cudaEvent_t x : h->events) cudaEventDestroy(x);
     h->events.clear();
@@ -1509,8 +1735,16 @@ pg_status pg_eval_status(pg_handle *h) {
     DeviceGuard g(h->ctx->device);
     PG_CUDA(cudaStreamSynchronize(h->last_stream));
     int st = 0;
-    PG_CUDA(cudaMemcpy(&st, h->desc.status, sizeof(int), cudaMemcpyDeviceToHost));
-    if (st) PG_CUDA(cudaMemset(h->desc.status, 0, sizeof(int)));
+    if (h->chunks.empty()) {
+        PG_CUDA(cudaMemcpy(&st, h->desc.status, sizeof(int), cudaMemcpyDeviceToHost));
+        if (st) PG_CUDA(cudaMemset(h->desc.status, 0, sizeof(int)));
+    }
+    for (pg_handle *c : h->chunks) {   // every chunk's status word
+        int cs = 0;
+        PG_CUDA(cudaMemcpy(&cs, c->desc.status, sizeof(int), cudaMemcpyDeviceToHost));
+        if (cs) PG_CUDA(cudaMemset(c->desc.status, 0, sizeof(int)));
+        st |= cs;
+    }
     if (st & pg::kStatusBadLength) return fail(PG_ERR_INVALID, "a branch length was negative or not finite");
     if (st & pg::kStatusNumeric) return fail(PG_ERR_NUMERIC, "a site likelihood was zero or not finite");
     if (st & pg::kStatusUnsettled)

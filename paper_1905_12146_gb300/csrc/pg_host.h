@@ -51,6 +51,16 @@ struct pg_handle {
     // nodes as the caller numbers them: 2N-1, or fewer for a tree with multifurcations, which the
     // handle holds resolved into a binary tree with added nodes n_user .. 2N-2 (branches of length 0)
     int n_user = 0;
+    // A problem whose arrays exceed the context's budget, evaluated in pattern chunks: the chunks'
+    // handles (contiguous pattern slices starting at chunk_p0) share one region for their
+    // per-evaluation arrays and run one after another on the evaluation's stream; their logL,
+    // gradient and Hessian land in part_out ([K], [K][n], [K][n]) and are summed in a fixed order.
+    std::vector<pg_handle *> chunks;
+    std::vector<int> chunk_p0;
+    void *scratch_block = nullptr;
+    size_t scratch_bytes = 0;
+    double *part_out = nullptr;
+    double *b_fwd = nullptr;   // [n] the branch lengths of the last forward pass (chunked backward)
     const pg::ProbDesc *d_desc = nullptr;   // device copy of desc (batched level kernels read it)
 };
 

@@ -250,6 +250,8 @@ template <int MAXB>
 cudaError_t launch_tree(const BatchArgs<MAXB> &args, bool hess, cudaStream_t s);
 template <int MAXB>
 cudaError_t launch_reduce(const BatchArgs<MAXB> &args, bool hess, cudaStream_t s);
+// the fixed-order sum of k per-chunk results of length n (a problem evaluated in pattern chunks)
+cudaError_t launch_chunk_sum(const double *parts, int k, int n, double *out, cudaStream_t s);
 // resident blocks per SM of the tree kernel for C categories and the given precision
 int tree_blocks_per_sm(int C, bool f64);
 // the levels [cut, n_levels) of a single FP32 problem with shared-memory-resident partials

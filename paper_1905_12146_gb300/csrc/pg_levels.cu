@@ -295,11 +295,15 @@ __device__ __forceinline__ void staged_walk(int n_items, Ring<Stage, STAGES> &ri
     if (warp == kConsumerWarps) {   // producer
         if (lane != 0) return;
         int i = 0;
+        // the next item's record (its node ids come from global memory) is loaded one item ahead,
+        // so that load overlaps the wait for a free stage instead of delaying the copies
+        Item nxt = b < n_items ? item_at(b) : Item{};
         for (;; ++i) {
             const int j = b + i * G;
             if (j >= n_items) break;
             const int s = i % STAGES, use = i / STAGES;
-            const Item it = item_at(j);
+            const Item it = nxt;
+            if (j + G < n_items) nxt = item_at(j + G);
             if (use > 0 && !mbar_wait_bounded(&ring.empty[s], (unsigned)(use - 1) & 1u, kWaitLimitCycles)) {
                 atomicOr(it.pd->status, kStatusTimeout);
                 break;

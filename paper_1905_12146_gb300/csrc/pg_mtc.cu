@@ -660,6 +660,7 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
     unsigned char *X[2] = {sm, sm + kRowTile};                 // children's rows (staging)
     unsigned char *QK = sm + 2 * kRowTile;                      // q_k rows
     // per child 64 KB: [D; G] hi in the lower half (then D^T hi | lo), [D; G] lo in the upper half
+    // (then the staged result q_c)
     unsigned char *T[2] = {sm + 3 * kRowTile, sm + 3 * kRowTile + 4 * kTab};
     enum { BX = 0, BQ = 1, BTH = 2, BTL = 3, BD = 4, BM = 5, NB = 6 };   // rows, q_k, [D;G] hi, lo, D^T, products
     __shared__ __align__(8) uint64_t bar[NB], drain_bar;
@@ -694,6 +695,7 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
     uint32_t ph[NB] = {0, 0, 0, 0, 0, 0};
     bool pend[NB] = {false, false, false, false, false, false};
     bool ok = true;
+    bool store_pending = false;   // (leader) results of the previous category still being read from the upper halves
     // copies (thread 0): rows of the internal children, q_k, tables
     auto issue_rows = [&](int l) {
         uint32_t bytes = 0;
@@ -792,6 +794,13 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
                 mma_tile_ta(acc, xa, tb, 2 * kMP, false);
                 if (!tip[side] || TV) mma_tile_ta(acc, xa + 64, tb, 2 * kMP, true);
             }
+            // while those run: the previous results leave the upper halves, this category's lo
+            // tables take their place
+            if (l > l0) {
+                if (store_pending) bulk_wait_read0();
+                store_pending = false;
+                issue_tables_lo(l);
+            }
         }
         if (!wait(BTL)) break;
         if (leader) {
@@ -804,7 +813,6 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
             mma_commit(&bar[BM]);
         }
         if (!wait(BM)) break;
-        if (leader && l + 1 < l1) issue_tables_lo(l + 1);   // the upper halves have been read
         if (leader && !any_int && l + 1 < l1) issue_tables_hi(l + 1);   // no D^T products: the lower halves are free
         // the D^T tables of the internal children into their (now free) table slots
         if (leader && any_int) {
@@ -888,8 +896,8 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
             if (leader && l + 1 < l1) issue_tables_hi(l + 1);   // the D^T tables have been read
         }
         if (any_int) {
-            // epilogue 2: q_c = qt_c + D_c^T qt_c, scaled by its largest state and stored from
-            // registers (each thread writes its half row, 128 contiguous bytes of the column)
+            // epilogue 2: q_c = qt_c + D_c^T qt_c, scaled, staged in the upper half of the child's
+            // table slot and stored by TMA
             tc_after();
             for (int side = 0; side < 2; ++side) {
                 if (tip[side]) continue;
@@ -916,7 +924,6 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
                 if (tip[side]) continue;
                 const uint32_t qa = lane_base + 256 + 128 * side, acc = lane_base + 128 * side;
                 const int e = scale_exponent(fmaxf(half_part[side][0][t], half_part[side][1][t]));
-                float4 *dst = reinterpret_cast<float4 *>(d.pre + (((size_t)(cs[side] - N) * C + l) * d.Ps + p0 + t) * kMP);
 #pragma unroll
                 for (int i = 0; i < 2; ++i) {
                     float a[16], q[16];
@@ -925,13 +932,20 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
                     tmem_wait_ld();
 #pragma unroll
                     for (int j = 0; j < 16; ++j) a[j] += q[j];
-                    if (on) {
-#pragma unroll
-                        for (int q4 = 0; q4 < 4; ++q4)
-                            __stcg(dst + 4 * (ch0 + i) + q4, scale4(f4(a[4 * q4], a[4 * q4 + 1], a[4 * q4 + 2], a[4 * q4 + 3]), e));
-                    }
+                    put16(T[side] + 2 * kTab, t, ch0 + i, a, e);
                 }
                 if (on && hf == 0) __stcg(d.qe + ((size_t)(cs[side] - N) * C + l) * d.Ps + p0 + t, Eq + Ex[1 - side] + e);
+            }
+            fence_async_smem();
+            __syncthreads();
+            if (leader) {
+                for (int side = 0; side < 2; ++side) {
+                    if (tip[side]) continue;
+                    for (int kb = 0; kb < 2; ++kb)
+                        tma_store_3d(&tm_pre, T[side] + 2 * kTab + kb * kRowKB, kb * 32, p0, (cs[side] - N) * C + l);
+                }
+                bulk_commit();
+                store_pending = true;   // waited for before the next lo tables are copied over them
             }
         }
         tc_before();
@@ -958,6 +972,7 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
         // let every copy (barriers BX .. BD) and product in flight finish
         if (!drain_block(&drain_bar, bar, ph, pend, BM)) atomicOr(d.status, kStatusUnsettled);
     }
+    if (leader) bulk_wait_read0();   // the staging smem is read before the block exits
     tc_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, 512);

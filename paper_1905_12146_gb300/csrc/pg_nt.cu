@@ -883,6 +883,21 @@ cudaError_t launch_eval_nt(const BatchArgs<MAXB> &args, bool hess, cudaStream_t 
     return e;
 }
 
+// out[i] = sum over j = 0 .. k-1, in that order, of parts[j n + i]
+__global__ void __launch_bounds__(256) chunk_sum_kernel(const double *parts, int k, int n, double *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double v = 0.0;
+    for (int j = 0; j < k; ++j) v += parts[(size_t)j * n + i];
+    out[i] = v;
+}
+
+cudaError_t launch_chunk_sum(const double *parts, int k, int n, double *out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    chunk_sum_kernel<<<(n + 255) / 256, 256, 0, s>>>(parts, k, n, out);
+    return cudaGetLastError();
+}
+
 template cudaError_t launch_eval_nt<1>(const BatchArgs<1> &, bool, cudaStream_t);
 template cudaError_t launch_pmatrix<1>(const BatchArgs<1> &, cudaStream_t);
 template cudaError_t launch_tree<1>(const BatchArgs<1> &, bool, cudaStream_t);
