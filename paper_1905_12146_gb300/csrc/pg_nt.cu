@@ -68,6 +68,7 @@ __device__ __forceinline__ double col_entry(double e, int k, int j, unsigned mas
 
 template <int MAXB>
 __global__ void __launch_bounds__(128) pmatrix4_kernel(const __grid_constant__ BatchArgs<MAXB> a) {
+    pdl_launch_dependents();   // the first level kernel may be scheduled now; it waits for these tables
     const int gid = (int)(blockIdx.x * blockDim.x + threadIdx.x);
     const int mat = gid >> 4, lane16 = gid & 15, i = lane16 >> 2, j = lane16 & 3;
     const int total = a.mat_base[a.n];
@@ -742,6 +743,7 @@ __global__ void __launch_bounds__(kBlock, 1) tree4d_kernel(const __grid_constant
 
 template <int MAXB>
 __global__ void __launch_bounds__(256) reduce_kernel(const __grid_constant__ BatchArgs<MAXB> a, int want_hess) {
+    pdl_wait();   // launched while the last pass drains: its slot sums are complete and visible after this
     const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (gw >= a.red_base[a.n]) return;
@@ -871,8 +873,16 @@ template <int MAXB>
 cudaError_t launch_reduce(const BatchArgs<MAXB> &args, bool hess, cudaStream_t s) {
     if (args.n <= 0) return cudaSuccess;
     const int warps = args.red_base[args.n];
-    reduce_kernel<MAXB><<<(warps + 7) / 8, 256, 0, s>>>(args, hess ? 1 : 0);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};   // programmatic dependent launch (the kernel waits in pdl_wait)
+    cfg.gridDim = dim3((unsigned)((warps + 7) / 8));
+    cfg.blockDim = dim3(256);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, reduce_kernel<MAXB>, args, hess ? 1 : 0);
 }
 
 template <int MAXB>

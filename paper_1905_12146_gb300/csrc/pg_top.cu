@@ -48,6 +48,8 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 template <int C, bool HESS>
 __global__ void __launch_bounds__(kBlock, 2) top_kernel(const __grid_constant__ BatchArgs<1> a) {
     extern __shared__ float4 dyn[];
+    pdl_wait();                // launched while the last post-order level drains
+    pdl_launch_dependents();   // the first pre-order level may be scheduled; it waits for this kernel
     const ProbDesc &d = a.d[0];
     const int N = d.n_tips, Ps = d.Ps, L = d.range_len;
     const int tile = blockIdx.x;
@@ -290,8 +292,17 @@ cudaError_t launch_top_c(const BatchArgs<1> &args, size_t smem, cudaStream_t s) 
     static DeviceOnce once;   // the shared-memory attribute, once per device
     if (cudaError_t e = device_once(once, [](int &) { return cudaFuncSetAttribute(top_kernel<C, HESS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTopSmemLimit); }); e != cudaSuccess)
         return e;
-    top_kernel<C, HESS><<<args.d[0].n_tiles, kBlock, smem, s>>>(args);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};   // programmatic dependent launch (the kernel waits in pdl_wait)
+    cfg.gridDim = dim3((unsigned)args.d[0].n_tiles);
+    cfg.blockDim = dim3(kBlock);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, top_kernel<C, HESS>, args);
 }
 
 }  // namespace
