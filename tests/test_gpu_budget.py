@@ -89,10 +89,10 @@ def test_chunked_forward_backward_recomputes_the_partials(native):
     dev = torch.device("cuda")
     pr = wl.random_problem(100, 2500, n_states=4, n_cat=4, seed=410, b_mean=0.05, ambiguous=0.03)
     whole, _ = _full_bytes(native, pr)
-    ctx = native.Context(0, hbm_budget_bytes=int(0.4 * whole) + (8 << 20))   # room for the small problem too
+    ctx = native.Context(0, hbm_budget_bytes=int(0.4 * whole) + (8 << 20))
+    h2 = ctx.upload(wl.random_problem(20, 300, n_states=4, n_cat=4, seed=411))   # first: the chunks take what is left
     h = ctx.upload(pr)
     assert h.info().device_bytes < whole
-    h2 = ctx.upload(wl.random_problem(20, 300, n_states=4, n_cat=4, seed=411))
     try:
         b = torch.tensor(pr["b"], device=dev)
         l0 = torch.zeros(1, dtype=torch.float64, device=dev)
