@@ -34,6 +34,8 @@ struct pg_handle {
     size_t bytes = 0;
     int max_tiles = 0;       // blocks one evaluation of this problem may use
     int cut = 0;             // levels [0, cut) run as level kernels when evaluated alone
+    int epoch = 0;           // evaluations whose DAG part was enqueued (completion flags reach 4 epoch)
+    unsigned long long *dag_counter = nullptr;   // the DAG kernel's item counter (device)
     std::vector<int> level_off;   // host copy of the level offsets
     std::vector<uint8_t> level_cherry;   // 1 when every node of the level has two tip children
     bool timing = false;
