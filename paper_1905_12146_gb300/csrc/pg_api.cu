@@ -940,7 +940,7 @@ static pg_status upload_binary(pg_ctx *ctx, const pg_problem *pr, pg_handle **ou
     d.flags = f64 ? nullptr : reinterpret_cast<int *>(base + o_fl);
     d.nlevel = reinterpret_cast<const int *>(base + o_nl);
     d.dag_counter = nullptr;   // set per evaluation that runs the DAG kernel
-    d.epoch = 0;
+    d.epoch = d.epoch_pre = 0;
     h->dag_counter = reinterpret_cast<unsigned long long *>(base + o_dc);
     d.cut = 0;
     h->cut = cut;
@@ -1315,9 +1315,11 @@ pg_status enqueue_single(pg_handle *h, int skip, const double *d_b, double *d_lo
     // DAG kernel; FP64 runs every level in the fused kernel
     const bool dag = d.precision == PG_PRECISION_FP32 && d.P > 0;
     set_tiling(d, single_target(h->ctx, d), max_range);
-    if (dag) {
-        if (fwd) ++h->epoch;   // a backward part completes the forward's evaluation
+    if (dag) {   // the flags' targets: this forward part, this backward part
+        if (fwd) ++h->epoch;
+        if (bwd) ++h->epoch_pre;
         d.epoch = h->epoch;
+        d.epoch_pre = h->epoch_pre;
         d.dag_counter = h->dag_counter;
     }
     fill_args_one(a, d);

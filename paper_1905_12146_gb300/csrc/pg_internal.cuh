@@ -119,9 +119,10 @@ struct ProbDesc {
     // the top of the tree in one persistent launch (pg_levels.cu, dag_kernel): nodes of levels
     // >= cut are items (node, range) that wait for the items they read through completion flags,
     // int [3][N-1][level_ranges] (post, pre, and at [2][0][r] the root of range r), each raised
-    // by 4 (one per consumer warp) per evaluation: evaluation e is complete at 4 e
+    // by 4 (one per consumer warp) per pass: the post-order and root flags by every forward part
+    // (complete at 4 epoch), the pre-order flags by every backward part (complete at 4 epoch_pre)
     int *flags;
-    int epoch;
+    int epoch, epoch_pre;
     const int *nlevel;             // [n] level of an internal node, -1 for a tip
     unsigned long long *dag_counter;   // items claimed so far in the running launch (reset by the
                                        // evaluation's reduction kernel); null without that launch

@@ -585,7 +585,7 @@ struct DagItems {
 
 template <int C>
 __device__ __forceinline__ bool issue_dag(const ProbDesc &d, const Item &it, DagStage<C> &st, uint64_t *bar) {
-    const int N = d.n_tips, target = 4 * d.epoch;
+    const int N = d.n_tips, target = 4 * d.epoch, target_pre = 4 * d.epoch_pre;
     if (it.kind == kItemPost || it.kind == kItemRoot) {
         // the children computed in this launch (levels from the cut up)
         for (int side = 0; side < 2; ++side) {
@@ -596,8 +596,9 @@ __device__ __forceinline__ bool issue_dag(const ProbDesc &d, const Item &it, Dag
         issue_post<C, false>(d, it, st.post, bar);
     } else {
         // q_k from the parent's pre-order item, or the site values of the root of this range
-        const int *f = it.kind == kItemPreRoot ? flag_of(d, 2, 0, it.rg) : flag_of(d, 1, it.op.x - N, it.rg);
-        if (!wait_flag(f, target)) return false;
+        const bool r = it.kind == kItemPreRoot;
+        if (!wait_flag(r ? flag_of(d, 2, 0, it.rg) : flag_of(d, 1, it.op.x - N, it.rg), r ? target : target_pre))
+            return false;
         asm volatile("fence.proxy.async.global;\n" ::: "memory");
         if (it.kind == kItemPreRoot) issue_pre<C, false, true>(d, it, st.pre, bar);
         else issue_pre<C, false, false>(d, it, st.pre, bar);
