@@ -94,13 +94,6 @@ struct DeviceGuard {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// a level runs as its own launch while it has at least kDagWaves * n_sm (node, range) items; the
-// levels above run in the persistent DAG kernel
-#ifndef PG_DAG_WAVES
-#define PG_DAG_WAVES 8
-#endif
-constexpr int kDagWaves = PG_DAG_WAVES;
-
 }  // namespace
 
 // ------------------------------------------------------------------------------------------
@@ -763,11 +756,9 @@ static pg_status upload_binary(pg_ctx *ctx, const pg_problem *pr, pg_handle **ou
     const int slot_cap = std::max((P + 31) / 32 + 3 * max_tiles + 2, level_ranges * (pg::kLevelRange / 32));
     // FP32 problems evaluated alone run every level with at least two blocks per SM of
     // (node, 256-pattern) work as its own launch; the narrower levels near the root stay fused
-    // FP32 problems evaluated alone run the wide levels (at least kDagWaves items per SM) as one
-    // launch each and the levels from the cut up in the persistent DAG kernel (pg_levels.cu)
     int cut = 0;
     if (!f64) {
-        while (cut < H - 1 && (int64_t)(tp.level_off[cut + 1] - tp.level_off[cut]) * level_ranges >= kDagWaves * ctx->n_sm)
+        while (cut < H - 1 && (int64_t)(tp.level_off[cut + 1] - tp.level_off[cut]) * level_ranges >= 2 * ctx->n_sm)
             ++cut;
     }
     std::vector<int> plevel(n, -1);   // level index of each node's parent
@@ -831,8 +822,6 @@ static pg_status upload_binary(pg_ctx *ctx, const pg_problem *pr, pg_handle **ou
     const size_t o_par = cv.take<int>(n);
     const size_t o_ib = cv.take<double>(n), o_il = cv.take<double>(1), o_ig = cv.take<double>(n);
     const size_t o_ih = cv.take<double>(n), o_is = cv.take<double>(std::max(P, 1));
-    const size_t n_flags = f64 ? 1 : 3 * (size_t)(N - 1) * level_ranges;
-    const size_t o_fl = cv.take<int>(n_flags), o_nl = cv.take<int>(n), o_dc = cv.take<unsigned long long>(1);
     const size_t bytes = align_up(cv.off, 256);
 
     DeviceGuard g(ctx->device);
@@ -894,12 +883,6 @@ static pg_status upload_binary(pg_ctx *ctx, const pg_problem *pr, pg_handle **ou
     if (e == cudaSuccess && n_bnd > 0) e = cp(o_bn, bnd_node.data(), sizeof(int) * n_bnd);
     if (e == cudaSuccess) e = cp(o_par, pr->parent, sizeof(int) * n);
     if (e == cudaSuccess) e = dzero(pl, base + o_st, sizeof(int));
-    std::vector<int> nlevel(n, -1);   // level of each internal node
-    for (int lv = 0; lv < H; ++lv)
-        for (int o = tp.level_off[lv]; o < tp.level_off[lv + 1]; ++o) nlevel[tp.ops[o].x] = lv;
-    if (e == cudaSuccess) e = cp(o_nl, nlevel.data(), sizeof(int) * n);
-    if (e == cudaSuccess) e = dzero(pl, base + o_fl, sizeof(int) * n_flags);   // completion flags: evaluation 0
-    if (e == cudaSuccess) e = dzero(pl, base + o_dc, sizeof(unsigned long long));
     if (e != cudaSuccess) {
         release_block(pl, block);
         delete h;
@@ -937,11 +920,6 @@ static pg_status upload_binary(pg_ctx *ctx, const pg_problem *pr, pg_handle **ou
     d.top_code = reinterpret_cast<const int2 *>(base + o_tc);
     d.bnd_node = reinterpret_cast<const int *>(base + o_bn);
     d.parent = reinterpret_cast<const int *>(base + o_par);
-    d.flags = f64 ? nullptr : reinterpret_cast<int *>(base + o_fl);
-    d.nlevel = reinterpret_cast<const int *>(base + o_nl);
-    d.dag_counter = nullptr;   // set per evaluation that runs the DAG kernel
-    d.epoch = d.epoch_pre = 0;
-    h->dag_counter = reinterpret_cast<unsigned long long *>(base + o_dc);
     d.cut = 0;
     h->cut = cut;
     h->level_off = tp.level_off;
@@ -1311,23 +1289,17 @@ pg_status enqueue_single(pg_handle *h, int skip, const double *d_b, double *d_lo
     const bool fwd = !(skip & pg::kSkipPost), bwd = !(skip & pg::kSkipPre);
     const int max_range = h->ctx->max_range ? h->ctx->max_range : pg::kMaxRange;
     d.cut = d.P > 0 ? h->cut : 0;
-    // FP32: the levels from the cut up, the root and their pre-order steps run in the persistent
-    // DAG kernel; FP64 runs every level in the fused kernel
-    const bool dag = d.precision == PG_PRECISION_FP32 && d.P > 0;
-    set_tiling(d, single_target(h->ctx, d), max_range);
-    if (dag) {   // the flags' targets: this forward part, this backward part
-        if (fwd) ++h->epoch;
-        if (bwd) ++h->epoch_pre;
-        d.epoch = h->epoch;
-        d.epoch_pre = h->epoch_pre;
-        d.dag_counter = h->dag_counter;
+    // FP32: the levels from the cut up run in the shared-memory top kernel when its per-block
+    // partials fit (two blocks per SM, else one); otherwise in the fused kernel
+    bool use_top = false;
+    if (d.precision == PG_PRECISION_FP32 && d.P > 0) {
+        for (int k = 2; k >= 1 && !use_top; --k) {
+            set_tiling(d, k * h->ctx->n_sm, max_range);
+            use_top = (size_t)k * (pg::top_smem_bytes(d) + 1024) <= (size_t)228 * 1024;   // 1 KB reserved per block
+        }
     }
+    if (!use_top) set_tiling(d, single_target(h->ctx, d), max_range);
     fill_args_one(a, d);
-    if (dag) {   // the reduction: every branch in level slots, logL in one slot per (range, warp)
-        a.d[0].cut = d.n_levels;
-        a.d[0].n_tg = d.level_ranges * (pg::kLevelRange / 32);
-    }
-    const int dag_o = h->level_off[d.cut], dag_items = ((d.n_tips - 1) - dag_o) * d.level_ranges;
     const bool hess = bwd && d_hess != nullptr;
     const bool timed = h->timing && fwd && bwd;
     cudaEvent_t ev[6] = {};
@@ -1346,9 +1318,7 @@ pg_status enqueue_single(pg_handle *h, int skip, const double *d_b, double *d_lo
         e = pg::launch_post_level(d, h->level_off[lv], h->level_off[lv + 1] - h->level_off[lv], h->ctx->n_sm,
                                   h->level_cherry[lv] != 0, s);
     mark(2);
-    if (e == cudaSuccess)
-        e = dag ? pg::launch_dag(d, dag_o, fwd ? dag_items : 0, bwd ? dag_items : 0, hess, h->ctx->n_sm, s)
-                : pg::launch_tree<1>(a, hess, s);
+    if (e == cudaSuccess) e = use_top ? pg::launch_top(a, hess, h->ctx->n_sm, s) : pg::launch_tree<1>(a, hess, s);
     mark(3);
     for (int lv = d.cut - 1; bwd && e == cudaSuccess && lv >= 0; --lv)
         e = pg::launch_pre_level(d, h->level_off[lv], h->level_off[lv + 1] - h->level_off[lv], hess, h->ctx->n_sm,

@@ -34,9 +34,6 @@ struct pg_handle {
     size_t bytes = 0;
     int max_tiles = 0;       // blocks one evaluation of this problem may use
     int cut = 0;             // levels [0, cut) run as level kernels when evaluated alone
-    int epoch = 0;           // forward parts enqueued (post-order and root flags complete at 4 epoch)
-    int epoch_pre = 0;       // backward parts enqueued (pre-order flags complete at 4 epoch_pre)
-    unsigned long long *dag_counter = nullptr;   // the DAG kernel's item counter (device)
     std::vector<int> level_off;   // host copy of the level offsets
     std::vector<uint8_t> level_cherry;   // 1 when every node of the level has two tip children
     bool timing = false;

@@ -116,16 +116,6 @@ struct ProbDesc {
     // [n] level index of each node's parent (-1 at the root): a branch whose parent lies below
     // the cut was summed in level-kernel slots, the others in fused-kernel slots
     const int *plevel;
-    // the top of the tree in one persistent launch (pg_levels.cu, dag_kernel): nodes of levels
-    // >= cut are items (node, range) that wait for the items they read through completion flags,
-    // int [3][N-1][level_ranges] (post, pre, and at [2][0][r] the root of range r), each raised
-    // by 4 (one per consumer warp) per pass: the post-order and root flags by every forward part
-    // (complete at 4 epoch), the pre-order flags by every backward part (complete at 4 epoch_pre)
-    int *flags;
-    int epoch, epoch_pre;
-    const int *nlevel;             // [n] level of an internal node, -1 for a tip
-    unsigned long long *dag_counter;   // items claimed so far in the running launch (reset by the
-                                       // evaluation's reduction kernel); null without that launch
     // sizes
     int n_tips, n_nodes, root, n_levels;
     int P;                         // site patterns
@@ -283,9 +273,6 @@ cudaError_t launch_pre_level_batch(const LevelBatch &lb, int C, bool hess, int n
 // one post-order (pre-order) level [o0, o0 + nd) of a single FP32 problem (pg_levels.cu)
 // (cherry: every node of the level has two tip children)
 cudaError_t launch_post_level(const ProbDesc &d, int o0, int nd, int n_sm, bool cherry, cudaStream_t s);
-// the levels [d.cut, n_levels) of a single FP32 problem in one persistent launch: n_post post-order
-// items (the nodes ops[o_cut ..] x ranges, the root last) then n_pre pre-order items (pg_levels.cu)
-cudaError_t launch_dag(const ProbDesc &d, int o_cut, int n_post, int n_pre, bool hess, int n_sm, cudaStream_t s);
 cudaError_t launch_pre_level(const ProbDesc &d, int o0, int nd, bool hess, int n_sm, bool cherry, cudaStream_t s);
 
 }  // namespace pg

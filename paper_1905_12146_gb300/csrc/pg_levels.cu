@@ -63,15 +63,10 @@ struct Ring {
 
 __device__ __forceinline__ unsigned round16(unsigned b) { return (b + 15u) & ~15u; }
 
-// what an item computes: a post-order node, the root (site likelihoods), a pre-order node, or the
-// pre-order step of the root's children (q_root = pi)
-constexpr int kItemPost = 0, kItemRoot = 1, kItemPre = 2, kItemPreRoot = 3;
-
 struct Item {
     const ProbDesc *pd;   // the item's problem
     int4 op;
     int rg, p0, cnt;
-    int kind = kItemPost;
 };
 
 __device__ __forceinline__ Item item_of(const ProbDesc &d, int o0, int nr, int j) {
@@ -110,15 +105,14 @@ __device__ void issue_post(const ProbDesc &d, const Item &it, PostStage<C, CHERR
     }
 }
 
-// ROOTK: k is the root, whose pre-order vector is pi (no q_k rows or exponents are copied)
-template <int C, bool CHERRY, bool ROOTK = false>
+template <int C, bool CHERRY>
 __device__ void issue_pre(const ProbDesc &d, const Item &it, PreStage<C, CHERRY> &sm, uint64_t *bar) {
     const int N = d.n_tips, Ps = d.Ps, k = it.op.x, c0 = it.op.y, c1 = it.op.z, p0 = it.p0;
     const bool t0 = c0 < N, t1 = c1 < N;
     const float4 *post = static_cast<const float4 *>(d.post);
     const float4 *pre = static_cast<const float4 *>(d.pre);
     const unsigned rowb = (unsigned)it.cnt * 16u, eb = round16(it.cnt * 4u), yb = round16((unsigned)it.cnt);
-    unsigned bytes = (ROOTK ? 0u : C * rowb + eb) + 3u * eb + 2u * C * 10u * 16u + 2u * 64u;
+    unsigned bytes = C * rowb + eb + 3u * eb + 2u * C * 10u * 16u + 2u * 64u;
     bytes += t0 ? yb : (C * rowb + eb);
     bytes += t1 ? yb : (C * rowb + eb);
     mbar_arrive_expect(bar, bytes);
@@ -127,10 +121,8 @@ __device__ void issue_pre(const ProbDesc &d, const Item &it, PreStage<C, CHERRY>
         for (int l = 0; l < C; ++l) bulk_load(sm.tab[side][l], d.Ptab + ((size_t)c * C + l) * kPtabCols, 10u * 16u, bar);
         bulk_load(sm.qtab[side], d.Qf + 4 * (d.bmodel ? d.bmodel[c] : 0), 64u, bar);
     }
-    if constexpr (!ROOTK) {
-        bulk_load(sm.eq, d.qe + (size_t)(k - N) * Ps + p0, eb, bar);
-        for (int l = 0; l < C; ++l) bulk_load(sm.qk[l], pre + ((size_t)(k - N) * C + l) * Ps + p0, rowb, bar);
-    }
+    bulk_load(sm.eq, d.qe + (size_t)(k - N) * Ps + p0, eb, bar);
+    for (int l = 0; l < C; ++l) bulk_load(sm.qk[l], pre + ((size_t)(k - N) * C + l) * Ps + p0, rowb, bar);
     bulk_load(sm.er, d.site_Er + p0, eb, bar);
     bulk_load(sm.inv, d.site_invL + p0, eb, bar);
     bulk_load(sm.w, d.wf + p0, eb, bar);
@@ -204,67 +196,9 @@ __device__ __forceinline__ void compute_post(const ProbDesc &d, const Item &it, 
     for (int tt = t; tt < PostStage<C, CHERRY>::R; tt += kLevelRange) compute_post_one<C, CHERRY>(d, it, sm, tt);
 }
 
-// The root of one item (its range of patterns): the site likelihood L_p = sum_l w_l pi'[(P_0 x_0) o
-// (P_1 x_1)] in FP64 from the children's FP32 rows (Section 2.3 root inner product, Section 2.5
-// mixture), its power-of-two scale and log (less the tips' pattern factors), the per-site values the
-// pre-order pass reads; returns w_p log L_p (0 past the item's patterns).
-template <int C>
-__device__ __forceinline__ double compute_root_one(const ProbDesc &d, const Item &it, const PostStage<C, false> &sm, int t) {
-    if (t >= it.cnt) return 0.0;
-    const int N = d.n_tips, c0 = it.op.y, c1 = it.op.z;
-    const bool t0 = c0 < N, t1 = c1 < N;
-    const int p = it.p0 + t;
-    const float r = pattern_factor((uint32_t)p);
-    const int y0 = t0 ? min((int)sm.y0[t], 4) : 0, y1 = t1 ? min((int)sm.y1[t], 4) : 0;
-    const int E = (t0 ? 0 : sm.e0[t]) + (t1 ? 0 : sm.e1[t]);
-    double Lsite = 0.0;
-#pragma unroll
-    for (int l = 0; l < C; ++l) {
-        float4 x[2], s2[2];
-#pragma unroll
-        for (int side = 0; side < 2; ++side) {
-            const bool tip = side ? t1 : t0;
-            const int y = side ? y1 : y0;
-            s2[side] = f4(0.f, 0.f, 0.f, 0.f);
-            if (tip) {
-                const float4 hi = sm.tab[side][l][y], lo = sm.tab[side][l][kColPlo + y];
-                x[side] = f4(fmaf(hi.x, r, lo.x * r), fmaf(hi.y, r, lo.y * r), fmaf(hi.z, r, lo.z * r), fmaf(hi.w, r, lo.w * r));
-            } else {
-                x[side] = side ? sm.x1[l][t] : sm.x0[l][t];
-                s2[side] = matvec_hilo_v(&sm.tab[side][l][kColDhi], &sm.tab[side][l][kColDlo], x[side]);
-            }
-        }
-        double v = d.pi[0] * (((double)x[0].x + s2[0].x) * ((double)x[1].x + s2[1].x));
-        v = fma(d.pi[1], ((double)x[0].y + s2[0].y) * ((double)x[1].y + s2[1].y), v);
-        v = fma(d.pi[2], ((double)x[0].z + s2[0].z) * ((double)x[1].z + s2[1].z), v);
-        v = fma(d.pi[3], ((double)x[0].w + s2[0].w) * ((double)x[1].w + s2[1].w), v);
-        Lsite = fma(d.cw[l], v, Lsite);
-    }
-    int e2 = 0;
-    const double f = (Lsite > 0.0 && isfinite(Lsite)) ? frexp(Lsite, &e2) : Lsite;
-    const int Erq = E + e2;
-    const double lp = log(f) + (double)Erq * 0.69314718055994530942 - (double)N * log((double)r);
-    d.site_invL[p] = (float)(1.0 / f);
-    d.site_Er[p] = Erq;
-    if (!(f > 0.0) || !isfinite(lp)) atomicOr(d.status, kStatusNumeric);
-    if (d.out_site) d.out_site[p] = lp;
-    const double w = d.weights[p];
-    return w != 0.0 ? w * lp : 0.0;
-}
-// the item's patterns t, t + kLevelRange, ... of consumer thread t; the warp's sum of w_p log L_p
-// goes to the logL slot 4 * range + warp
-template <int C>
-__device__ __forceinline__ void compute_root(const ProbDesc &d, const Item &it, const PostStage<C, false> &sm, int t) {
-    double acc = 0.0;
-#pragma unroll 1
-    for (int tt = t; tt < PostStage<C, false>::R; tt += kLevelRange) acc += compute_root_one<C>(d, it, sm, tt);
-    acc = warp_sum(acc);
-    if ((t & 31) == 0) d.lpart[it.rg * kConsumerWarps + (t >> 5)] = acc;
-}
-
 // pre-order step (Section 2.4) with the branch gradient (2.5) and Hessian diagonal (2.6) of pattern
 // t of one item: writes q of internal children, returns the pattern's weighted branch terms
-template <int C, bool HESS, bool CHERRY, bool ROOTK = false>
+template <int C, bool HESS, bool CHERRY>
 __device__ __forceinline__ void compute_pre_one(const ProbDesc &d, const Item &it, const PreStage<C, CHERRY> &sm, int t,
                                                 float (&sums)[4]) {
     const int N = d.n_tips, Ps = d.Ps, c0 = it.op.y, c1 = it.op.z;
@@ -274,7 +208,7 @@ __device__ __forceinline__ void compute_pre_one(const ProbDesc &d, const Item &i
     const int p = it.p0 + tt;
     const float r = pattern_factor((uint32_t)p);
     const int y0 = t0 ? min((int)sm.y0[tt], 4) : 0, y1 = t1 ? min((int)sm.y1[tt], 4) : 0;
-    const int Eq = ROOTK ? 0 : sm.eq[tt], E0 = t0 ? 0 : sm.e0[tt], E1 = t1 ? 0 : sm.e1[tt];
+    const int Eq = sm.eq[tt], E0 = t0 ? 0 : sm.e0[tt], E1 = t1 ? 0 : sm.e1[tt];
     const float inv = sm.inv[tt], wt = active ? sm.w[tt] : 0.f;
     const int dE = Eq + E0 + E1 - sm.er[tt];
     float4 q0[C], q1[C];
@@ -283,7 +217,7 @@ __device__ __forceinline__ void compute_pre_one(const ProbDesc &d, const Item &i
     for (int l = 0; l < C; ++l) {
         const float4 a0 = t0 ? scal(sm.tab[0][l][y0], r) : matvec_p(sm.tab[0][l], sm.x0[l][CHERRY ? 0 : tt]);
         const float4 a1 = t1 ? scal(sm.tab[1][l][y1], r) : matvec_p(sm.tab[1][l], sm.x1[l][CHERRY ? 0 : tt]);
-        const float4 qk = ROOTK ? f4(d.pif[0], d.pif[1], d.pif[2], d.pif[3]) : sm.qk[l][tt];
+        const float4 qk = sm.qk[l][tt];
         const float4 qt0 = mul(qk, a1), qt1 = mul(qk, a0);   // top of branches c0 and c1
         // Q a_c: a gathered column of G = Q P for tips, a matvec otherwise
         const float4 u0 = t0 ? scal(sm.tab[0][l][kColG + y0], r) : matvec_p(sm.qtab[0], a0);
@@ -319,11 +253,11 @@ __device__ __forceinline__ void compute_pre_one(const ProbDesc &d, const Item &i
 // the item's patterns t, t + kLevelRange, ... of consumer thread t; the warp's sums (32 patterns at a
 // time in FP32, those added in FP64) go to its own slot of both child branches (slot = 4 * range +
 // warp; the reduction adds the slots in a fixed order)
-template <int C, bool HESS, bool CHERRY, bool ROOTK = false>
+template <int C, bool HESS, bool CHERRY>
 __device__ __forceinline__ void compute_pre(const ProbDesc &d, const Item &it, const PreStage<C, CHERRY> &sm, int t) {
     if constexpr (PreStage<C, CHERRY>::R == kLevelRange) {   // one pattern per thread
         float sums[4];
-        compute_pre_one<C, HESS, CHERRY, ROOTK>(d, it, sm, t, sums);
+        compute_pre_one<C, HESS, CHERRY>(d, it, sm, t, sums);
         const int lane = t & 31, slot = it.rg * kConsumerWarps + (t >> 5);
 #pragma unroll
         for (int s = 0; s < (HESS ? 4 : 2); ++s) {
@@ -339,7 +273,7 @@ __device__ __forceinline__ void compute_pre(const ProbDesc &d, const Item &it, c
 #pragma unroll 1
     for (int tt = t; tt < PreStage<C, CHERRY>::R; tt += kLevelRange) {
         float sums[4];
-        compute_pre_one<C, HESS, CHERRY, ROOTK>(d, it, sm, tt, sums);
+        compute_pre_one<C, HESS, CHERRY>(d, it, sm, tt, sums);
 #pragma unroll
         for (int s = 0; s < (HESS ? 4 : 2); ++s) acc[s] += (double)warp_sum_f(sums[s]);
     }
@@ -516,212 +450,6 @@ cudaError_t launch_pdl_batch(K kernel, int blocks, size_t smem, cudaStream_t s, 
     return cudaLaunchKernelEx(&cfg, kernel, lb, n_items);
 }
 
-// ---- the top of the tree in one persistent launch ------------------------------------------------------
-// The narrow levels near the root hold few nodes: as one launch per level each is a short dependent
-// step, latency-bound.  Here every (node, range) item of the levels from the cut up -- post-order
-// nodes, the root (site likelihoods), then pre-order nodes from the root down -- is claimed from one
-// counter in a fixed order in which every item comes after the items it reads (children before
-// parents; the root; parents before children).  A block's producer claims the next item, waits
-// (bounded) until the items it reads are complete, and stages it; its consumer warps compute it and
-// raise the item's completion flag.  Ranges are independent, so the steps of different ranges and
-// nodes overlap.  Progress does not depend on which blocks are resident: an item is claimed only by a
-// running block, after every item it reads was claimed.
-template <int C>
-union DagStage {
-    PostStage<C, false> post;
-    PreStage<C, false> pre;
-};
-
-__device__ __forceinline__ int *flag_of(const ProbDesc &d, int which, int node_rel, int rg) {
-    return d.flags + ((size_t)which * (d.n_tips - 1) + node_rel) * d.level_ranges + rg;
-}
-// waits (bounded) until the flag reaches target, then lets the TMA (async proxy) see what the
-// flag's writers stored
-__device__ __forceinline__ bool wait_flag(const int *f, int target) {
-    const long long t0 = clock64();
-    for (;;) {
-        int v;
-        asm volatile("ld.acquire.gpu.global.b32 %0, [%1];\n" : "=r"(v) : "l"(f) : "memory");
-        if (v >= target) break;
-        if (clock64() - t0 > kWaitLimitCycles) return false;
-        __nanosleep(32);
-    }
-    return true;
-}
-// one consumer warp's part of an item is stored: make it visible, then count it (4 per item)
-__device__ __forceinline__ void raise_flag(int *f) {
-    __threadfence();
-    __syncwarp();
-    if ((threadIdx.x & 31) == 0) atomicAdd(f, 1);
-}
-
-// the items of one launch: n_post post-order items of the nodes ops[o_cut ..] (the last one is the
-// root), then n_pre pre-order items of the same nodes from the root down
-struct DagItems {
-    const ProbDesc &d;
-    int o_cut, n_post, n_pre;
-    __device__ Item operator()(int j) const {
-        const int nr = d.level_ranges, last = d.n_tips - 2;   // ops[N-2] is the root (the highest level)
-        Item it;
-        it.pd = &d;
-        int o;
-        if (j < n_post) {
-            o = o_cut + j / nr;
-            it.rg = j - (j / nr) * nr;
-            it.kind = o == last ? kItemRoot : kItemPost;
-        } else {
-            const int jj = j - n_post;
-            o = last - jj / nr;
-            it.rg = jj - (jj / nr) * nr;
-            it.kind = o == last ? kItemPreRoot : kItemPre;
-        }
-        it.op = __ldg(d.ops + o);
-        const int RL = level_range(d.C);
-        it.p0 = it.rg * RL;
-        it.cnt = min(RL, d.P - it.p0);
-        return it;
-    }
-};
-
-template <int C>
-__device__ __forceinline__ bool issue_dag(const ProbDesc &d, const Item &it, DagStage<C> &st, uint64_t *bar) {
-    const int N = d.n_tips, target = 4 * d.epoch, target_pre = 4 * d.epoch_pre;
-    if (it.kind == kItemPost || it.kind == kItemRoot) {
-        // the children computed in this launch (levels from the cut up)
-        for (int side = 0; side < 2; ++side) {
-            const int c = side ? it.op.z : it.op.y;
-            if (c >= N && __ldg(d.nlevel + c) >= d.cut && !wait_flag(flag_of(d, 0, c - N, it.rg), target)) return false;
-        }
-        asm volatile("fence.proxy.async.global;\n" ::: "memory");
-        issue_post<C, false>(d, it, st.post, bar);
-    } else {
-        // q_k from the parent's pre-order item, or the site values of the root of this range
-        const bool r = it.kind == kItemPreRoot;
-        if (!wait_flag(r ? flag_of(d, 2, 0, it.rg) : flag_of(d, 1, it.op.x - N, it.rg), r ? target : target_pre))
-            return false;
-        asm volatile("fence.proxy.async.global;\n" ::: "memory");
-        if (it.kind == kItemPreRoot) issue_pre<C, false, true>(d, it, st.pre, bar);
-        else issue_pre<C, false, false>(d, it, st.pre, bar);
-    }
-    return true;
-}
-
-template <int C, bool HESS>
-__device__ __forceinline__ void compute_dag(const ProbDesc &d, const Item &it, const DagStage<C> &st, int t) {
-    const int N = d.n_tips;
-    switch (it.kind) {
-        case kItemPost:
-            compute_post<C, false>(d, it, st.post, t);
-            raise_flag(flag_of(d, 0, it.op.x - N, it.rg));
-            break;
-        case kItemRoot:
-            compute_root<C>(d, it, st.post, t);
-            raise_flag(flag_of(d, 2, 0, it.rg));
-            break;
-        default:
-            if (it.kind == kItemPreRoot) compute_pre<C, HESS, false, true>(d, it, st.pre, t);
-            else compute_pre<C, HESS, false, false>(d, it, st.pre, t);
-            for (int side = 0; side < 2; ++side) {   // q of the internal children
-                const int c = side ? it.op.z : it.op.y;
-                if (c >= N) raise_flag(flag_of(d, 1, c - N, it.rg));
-            }
-    }
-}
-
-constexpr int kDagStages = 2;
-
-template <int C>
-struct DagRing {
-    DagStage<C> st[kDagStages];
-    uint64_t full[kDagStages], empty[kDagStages];
-    int item[kDagStages];   // the claimed item in each stage (-1: no more items)
-};
-
-template <int C, bool HESS>
-__global__ void __launch_bounds__(kLevelThreads)
-dag_kernel(const __grid_constant__ ProbDesc d, int o_cut, int n_post, int n_pre) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto &ring = *reinterpret_cast<DagRing<C> *>(smem_raw);
-    const int n_items = n_post + n_pre;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const DagItems src{d, o_cut, n_post, n_pre};
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < kDagStages; ++s) {
-            mbar_init(&ring.full[s], 1);
-            mbar_init(&ring.empty[s], kConsumerWarps);
-        }
-    }
-    __syncthreads();
-    pdl_launch_dependents();
-    pdl_wait();   // the lower levels' partials are complete and visible
-    if (warp == kConsumerWarps) {   // producer
-        if (lane != 0) return;
-        int i = 0;
-        for (;; ++i) {
-            const int s = i % kDagStages, use = i / kDagStages;
-            if (use > 0 && !mbar_wait_bounded(&ring.empty[s], (unsigned)(use - 1) & 1u, kWaitLimitCycles)) {
-                atomicOr(d.status, kStatusTimeout);
-                break;
-            }
-            // claims in increasing order (the counter starts at 0; the evaluation's reduction resets it)
-            const long long j = (long long)atomicAdd(d.dag_counter, 1ull);
-            if (j >= n_items) {   // no items left: tell the consumers
-                ring.item[s] = -1;
-                mbar_arrive(&ring.full[s]);
-                ++i;
-                break;
-            }
-            const Item it = src((int)j);
-            ring.item[s] = (int)j;
-            if (!issue_dag<C>(d, it, ring.st[s], &ring.full[s])) {
-                atomicOr(d.status, kStatusTimeout);
-                ring.item[s] = -1;   // the consumers stop here
-                mbar_arrive(&ring.full[s]);
-                ++i;
-                break;
-            }
-        }
-        // let every copy issued by this warp land before the block may leave
-        for (int q = (i > kDagStages ? i - kDagStages : 0); q < i; ++q)
-            if (!mbar_wait_bounded(&ring.full[q % kDagStages], (unsigned)(q / kDagStages) & 1u, kWaitLimitCycles))
-                atomicOr(d.status, kStatusTimeout | kStatusUnsettled);
-        return;
-    }
-    for (int i = 0;; ++i) {   // consumers
-        const int s = i % kDagStages;
-        if (!mbar_wait_bounded(&ring.full[s], (unsigned)(i / kDagStages) & 1u, kWaitLimitCycles)) {
-            if (lane == 0) atomicOr(d.status, kStatusTimeout);
-            return;
-        }
-        const int j = ring.item[s];
-        if (j < 0) return;
-        const Item it = src(j);
-        compute_dag<C, HESS>(d, it, ring.st[s], threadIdx.x);
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&ring.empty[s]);
-    }
-}
-
-template <int C, bool HESS>
-cudaError_t launch_dag_c(const ProbDesc &d, int o_cut, int n_post, int n_pre, int n_sm, cudaStream_t s) {
-    static DeviceOnce once;
-    const size_t smem = sizeof(DagRing<C>);
-    const int n_items = n_post + n_pre;
-    const int blocks = persistent_blocks(dag_kernel<C, HESS>, smem, n_sm, n_items, once);
-    if (blocks < 0) return cudaErrorInvalidConfiguration;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)blocks);
-    cfg.blockDim = dim3(kLevelThreads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, dag_kernel<C, HESS>, d, o_cut, n_post, n_pre);
-}
-
 template <int C, bool CHERRY>
 cudaError_t post_batch_c(const LevelBatch &lb, int n_sm, cudaStream_t s) {
     static DeviceOnce once;
@@ -769,21 +497,6 @@ cudaError_t pre_c(const ProbDesc &d, int o0, int nd, int n_sm, cudaStream_t s) {
 }
 
 }  // namespace
-
-cudaError_t launch_dag(const ProbDesc &d, int o_cut, int n_post, int n_pre, bool hess, int n_sm, cudaStream_t s) {
-    if (n_post + n_pre <= 0) return cudaSuccess;
-    switch (d.C * 2 + (hess ? 1 : 0)) {
-        case 2: return launch_dag_c<1, false>(d, o_cut, n_post, n_pre, n_sm, s);
-        case 3: return launch_dag_c<1, true>(d, o_cut, n_post, n_pre, n_sm, s);
-        case 4: return launch_dag_c<2, false>(d, o_cut, n_post, n_pre, n_sm, s);
-        case 5: return launch_dag_c<2, true>(d, o_cut, n_post, n_pre, n_sm, s);
-        case 6: return launch_dag_c<3, false>(d, o_cut, n_post, n_pre, n_sm, s);
-        case 7: return launch_dag_c<3, true>(d, o_cut, n_post, n_pre, n_sm, s);
-        case 8: return launch_dag_c<4, false>(d, o_cut, n_post, n_pre, n_sm, s);
-        case 9: return launch_dag_c<4, true>(d, o_cut, n_post, n_pre, n_sm, s);
-        default: return cudaErrorInvalidValue;
-    }
-}
 
 cudaError_t launch_post_level(const ProbDesc &d, int o0, int nd, int n_sm, bool cherry, cudaStream_t s) {
     switch (d.C * 2 + (cherry ? 1 : 0)) {

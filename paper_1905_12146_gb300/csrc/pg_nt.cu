@@ -755,7 +755,6 @@ __global__ void __launch_bounds__(256) reduce_kernel(const __grid_constant__ Bat
         for (int j = lane; j < d.n_tg; j += 32) s += d.lpart[j];
         s = warp_sum(s);
         if (lane == 0 && d.out_logL) *d.out_logL = s;
-        if (lane == 0 && d.dag_counter) *d.dag_counter = 0ull;   // for the next evaluation's item claims
         return;
     }
     double g = 0.0, h = 0.0;
