@@ -59,6 +59,11 @@ typedef struct pg_options {
  * TF32 with FP32 accumulation) unless this flag selects the CUDA-core (SIMT FP32) kernels. */
 #define PG_FLAG_SIMT_MSTATE 1u
 
+/* A 4-state FP64 problem evaluated alone runs its tree pass in a latency kernel that keeps each
+ * block's per-pattern vectors in shared memory when they fit (about 200 KB per block at one block
+ * per SM); this flag selects the kernel with the partials in device memory instead (comparisons). */
+#define PG_FLAG_FP64_DEVICE_PARTIALS 2u
+
 /* Storage and arithmetic of the partial likelihood vectors.  FP32: partials in FP32 with FP64
  * transition matrices split into FP32 hi/lo pairs, an exact-product form of the post-order
  * update and FP64 site likelihoods (the fast path; its error against FP64 is stated per result).

@@ -39,6 +39,7 @@ class pg_options(ctypes.Structure):
 
 
 PG_FLAG_SIMT_MSTATE = 1
+PG_FLAG_FP64_DEVICE_PARTIALS = 2
 
 
 class pg_problem(ctypes.Structure):

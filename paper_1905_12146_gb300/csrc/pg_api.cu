@@ -685,6 +685,7 @@ pg_status pg_free(pg_handle *h) {
         c->used -= h->scratch_bytes;
     }
     for (cudaEvent_t x : h->events) cudaEventDestroy(x);
+    if (h->io_host) cudaFreeHost(h->io_host);
     if (h->block && !h->external) cudaFree(h->block);
     {
         std::lock_guard<std::mutex> gl(c->mu);
@@ -1298,7 +1299,15 @@ pg_status enqueue_single(pg_handle *h, int skip, const double *d_b, double *d_lo
             use_top = (size_t)k * (pg::top_smem_bytes(d) + 1024) <= (size_t)228 * 1024;   // 1 KB reserved per block
         }
     }
-    if (!use_top) set_tiling(d, single_target(h->ctx, d), max_range);
+    // FP64: the whole tree pass in the shared-memory latency kernel when a block's vectors fit at
+    // one block per SM (one slot per block and branch); otherwise in the fused kernel
+    if (d.precision == PG_PRECISION_FP64 && d.P > 0 && !(h->ctx->flags & PG_FLAG_FP64_DEVICE_PARTIALS)) {
+        set_tiling(d, h->ctx->n_sm, max_range);
+        d.pieces = 1;
+        d.n_tg = d.n_tiles;
+        d.small64 = pg::small64_smem_bytes(d) != 0;
+    }
+    if (!use_top && !d.small64) set_tiling(d, single_target(h->ctx, d), max_range);
     fill_args_one(a, d);
     const bool hess = bwd && d_hess != nullptr;
     const bool timed = h->timing && fwd && bwd;
@@ -1730,6 +1739,17 @@ pg_status pg_get_phase_times(pg_handle *h, pg_phase_times *out) {
     return PG_OK;
 }
 
+// The API status of a handle's sticky device status word (kStatus* bits; 0 = PG_OK).
+static pg_status status_result(int st) {
+    if (st & pg::kStatusBadLength) return fail(PG_ERR_INVALID, "a branch length was negative or not finite");
+    if (st & pg::kStatusNumeric) return fail(PG_ERR_NUMERIC, "a site likelihood was zero or not finite");
+    if (st & pg::kStatusUnsettled)
+        return fail(PG_ERR_TIMEOUT, "a device-side wait gave up and a block left before the copies or products it "
+                                    "issued were confirmed complete: the device state is suspect, destroy the context");
+    if (st & pg::kStatusTimeout) return fail(PG_ERR_TIMEOUT, "a device-side wait for staged data gave up");
+    return PG_OK;
+}
+
 pg_status pg_eval_status(pg_handle *h) {
     if (!h) return fail(PG_ERR_INVALID, "NULL handle");
     DeviceGuard g(h->ctx->device);
@@ -1745,31 +1765,55 @@ pg_status pg_eval_status(pg_handle *h) {
         if (cs) PG_CUDA(cudaMemset(c->desc.status, 0, sizeof(int)));
         st |= cs;
     }
-    if (st & pg::kStatusBadLength) return fail(PG_ERR_INVALID, "a branch length was negative or not finite");
-    if (st & pg::kStatusNumeric) return fail(PG_ERR_NUMERIC, "a site likelihood was zero or not finite");
-    if (st & pg::kStatusUnsettled)
-        return fail(PG_ERR_TIMEOUT, "a device-side wait gave up and a block left before the copies or products it "
-                                    "issued were confirmed complete: the device state is suspect, destroy the context");
-    if (st & pg::kStatusTimeout) return fail(PG_ERR_TIMEOUT, "a device-side wait for staged data gave up");
-    return PG_OK;
+    return status_result(st);
 }
 
+// Host arrays through one pinned staging buffer: the lengths go in with one copy, the outputs and
+// the status word come back with two, and the call waits on the stream once.
 pg_status pg_eval(pg_handle *h, const double *b, double *logL, double *grad, double *hess,
                   double *site_logL) {
     if (!h || !b) return fail(PG_ERR_INVALID, "NULL handle or branch lengths");
     DeviceGuard g(h->ctx->device);
     if (!g.ok) return fail(PG_ERR_CUDA, "cannot select device %d", h->ctx->device);
     const int n = h->n_user, P = h->desc.P;   // the caller's nodes; added nodes keep b = 0 in io_b
-    PG_CUDA(cudaMemcpy(h->io_b, b, sizeof(double) * n, cudaMemcpyHostToDevice));
+    // the outputs were carved in this order from one block: one copy covers the requested ones
+    const char *lo = reinterpret_cast<const char *>(h->io_logL);
+    const auto end_of = [lo](const double *p, size_t count) {
+        return (size_t)(reinterpret_cast<const char *>(p + count) - lo);
+    };
+    size_t span = sizeof(double);
+    if (grad) span = std::max(span, end_of(h->io_grad, n));
+    if (hess) span = std::max(span, end_of(h->io_hess, n));
+    if (site_logL && P > 0) span = std::max(span, end_of(h->io_site, P));
+    const size_t o_st = align_up(sizeof(double) * n, 16), o_out = o_st + 16;
+    const size_t need = o_out + align_up(end_of(h->io_site, std::max(P, 1)), 16);   // every output
+    if (!h->io_host) {
+        void *p = nullptr;
+        PG_CUDA(cudaHostAlloc(&p, need, cudaHostAllocDefault));
+        h->io_host = static_cast<char *>(p);
+        h->io_host_bytes = need;
+    }
+    double *hb = reinterpret_cast<double *>(h->io_host);
+    int *hst = reinterpret_cast<int *>(h->io_host + o_st);
+    const char *hout = h->io_host + o_out;
+    std::memcpy(hb, b, sizeof(double) * n);
+    *hst = 0;
+    PG_CUDA(cudaMemcpyAsync(h->io_b, hb, sizeof(double) * n, cudaMemcpyHostToDevice, nullptr));
     pg_status st = enqueue_single(h, 0, h->io_b, h->io_logL, grad ? h->io_grad : nullptr, hess ? h->io_hess : nullptr,
                                   site_logL ? h->io_site : nullptr, nullptr, nullptr);
     if (st != PG_OK) return st;
+    PG_CUDA(cudaMemcpyAsync(h->io_host + o_out, lo, span, cudaMemcpyDeviceToHost, nullptr));
+    const bool chunked = !h->chunks.empty();
+    if (!chunked) PG_CUDA(cudaMemcpyAsync(hst, h->desc.status, sizeof(int), cudaMemcpyDeviceToHost, nullptr));
     PG_CUDA(cudaStreamSynchronize(nullptr));
-    if (logL) PG_CUDA(cudaMemcpy(logL, h->io_logL, sizeof(double), cudaMemcpyDeviceToHost));
-    if (grad) PG_CUDA(cudaMemcpy(grad, h->io_grad, sizeof(double) * n, cudaMemcpyDeviceToHost));
-    if (hess) PG_CUDA(cudaMemcpy(hess, h->io_hess, sizeof(double) * n, cudaMemcpyDeviceToHost));
-    if (site_logL && P > 0) PG_CUDA(cudaMemcpy(site_logL, h->io_site, sizeof(double) * P, cudaMemcpyDeviceToHost));
-    return pg_eval_status(h);
+    const auto at = [&](const double *p) { return reinterpret_cast<const double *>(hout + (reinterpret_cast<const char *>(p) - lo)); };
+    if (logL) *logL = *at(h->io_logL);
+    if (grad) std::memcpy(grad, at(h->io_grad), sizeof(double) * n);
+    if (hess) std::memcpy(hess, at(h->io_hess), sizeof(double) * n);
+    if (site_logL && P > 0) std::memcpy(site_logL, at(h->io_site), sizeof(double) * P);
+    if (chunked) return pg_eval_status(h);
+    if (*hst) PG_CUDA(cudaMemset(h->desc.status, 0, sizeof(int)));
+    return status_result(*hst);
 }
 
 }  // extern "C"

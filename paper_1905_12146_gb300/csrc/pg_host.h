@@ -41,6 +41,10 @@ struct pg_handle {
     uint64_t post_levels_bytes = 0, fused_bytes = 0, pre_levels_bytes = 0;
     double *io_b = nullptr, *io_logL = nullptr, *io_grad = nullptr, *io_hess = nullptr,
            *io_site = nullptr;   // device staging for the host-pointer pg_eval
+    // pinned host staging of pg_eval (allocated on its first call, freed with the handle): the branch
+    // lengths, the status word and the device span io_logL .. io_site + P, each 16-byte aligned
+    char *io_host = nullptr;
+    size_t io_host_bytes = 0;
     pg_handle_info info{};
     cudaStream_t last_stream = nullptr;
     bool have_post = false;   // an enqueued post-order left partials a backward pass can use

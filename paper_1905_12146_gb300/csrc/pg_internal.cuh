@@ -127,6 +127,8 @@ struct ProbDesc {
     int n_tiles, range_len, pieces, n_tg;   // n_tg = n_tiles * pieces used slots
     int C, n_models;
     int precision;                 // 0 FP32 partials, 1 FP64 partials
+    int small64;                   // 1: the tree pass of this FP64 problem runs in the shared-memory
+                                   // latency kernel (pg_small64.cu), tiled for it with pieces = 1
     double pi[kStates], cw[kMaxCat], rates[kMaxCat];
     float pif[kStates], gw[kMaxCat], gw2[kMaxCat];   // FP32 pi, r_l w_l, r_l^2 w_l
 };
@@ -254,6 +256,15 @@ cudaError_t launch_reduce(const BatchArgs<MAXB> &args, bool hess, cudaStream_t s
 cudaError_t launch_chunk_sum(const double *parts, int k, int n, double *out, cudaStream_t s);
 // resident blocks per SM of the tree kernel for C categories and the given precision
 int tree_blocks_per_sm(int C, bool f64);
+// the whole tree pass of a single small FP64 problem with its per-block vectors in shared memory
+// (pg_small64.cu): the shared bytes one block of d's tiling needs, 0 when the kernel does not take
+// d: not an FP64 problem with patterns, more than kSmall64MaxRange patterns per block (there the
+// FP64 pipe, not the dependent chain, bounds a level, and the fused kernel's wider blocks keep it
+// busier: measured 143 us against 94 us at 33 patterns per block), or more than kSmall64MaxSmem
+constexpr size_t kSmall64MaxSmem = 200 * 1024;
+constexpr int kSmall64MaxRange = 16;
+size_t small64_smem_bytes(const ProbDesc &d);
+cudaError_t launch_small64(const BatchArgs<1> &args, bool hess, cudaStream_t s);
 // the levels [cut, n_levels) of a single FP32 problem with shared-memory-resident partials
 // (pg_top.cu); returns cudaErrorNotSupported when they do not fit
 cudaError_t launch_top(const BatchArgs<1> &args, bool hess, int n_sm, cudaStream_t s);

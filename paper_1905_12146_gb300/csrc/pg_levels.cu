@@ -47,8 +47,12 @@ struct PreStage {
     float inv[R];                // 1 / Lhat_p
     float w[R];                  // pattern weights
     uint8_t y0[R], y1[R];
-    float4 tab[2][C][10];        // P hi columns and row sums, then G = Q P alike, both branches
-    float4 qtab[2][4];           // Q columns of both children's models
+    // both branches' tables: P hi columns and row sums, then G = Q P alike (the first 10 columns),
+    // staged with one copy per branch (all C tables, which for C > 1 includes the other columns)
+    static constexpr int TC = C == 1 ? 10 : kPtabCols;
+    float4 tab[2][C][TC];
+    float4 qtab[2][4];           // Q columns of both children's models (not staged for a cherry level
+                                 // without the Hessian: tips take G's columns)
 };
 
 constexpr int kConsumerWarps = kLevelRange / 32;
@@ -105,21 +109,23 @@ __device__ void issue_post(const ProbDesc &d, const Item &it, PostStage<C, CHERR
     }
 }
 
-template <int C, bool CHERRY>
+template <int C, bool HESS, bool CHERRY>
 __device__ void issue_pre(const ProbDesc &d, const Item &it, PreStage<C, CHERRY> &sm, uint64_t *bar) {
     const int N = d.n_tips, Ps = d.Ps, k = it.op.x, c0 = it.op.y, c1 = it.op.z, p0 = it.p0;
     const bool t0 = c0 < N, t1 = c1 < N;
     const float4 *post = static_cast<const float4 *>(d.post);
     const float4 *pre = static_cast<const float4 *>(d.pre);
     const unsigned rowb = (unsigned)it.cnt * 16u, eb = round16(it.cnt * 4u), yb = round16((unsigned)it.cnt);
-    unsigned bytes = C * rowb + eb + 3u * eb + 2u * C * 10u * 16u + 2u * 64u;
+    constexpr bool kQ = HESS || !CHERRY;   // the Q columns are read by some product
+    constexpr unsigned tb = C * PreStage<C, CHERRY>::TC * 16u;   // a branch's staged tables
+    unsigned bytes = C * rowb + eb + 3u * eb + 2u * tb + (kQ ? 2u * 64u : 0u);
     bytes += t0 ? yb : (C * rowb + eb);
     bytes += t1 ? yb : (C * rowb + eb);
     mbar_arrive_expect(bar, bytes);
-    for (int side = 0; side < 2; ++side) {
+    for (int side = 0; side < 2; ++side) {   // one copy per branch: its C tables are contiguous
         const int c = side ? c1 : c0;
-        for (int l = 0; l < C; ++l) bulk_load(sm.tab[side][l], d.Ptab + ((size_t)c * C + l) * kPtabCols, 10u * 16u, bar);
-        bulk_load(sm.qtab[side], d.Qf + 4 * (d.bmodel ? d.bmodel[c] : 0), 64u, bar);
+        bulk_load(sm.tab[side], d.Ptab + (size_t)c * C * kPtabCols, tb, bar);
+        if (kQ) bulk_load(sm.qtab[side], d.Qf + 4 * (d.bmodel ? d.bmodel[c] : 0), 64u, bar);
     }
     bulk_load(sm.eq, d.qe + (size_t)(k - N) * Ps + p0, eb, bar);
     for (int l = 0; l < C; ++l) bulk_load(sm.qk[l], pre + ((size_t)(k - N) * C + l) * Ps + p0, rowb, bar);
@@ -379,7 +385,7 @@ __device__ __forceinline__ void pre_walk(int n_items, const Src &src) {
     using St = PreStage<C, CHERRY>;
     auto &ring = *reinterpret_cast<Ring<St, STAGES> *>(smem_raw);
     staged_walk<false>(n_items, ring, src,
-                [&](const Item &it, St &st, uint64_t *bar) { issue_pre<C, CHERRY>(*it.pd, it, st, bar); },
+                [&](const Item &it, St &st, uint64_t *bar) { issue_pre<C, HESS, CHERRY>(*it.pd, it, st, bar); },
                 [&](const Item &it, const St &st, int t) { compute_pre<C, HESS, CHERRY>(*it.pd, it, st, t); });
 }
 

@@ -5,7 +5,10 @@
 // of an allocation inside a latency-critical loop, code running under an external memory manager
 // that owns every device allocation of the process, or plug-ins whose host application forbids
 // allocation after start-up.  They pass host arrays in and out; every intermediate array lives in
-// the fixed device array below, and host-side planning uses fixed static buffers.
+// the fixed device array below, and host-side planning uses fixed static buffers.  The inputs are
+// laid out at the start of the array and go in with one copy from a static host image; the status
+// word and the outputs follow them and come back with one copy (array by array when a problem's
+// regions exceed the static images).
 //
 // The scratch array is g_noalloc_scratch (PG_NOALLOC_SCRATCH_BYTES, 64 MiB).  Being a file-scope
 // __device__ variable it is created on every GPU that loads this library's code and stays there
@@ -25,6 +28,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstring>
 
 #include "phylograd.h"
 #include "pg_host.h"
@@ -48,6 +52,10 @@ int g_level_off[kMaxTips + 1];
 float4 g_qf[kMaxModels * 4];
 double g_mpow[kMaxModels * (pg::kTaylorDeg + 1) * 16];
 double g_qnorm[kMaxModels];
+// host images of the input and output regions of the scratch array (one copy each way when the
+// problem's regions fit; larger problems copy array by array)
+alignas(256) unsigned char g_stage_in[4u << 20];
+alignas(256) unsigned char g_stage_out[1u << 20];
 
 // the message of the last failure: a fixed buffer, formatted with vsnprintf (integer and string
 // conversions only, which allocate nothing), then published to pg_last_error
@@ -213,15 +221,18 @@ extern "C" pg_status pg_eval_noalloc(const pg_problem *pr, const double *b, doub
     const size_t o_Qd = take(sizeof(double) * 16 * M), o_Qf = take(sizeof(float4) * 4 * M);
     const size_t o_Mp = take(sizeof(double) * (pg::kTaylorDeg + 1) * 16 * M), o_qn = take(sizeof(double) * M);
     const size_t o_bm = take(pr->branch_model ? sizeof(int) * n : 0);
+    const size_t o_ib = take(sizeof(double) * n);
+    // the status word ends the inputs (it goes in as zero) and starts the outputs
+    const size_t o_st = take(sizeof(int)), o_il = take(sizeof(double)), o_ig = take(sizeof(double) * n);
+    const size_t o_ih = take(sizeof(double) * n), o_is = take(sizeof(double) * (P > 0 ? P : 1));
+    const size_t in_bytes = o_st + sizeof(int), out_bytes = o_is + sizeof(double) * (P > 0 ? P : 1) - o_st;
     const size_t o_P = take(f64 ? sizeof(double2) * n * C * pg::kPtab64Pairs : sizeof(float4) * n * C * pg::kPtabCols);
     const size_t part = (size_t)(N - 1) * C * Ps * (f64 ? 2 * sizeof(double2) : sizeof(float4));
     const size_t o_post = take(part), o_pre = take(part);
     const size_t o_pe = take(sizeof(int) * (N - 1) * Ps), o_qe = take(sizeof(int) * (N - 1) * Ps);
     const size_t o_gp = take(sizeof(double) * n * slot_cap), o_hp = take(sizeof(double) * n * slot_cap);
-    const size_t o_lp = take(sizeof(double) * slot_cap), o_st = take(sizeof(int));
+    const size_t o_lp = take(sizeof(double) * slot_cap);
     const size_t o_sinv = take(sizeof(float) * (Ps > 16 ? Ps : 16)), o_ser = take(sizeof(int) * (Ps > 16 ? Ps : 16));
-    const size_t o_ib = take(sizeof(double) * n), o_il = take(sizeof(double)), o_ig = take(sizeof(double) * n);
-    const size_t o_ih = take(sizeof(double) * n), o_is = take(sizeof(double) * (P > 0 ? P : 1));
     if (off > (size_t)PG_NOALLOC_SCRATCH_BYTES)
         return noalloc_fail(PG_ERR_UNSUPPORTED, "problem needs %zu bytes of scratch; the fixed array holds %u",
                             off, (unsigned)PG_NOALLOC_SCRATCH_BYTES);
@@ -247,22 +258,38 @@ extern "C" pg_status pg_eval_noalloc(const pg_problem *pr, const double *b, doub
         g_qnorm[md] = nrm;
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    NOALLOC_CUDA(cudaMemcpyAsync(base + o_ops, g_ops, sizeof(int4) * (N - 1), cudaMemcpyHostToDevice, s));
-    NOALLOC_CUDA(cudaMemcpyAsync(base + o_lv, g_level_off, sizeof(int) * (H + 1), cudaMemcpyHostToDevice, s));
-    if (P > 0) {
-        NOALLOC_CUDA(cudaMemcpy2DAsync(base + o_tips, Ps, pr->tip_states, pr->tip_stride > 0 ? pr->tip_stride : P, P, N,
-                                       cudaMemcpyHostToDevice, s));
-        NOALLOC_CUDA(cudaMemcpyAsync(base + o_w, pr->pattern_weights, sizeof(double) * P, cudaMemcpyHostToDevice, s));
+    const size_t tip_stride = pr->tip_stride > 0 ? (size_t)pr->tip_stride : (size_t)P;
+    if (in_bytes <= sizeof g_stage_in) {   // the inputs as laid out on the device: one copy
+        unsigned char *h = g_stage_in;
+        std::memcpy(h + o_ops, g_ops, sizeof(int4) * (N - 1));
+        std::memcpy(h + o_lv, g_level_off, sizeof(int) * (H + 1));
+        for (int t = 0; t < N && P > 0; ++t) std::memcpy(h + o_tips + (size_t)t * Ps, pr->tip_states + t * tip_stride, P);
+        if (P > 0) std::memcpy(h + o_w, pr->pattern_weights, sizeof(double) * P);
+        std::memcpy(h + o_Qd, pr->Q, sizeof(double) * 16 * M);
+        std::memcpy(h + o_Qf, g_qf, sizeof(float4) * 4 * M);
+        std::memcpy(h + o_Mp, g_mpow, sizeof(double) * (pg::kTaylorDeg + 1) * 16 * M);
+        std::memcpy(h + o_qn, g_qnorm, sizeof(double) * M);
+        if (pr->branch_model) std::memcpy(h + o_bm, pr->branch_model, sizeof(int) * n);
+        std::memcpy(h + o_ib, b, sizeof(double) * n);
+        std::memset(h + o_st, 0, sizeof(int));   // the sticky status starts clear
+        NOALLOC_CUDA(cudaMemcpyAsync(base, h, in_bytes, cudaMemcpyHostToDevice, s));
+    } else {
+        NOALLOC_CUDA(cudaMemcpyAsync(base + o_ops, g_ops, sizeof(int4) * (N - 1), cudaMemcpyHostToDevice, s));
+        NOALLOC_CUDA(cudaMemcpyAsync(base + o_lv, g_level_off, sizeof(int) * (H + 1), cudaMemcpyHostToDevice, s));
+        if (P > 0) {
+            NOALLOC_CUDA(cudaMemcpy2DAsync(base + o_tips, Ps, pr->tip_states, tip_stride, P, N, cudaMemcpyHostToDevice, s));
+            NOALLOC_CUDA(cudaMemcpyAsync(base + o_w, pr->pattern_weights, sizeof(double) * P, cudaMemcpyHostToDevice, s));
+        }
+        NOALLOC_CUDA(cudaMemcpyAsync(base + o_Qd, pr->Q, sizeof(double) * 16 * M, cudaMemcpyHostToDevice, s));
+        NOALLOC_CUDA(cudaMemcpyAsync(base + o_Qf, g_qf, sizeof(float4) * 4 * M, cudaMemcpyHostToDevice, s));
+        NOALLOC_CUDA(cudaMemcpyAsync(base + o_Mp, g_mpow, sizeof(double) * (pg::kTaylorDeg + 1) * 16 * M,
+                                     cudaMemcpyHostToDevice, s));
+        NOALLOC_CUDA(cudaMemcpyAsync(base + o_qn, g_qnorm, sizeof(double) * M, cudaMemcpyHostToDevice, s));
+        if (pr->branch_model)
+            NOALLOC_CUDA(cudaMemcpyAsync(base + o_bm, pr->branch_model, sizeof(int) * n, cudaMemcpyHostToDevice, s));
+        NOALLOC_CUDA(cudaMemcpyAsync(base + o_ib, b, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+        NOALLOC_CUDA(cudaMemsetAsync(base + o_st, 0, sizeof(int), s));   // the sticky status starts clear
     }
-    NOALLOC_CUDA(cudaMemcpyAsync(base + o_Qd, pr->Q, sizeof(double) * 16 * M, cudaMemcpyHostToDevice, s));
-    NOALLOC_CUDA(cudaMemcpyAsync(base + o_Qf, g_qf, sizeof(float4) * 4 * M, cudaMemcpyHostToDevice, s));
-    NOALLOC_CUDA(cudaMemcpyAsync(base + o_Mp, g_mpow, sizeof(double) * (pg::kTaylorDeg + 1) * 16 * M,
-                                 cudaMemcpyHostToDevice, s));
-    NOALLOC_CUDA(cudaMemcpyAsync(base + o_qn, g_qnorm, sizeof(double) * M, cudaMemcpyHostToDevice, s));
-    if (pr->branch_model)
-        NOALLOC_CUDA(cudaMemcpyAsync(base + o_bm, pr->branch_model, sizeof(int) * n, cudaMemcpyHostToDevice, s));
-    NOALLOC_CUDA(cudaMemcpyAsync(base + o_ib, b, sizeof(double) * n, cudaMemcpyHostToDevice, s));
-    NOALLOC_CUDA(cudaMemsetAsync(base + o_st, 0, sizeof(int), s));   // the sticky status starts clear
 
     pg::BatchArgs<1> a;
     pg::ProbDesc &d = a.d[0];
@@ -317,6 +344,19 @@ extern "C" pg_status pg_eval_noalloc(const pg_problem *pr, const double *b, doub
         d.gw[l] = on ? (float)(pr->cat_rates[l] * pr->cat_weights[l]) : 0.f;
         d.gw2[l] = on ? (float)(pr->cat_rates[l] * pr->cat_rates[l] * pr->cat_weights[l]) : 0.f;
     }
+    if (f64 && P > 0) {   // the shared-memory latency kernel when a block's vectors fit at one block per SM
+        pg::ProbDesc ds = d;
+        ds.range_len = (P + n_sm - 1) / n_sm;
+        if (ds.range_len > pg::kMaxRange) ds.range_len = pg::kMaxRange;
+        ds.n_tiles = (P + ds.range_len - 1) / ds.range_len;
+        ds.pieces = 1;
+        ds.n_tg = ds.n_tiles;
+        ds.small64 = 1;
+        if (pg::small64_smem_bytes(ds) != 0) {
+            d = ds;
+            T = ds.n_tiles;
+        }
+    }
     a.n = 1;
     a.tile_base[0] = 0;
     a.tile_base[1] = T;
@@ -326,14 +366,25 @@ extern "C" pg_status pg_eval_noalloc(const pg_problem *pr, const double *b, doub
     a.red_base[1] = n + 1;
     NOALLOC_CUDA(pg::launch_eval_nt<1>(a, hess != nullptr, s));
 
-    if (logL) NOALLOC_CUDA(cudaMemcpyAsync(logL, base + o_il, sizeof(double), cudaMemcpyDeviceToHost, s));
-    if (grad) NOALLOC_CUDA(cudaMemcpyAsync(grad, base + o_ig, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
-    if (hess) NOALLOC_CUDA(cudaMemcpyAsync(hess, base + o_ih, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
-    if (site_logL && P > 0)
-        NOALLOC_CUDA(cudaMemcpyAsync(site_logL, base + o_is, sizeof(double) * P, cudaMemcpyDeviceToHost, s));
     int status = 0;
-    NOALLOC_CUDA(cudaMemcpyAsync(&status, base + o_st, sizeof(int), cudaMemcpyDeviceToHost, s));
-    NOALLOC_CUDA(cudaStreamSynchronize(s));
+    if (out_bytes <= sizeof g_stage_out) {   // status and outputs as laid out on the device: one copy
+        const unsigned char *h = g_stage_out;
+        NOALLOC_CUDA(cudaMemcpyAsync(g_stage_out, base + o_st, out_bytes, cudaMemcpyDeviceToHost, s));
+        NOALLOC_CUDA(cudaStreamSynchronize(s));
+        std::memcpy(&status, h, sizeof(int));
+        if (logL) std::memcpy(logL, h + (o_il - o_st), sizeof(double));
+        if (grad) std::memcpy(grad, h + (o_ig - o_st), sizeof(double) * n);
+        if (hess) std::memcpy(hess, h + (o_ih - o_st), sizeof(double) * n);
+        if (site_logL && P > 0) std::memcpy(site_logL, h + (o_is - o_st), sizeof(double) * P);
+    } else {
+        if (logL) NOALLOC_CUDA(cudaMemcpyAsync(logL, base + o_il, sizeof(double), cudaMemcpyDeviceToHost, s));
+        if (grad) NOALLOC_CUDA(cudaMemcpyAsync(grad, base + o_ig, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        if (hess) NOALLOC_CUDA(cudaMemcpyAsync(hess, base + o_ih, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        if (site_logL && P > 0)
+            NOALLOC_CUDA(cudaMemcpyAsync(site_logL, base + o_is, sizeof(double) * P, cudaMemcpyDeviceToHost, s));
+        NOALLOC_CUDA(cudaMemcpyAsync(&status, base + o_st, sizeof(int), cudaMemcpyDeviceToHost, s));
+        NOALLOC_CUDA(cudaStreamSynchronize(s));
+    }
     if (status & pg::kStatusBadLength) return noalloc_fail(PG_ERR_INVALID, "a branch length was negative or not finite");
     if (status & pg::kStatusNumeric) return noalloc_fail(PG_ERR_NUMERIC, "a site likelihood was zero or not finite");
     if (status & pg::kStatusUnsettled)

@@ -741,6 +741,20 @@ __global__ void __launch_bounds__(kBlock, 1) tree4d_kernel(const __grid_constant
 // K5: fixed-order reduction over tile groups: one warp per branch (grad, hess), one per logL
 // ------------------------------------------------------------------------------------------
 
+// sum of v[lane], v[lane + 32], ... below ns: four independent loads in flight, fixed order
+__device__ __forceinline__ double lane_sum(const double *v, int ns, int lane) {
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int j = lane;
+    for (; j + 96 < ns; j += 128) {
+        a0 += v[j];
+        a1 += v[j + 32];
+        a2 += v[j + 64];
+        a3 += v[j + 96];
+    }
+    for (; j < ns; j += 32) a0 += v[j];
+    return (a0 + a1) + (a2 + a3);
+}
+
 template <int MAXB>
 __global__ void __launch_bounds__(256) reduce_kernel(const __grid_constant__ BatchArgs<MAXB> a, int want_hess) {
     pdl_wait();   // launched while the last pass drains: its slot sums are complete and visible after this
@@ -751,9 +765,7 @@ __global__ void __launch_bounds__(256) reduce_kernel(const __grid_constant__ Bat
     const ProbDesc &d = a.d[pid];
     const int item = gw - a.red_base[pid];
     if (item == d.n_nodes) {
-        double s = 0.0;
-        for (int j = lane; j < d.n_tg; j += 32) s += d.lpart[j];
-        s = warp_sum(s);
+        const double s = warp_sum(lane_sum(d.lpart, d.n_tg, lane));
         if (lane == 0 && d.out_logL) *d.out_logL = s;
         return;
     }
@@ -761,14 +773,8 @@ __global__ void __launch_bounds__(256) reduce_kernel(const __grid_constant__ Bat
     if (item != d.root) {
         // branches below the cut were reduced per level-kernel block, the others per fused slot
         const int ns = (d.cut > 0 && d.plevel[item] < d.cut) ? d.level_ranges * (kLevelRange / 32) : d.n_tg;
-        const double *gp = d.gpart + (size_t)item * d.slot_cap;
-        for (int j = lane; j < ns; j += 32) g += gp[j];
-        g = warp_sum(g);
-        if (want_hess) {
-            const double *hp = d.hpart + (size_t)item * d.slot_cap;
-            for (int j = lane; j < ns; j += 32) h += hp[j];
-            h = warp_sum(h);
-        }
+        g = warp_sum(lane_sum(d.gpart + (size_t)item * d.slot_cap, ns, lane));
+        if (want_hess) h = warp_sum(lane_sum(d.hpart + (size_t)item * d.slot_cap, ns, lane));
     }
     if (lane == 0) {
         if (d.gscale) g *= *d.gscale;
@@ -864,6 +870,9 @@ cudaError_t launch_pmatrix(const BatchArgs<MAXB> &args, cudaStream_t s) {
 template <int MAXB>
 cudaError_t launch_tree(const BatchArgs<MAXB> &args, bool hess, cudaStream_t s) {
     if (args.n <= 0 || args.tile_base[args.n] <= 0) return cudaSuccess;
+    if constexpr (MAXB == 1) {
+        if (args.d[0].small64) return launch_small64(args, hess, s);
+    }
     const bool f64 = args.d[0].precision == 1;
     return hess ? launch_tree_c<MAXB, true>(args, args.d[0].C, f64, s)
                 : launch_tree_c<MAXB, false>(args, args.d[0].C, f64, s);

@@ -84,6 +84,52 @@ def test_small_configuration_fp64(ctx, oracle_mod):
     assert np.abs(got["grad"] - ref.grad).max() <= 1e-11 * np.abs(ref.grad).max()
 
 
+@pytest.mark.parametrize("case", ["small", "cat4", "caterpillar", "two_taxa", "models", "zero_and_long", "wide"])
+def test_fp64_latency_kernel_and_device_partials_kernel(ctx, oracle_mod, case):
+    """FP64 problems evaluated alone run in the shared-memory latency kernel when a block's vectors
+    fit; PG_FLAG_FP64_DEVICE_PARTIALS selects the kernel with the partials in device memory.  Both
+    against the oracle at the FP64 bounds, and against each other (the same products, summed in
+    another order)."""
+    from paper_1905_12146_gb300 import _native
+    pr = {"small": lambda: wl.config_small(seed=3),
+          "cat4": lambda: wl.random_problem(60, 333, n_states=4, n_cat=4, seed=31, b_mean=0.05, ambiguous=0.03,
+                                            weights="int"),
+          "caterpillar": lambda: wl.random_problem(120, 200, n_states=4, n_cat=2, seed=32, tree="caterpillar",
+                                                   b_mean=0.02, ambiguous=0.02),
+          "two_taxa": lambda: wl.random_problem(2, 70, n_states=4, n_cat=3, seed=33, b_mean=0.3, ambiguous=0.2),
+          "models": lambda: wl.random_problem(40, 257, n_states=4, n_cat=2, seed=34, n_models=3, relabel=True,
+                                              ambiguous=0.05, weights="int"),
+          "zero_and_long": lambda: wl.random_problem(30, 150, n_states=4, n_cat=2, seed=35, b_mean=0.05),
+          "wide": lambda: wl.random_problem(24, 2400, n_states=4, n_cat=1, seed=36, b_mean=0.1, weights="int"),
+          }[case]()
+    b = pr["b"].copy()
+    if case == "zero_and_long":
+        b[::5] = 0.0
+        b[2::9] = 20.0
+        b[wl.root_of(pr["parent"])] = 0.0
+    ref = oracle_mod.evaluate(pr, b)
+    out = []
+    for flags in (0, _native.PG_FLAG_FP64_DEVICE_PARTIALS):
+        c = _native.Context(0, flags=flags)
+        h = c.upload(pr, "fp64")
+        try:
+            got = h.eval(b, grad=True, hess=True, site=True)
+        finally:
+            h.close()
+            c.close()
+        assert got["status"] == 0
+        assert abs(got["logL"] - ref.logL) <= 1e-12 * abs(ref.logL)
+        assert np.abs(got["grad"] - ref.grad).max() <= 1e-11 * np.abs(ref.grad).max()
+        assert np.abs(got["hess"] - ref.hess).max() <= 1e-10 * np.abs(ref.hess).max()
+        np.testing.assert_allclose(got["site_logL"], ref.site_logL, rtol=0, atol=1e-10)
+        assert got["grad"][wl.root_of(pr["parent"])] == 0.0
+        out.append(got)
+    a, d = out
+    assert abs(a["logL"] - d["logL"]) <= 1e-13 * abs(d["logL"])
+    assert np.abs(a["grad"] - d["grad"]).max() <= 1e-12 * np.abs(d["grad"]).max()
+    np.testing.assert_allclose(a["site_logL"], d["site_logL"], rtol=0, atol=1e-12)
+
+
 def test_small_configuration_fp32(ctx, oracle_mod):
     _compare(ctx, oracle_mod, wl.config_small(seed=0), precision="fp32")
 
