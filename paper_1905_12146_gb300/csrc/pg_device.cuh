@@ -107,6 +107,12 @@ __device__ __forceinline__ int scale_exponent64(double mx) {
 __device__ __forceinline__ float pow2f(int e) {   // 2^e, e in [-126, 127]
     return __int_as_float((e + 127) << 23);
 }
+// x * 2^e in FP32 arithmetic: a multiplication by an exact power of two for e in [-126, 127]
+// (exact for a normal result, one rounding for a subnormal one, as ldexpf), ldexpf beyond
+__device__ __forceinline__ float ldexp2f(float x, int e) {
+    if (e >= -126 && e <= 127) return x * pow2f(e);
+    return ldexpf(x, e);
+}
 __device__ __forceinline__ float4 scale4(float4 v, int e) {   // v * 2^-e exactly
     if (e >= -126 && e <= 126) return scal(v, pow2f(-e));
     return f4(ldexpf(v.x, -e), ldexpf(v.y, -e), ldexpf(v.z, -e), ldexpf(v.w, -e));

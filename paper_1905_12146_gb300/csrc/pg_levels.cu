@@ -250,15 +250,17 @@ __device__ __forceinline__ void compute_pre_one(const ProbDesc &d, const Item &i
         for (int l = 0; l < C; ++l) __stcg(pre + ((size_t)(c1 - N) * C + l) * Ps + p, scale4(q1[l], e));
         __stcg(d.qe + (size_t)(c1 - N) * Ps + p, Eq + E0 + e);
     }
-    const float d0 = ldexpf(g0, dE) * inv, d1 = ldexpf(g1, dE) * inv;
+    const float d0 = ldexp2f(g0, dE) * inv, d1 = ldexp2f(g1, dE) * inv;
     sums[0] = wt != 0.f ? wt * d0 : 0.f;
     sums[1] = wt != 0.f ? wt * d1 : 0.f;
-    sums[2] = (HESS && wt != 0.f) ? wt * (ldexpf(h0, dE) * inv - d0 * d0) : 0.f;
-    sums[3] = (HESS && wt != 0.f) ? wt * (ldexpf(h1, dE) * inv - d1 * d1) : 0.f;
+    sums[2] = (HESS && wt != 0.f) ? wt * (ldexp2f(h0, dE) * inv - d0 * d0) : 0.f;
+    sums[3] = (HESS && wt != 0.f) ? wt * (ldexp2f(h1, dE) * inv - d1 * d1) : 0.f;
 }
-// the item's patterns t, t + kLevelRange, ... of consumer thread t; the warp's sums (32 patterns at a
-// time in FP32, those added in FP64) go to its own slot of both child branches (slot = 4 * range +
-// warp; the reduction adds the slots in a fixed order)
+// the item's patterns t, t + kLevelRange, ... of consumer thread t; each thread adds its patterns'
+// terms, then the warp adds its 32 lanes (all in FP32: R / 4 patterns per slot, no FP64 instruction,
+// which this GPU issues at a small fraction of the FP32 rate), and lane 0 stores the warp's sums in
+// its own slot of both child branches (slot = 4 * range + warp; the reduction adds the slots in FP64
+// in a fixed order)
 template <int C, bool HESS, bool CHERRY>
 __device__ __forceinline__ void compute_pre(const ProbDesc &d, const Item &it, const PreStage<C, CHERRY> &sm, int t) {
     if constexpr (PreStage<C, CHERRY>::R == kLevelRange) {   // one pattern per thread
@@ -275,20 +277,21 @@ __device__ __forceinline__ void compute_pre(const ProbDesc &d, const Item &it, c
         }
         return;
     }
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 1
     for (int tt = t; tt < PreStage<C, CHERRY>::R; tt += kLevelRange) {
         float sums[4];
         compute_pre_one<C, HESS, CHERRY>(d, it, sm, tt, sums);
 #pragma unroll
-        for (int s = 0; s < (HESS ? 4 : 2); ++s) acc[s] += (double)warp_sum_f(sums[s]);
+        for (int s = 0; s < (HESS ? 4 : 2); ++s) acc[s] += sums[s];
     }
     const int lane = t & 31, slot = it.rg * kConsumerWarps + (t >> 5);
-    if (lane == 0) {
 #pragma unroll
-        for (int s = 0; s < (HESS ? 4 : 2); ++s) {
+    for (int s = 0; s < (HESS ? 4 : 2); ++s) {
+        const float v = warp_sum_f(acc[s]);
+        if (lane == 0) {
             double *dst = (s < 2) ? d.gpart : d.hpart;
-            dst[(size_t)((s & 1) ? it.op.z : it.op.y) * d.slot_cap + slot] = acc[s];
+            dst[(size_t)((s & 1) ? it.op.z : it.op.y) * d.slot_cap + slot] = (double)v;
         }
     }
 }

@@ -234,8 +234,8 @@ __global__ void __launch_bounds__(kChThreads) m_pre_cherry_kernel(const __grid_c
             }
         }
         if (onl && wl != 0.0) {
-            acc[0] += wl * (double)(cw * ldexpf(my0, dEl) * invl);
-            acc[1] += wl * (double)(cw * ldexpf(my1, dEl) * invl);
+            acc[0] += wl * (double)(cw * ldexp2f(my0, dEl) * invl);
+            acc[1] += wl * (double)(cw * ldexp2f(my1, dEl) * invl);
         }
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

@@ -527,7 +527,7 @@ __global__ void __launch_bounds__(kMThreads) m_pre_kernel(const __grid_constant_
                     t = fmaf(qt[i][3], uu[i][3], t);
                     t = sum16(t);
                     const int dE = Eq[i] + Ex[1 - side][i] + Ex[side][i] - Er[i];
-                    const float term = (float)d.cw[l] * ldexpf(t, dE) * inv[i];
+                    const float term = (float)d.cw[l] * ldexp2f(t, dE) * inv[i];
                     if (kind == 0) dsum[side][i] += term;
                     else hsum[side][i] += term;
                 }

@@ -554,8 +554,8 @@ m_pre_tc_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtenso
             const float cw = (float)d.cw[l];
 #pragma unroll
             for (int side = 0; side < 2; ++side) {
-                dsum[side] += cw * ldexpf(dot[side], dE) * inv;
-                if (HESS) hsum[side] += cw * ldexpf(hdot[side], dE) * inv;
+                dsum[side] += cw * ldexp2f(dot[side], dE) * inv;
+                if (HESS) hsum[side] += cw * ldexp2f(hdot[side], dE) * inv;
             }
         }
         fence_async_smem();
@@ -874,7 +874,7 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
             const int dE = Eq + Ex[0] + Ex[1] - Er;
             const float cw = (float)d.cw[l];
             for (int side = 0; side < 2; ++side)
-                dsum[side] += cw * ldexpf(half_part[side][0][t] + half_part[side][1][t], dE) * inv;
+                dsum[side] += cw * ldexp2f(half_part[side][0][t] + half_part[side][1][t], dE) * inv;
         }
         if (leader && !root && l + 1 < l1) issue_qk(l + 1);
         if (any_int) {

@@ -544,14 +544,14 @@ __device__ __forceinline__ void pre_level_chunk(const ProbDesc &d, const PairMet
     const float inv = ra.invL[m.q];
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-        const float dd = ldexpf(g[s], dE) * inv;
+        const float dd = ldexp2f(g[s], dE) * inv;
         const double dg = wt != 0.0 ? wt * (double)dd : 0.0;
         segment_sums(m.u, m.active, dg, chunk, cnt, pieces, [&](int us, int pc, double v) {
             const int4 o = __ldg(d.ops + o0 + us);
             d.gpart[(size_t)(s ? o.z : o.y) * d.slot_cap + slot0 + pc] = v;
         });
         if (HESS) {
-            const double dh = wt != 0.0 ? wt * (double)(ldexpf(h[s], dE) * inv - dd * dd) : 0.0;
+            const double dh = wt != 0.0 ? wt * (double)(ldexp2f(h[s], dE) * inv - dd * dd) : 0.0;
             segment_sums(m.u, m.active, dh, chunk, cnt, pieces, [&](int us, int pc, double v) {
                 const int4 o = __ldg(d.ops + o0 + us);
                 d.hpart[(size_t)(s ? o.z : o.y) * d.slot_cap + slot0 + pc] = v;

@@ -266,9 +266,9 @@ __global__ void __launch_bounds__(kBlock, 2) top_kernel(const __grid_constant__ 
                         __stcg(d.qe + (size_t)(c - N) * Ps + p, eq_c);
                     }
                 }
-                const float dd = ldexpf(gs, dE) * inv;
+                const float dd = ldexp2f(gs, dE) * inv;
                 dg[side] = wt != 0.f ? wt * dd : 0.f;
-                dh[side] = (HESS && wt != 0.f) ? wt * (ldexpf(hs, dE) * inv - dd * dd) : 0.f;
+                dh[side] = (HESS && wt != 0.f) ? wt * (ldexp2f(hs, dE) * inv - dd * dd) : 0.f;
             }
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
