@@ -37,14 +37,16 @@ cudaError_t device_once(DeviceOnce &o, F &&setup, int *value = nullptr) {
 
 constexpr int kStates = 4;      // nucleotide state space handled by the kernels in pg_nt.cu
 constexpr int kMaxCat = 4;      // rate categories held in registers per pattern
-constexpr int kMaxBatch = 32;   // problems per batched launch (kernel-parameter descriptors)
+// problems per batched launch (kernel-parameter descriptors): BatchArgs<64> is 32,528 bytes, within
+// the 32,764 bytes a kernel's parameters may take
+constexpr int kMaxBatch = 64;
 constexpr int kMaxRange = 1024;  // patterns per thread block of the tree kernel (shared arrays)
 constexpr int kBlock = 256;      // threads per block of the tree kernel
 constexpr int kLevelRange = 128; // consumer threads per block of the level kernels (4 warps)
 // patterns per item of the level kernels for C rate categories: an item's copies and barrier round
 // trips cost the same whatever its size, so with fewer categories (smaller rows) an item takes more
 // patterns (each consumer thread kLevelRange apart), keeping items at several KB
-__host__ __device__ constexpr int level_range(int C) { return C == 1 ? 4 * kLevelRange : (C == 2 ? 2 * kLevelRange : kLevelRange); }
+__host__ __device__ constexpr int level_range(int C) { return C <= 2 ? 2 * kLevelRange : kLevelRange; }
 constexpr int kTaylorDeg = 12;   // degree of the Taylor polynomial of e^{Q t} (||Q t||_1 <= 1/4)
 // FP32 transition table per (branch, category), float4 columns of the 4x4 matrices:
 //   [0..4]   P hi (columns 0..3, then the row sums = P applied to the all-ones vector)
@@ -144,6 +146,7 @@ struct BatchArgs {
     int red_base[MAXB + 1];    // prefix sums of n + 1     (reduce warps)
     ProbDesc d[MAXB];
 };
+static_assert(sizeof(BatchArgs<kMaxBatch>) + sizeof(int) <= 32764, "batched launch parameters exceed 32,764 bytes");
 
 // one problem of the clock parameterisation b_i = mu eps_i (t_i - t_parent(i)) (pg_clock.cu);
 // every array is [n_nodes] on the device, mu and g_mu are device scalars

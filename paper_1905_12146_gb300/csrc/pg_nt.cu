@@ -783,6 +783,18 @@ __global__ void __launch_bounds__(256) reduce_kernel(const __grid_constant__ Bat
     }
 }
 
+// logL alone (a forward part): warp i sums problem i's slots in the order reduce_kernel does
+template <int MAXB>
+__global__ void __launch_bounds__(256) reduce_logl_kernel(const __grid_constant__ BatchArgs<MAXB> a) {
+    pdl_wait();
+    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (gw >= a.n) return;
+    const ProbDesc &d = a.d[gw];
+    const double s = warp_sum(lane_sum(d.lpart, d.n_tg, lane));
+    if (lane == 0 && d.out_logL) *d.out_logL = s;
+}
+
 template <int C>
 size_t f32_dyn_smem(int range_len) {
     return f32_stage_bytes<C>(kBlock / 32) + (size_t)range_len * (2 * sizeof(float) + sizeof(int));
@@ -881,7 +893,14 @@ cudaError_t launch_tree(const BatchArgs<MAXB> &args, bool hess, cudaStream_t s) 
 template <int MAXB>
 cudaError_t launch_reduce(const BatchArgs<MAXB> &args, bool hess, cudaStream_t s) {
     if (args.n <= 0) return cudaSuccess;
-    const int warps = args.red_base[args.n];
+    bool branches = false, logl = false;   // what the launch's problems want
+    for (int i = 0; i < args.n; ++i) {
+        branches = branches || args.d[i].out_grad || (hess && args.d[i].out_hess);
+        logl = logl || args.d[i].out_logL;
+    }
+    if (!branches && !logl) return cudaSuccess;
+    // a forward part (logL only) needs one warp per problem, not one per branch
+    const int warps = branches ? args.red_base[args.n] : args.n;
     cudaLaunchConfig_t cfg = {};   // programmatic dependent launch (the kernel waits in pdl_wait)
     cfg.gridDim = dim3((unsigned)((warps + 7) / 8));
     cfg.blockDim = dim3(256);
@@ -891,6 +910,7 @@ cudaError_t launch_reduce(const BatchArgs<MAXB> &args, bool hess, cudaStream_t s
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    if (!branches) return cudaLaunchKernelEx(&cfg, reduce_logl_kernel<MAXB>, args);
     return cudaLaunchKernelEx(&cfg, reduce_kernel<MAXB>, args, hess ? 1 : 0);
 }
 
