@@ -63,20 +63,38 @@ __host__ __device__ inline Small64Layout small64_layout(int N, int n, int C, int
     return L;
 }
 
-// v * 2^-e exactly (e from scale_exponent64: the multiplier is a normal double unless e is far
-// outside the range of normalised partials)
-__device__ __forceinline__ double unscale(double v, int e) {
-    if (e >= -1022 && e <= 1022) return v * __longlong_as_double((long long)(1023 - e) << 52);
-    return ldexp(v, -e);
+// FP64 helpers that keep FP64 instructions off the dependent chain where integer ones do: on this
+// GPU each FP64 warp instruction holds an SM sub-partition's FP64 pipe for dozens of cycles.
+
+// x * 2^e: one multiplication by an exact power of two for e in [-1022, 1023] (exact for a normal
+// result, one rounding for a subnormal one, as ldexp), ldexp beyond
+__device__ __forceinline__ double ldexp2(double x, int e) {
+    if (e >= -1022 && e <= 1023) return x * __longlong_as_double((long long)(1023 + e) << 52);
+    return ldexp(x, e);
+}
+// v * 2^-e exactly (e from scale_exp)
+__device__ __forceinline__ double unscale(double v, int e) { return ldexp2(v, -e); }
+
+// The maximum of non-negative doubles is the maximum of their bit patterns as signed integers
+// (a negative value, which products of these tables can only be through rounding, loses to any
+// non-negative one; a NaN wins and then gets scale 0, as the root reports it).
+__device__ __forceinline__ long long max_bits(long long a, double v) { return max(a, __double_as_longlong(v)); }
+__device__ __forceinline__ long long grp_max(long long b) {   // over the four lanes of a unit
+    b = max(b, __shfl_xor_sync(0xffffffffu, b, 1));
+    return max(b, __shfl_xor_sync(0xffffffffu, b, 2));
+}
+// scale_exponent64 of the double with bit pattern b, from its exponent field: mx * 2^-e in [1, 2)
+// for a positive normal mx; 0 for zero, negative, infinite or NaN; frexp for a subnormal one
+__device__ __forceinline__ int scale_exp(long long b) {
+    const int eb = (int)((b >> 52) & 0x7ff);
+    if (b <= 0 || eb == 0x7ff) return 0;
+    if (eb == 0) return scale_exponent64(__longlong_as_double(b));
+    return eb - 1023;
 }
 
 __device__ __forceinline__ double grp_sum(double v) {   // over the four lanes of a unit
     v += __shfl_xor_sync(0xffffffffu, v, 1);
     return v + __shfl_xor_sync(0xffffffffu, v, 2);
-}
-__device__ __forceinline__ double grp_max(double v) {
-    v = fmax(v, __shfl_xor_sync(0xffffffffu, v, 1));
-    return fmax(v, __shfl_xor_sync(0xffffffffu, v, 2));
 }
 
 template <int C, bool HESS>
@@ -138,7 +156,8 @@ __global__ void __launch_bounds__(kSmallThreads) small64_kernel(const __grid_con
             const int4 op = ops[o0 + u];
             const int k = op.x, c0 = op.y, c1 = op.z;
             const bool t0 = c0 < N, t1 = c1 < N;
-            double v[C], mx = 0.0;
+            double v[C];
+            long long mx = 0;   // bit pattern of the largest v
 #pragma unroll
             for (int l = 0; l < C; ++l) {
                 double A0, A1;   // state s of a_c0 and a_c1
@@ -147,7 +166,7 @@ __global__ void __launch_bounds__(kSmallThreads) small64_kernel(const __grid_con
                 if (t1) A1 = tab[((size_t)c1 * C + l) * kTab + 4 * tips[c1 * cm + q] + s];
                 else A1 = top[((((size_t)(c1 - N) * C + l) * cm + q) << 2) + s];
                 v[l] = A0 * A1;
-                mx = fmax(mx, v[l]);
+                mx = max_bits(mx, v[l]);
             }
             const int E = (t0 ? 0 : pe[(c0 - N) * cm + q]) + (t1 ? 0 : pe[(c1 - N) * cm + q]);
             if (k == root) {   // the root is alone on its level: the same branch in every lane
@@ -168,7 +187,7 @@ __global__ void __launch_bounds__(kSmallThreads) small64_kernel(const __grid_con
                 }
                 continue;
             }
-            const int e = scale_exponent64(grp_max(mx));
+            const int e = scale_exp(grp_max(mx));
 #pragma unroll
             for (int l = 0; l < C; ++l) {
                 const double x = unscale(v[l], e);   // state s of p_k
@@ -212,7 +231,8 @@ __global__ void __launch_bounds__(kSmallThreads) small64_kernel(const __grid_con
 #pragma unroll
                 for (int i = 0; i < 4; ++i) { Q0[i] = __ldg(r0 + i); Q1[i] = __ldg(r1 + i); }
             }
-            double g0 = 0.0, g1 = 0.0, h0 = 0.0, h1 = 0.0, m0 = 0.0, m1 = 0.0;
+            double g0 = 0.0, g1 = 0.0, h0 = 0.0, h1 = 0.0;
+            long long m0 = 0, m1 = 0;   // bit patterns of the largest q_c0, q_c1 entries
             double x0[C], x1[C];   // state s of q_c0 and q_c1 before rescaling
 #pragma unroll
             for (int l = 0; l < C; ++l) {
@@ -251,8 +271,8 @@ __global__ void __launch_bounds__(kSmallThreads) small64_kernel(const __grid_con
                 }
                 x0[l] = y0;
                 x1[l] = y1;
-                m0 = fmax(m0, y0);
-                m1 = fmax(m1, y1);
+                m0 = max_bits(m0, y0);
+                m1 = max_bits(m1, y1);
             }
             g0 = grp_sum(g0);
             g1 = grp_sum(g1);
@@ -260,7 +280,7 @@ __global__ void __launch_bounds__(kSmallThreads) small64_kernel(const __grid_con
                 h0 = grp_sum(h0);
                 h1 = grp_sum(h1);
             }
-            const int e0 = scale_exponent64(grp_max(m0)), e1 = scale_exponent64(grp_max(m1));
+            const int e0 = scale_exp(grp_max(m0)), e1 = scale_exp(grp_max(m1));
             if (active && !t0) {
 #pragma unroll
                 for (int l = 0; l < C; ++l) pre[((((size_t)(c0 - N) * C + l) * cm + q) << 2) + s] = unscale(x0[l], e0);
@@ -276,9 +296,9 @@ __global__ void __launch_bounds__(kSmallThreads) small64_kernel(const __grid_con
                 const int c = side ? c1 : c0;
                 const int dE = Eq + E0 + E1 - Er[q];
                 const double inv = invL[q], wt = wq[q];
-                const double dd = ldexp(side ? g1 : g0, dE) * inv;
+                const double dd = ldexp2(side ? g1 : g0, dE) * inv;
                 if (s < 2) gq[c * cm + q] = wt != 0.0 ? wt * dd : 0.0;
-                else hq[c * cm + q] = wt != 0.0 ? wt * (ldexp(side ? h1 : h0, dE) * inv - dd * dd) : 0.0;
+                else hq[c * cm + q] = wt != 0.0 ? wt * (ldexp2(side ? h1 : h0, dE) * inv - dd * dd) : 0.0;
             }
         }
         __syncthreads();
