@@ -228,6 +228,19 @@ int single_target(const pg_ctx *ctx, const pg::ProbDesc &d) {
     return std::min(4 * ctx->n_sm, ctx->n_sm * ctx->blocks_per_sm[d.precision][d.C]);
 }
 
+// The pattern factor r_p in [1, 2) of the FP32 kernels (pg_device.cuh: pattern_factor): the
+// lowbias32 integer hash (C. Wellons) of p as a 23-bit mantissa, the same bits on the host.
+float host_pattern_factor(uint32_t p) {
+    uint32_t x = p + 0x9E3779B9u;
+    x ^= x >> 16; x *= 0x21F0AAADu;
+    x ^= x >> 15; x *= 0x735A2D97u;
+    x ^= x >> 15;
+    const uint32_t bits = 0x3F800000u | (x >> 9);
+    float r;
+    std::memcpy(&r, &bits, sizeof r);
+    return r;
+}
+
 // Carves one device allocation into aligned arrays.
 struct Carver {
     size_t off = 0;
@@ -540,7 +553,7 @@ pg_status upload_m(pg_ctx *ctx, const pg_problem *pr, const TreePlan &tp, pg_han
     pg::ProbDesc &pd = h->desc;
     pd.ops = d.ops;
     pd.level_off = d.level_off;
-    pd.parent = reinterpret_cast<const int *>(base + o_par);
+    h->d_parent = reinterpret_cast<const int *>(base + o_par);
     pd.status = d.status;
     pd.n_tips = N;
     pd.n_nodes = n;
@@ -796,7 +809,7 @@ static pg_status upload_binary(pg_ctx *ctx, const pg_problem *pr, pg_handle **ou
     Carver cv;
     const size_t o_ops = cv.take<int4>(N - 1), o_lv = cv.take<int>(H + 1);
     const size_t o_tips = cv.take<uint8_t>((size_t)N * Ps), o_w = cv.take<double>(Ps);
-    const size_t o_wf = cv.take<float>(Ps);
+    const size_t o_wf = cv.take<float>(Ps), o_rl = f64 ? 0 : cv.take<double>(Ps);
     const size_t o_Qd = cv.take<double>((size_t)M * 16), o_Qf = cv.take<float4>((size_t)M * 4);
     const size_t o_Mp = cv.take<double>((size_t)M * (pg::kTaylorDeg + 1) * 16), o_qn = cv.take<double>(M);
     const size_t o_bm = pr->branch_model ? cv.take<int>(n) : 0;
@@ -874,6 +887,11 @@ static pg_status upload_binary(pg_ctx *ctx, const pg_problem *pr, pg_handle **ou
         e = h2d_rows(pl, base + o_tips, Ps, pr->tip_states, pr->tip_stride ? pr->tip_stride : P, P, N);
     if (e == cudaSuccess && P > 0) e = cp(o_w, pr->pattern_weights, sizeof(double) * P);
     if (e == cudaSuccess && P > 0) e = cp(o_wf, wf.data(), sizeof(float) * Ps);
+    if (!f64 && P > 0) {   // N log r_p of the FP32 kernels' pattern factors
+        std::vector<double> rl(Ps, 0.0);
+        for (int p = 0; p < P; ++p) rl[p] = (double)N * std::log((double)host_pattern_factor((uint32_t)p));
+        if (e == cudaSuccess) e = cp(o_rl, rl.data(), sizeof(double) * Ps);
+    }
     if (e == cudaSuccess) e = cp(o_Qd, pr->Q, sizeof(double) * 16 * M);
     if (e == cudaSuccess) e = cp(o_Qf, Qf.data(), sizeof(float4) * Qf.size());
     if (e == cudaSuccess) e = cp(o_Mp, Mpow.data(), sizeof(double) * Mpow.size());
@@ -896,6 +914,7 @@ static pg_status upload_binary(pg_ctx *ctx, const pg_problem *pr, pg_handle **ou
     d.tips = reinterpret_cast<const uint8_t *>(base + o_tips);
     d.weights = reinterpret_cast<const double *>(base + o_w);
     d.wf = reinterpret_cast<const float *>(base + o_wf);
+    d.rlog = (f64 || P == 0) ? nullptr : reinterpret_cast<const double *>(base + o_rl);
     d.Qd = reinterpret_cast<const double *>(base + o_Qd);
     d.Qf = reinterpret_cast<const float4 *>(base + o_Qf);
     d.Mpow = reinterpret_cast<const double *>(base + o_Mp);
@@ -920,7 +939,7 @@ static pg_status upload_binary(pg_ctx *ctx, const pg_problem *pr, pg_handle **ou
     d.n_bnd = n_bnd;
     d.top_code = reinterpret_cast<const int2 *>(base + o_tc);
     d.bnd_node = reinterpret_cast<const int *>(base + o_bn);
-    d.parent = reinterpret_cast<const int *>(base + o_par);
+    h->d_parent = reinterpret_cast<const int *>(base + o_par);
     d.cut = 0;
     h->cut = cut;
     h->level_off = tp.level_off;
@@ -1165,6 +1184,7 @@ pg_status upload_chunked(pg_ctx *ctx, const pg_problem *pr, pg_handle **out) {
         h->block = pblock;
         h->bytes = pbytes;
         h->desc = c0h->desc;   // tree, sizes and model of the problem (pointers of chunk 0)
+        h->d_parent = c0h->d_parent;
         h->desc.P = P;
         h->mstate = c0h->mstate;
         h->md = c0h->md;
@@ -1661,7 +1681,7 @@ pg_status enqueue_clock(pg_handle *const *hs, int32_t k, bool grad, const double
             const int i = at + j;
             const pg::ProbDesc &d = hs[i]->desc;
             pg::ClockDesc c{};
-            c.parent = d.parent;
+            c.parent = hs[i]->d_parent;
             c.ops = d.ops;
             c.n_tips = d.n_tips;
             c.n_nodes = d.n_nodes;

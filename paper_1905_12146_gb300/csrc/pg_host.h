@@ -66,6 +66,7 @@ struct pg_handle {
     double *part_out = nullptr;
     double *b_fwd = nullptr;   // [n] the branch lengths of the last forward pass (chunked backward)
     const pg::ProbDesc *d_desc = nullptr;   // device copy of desc (batched level kernels read it)
+    const int *d_parent = nullptr;          // [n] parent index on the device (the clock kernels)
 };
 
 namespace pg {

@@ -114,7 +114,9 @@ struct ProbDesc {
     // launch left in the handle; gscale (device scalar, may be null = 1) multiplies the gradient
     int skip;
     const double *gscale;
-    const int *parent;             // [n] parent index, -1 at the root
+    // [Ps] N log r_p, the log of the pattern factors the FP32 post-order multiplies into L_p
+    // (computed once on upload; null: the kernels compute it)
+    const double *rlog;
     // [n] level index of each node's parent (-1 at the root): a branch whose parent lies below
     // the cut was summed in level-kernel slots, the others in fused-kernel slots
     const int *plevel;

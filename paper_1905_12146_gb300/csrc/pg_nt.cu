@@ -26,8 +26,9 @@
 //     (the lowbias32 integer hash of p), so exactly representable sub-patterns shared by many
 //     sites get different mantissas at different sites.  Each tip contributes r_p once, so L_p
 //     carries r_p^N and log L_p loses N log r_p, subtracted in FP64.
-// The root likelihood, the logarithm and all sums over patterns and tiles are FP64.  The
-// pre-order pass feeds only the gradient and uses plain FP32.
+// The root's state products are rounded once in FP32 like every node's; the root inner product
+// with pi, the mixture over categories, the logarithm and all sums over patterns and tiles are
+// FP64.  The pre-order pass feeds only the gradient and uses plain FP32.
 //
 // FP64 numerics.  Every partial, product and sum in FP64 (no dither, no splitting).
 #include <cuda_runtime.h>
@@ -421,15 +422,15 @@ __device__ __forceinline__ void post_compute32(const ProbDesc &d, const PairMeta
             x1 = slot[(C + l) * 32];
             s1 = matvec_hilo(P1 + kColDhi, P1 + kColDlo, x1);
         }
-        if (root) {
-            double s = d.pi[0] * (((double)x0.x + s0.x) * ((double)x1.x + s1.x));
-            s = fma(d.pi[1], ((double)x0.y + s0.y) * ((double)x1.y + s1.y), s);
-            s = fma(d.pi[2], ((double)x0.z + s0.z) * ((double)x1.z + s1.z), s);
-            s = fma(d.pi[3], ((double)x0.w + s0.w) * ((double)x1.w + s1.w), s);
+        v[l] = f4(prod_split(x0.x, s0.x, x1.x, s1.x), prod_split(x0.y, s0.y, x1.y, s1.y),
+                  prod_split(x0.z, s0.z, x1.z, s1.z), prod_split(x0.w, s0.w, x1.w, s1.w));
+        if (root) {   // the root's products rounded once in FP32, as every node's; their sums in FP64
+            double s = d.pi[0] * (double)v[l].x;
+            s = fma(d.pi[1], (double)v[l].y, s);
+            s = fma(d.pi[2], (double)v[l].z, s);
+            s = fma(d.pi[3], (double)v[l].w, s);
             L = fma(d.cw[l], s, L);
         } else {
-            v[l] = f4(prod_split(x0.x, s0.x, x1.x, s1.x), prod_split(x0.y, s0.y, x1.y, s1.y),
-                      prod_split(x0.z, s0.z, x1.z, s1.z), prod_split(x0.w, s0.w, x1.w, s1.w));
             mx = fmaxf(mx, hmax(v[l]));
         }
     }
@@ -518,7 +519,7 @@ __device__ __forceinline__ void post_level_chunk(const ProbDesc &d, const PairMe
     const int Er = E + e2;
     const double wgt = d.weights[m.p];
     const double lp = log(f) + (double)Er * 0.69314718055994530942 -
-                      (double)d.n_tips * log((double)pattern_factor((uint32_t)m.p));
+                      (d.rlog ? __ldg(d.rlog + m.p) : (double)d.n_tips * log((double)pattern_factor((uint32_t)m.p)));
     if (m.active) {
         ra.invL[m.q] = (float)(1.0 / f);
         ra.Eroot[m.q] = Er;

@@ -28,11 +28,26 @@ constexpr size_t kTopSmemLimit = 227 * 1024;
 // partial rows and scales of top and boundary nodes, site values, the top ops and codes, and the
 // tip codes of the top nodes' tip children (at most n_top + 1 of them)
 __host__ __device__ size_t top_bytes(int n_top, int n_bnd, int C, int L) {
-    const size_t tabs = (size_t)n_top * 2 * C * kPtabCols * 16;   // the top nodes' child-branch tables
+    const size_t tabs = (size_t)n_top * 2 * (C * kPtabCols + 4) * 16;   // child-branch tables and Q columns
     const size_t rows = tabs + (size_t)(2 * n_top + n_bnd) * L * (16 * C + 4) + (size_t)L * 12;
     const size_t meta = (size_t)n_top * (sizeof(int4) + sizeof(int2));
     const size_t tipc = (size_t)(n_top + 1) * ((L + 15) / 16 * 16);
     return rows + meta + tipc + 64;
+}
+
+// f in [0.5, 1) and e with x = f 2^e for a positive normal x, from the bit pattern (integer
+// instructions only); frexp's result otherwise (zero, subnormal, infinite, NaN: x itself, e = 0,
+// unless subnormal)
+__device__ __forceinline__ double split_exponent(double x, int &e) {
+    const long long b = __double_as_longlong(x);
+    const int eb = (int)((b >> 52) & 0x7ff);
+    if (b > 0 && eb != 0 && eb != 0x7ff) {
+        e = eb - 1022;
+        return __longlong_as_double((b & ~(0x7ffLL << 52)) | (1022LL << 52));
+    }
+    e = 0;
+    if (b > 0 && eb == 0) return frexp(x, &e);
+    return x;
 }
 
 __device__ __forceinline__ void cols_from_smem(const float4 *p, float4 (&c)[4]) {   // load_cols for shared memory
@@ -48,8 +63,6 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 template <int C, bool HESS>
 __global__ void __launch_bounds__(kBlock, 2) top_kernel(const __grid_constant__ BatchArgs<1> a) {
     extern __shared__ float4 dyn[];
-    pdl_wait();                // launched while the last post-order level drains
-    pdl_launch_dependents();   // the first pre-order level may be scheduled; it waits for this kernel
     const ProbDesc &d = a.d[0];
     const int N = d.n_tips, Ps = d.Ps, L = d.range_len;
     const int tile = blockIdx.x;
@@ -61,7 +74,8 @@ __global__ void __launch_bounds__(kBlock, 2) top_kernel(const __grid_constant__ 
     // shared layout: the top nodes' child-branch tables [node][side][C][kPtabCols], float4 rows
     // [node][C][L], then int scales [node][L], then site values [L]
     float4 *Tt = dyn;                                   // tables (each read many times per level)
-    float4 *Pt = Tt + (size_t)n_top * 2 * C * kPtabCols; // post partials of top nodes
+    float4 *Qs = Tt + (size_t)n_top * 2 * C * kPtabCols; // [node][side][4] Q columns of the child's model
+    float4 *Pt = Qs + (size_t)n_top * 2 * 4;            // post partials of top nodes
     float4 *Qt = Pt + (size_t)n_top * C * L;            // pre partials of top nodes
     float4 *Bt = Qt + (size_t)n_top * C * L;            // post partials of boundary nodes
     int *EP = reinterpret_cast<int *>(Bt + (size_t)n_bnd * C * L);
@@ -77,15 +91,12 @@ __global__ void __launch_bounds__(kBlock, 2) top_kernel(const __grid_constant__ 
     const float4 *post_g = static_cast<const float4 *>(d.post);
     float4 *pre_g = static_cast<float4 *>(d.pre);
 
-    // the top nodes' operations and child codes, and their child branches' tables warmed into L1
+    // What does not depend on the previous kernels (the tree, the tip codes, the models' Q
+    // columns) is loaded while the last post-order level drains; then the tables of this
+    // evaluation and the boundary nodes' rows.
     for (int t = threadIdx.x; t < n_top; t += blockDim.x) {
         ops_s[t] = __ldg(d.ops + o_cut + t);
         code_s[t] = __ldg(d.top_code + t);
-    }
-    for (int t = threadIdx.x; t < n_top * 2 * C * kPtabCols; t += blockDim.x) {   // the tables, once
-        const int per = C * kPtabCols, nb = t / per, e = t - nb * per;
-        const int4 op = __ldg(d.ops + o_cut + (nb >> 1));
-        cp_async16(Tt + (size_t)nb * per + e, d.Ptab + (size_t)((nb & 1) ? op.z : op.y) * per + e);
     }
     __syncthreads();
     // tip codes of the top nodes' tip children (code -1 - slot)
@@ -95,6 +106,19 @@ __global__ void __launch_bounds__(kBlock, 2) top_kernel(const __grid_constant__ 
         const int2 code = code_s[nb >> 1];
         const int cc = (nb & 1) ? code.y : code.x, c = (nb & 1) ? op.z : op.y;
         if (cc < 0) tips_s[(size_t)(-1 - cc) * L16 + q] = min((int)__ldg(d.tips + (size_t)c * Ps + p0 + q), 4);
+    }
+    for (int t = threadIdx.x; t < n_top * 2 * 4; t += blockDim.x) {   // Q columns of each child branch's model
+        const int nb = t >> 2, col = t & 3;
+        const int4 op = ops_s[nb >> 1];
+        const int c = (nb & 1) ? op.z : op.y;
+        Qs[t] = __ldg(d.Qf + 4 * (d.bmodel ? __ldg(d.bmodel + c) : 0) + col);
+    }
+    pdl_wait();                // the last post-order level has completed and its rows are visible
+    pdl_launch_dependents();   // the first pre-order level may be scheduled; it waits for this kernel
+    for (int t = threadIdx.x; t < n_top * 2 * C * kPtabCols; t += blockDim.x) {   // the tables, once
+        const int per = C * kPtabCols, nb = t / per, e = t - nb * per;
+        const int4 op = __ldg(d.ops + o_cut + (nb >> 1));
+        cp_async16(Tt + (size_t)nb * per + e, d.Ptab + (size_t)((nb & 1) ? op.z : op.y) * per + e);
     }
 
     // boundary nodes' post-order rows and scales
@@ -148,15 +172,15 @@ __global__ void __launch_bounds__(kBlock, 2) top_kernel(const __grid_constant__ 
                         if (l == 0) E += cc < n_top ? EP[cc * L + q] : EB[(cc - n_top) * L + q];
                     }
                 }
-                if (root) {
-                    double s = d.pi[0] * (((double)x[0].x + sm[0].x) * ((double)x[1].x + sm[1].x));
-                    s = fma(d.pi[1], ((double)x[0].y + sm[0].y) * ((double)x[1].y + sm[1].y), s);
-                    s = fma(d.pi[2], ((double)x[0].z + sm[0].z) * ((double)x[1].z + sm[1].z), s);
-                    s = fma(d.pi[3], ((double)x[0].w + sm[0].w) * ((double)x[1].w + sm[1].w), s);
+                v[l] = f4(prod_split(x[0].x, sm[0].x, x[1].x, sm[1].x), prod_split(x[0].y, sm[0].y, x[1].y, sm[1].y),
+                          prod_split(x[0].z, sm[0].z, x[1].z, sm[1].z), prod_split(x[0].w, sm[0].w, x[1].w, sm[1].w));
+                if (root) {   // the root's products rounded once in FP32, as every node's; their sums in FP64
+                    double s = d.pi[0] * (double)v[l].x;
+                    s = fma(d.pi[1], (double)v[l].y, s);
+                    s = fma(d.pi[2], (double)v[l].z, s);
+                    s = fma(d.pi[3], (double)v[l].w, s);
                     Lsite = fma(d.cw[l], s, Lsite);
                 } else {
-                    v[l] = f4(prod_split(x[0].x, sm[0].x, x[1].x, sm[1].x), prod_split(x[0].y, sm[0].y, x[1].y, sm[1].y),
-                              prod_split(x[0].z, sm[0].z, x[1].z, sm[1].z), prod_split(x[0].w, sm[0].w, x[1].w, sm[1].w));
                     mx = fmaxf(mx, hmax(v[l]));
                 }
             }
@@ -169,20 +193,24 @@ __global__ void __launch_bounds__(kBlock, 2) top_kernel(const __grid_constant__ 
                 }
                 continue;
             }
-            // the site likelihood (Section 2.3 root inner product, Section 2.5 mixture)
+            // the site likelihood (Section 2.3 root inner product, Section 2.5 mixture).  This GPU
+            // issues FP64 at a small fraction of the FP32 rate and the root level is bound by its FP64
+            // work per SM, so the exponent split and the stored reciprocal avoid FP64 instructions.
             int e2 = 0;
-            const double f = (Lsite > 0.0 && isfinite(Lsite)) ? frexp(Lsite, &e2) : Lsite;
+            const double f = split_exponent(Lsite, e2);
             const int Erq = E + e2;
             const double wgt = d.weights[p];
-            const double lp = log(f) + (double)Erq * 0.69314718055994530942 - (double)N * log((double)r);
+            const double lp = log(f) + (double)Erq * 0.69314718055994530942 -
+                              (d.rlog ? d.rlog[p] : (double)N * log((double)r));
+            const float rf = __frcp_rn((float)f);   // 1 / Lhat_p for the FP32 branch terms
             if (active) {
-                invL[q] = (float)(1.0 / f);
+                invL[q] = rf;
                 Er[q] = Erq;
                 wv[q] = (float)wgt;
             }
             if (d.skip & kSkipPost) continue;   // recomputed for the pre-order only
             if (active) {
-                d.site_invL[p] = (float)(1.0 / f);
+                d.site_invL[p] = rf;
                 d.site_Er[p] = Erq;
                 if (!(f > 0.0) || !isfinite(lp)) atomicOr(d.status, kStatusNumeric);
                 if (d.out_site) d.out_site[p] = lp;
@@ -236,7 +264,7 @@ __global__ void __launch_bounds__(kBlock, 2) top_kernel(const __grid_constant__ 
             for (int side = 0; side < 2; ++side) {
                 const int c = side ? op.z : op.y, cc = side ? code.y : code.x;
                 float4 Qc[4];
-                load_cols(d.Qf + 4 * (d.bmodel ? d.bmodel[c] : 0), Qc);
+                cols_from_smem(Qs + (size_t)(2 * ti + side) * 4, Qc);
                 float4 qv[C];
                 float mq = 0.f, gs = 0.f, hs = 0.f;
 #pragma unroll
