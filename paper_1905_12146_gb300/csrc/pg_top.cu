@@ -30,7 +30,7 @@ constexpr size_t kTopSmemLimit = 227 * 1024;
 __host__ __device__ size_t top_bytes(int n_top, int n_bnd, int C, int L) {
     const size_t tabs = (size_t)n_top * 2 * (C * kPtabCols + 4) * 16;   // child-branch tables and Q columns
     const size_t rows = tabs + (size_t)(2 * n_top + n_bnd) * L * (16 * C + 4) + (size_t)L * 12;
-    const size_t meta = (size_t)n_top * (sizeof(int4) + sizeof(int2));
+    const size_t meta = (size_t)n_top * (sizeof(int4) + sizeof(int2)) + (size_t)(n_bnd + n_top + 1) * sizeof(int);
     const size_t tipc = (size_t)(n_top + 1) * ((L + 15) / 16 * 16);
     return rows + meta + tipc + 64;
 }
@@ -86,7 +86,10 @@ __global__ void __launch_bounds__(kBlock, 2) top_kernel(const __grid_constant__ 
     float *wv = reinterpret_cast<float *>(Er + L);
     int4 *ops_s = reinterpret_cast<int4 *>(reinterpret_cast<uintptr_t>(wv + L + 3) & ~(uintptr_t)15);
     int2 *code_s = reinterpret_cast<int2 *>(ops_s + n_top);
-    uint8_t *tips_s = reinterpret_cast<uint8_t *>(code_s + n_top);   // [n_top + 1][L16]
+    int *bnd_s = reinterpret_cast<int *>(code_s + n_top);            // boundary node ids
+    int *lvo_s = bnd_s + n_bnd;                                      // level offsets from the cut
+    const int n_lv = d.n_levels - d.cut;                             // (at most n_top levels)
+    uint8_t *tips_s = reinterpret_cast<uint8_t *>(lvo_s + n_lv + 1); // [n_top + 1][L16]
     const int L16 = (L + 15) / 16 * 16;
     const float4 *post_g = static_cast<const float4 *>(d.post);
     float4 *pre_g = static_cast<float4 *>(d.pre);
@@ -98,6 +101,8 @@ __global__ void __launch_bounds__(kBlock, 2) top_kernel(const __grid_constant__ 
         ops_s[t] = __ldg(d.ops + o_cut + t);
         code_s[t] = __ldg(d.top_code + t);
     }
+    for (int t = threadIdx.x; t < n_bnd; t += blockDim.x) bnd_s[t] = __ldg(d.bnd_node + t);
+    for (int t = threadIdx.x; t <= n_lv; t += blockDim.x) lvo_s[t] = __ldg(d.level_off + d.cut + t);
     __syncthreads();
     // tip codes of the top nodes' tip children (code -1 - slot)
     for (int t = threadIdx.x; t < n_top * 2 * cnt; t += blockDim.x) {
@@ -115,29 +120,29 @@ __global__ void __launch_bounds__(kBlock, 2) top_kernel(const __grid_constant__ 
     }
     pdl_wait();                // the last post-order level has completed and its rows are visible
     pdl_launch_dependents();   // the first pre-order level may be scheduled; it waits for this kernel
+    // (the copies' node ids come from shared memory, so no copy waits for a global load)
     for (int t = threadIdx.x; t < n_top * 2 * C * kPtabCols; t += blockDim.x) {   // the tables, once
         const int per = C * kPtabCols, nb = t / per, e = t - nb * per;
-        const int4 op = __ldg(d.ops + o_cut + (nb >> 1));
+        const int4 op = ops_s[nb >> 1];
         cp_async16(Tt + (size_t)nb * per + e, d.Ptab + (size_t)((nb & 1) ? op.z : op.y) * per + e);
     }
 
     // boundary nodes' post-order rows and scales
     for (int idx = threadIdx.x; idx < n_bnd * C * cnt; idx += blockDim.x) {
         const int bl = idx / cnt, q = idx - bl * cnt, b = bl / C, l = bl - b * C;
-        const int node = __ldg(d.bnd_node + b);
-        cp_async16(Bt + (size_t)bl * L + q, post_g + ((size_t)(node - N) * C + l) * Ps + p0 + q);
+        cp_async16(Bt + (size_t)bl * L + q, post_g + ((size_t)(bnd_s[b] - N) * C + l) * Ps + p0 + q);
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     for (int idx = threadIdx.x; idx < n_bnd * cnt; idx += blockDim.x) {
         const int b = idx / cnt, q = idx - b * cnt;
-        EB[b * L + q] = __ldcg(d.pe + (size_t)(__ldg(d.bnd_node + b) - N) * Ps + p0 + q);
+        EB[b * L + q] = __ldcg(d.pe + (size_t)(bnd_s[b] - N) * Ps + p0 + q);
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
 
     // post-order, levels cut .. top (Section 2.3); the last level is the root alone
     for (int lv = d.cut; lv < d.n_levels; ++lv) {
-        const int o0 = d.level_off[lv], npairs = (d.level_off[lv + 1] - o0) * cnt;
+        const int o0 = lvo_s[lv - d.cut], npairs = (lvo_s[lv - d.cut + 1] - o0) * cnt;
         for (int chunk = warp; chunk * 32 < npairs; chunk += W) {
             const int j = chunk * 32 + lane;
             const bool active = j < npairs;
@@ -224,7 +229,7 @@ __global__ void __launch_bounds__(kBlock, 2) top_kernel(const __grid_constant__ 
     if (d.skip & kSkipPre) return;
     // pre-order, top .. cut (Section 2.4) with the gradient (2.5) and Hessian diagonal (2.6)
     for (int lv = d.n_levels - 1; lv >= d.cut; --lv) {
-        const int o0 = d.level_off[lv], npairs = (d.level_off[lv + 1] - o0) * cnt;
+        const int o0 = lvo_s[lv - d.cut], npairs = (lvo_s[lv - d.cut + 1] - o0) * cnt;
         for (int chunk = warp; chunk * 32 < npairs; chunk += W) {
             const int j = chunk * 32 + lane;
             const bool active = j < npairs;
