@@ -104,6 +104,21 @@ __device__ __forceinline__ int scale_exponent64(double mx) {
     return e - 1;
 }
 
+// f in [0.5, 1) and e with x = f 2^e for a positive normal x, from the bit pattern (integer
+// instructions only); frexp's result otherwise (zero, subnormal, infinite, NaN: x itself, e = 0,
+// unless subnormal)
+__device__ __forceinline__ double split_exponent(double x, int &e) {
+    const long long b = __double_as_longlong(x);
+    const int eb = (int)((b >> 52) & 0x7ff);
+    if (b > 0 && eb != 0 && eb != 0x7ff) {
+        e = eb - 1022;
+        return __longlong_as_double((b & ~(0x7ffLL << 52)) | (1022LL << 52));
+    }
+    e = 0;
+    if (b > 0 && eb == 0) return frexp(x, &e);
+    return x;
+}
+
 __device__ __forceinline__ float pow2f(int e) {   // 2^e, e in [-126, 127]
     return __int_as_float((e + 127) << 23);
 }

@@ -515,16 +515,17 @@ __device__ __forceinline__ void post_level_chunk(const ProbDesc &d, const PairMe
     post_compute32<C>(d, m, slot, L, E);
     if (m.op.x != d.root) return;   // uniform: the root is alone on its level
     int e2 = 0;
-    const double f = (L > 0.0 && isfinite(L)) ? frexp(L, &e2) : L;
+    const double f = split_exponent(L, e2);   // (integer instructions: FP64 bounds this level)
     const int Er = E + e2;
     const double wgt = d.weights[m.p];
     const double lp = log(f) + (double)Er * 0.69314718055994530942 -
                       (d.rlog ? __ldg(d.rlog + m.p) : (double)d.n_tips * log((double)pattern_factor((uint32_t)m.p)));
+    const float rf = __frcp_rn((float)f);   // 1 / Lhat_p for the FP32 branch terms
     if (m.active) {
-        ra.invL[m.q] = (float)(1.0 / f);
+        ra.invL[m.q] = rf;
         ra.Eroot[m.q] = Er;
         ra.w[m.q] = (float)wgt;
-        d.site_invL[m.p] = (float)(1.0 / f);
+        d.site_invL[m.p] = rf;
         d.site_Er[m.p] = Er;
         if (!(f > 0.0) || !isfinite(lp)) atomicOr(d.status, kStatusNumeric);
         if (d.out_site) d.out_site[m.p] = lp;

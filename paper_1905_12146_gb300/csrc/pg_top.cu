@@ -35,21 +35,6 @@ __host__ __device__ size_t top_bytes(int n_top, int n_bnd, int C, int L) {
     return rows + meta + tipc + 64;
 }
 
-// f in [0.5, 1) and e with x = f 2^e for a positive normal x, from the bit pattern (integer
-// instructions only); frexp's result otherwise (zero, subnormal, infinite, NaN: x itself, e = 0,
-// unless subnormal)
-__device__ __forceinline__ double split_exponent(double x, int &e) {
-    const long long b = __double_as_longlong(x);
-    const int eb = (int)((b >> 52) & 0x7ff);
-    if (b > 0 && eb != 0 && eb != 0x7ff) {
-        e = eb - 1022;
-        return __longlong_as_double((b & ~(0x7ffLL << 52)) | (1022LL << 52));
-    }
-    e = 0;
-    if (b > 0 && eb == 0) return frexp(x, &e);
-    return x;
-}
-
 __device__ __forceinline__ void cols_from_smem(const float4 *p, float4 (&c)[4]) {   // load_cols for shared memory
 #pragma unroll
     for (int t = 0; t < 4; ++t) c[t] = p[t];
