@@ -160,9 +160,11 @@ pg_status pg_free(pg_handle *h);
 
 /* Blocking evaluation with HOST pointers: b[2N-1] branch lengths (root entry ignored; each other
  * entry finite and >= 0), outputs logL (scalar), grad[2N-1], hess[2N-1] (diagonal of the Hessian
- * of logL in the branch lengths), site_logL[P]; any output may be NULL.  Copies b to the device
- * and the results back.  Errors: PG_ERR_INVALID (bad b), PG_ERR_NUMERIC (a site likelihood 0 or
- * not finite; outputs are still written), PG_ERR_CUDA. */
+ * of logL in the branch lengths), site_logL[P]; any output may be NULL.  The first call on a
+ * handle allocates a pinned host staging buffer (freed by pg_free); every call copies b in through
+ * it with one copy, the requested outputs and the device status back with two, and waits on the
+ * stream once.  Errors: PG_ERR_INVALID (bad b), PG_ERR_NUMERIC (a site likelihood 0 or not
+ * finite; outputs are still written), PG_ERR_CUDA. */
 pg_status pg_eval(pg_handle *h, const double *b, double *logL, double *grad, double *hess,
                   double *site_logL);
 
@@ -300,7 +302,10 @@ pg_status pg_get_info(const pg_handle *h, pg_handle_info *out);
  * `stream` (NULL = legacy default stream), and returns when the results are on the host.
  * Every intermediate array lives in one fixed device array of PG_NOALLOC_SCRATCH_BYTES that each
  * GPU loading the library holds until the process exits; host-side planning uses fixed static
- * buffers.  The first call on a device looks up that array's device address (set-up), so make it
+ * buffers (inputs up to 4 MiB and outputs up to 1 MiB go through static host images with one copy
+ * each way; larger ones array by array).  FP64 problems with at most 16 patterns per block at one
+ * block per SM run the shared-memory latency kernel, as pg_eval does.  The first call on a device
+ * looks up that array's device address (set-up), so make it
  * before any stream capture.  All calls share the array and the static buffers: calls that
  * overlap, on the GPU or from several host threads, race and must be serialised by the caller.
  * Errors: PG_ERR_UNSUPPORTED when the problem needs more scratch than PG_NOALLOC_SCRATCH_BYTES, has
