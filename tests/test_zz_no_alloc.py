@@ -56,6 +56,20 @@ def test_noalloc_matches_pg_eval_on_two_calls_in_a_row(native, oracle_mod, preci
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_noalloc_outputs_beyond_the_static_image(native, oracle_mod, precision):
+    """150,000 site likelihoods (1.2 MB, over the 1 MiB static host image of the outputs) come back
+    array by array; they and logL match the regular entry point."""
+    pr = wl.random_problem(5, 150000, n_states=4, n_cat=1, seed=305, b_mean=0.1, ambiguous=0.02)
+    ref = _regular(native, pr, precision)
+    got = native.eval_noalloc(pr, pr["b"], precision, grad=True, hess=True, site=True)
+    assert got["status"] == 0
+    tol = 1e-12 if precision == "fp64" else 6 * 4 * 2.0 ** -24
+    np.testing.assert_allclose(got["site_logL"], ref["site_logL"], rtol=0, atol=tol)
+    assert abs(got["logL"] - ref["logL"]) <= (1e-12 if precision == "fp64" else 1e-7) * abs(ref["logL"])
+    assert np.abs(got["grad"] - ref["grad"]).max() <= 1e-5 * np.abs(ref["grad"]).max()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_noalloc_without_patterns(native, precision):
     """No site patterns: logL, gradient and Hessian diagonal are exactly zero, as from pg_eval."""
     pr = wl.config_small(seed=3)
