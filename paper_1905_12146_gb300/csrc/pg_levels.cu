@@ -109,8 +109,12 @@ __device__ void issue_post(const ProbDesc &d, const Item &it, PostStage<C, CHERR
     }
 }
 
+// part 0: every copy of the item; part 1: the stage's byte count and the copies that do not depend
+// on the previous pre-order launch (tables, the children's post-order rows and scales, tip codes,
+// weights: complete before any pre-order launch starts); part 2: the rest (q_k and its scales, the
+// per-site values written by the root's kernel)
 template <int C, bool HESS, bool CHERRY>
-__device__ void issue_pre(const ProbDesc &d, const Item &it, PreStage<C, CHERRY> &sm, uint64_t *bar) {
+__device__ void issue_pre(const ProbDesc &d, const Item &it, PreStage<C, CHERRY> &sm, uint64_t *bar, int part = 0) {
     const int N = d.n_tips, Ps = d.Ps, k = it.op.x, c0 = it.op.y, c1 = it.op.z, p0 = it.p0;
     const bool t0 = c0 < N, t1 = c1 < N;
     const float4 *post = static_cast<const float4 *>(d.post);
@@ -121,16 +125,25 @@ __device__ void issue_pre(const ProbDesc &d, const Item &it, PreStage<C, CHERRY>
     unsigned bytes = C * rowb + eb + 3u * eb + 2u * tb + (kQ ? 2u * 64u : 0u);
     bytes += t0 ? yb : (C * rowb + eb);
     bytes += t1 ? yb : (C * rowb + eb);
+    if (part == 2) {
+        bulk_load(sm.eq, d.qe + (size_t)(k - N) * Ps + p0, eb, bar);
+        for (int l = 0; l < C; ++l) bulk_load(sm.qk[l], pre + ((size_t)(k - N) * C + l) * Ps + p0, rowb, bar);
+        bulk_load(sm.er, d.site_Er + p0, eb, bar);
+        bulk_load(sm.inv, d.site_invL + p0, eb, bar);
+        return;
+    }
     mbar_arrive_expect(bar, bytes);
     for (int side = 0; side < 2; ++side) {   // one copy per branch: its C tables are contiguous
         const int c = side ? c1 : c0;
         bulk_load(sm.tab[side], d.Ptab + (size_t)c * C * kPtabCols, tb, bar);
         if (kQ) bulk_load(sm.qtab[side], d.Qf + 4 * (d.bmodel ? d.bmodel[c] : 0), 64u, bar);
     }
-    bulk_load(sm.eq, d.qe + (size_t)(k - N) * Ps + p0, eb, bar);
-    for (int l = 0; l < C; ++l) bulk_load(sm.qk[l], pre + ((size_t)(k - N) * C + l) * Ps + p0, rowb, bar);
-    bulk_load(sm.er, d.site_Er + p0, eb, bar);
-    bulk_load(sm.inv, d.site_invL + p0, eb, bar);
+    if (part == 0) {
+        bulk_load(sm.eq, d.qe + (size_t)(k - N) * Ps + p0, eb, bar);
+        for (int l = 0; l < C; ++l) bulk_load(sm.qk[l], pre + ((size_t)(k - N) * C + l) * Ps + p0, rowb, bar);
+        bulk_load(sm.er, d.site_Er + p0, eb, bar);
+        bulk_load(sm.inv, d.site_invL + p0, eb, bar);
+    }
     bulk_load(sm.w, d.wf + p0, eb, bar);
     if (t0) bulk_load(sm.y0, d.tips + (size_t)c0 * Ps + p0, yb, bar);
     else if constexpr (!CHERRY) {
@@ -303,7 +316,10 @@ __device__ __forceinline__ void compute_pre(const ProbDesc &d, const Item &it, c
 // leaves (the producer first lets the copies it issued land).
 // PREFETCH: the producer loads the next item's record one item ahead (measured: faster for the
 // post-order levels, slower for the pre-order levels)
-template <bool PREFETCH, class Stage, int STAGES, class ItemFn, class Issue, class Compute>
+// EARLY: before waiting for the previous launch, the producer issues the part of its first STAGES
+// items' copies that does not depend on that launch (issue part 1), and the rest after the wait
+// (part 2); the copies of later items are issued whole (part 0).
+template <bool PREFETCH, bool EARLY, class Stage, int STAGES, class ItemFn, class Issue, class Compute>
 __device__ __forceinline__ void staged_walk(int n_items, Ring<Stage, STAGES> &ring, ItemFn &&item_at, Issue &&issue,
                                             Compute &&compute) {
     const int G = gridDim.x, b = blockIdx.x;
@@ -316,11 +332,15 @@ __device__ __forceinline__ void staged_walk(int n_items, Ring<Stage, STAGES> &ri
     }
     __syncthreads();   // barriers initialised before anyone uses them
     pdl_launch_dependents();
-    pdl_wait();        // the previous level's partials are complete and visible
     if (warp == kConsumerWarps) {   // producer
         if (lane != 0) return;
         int i = 0;
-        Item nxt = (PREFETCH && b < n_items) ? item_at(b) : Item{};
+        if constexpr (EARLY) {
+            for (; i < STAGES && b + i * G < n_items; ++i) issue(item_at(b + i * G), ring.st[i], &ring.full[i], 1);
+        }
+        pdl_wait();   // the previous level's partials are complete and visible
+        for (int q = 0; q < i; ++q) issue(item_at(b + q * G), ring.st[q], &ring.full[q], 2);
+        Item nxt = (PREFETCH && b + i * G < n_items) ? item_at(b + i * G) : Item{};
         for (;; ++i) {
             const int j = b + i * G;
             if (j >= n_items) break;
@@ -331,7 +351,7 @@ __device__ __forceinline__ void staged_walk(int n_items, Ring<Stage, STAGES> &ri
                 atomicOr(it.pd->status, kStatusTimeout);
                 break;
             }
-            issue(it, ring.st[s], &ring.full[s]);
+            issue(it, ring.st[s], &ring.full[s], 0);
         }
         // let every copy issued by this warp land before the block may leave
         for (int q = (i > STAGES ? i - STAGES : 0); q < i; ++q)
@@ -339,6 +359,7 @@ __device__ __forceinline__ void staged_walk(int n_items, Ring<Stage, STAGES> &ri
                 atomicOr(item_at(b + q * G).pd->status, kStatusTimeout | kStatusUnsettled);
         return;
     }
+    pdl_wait();   // (the consumers read only the stages; kept so no thread runs ahead of the launch order)
     for (int i = 0;; ++i) {   // consumers
         const int j = b + i * G;
         if (j >= n_items) break;
@@ -378,8 +399,8 @@ __device__ __forceinline__ void post_walk(int n_items, const Src &src) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using St = PostStage<C, CHERRY>;
     auto &ring = *reinterpret_cast<Ring<St, STAGES> *>(smem_raw);
-    staged_walk<true>(n_items, ring, src,
-                [&](const Item &it, St &st, uint64_t *bar) { issue_post<C, CHERRY>(*it.pd, it, st, bar); },
+    staged_walk<true, false>(n_items, ring, src,
+                [&](const Item &it, St &st, uint64_t *bar, int) { issue_post<C, CHERRY>(*it.pd, it, st, bar); },
                 [&](const Item &it, const St &st, int t) { compute_post<C, CHERRY>(*it.pd, it, st, t); });
 }
 template <int C, bool HESS, int STAGES, bool CHERRY, class Src>
@@ -387,8 +408,8 @@ __device__ __forceinline__ void pre_walk(int n_items, const Src &src) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using St = PreStage<C, CHERRY>;
     auto &ring = *reinterpret_cast<Ring<St, STAGES> *>(smem_raw);
-    staged_walk<false>(n_items, ring, src,
-                [&](const Item &it, St &st, uint64_t *bar) { issue_pre<C, HESS, CHERRY>(*it.pd, it, st, bar); },
+    staged_walk<false, true>(n_items, ring, src,
+                [&](const Item &it, St &st, uint64_t *bar, int part) { issue_pre<C, HESS, CHERRY>(*it.pd, it, st, bar, part); },
                 [&](const Item &it, const St &st, int t) { compute_pre<C, HESS, CHERRY>(*it.pd, it, st, t); });
 }
 
