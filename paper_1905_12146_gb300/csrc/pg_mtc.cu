@@ -652,6 +652,7 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
                  const __grid_constant__ CUtensorMap tm_pre, const __grid_constant__ CUtensorMap tm_tab, int o0, int n_pt,
                  int n_cg) {
     extern __shared__ __align__(1024) unsigned char tc_raw[];
+    pdl_launch_dependents();   // the next level may be scheduled; its copies of q rows wait for this one
     if (smem_u32(tc_raw) & 1023u) {   // the layout needs a 1024-byte aligned base (see kPre2TcSmem)
         if (threadIdx.x == 0) atomicOr(d.status, kStatusTimeout);
         return;
@@ -729,12 +730,17 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
         if (ok) pend[i] = false;
         return ok;
     };
+    // Launched with programmatic stream serialisation: the copies that do not depend on the previous
+    // pre-order level (the children's rows and tables, the per-site values of the root kernel: the
+    // first pre-order level follows the root kernel's completion, and each later one starts after
+    // its predecessor started) go out before the wait; q_k and its scales after it.
     if (leader) {
         issue_rows(l0);
-        if (!root) issue_qk(l0);
         issue_tables_hi(l0);
         issue_tables_lo(l0);
     }
+    pdl_wait();   // the previous level's q rows are complete and visible
+    if (leader && !root) issue_qk(l0);
     for (int l = l0; l < l1 && ok; ++l) {
         const int Eq = (on && !root) ? __ldcg(d.qe + ((size_t)(k - N) * C + l) * d.Ps + p0 + t) : 0;
         int Ex[2];
@@ -1019,10 +1025,19 @@ cudaError_t launch_pre_tc2(const MDesc &d, const void *tm_post, const void *tm_p
     static DeviceOnce once;   // the shared-memory attribute, once per device
     if (cudaError_t e = device_once(once, [](int &) { return cudaFuncSetAttribute(m_pre_tc2_kernel<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPre2TcSmem); }); e != cudaSuccess)
         return e;
-    m_pre_tc2_kernel<TV><<<nd * n_cg * n_pt, 2 * kTcThreads, kPre2TcSmem, s>>>(
-        d, *static_cast<const CUtensorMap *>(tm_post), *static_cast<const CUtensorMap *>(tm_pre),
-        *static_cast<const CUtensorMap *>(tm_tab), o0, n_pt, n_cg);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};   // programmatic dependent launch (the kernel waits in pdl_wait)
+    cfg.gridDim = dim3((unsigned)(nd * n_cg * n_pt));
+    cfg.blockDim = dim3(2 * kTcThreads);
+    cfg.dynamicSmemBytes = kPre2TcSmem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, m_pre_tc2_kernel<TV>, d, *static_cast<const CUtensorMap *>(tm_post),
+                              *static_cast<const CUtensorMap *>(tm_pre), *static_cast<const CUtensorMap *>(tm_tab), o0,
+                              n_pt, n_cg);
 }
 
 }  // namespace
