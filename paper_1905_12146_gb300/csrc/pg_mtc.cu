@@ -265,6 +265,7 @@ __global__ void __launch_bounds__(kTcThreads, 3)
 m_post_tc_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtensorMap tm_post,
                  const __grid_constant__ CUtensorMap tm_tab, int o0, int n_pt) {
     extern __shared__ __align__(1024) unsigned char tc_raw[];
+    pdl_launch_dependents();   // the next level may be scheduled; its copies of rows wait for this one
     unsigned char *sm = align1024(tc_raw);
     unsigned char *XA = sm, *TB = sm + kRowTile;   // rows (then the result), D hi | D lo
     __shared__ __align__(8) uint64_t bar[2], drain_bar;
@@ -294,9 +295,13 @@ m_post_tc_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
             mbar_arrive_expect(&bar[0], 2 * kTab + (tip ? 0u : kRowTile));
             load_tables(TB, &tm_tab, d, c, l, kTcD, 1, &bar[0]);
             load_tables(TB + kTab, &tm_tab, d, c, l, kTcDlo, 1, &bar[0]);
-            if (!tip)
-                for (int kb = 0; kb < 2; ++kb) tma_load_3d(XA + kb * kRowKB, &tm_post, kb * 32, p0, (c - N) * C + l, &bar[0]);
         }
+        // Launched with programmatic stream serialisation: the first child's tables (complete before
+        // the first tensor-core post-order level, which follows the cherry level's completion) go out
+        // before the wait; the rows and scales that earlier levels wrote after it.
+        if (side == 0) pdl_wait();
+        if (t == 0 && !tip)
+            for (int kb = 0; kb < 2; ++kb) tma_load_3d(XA + kb * kRowKB, &tm_post, kb * 32, p0, (c - N) * C + l, &bar[0]);
         // TF32 remainders: of internal rows, and of tip rows when some tip vectors are not exact
         const bool lo_pass = !tip || TV;
         if (tip) tip_row<TV>(XA, d, c, p0, cnt, t);
@@ -1002,9 +1007,18 @@ cudaError_t launch_post_tc(const MDesc &d, const void *tm_post, const void *tm_t
     static DeviceOnce once;   // the shared-memory attribute, once per device
     if (cudaError_t e = device_once(once, [](int &) { return cudaFuncSetAttribute(m_post_tc_kernel<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPostTcSmem); }); e != cudaSuccess)
         return e;
-    m_post_tc_kernel<TV><<<nd * d.C * n_pt, kTcThreads, kPostTcSmem, s>>>(
-        d, *static_cast<const CUtensorMap *>(tm_post), *static_cast<const CUtensorMap *>(tm_tab), o0, n_pt);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};   // programmatic dependent launch (the kernel waits in pdl_wait)
+    cfg.gridDim = dim3((unsigned)(nd * d.C * n_pt));
+    cfg.blockDim = dim3(kTcThreads);
+    cfg.dynamicSmemBytes = kPostTcSmem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, m_post_tc_kernel<TV>, d, *static_cast<const CUtensorMap *>(tm_post),
+                              *static_cast<const CUtensorMap *>(tm_tab), o0, n_pt);
 }
 
 template <bool HESS, bool TV>
