@@ -331,6 +331,12 @@ __device__ __forceinline__ void staged_walk(int n_items, Ring<Stage, STAGES> &ri
         }
     }
     __syncthreads();   // barriers initialised before anyone uses them
+    if constexpr (!EARLY) {
+        // A post-order level lets the next launch be scheduled only once the previous level has
+        // completed (after this wait): a launch that has started then knows every level but its
+        // predecessor complete, and the top kernel its P tables (it copies them before its wait).
+        pdl_wait();
+    }
     pdl_launch_dependents();
     if (warp == kConsumerWarps) {   // producer
         if (lane != 0) return;

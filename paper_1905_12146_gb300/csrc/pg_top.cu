@@ -103,14 +103,22 @@ __global__ void __launch_bounds__(kBlock, 2) top_kernel(const __grid_constant__ 
         const int c = (nb & 1) ? op.z : op.y;
         Qs[t] = __ldg(d.Qf + 4 * (d.bmodel ? __ldg(d.bmodel + c) : 0) + col);
     }
+    // The tables of this evaluation.  Every post-order level lets its successor start only after its
+    // own wait, so when this kernel runs behind a post-order level, every launch before that level
+    // (the P build among them) has completed and the tables can be copied before the wait; not
+    // when the P build itself precedes this kernel (no level kernels: cut = 0).
+    auto copy_tables = [&]() {   // (the copies' node ids come from shared memory)
+        for (int t = threadIdx.x; t < n_top * 2 * C * kPtabCols; t += blockDim.x) {
+            const int per = C * kPtabCols, nb = t / per, e = t - nb * per;
+            const int4 op = ops_s[nb >> 1];
+            cp_async16(Tt + (size_t)nb * per + e, d.Ptab + (size_t)((nb & 1) ? op.z : op.y) * per + e);
+        }
+    };
+    const bool tables_early = d.cut > 0 || (d.skip & kSkipPost);
+    if (tables_early) copy_tables();
     pdl_wait();                // the last post-order level has completed and its rows are visible
     pdl_launch_dependents();   // the first pre-order level may be scheduled; it waits for this kernel
-    // (the copies' node ids come from shared memory, so no copy waits for a global load)
-    for (int t = threadIdx.x; t < n_top * 2 * C * kPtabCols; t += blockDim.x) {   // the tables, once
-        const int per = C * kPtabCols, nb = t / per, e = t - nb * per;
-        const int4 op = ops_s[nb >> 1];
-        cp_async16(Tt + (size_t)nb * per + e, d.Ptab + (size_t)((nb & 1) ? op.z : op.y) * per + e);
-    }
+    if (!tables_early) copy_tables();
 
     // boundary nodes' post-order rows and scales
     for (int idx = threadIdx.x; idx < n_bnd * C * cnt; idx += blockDim.x) {
