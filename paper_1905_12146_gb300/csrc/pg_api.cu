@@ -781,6 +781,16 @@ static pg_status upload_binary(pg_ctx *ctx, const pg_problem *pr, pg_handle **ou
             plevel[tp.ops[o].y] = lv;
             plevel[tp.ops[o].z] = lv;
         }
+    // ops[].w: bit 0 (bit 1) when c0 (c1) is an internal node on the level just below, whose row the
+    // post-order level kernels copy only after waiting for the previous launch
+    {
+        std::vector<int> lev(n, -1);
+        for (int lv = 0; lv < H; ++lv)
+            for (int o = tp.level_off[lv]; o < tp.level_off[lv + 1]; ++o) lev[tp.ops[o].x] = lv;
+        for (int lv = 1; lv < H; ++lv)
+            for (int o = tp.level_off[lv]; o < tp.level_off[lv + 1]; ++o)
+                tp.ops[o].w = (lev[tp.ops[o].y] == lv - 1 ? 1 : 0) | (lev[tp.ops[o].z] == lv - 1 ? 2 : 0);
+    }
     // the top part (levels >= cut) for the shared-memory top kernel: children of top nodes coded
     // as -1 - slot (a tip), their top index, or n_top + their boundary index
     const int o_cut = tp.level_off[cut];

@@ -70,7 +70,9 @@ constexpr long long kWaitLimitCycles = 2000000000LL;
 // Everything one problem's kernels need.  Lives in kernel parameter space (by value), so a
 // launch never depends on host memory that may change afterwards.
 struct ProbDesc {
-    // tree: internal-node operations sorted by height, {k, c0, c1, 0} as node ids
+    // tree: internal-node operations sorted by height, {k, c0, c1, flags} (node ids); flags bit 0
+    // (bit 1) when c0 (c1) is internal and on the level just below k's (read by the post-order
+    // level kernels to split a stage's copies around their programmatic-launch wait)
     const int4 *ops;
     const int *level_off;          // [n_levels + 1] offsets into ops
     // data

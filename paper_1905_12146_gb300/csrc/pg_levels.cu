@@ -85,27 +85,40 @@ __device__ __forceinline__ Item item_of(const ProbDesc &d, int o0, int nr, int j
     return it;
 }
 
+// part 0: every copy of the item; part 1: the stage's byte count and the copies that do not depend
+// on the previous post-order launch (tables, tip codes, and the rows and scales of internal children
+// two or more levels below: a post-order level above level 0 starts only after its predecessor's
+// wait, i.e. after every earlier launch completed); part 2: the rows and scales of children on the
+// level just below (op.w bits 0 and 1)
 template <int C, bool CHERRY>
-__device__ void issue_post(const ProbDesc &d, const Item &it, PostStage<C, CHERRY> &sm, uint64_t *bar) {
+__device__ void issue_post(const ProbDesc &d, const Item &it, PostStage<C, CHERRY> &sm, uint64_t *bar, int part = 0) {
     const int N = d.n_tips, Ps = d.Ps, c0 = it.op.y, c1 = it.op.z, p0 = it.p0;
     const bool t0 = c0 < N, t1 = c1 < N;
     const float4 *post = static_cast<const float4 *>(d.post);
     const unsigned rowb = (unsigned)it.cnt * 16u, eb = round16(it.cnt * 4u), yb = round16((unsigned)it.cnt);
-    unsigned bytes = 2u * C * kPtabCols * 16u;
-    bytes += t0 ? yb : (C * rowb + eb);
-    bytes += t1 ? yb : (C * rowb + eb);
-    mbar_arrive_expect(bar, bytes);
-    bulk_load(sm.tab[0], d.Ptab + (size_t)c0 * C * kPtabCols, C * kPtabCols * 16u, bar);
-    bulk_load(sm.tab[1], d.Ptab + (size_t)c1 * C * kPtabCols, C * kPtabCols * 16u, bar);
-    if (t0) bulk_load(sm.y0, d.tips + (size_t)c0 * Ps + p0, yb, bar);
-    else if constexpr (!CHERRY) {
-        bulk_load(sm.e0, d.pe + (size_t)(c0 - N) * Ps + p0, eb, bar);
-        for (int l = 0; l < C; ++l) bulk_load(sm.x0[l], post + ((size_t)(c0 - N) * C + l) * Ps + p0, rowb, bar);
+    // which copies this call makes: part 1 the independent ones, part 2 the rest
+    const int fl = it.op.w;
+    const bool late0 = (fl & 1) != 0, late1 = (fl & 2) != 0;
+    const bool rows0 = !t0 && (part == 0 || (part == 1) != late0), rows1 = !t1 && (part == 0 || (part == 1) != late1);
+    if (part != 2) {
+        unsigned bytes = 2u * C * kPtabCols * 16u;
+        bytes += t0 ? yb : (C * rowb + eb);
+        bytes += t1 ? yb : (C * rowb + eb);
+        mbar_arrive_expect(bar, bytes);
+        bulk_load(sm.tab[0], d.Ptab + (size_t)c0 * C * kPtabCols, C * kPtabCols * 16u, bar);
+        bulk_load(sm.tab[1], d.Ptab + (size_t)c1 * C * kPtabCols, C * kPtabCols * 16u, bar);
+        if (t0) bulk_load(sm.y0, d.tips + (size_t)c0 * Ps + p0, yb, bar);
+        if (t1) bulk_load(sm.y1, d.tips + (size_t)c1 * Ps + p0, yb, bar);
     }
-    if (t1) bulk_load(sm.y1, d.tips + (size_t)c1 * Ps + p0, yb, bar);
-    else if constexpr (!CHERRY) {
-        bulk_load(sm.e1, d.pe + (size_t)(c1 - N) * Ps + p0, eb, bar);
-        for (int l = 0; l < C; ++l) bulk_load(sm.x1[l], post + ((size_t)(c1 - N) * C + l) * Ps + p0, rowb, bar);
+    if constexpr (!CHERRY) {
+        if (rows0) {
+            bulk_load(sm.e0, d.pe + (size_t)(c0 - N) * Ps + p0, eb, bar);
+            for (int l = 0; l < C; ++l) bulk_load(sm.x0[l], post + ((size_t)(c0 - N) * C + l) * Ps + p0, rowb, bar);
+        }
+        if (rows1) {
+            bulk_load(sm.e1, d.pe + (size_t)(c1 - N) * Ps + p0, eb, bar);
+            for (int l = 0; l < C; ++l) bulk_load(sm.x1[l], post + ((size_t)(c1 - N) * C + l) * Ps + p0, rowb, bar);
+        }
     }
 }
 
@@ -319,7 +332,7 @@ __device__ __forceinline__ void compute_pre(const ProbDesc &d, const Item &it, c
 // EARLY: before waiting for the previous launch, the producer issues the part of its first STAGES
 // items' copies that does not depend on that launch (issue part 1), and the rest after the wait
 // (part 2); the copies of later items are issued whole (part 0).
-template <bool PREFETCH, bool EARLY, class Stage, int STAGES, class ItemFn, class Issue, class Compute>
+template <bool PREFETCH, bool EARLY, bool LATE_TRIGGER, class Stage, int STAGES, class ItemFn, class Issue, class Compute>
 __device__ __forceinline__ void staged_walk(int n_items, Ring<Stage, STAGES> &ring, ItemFn &&item_at, Issue &&issue,
                                             Compute &&compute) {
     const int G = gridDim.x, b = blockIdx.x;
@@ -331,13 +344,10 @@ __device__ __forceinline__ void staged_walk(int n_items, Ring<Stage, STAGES> &ri
         }
     }
     __syncthreads();   // barriers initialised before anyone uses them
-    if constexpr (!EARLY) {
-        // A post-order level lets the next launch be scheduled only once the previous level has
-        // completed (after this wait): a launch that has started then knows every level but its
-        // predecessor complete, and the top kernel its P tables (it copies them before its wait).
-        pdl_wait();
-    }
-    pdl_launch_dependents();
+    // LATE_TRIGGER (post-order levels): a thread lets the next launch be scheduled only after its own
+    // wait, so a launch that has started knows every launch but its predecessor complete (the next
+    // post-order level copies older children's rows early; the top kernel its P tables)
+    if constexpr (!LATE_TRIGGER) pdl_launch_dependents();
     if (warp == kConsumerWarps) {   // producer
         if (lane != 0) return;
         int i = 0;
@@ -345,6 +355,7 @@ __device__ __forceinline__ void staged_walk(int n_items, Ring<Stage, STAGES> &ri
             for (; i < STAGES && b + i * G < n_items; ++i) issue(item_at(b + i * G), ring.st[i], &ring.full[i], 1);
         }
         pdl_wait();   // the previous level's partials are complete and visible
+        if constexpr (LATE_TRIGGER) pdl_launch_dependents();
         for (int q = 0; q < i; ++q) issue(item_at(b + q * G), ring.st[q], &ring.full[q], 2);
         Item nxt = (PREFETCH && b + i * G < n_items) ? item_at(b + i * G) : Item{};
         for (;; ++i) {
@@ -366,6 +377,7 @@ __device__ __forceinline__ void staged_walk(int n_items, Ring<Stage, STAGES> &ri
         return;
     }
     pdl_wait();   // (the consumers read only the stages; kept so no thread runs ahead of the launch order)
+    if constexpr (LATE_TRIGGER) pdl_launch_dependents();
     for (int i = 0;; ++i) {   // consumers
         const int j = b + i * G;
         if (j >= n_items) break;
@@ -405,8 +417,8 @@ __device__ __forceinline__ void post_walk(int n_items, const Src &src) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using St = PostStage<C, CHERRY>;
     auto &ring = *reinterpret_cast<Ring<St, STAGES> *>(smem_raw);
-    staged_walk<true, false>(n_items, ring, src,
-                [&](const Item &it, St &st, uint64_t *bar, int) { issue_post<C, CHERRY>(*it.pd, it, st, bar); },
+    staged_walk<true, !CHERRY, true>(n_items, ring, src,
+                [&](const Item &it, St &st, uint64_t *bar, int part) { issue_post<C, CHERRY>(*it.pd, it, st, bar, part); },
                 [&](const Item &it, const St &st, int t) { compute_post<C, CHERRY>(*it.pd, it, st, t); });
 }
 template <int C, bool HESS, int STAGES, bool CHERRY, class Src>
@@ -414,7 +426,7 @@ __device__ __forceinline__ void pre_walk(int n_items, const Src &src) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using St = PreStage<C, CHERRY>;
     auto &ring = *reinterpret_cast<Ring<St, STAGES> *>(smem_raw);
-    staged_walk<false, true>(n_items, ring, src,
+    staged_walk<false, true, false>(n_items, ring, src,
                 [&](const Item &it, St &st, uint64_t *bar, int part) { issue_pre<C, HESS, CHERRY>(*it.pd, it, st, bar, part); },
                 [&](const Item &it, const St &st, int t) { compute_pre<C, HESS, CHERRY>(*it.pd, it, st, t); });
 }
