@@ -1406,6 +1406,9 @@ pg_status enqueue_chunked(pg_handle *h, int skip, const double *d_b, double *d_l
 
 // k problems in as few launches as possible: grouped by category count and precision, each
 // launch covers every tile of every problem of the group, every level in the fused kernel
+// patterns per tile of the fused kernel when it runs only the root's level of a batch
+constexpr int kRootRange = 512;
+
 pg_status enqueue_batch(pg_handle *const *hs, int32_t k, int skip, const double *const *d_b, double *d_logL,
                         double *const *d_grad, double *const *d_hess, const double *d_gscale, cudaStream_t s) {
     const bool fwd = !(skip & pg::kSkipPost), bwd = !(skip & pg::kSkipPre);
@@ -1459,7 +1462,11 @@ pg_status enqueue_batch(pg_handle *const *hs, int32_t k, int skip, const double 
                 const int i = idx[at + j];
                 pg::ProbDesc d = hs[i]->desc;
                 const double share = ((double)hs[i]->info.stream_bytes + 1.0) / work;
-                set_tiling(d, std::min(hs[i]->max_tiles, std::max(1, (int)(slots * share))), max_range);
+                int target = std::max(1, (int)(slots * share));
+                // FP32: the fused kernel runs the root's level alone, one short step per tile, so
+                // the tiles are many and small rather than one wave of long ones
+                if (prec == PG_PRECISION_FP32) target = std::max(target, (d.P + kRootRange - 1) / kRootRange);
+                set_tiling(d, std::min(hs[i]->max_tiles, target), max_range);
                 d.b = d_b ? d_b[i] : nullptr;
                 d.out_logL = d_logL ? d_logL + i : nullptr;
                 d.out_grad = (bwd && d_grad) ? d_grad[i] : nullptr;
@@ -1502,10 +1509,14 @@ pg_status enqueue_batch(pg_handle *const *hs, int32_t k, int skip, const double 
                 if (L >= cut_of[j]) continue;
                 const pg_handle *hj = hs[idx[j]];
                 const int o0 = hj->level_off[L], nd = hj->level_off[L + 1] - o0;
+                // level 0 holds the cherries, whose items take several ranges
+                const int nr = L > 0 ? hj->desc.level_ranges
+                                     : pg::level_items_per_node(hj->desc.P, C, post ? pg::post_cherry_ranges(C)
+                                                                                    : pg::pre_cherry_ranges(C));
                 lb.d[lb.n] = hj->d_desc;
                 lb.o0[lb.n] = o0;
-                lb.nr[lb.n] = hj->desc.level_ranges;
-                lb.base[lb.n + 1] = lb.base[lb.n] + nd * hj->desc.level_ranges;
+                lb.nr[lb.n] = nr;
+                lb.base[lb.n + 1] = lb.base[lb.n] + nd * nr;
                 ++lb.n;
             }
             return cudaSuccess;

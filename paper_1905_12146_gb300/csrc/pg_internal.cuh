@@ -47,6 +47,16 @@ constexpr int kLevelRange = 128; // consumer threads per block of the level kern
 // trips cost the same whatever its size, so with fewer categories (smaller rows) an item takes more
 // patterns (each consumer thread kLevelRange apart), keeping items at several KB
 __host__ __device__ constexpr int level_range(int C) { return C <= 2 ? 2 * kLevelRange : kLevelRange; }
+// A cherry level's item (both children tips: a few table lookups per pattern, no child rows) covers
+// this many consecutive ranges of level_range(C) patterns, so its fixed costs are spread over more
+// patterns; the pre-order step still stores one slot per (range, consumer warp).  With C <= 2 a
+// range's rows are small; with more categories larger cherry items measured no faster.
+__host__ __device__ constexpr int post_cherry_ranges(int C) { return C <= 2 ? 4 : 1; }
+__host__ __device__ constexpr int pre_cherry_ranges(int C) { return C <= 2 ? 4 : 1; }
+// items of one node of a level: ranges of level_range(C) patterns, or of `ranges` such ranges
+__host__ __device__ constexpr int level_items_per_node(int P, int C, int ranges) {
+    return (P + level_range(C) * ranges - 1) / (level_range(C) * ranges);
+}
 constexpr int kTaylorDeg = 12;   // degree of the Taylor polynomial of e^{Q t} (||Q t||_1 <= 1/4)
 // FP32 transition table per (branch, category), float4 columns of the 4x4 matrices:
 //   [0..4]   P hi (columns 0..3, then the row sums = P applied to the all-ones vector)

@@ -28,30 +28,42 @@ namespace {
 using namespace dev;
 
 // CHERRY: every node of the level has two tip children (height-1 nodes), so a stage carries no
-// child partial rows.  A stage holds one item of R = level_range(C) patterns.
+// child partial rows or scales.  A stage holds one item of R patterns: level_range(C), or that many
+// times post_cherry_ranges(C) / pre_cherry_ranges(C) for a cherry level.  Every bulk-copy
+// destination starts on a 16-byte boundary.
 template <int C, bool CHERRY = false>
 struct PostStage {
-    static constexpr int R = level_range(C);
-    float4 x0[C][CHERRY ? 1 : R], x1[C][CHERRY ? 1 : R];   // children's partial rows
-    int e0[R], e1[R];            // children's log2 scales
-    uint8_t y0[R], y1[R];        // tip codes
-    float4 tab[2][C][kPtabCols]; // both branches' tables
+    static constexpr int R = level_range(C) * (CHERRY ? post_cherry_ranges(C) : 1);
+    static constexpr int RX = CHERRY ? 1 : R;   // child rows and scales (none for a cherry level)
+    alignas(16) float4 x0[C][RX];
+    alignas(16) float4 x1[C][RX];   // children's partial rows
+    alignas(16) int e0[RX];
+    alignas(16) int e1[RX];         // children's log2 scales
+    alignas(16) uint8_t y0[R];
+    alignas(16) uint8_t y1[R];      // tip codes
+    alignas(16) float4 tab[2][C][kPtabCols];   // both branches' tables
 };
 
 template <int C, bool CHERRY = false>
 struct PreStage {
-    static constexpr int R = level_range(C);
-    float4 qk[C][R], x0[C][CHERRY ? 1 : R], x1[C][CHERRY ? 1 : R];
-    int eq[R], e0[R], e1[R];
-    int er[R];                   // log2 scale of L_p
-    float inv[R];                // 1 / Lhat_p
-    float w[R];                  // pattern weights
-    uint8_t y0[R], y1[R];
+    static constexpr int R = level_range(C) * (CHERRY ? pre_cherry_ranges(C) : 1);
+    static constexpr int RX = CHERRY ? 1 : R;
+    alignas(16) float4 qk[C][R];
+    alignas(16) float4 x0[C][RX];
+    alignas(16) float4 x1[C][RX];
+    alignas(16) int eq[R];
+    alignas(16) int e0[RX];
+    alignas(16) int e1[RX];
+    alignas(16) int er[R];          // log2 scale of L_p
+    alignas(16) float inv[R];       // 1 / Lhat_p
+    alignas(16) float w[R];         // pattern weights
+    alignas(16) uint8_t y0[R];
+    alignas(16) uint8_t y1[R];
     // both branches' tables: P hi columns and row sums, then G = Q P alike (the first 10 columns),
     // staged with one copy per branch (all C tables, which for C > 1 includes the other columns)
     static constexpr int TC = C == 1 ? 10 : kPtabCols;
-    float4 tab[2][C][TC];
-    float4 qtab[2][4];           // Q columns of both children's models (not staged for a cherry level
+    alignas(16) float4 tab[2][C][TC];
+    alignas(16) float4 qtab[2][4];           // Q columns of both children's models (not staged for a cherry level
                                  // without the Hessian: tips take G's columns)
 };
 
@@ -73,13 +85,16 @@ struct Item {
     int rg, p0, cnt;
 };
 
+// item j of a level whose nodes (from ops[o0]) have nr items each of KC ranges of level_range(C)
+// patterns; it.rg counts items, i.e. KC ranges
+template <int KC>
 __device__ __forceinline__ Item item_of(const ProbDesc &d, int o0, int nr, int j) {
     Item it;
     it.pd = &d;
     const int u = j / nr;
     it.rg = j - u * nr;
     it.op = __ldg(d.ops + o0 + u);
-    const int RL = level_range(d.C);
+    const int RL = level_range(d.C) * KC;
     it.p0 = it.rg * RL;
     it.cnt = min(RL, d.P - it.p0);
     return it;
@@ -282,42 +297,57 @@ __device__ __forceinline__ void compute_pre_one(const ProbDesc &d, const Item &i
     sums[2] = (HESS && wt != 0.f) ? wt * (ldexp2f(h0, dE) * inv - d0 * d0) : 0.f;
     sums[3] = (HESS && wt != 0.f) ? wt * (ldexp2f(h1, dE) * inv - d1 * d1) : 0.f;
 }
-// the item's patterns t, t + kLevelRange, ... of consumer thread t; each thread adds its patterns'
-// terms, then the warp adds its 32 lanes (all in FP32: R / 4 patterns per slot, no FP64 instruction,
-// which this GPU issues at a small fraction of the FP32 rate), and lane 0 stores the warp's sums in
-// its own slot of both child branches (slot = 4 * range + warp; the reduction adds the slots in FP64
-// in a fixed order)
-template <int C, bool HESS, bool CHERRY>
-__device__ __forceinline__ void compute_pre(const ProbDesc &d, const Item &it, const PreStage<C, CHERRY> &sm, int t) {
-    if constexpr (PreStage<C, CHERRY>::R == kLevelRange) {   // one pattern per thread
-        float sums[4];
-        compute_pre_one<C, HESS, CHERRY>(d, it, sm, t, sums);
-        const int lane = t & 31, slot = it.rg * kConsumerWarps + (t >> 5);
-#pragma unroll
-        for (int s = 0; s < (HESS ? 4 : 2); ++s) {
-            const float v = warp_sum_f(sums[s]);
-            if (lane == 0) {
-                double *dst = (s < 2) ? d.gpart : d.hpart;
-                dst[(size_t)((s & 1) ? it.op.z : it.op.y) * d.slot_cap + slot] = (double)v;
-            }
-        }
-        return;
-    }
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 1
-    for (int tt = t; tt < PreStage<C, CHERRY>::R; tt += kLevelRange) {
-        float sums[4];
-        compute_pre_one<C, HESS, CHERRY>(d, it, sm, tt, sums);
-#pragma unroll
-        for (int s = 0; s < (HESS ? 4 : 2); ++s) acc[s] += sums[s];
-    }
-    const int lane = t & 31, slot = it.rg * kConsumerWarps + (t >> 5);
+// the warp's sums of one range into its slot of both child branches (lane 0; slot = 4 * range + warp;
+// the reduction adds the slots in FP64 in a fixed order)
+template <bool HESS>
+__device__ __forceinline__ void store_slot_sums(const ProbDesc &d, const int4 op, int slot, int lane, const float (&acc)[4]) {
 #pragma unroll
     for (int s = 0; s < (HESS ? 4 : 2); ++s) {
         const float v = warp_sum_f(acc[s]);
         if (lane == 0) {
             double *dst = (s < 2) ? d.gpart : d.hpart;
-            dst[(size_t)((s & 1) ? it.op.z : it.op.y) * d.slot_cap + slot] = (double)v;
+            dst[(size_t)((s & 1) ? op.z : op.y) * d.slot_cap + slot] = (double)v;
+        }
+    }
+}
+
+// the item's patterns t, t + kLevelRange, ... of consumer thread t; per range of level_range(C)
+// patterns each thread adds its patterns' terms, then the warp adds its 32 lanes (all in FP32:
+// level_range(C) / 4 patterns per slot, no FP64 instruction, which this GPU issues at a small
+// fraction of the FP32 rate) and stores the sums in its slot.  A cherry item of KC > 1 ranges does
+// this range by range.
+template <int C, bool HESS, bool CHERRY>
+__device__ __forceinline__ void compute_pre(const ProbDesc &d, const Item &it, const PreStage<C, CHERRY> &sm, int t) {
+    constexpr int LR = level_range(C), KC = PreStage<C, CHERRY>::R / LR;
+    const int lane = t & 31;
+    if constexpr (KC == 1 && LR == kLevelRange) {   // one pattern per thread
+        float sums[4];
+        compute_pre_one<C, HESS, CHERRY>(d, it, sm, t, sums);
+        store_slot_sums<HESS>(d, it.op, it.rg * kConsumerWarps + (t >> 5), lane, sums);
+    } else if constexpr (KC == 1) {
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+        for (int tt = t; tt < LR; tt += kLevelRange) {
+            float sums[4];
+            compute_pre_one<C, HESS, CHERRY>(d, it, sm, tt, sums);
+#pragma unroll
+            for (int s = 0; s < (HESS ? 4 : 2); ++s) acc[s] += sums[s];
+        }
+        store_slot_sums<HESS>(d, it.op, it.rg * kConsumerWarps + (t >> 5), lane, acc);
+    } else {
+#pragma unroll 1
+        for (int h = 0; h < KC; ++h) {
+            const int g = it.rg * KC + h;   // the range whose slots this pass fills
+            if (g >= d.level_ranges) break; // (the last item's ranges past the last pattern)
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+            for (int tt = t + h * LR; tt < (h + 1) * LR; tt += kLevelRange) {
+                float sums[4];
+                compute_pre_one<C, HESS, CHERRY>(d, it, sm, tt, sums);
+#pragma unroll
+                for (int s = 0; s < (HESS ? 4 : 2); ++s) acc[s] += sums[s];
+            }
+            store_slot_sums<HESS>(d, it.op, g * kConsumerWarps + (t >> 5), lane, acc);
         }
     }
 }
@@ -394,11 +424,14 @@ __device__ __forceinline__ void staged_walk(int n_items, Ring<Stage, STAGES> &ri
 }
 
 // the item source of one problem's level, or of one level index across a batch of problems
+// (KC ranges of level_range(C) patterns per item)
+template <int KC>
 struct OneLevel {
     const ProbDesc &d;
     int o0, nr;
-    __device__ Item operator()(int j) const { return item_of(d, o0, nr, j); }
+    __device__ Item operator()(int j) const { return item_of<KC>(d, o0, nr, j); }
 };
+template <int KC>
 struct BatchLevel {
     const LevelBatch &lb;
     __device__ Item operator()(int j) const {
@@ -408,7 +441,7 @@ struct BatchLevel {
             if (lb.base[mid] <= j) lo = mid;
             else hi = mid - 1;
         }
-        return item_of(*lb.d[lo], lb.o0[lo], lb.nr[lo], j - lb.base[lo]);
+        return item_of<KC>(*lb.d[lo], lb.o0[lo], lb.nr[lo], j - lb.base[lo]);
     }
 };
 
@@ -433,23 +466,26 @@ __device__ __forceinline__ void pre_walk(int n_items, const Src &src) {
 
 template <int C, int STAGES, bool CHERRY>
 __global__ void __launch_bounds__(kLevelThreads) post_level_kernel(const __grid_constant__ ProbDesc d, int o0, int nr, int n_items) {
-    post_walk<C, STAGES, CHERRY>(n_items, OneLevel{d, o0, nr});
+    post_walk<C, STAGES, CHERRY>(n_items, OneLevel<CHERRY ? post_cherry_ranges(C) : 1>{d, o0, nr});
 }
 template <int C, bool HESS, int STAGES, bool CHERRY>
 __global__ void __launch_bounds__(kLevelThreads) pre_level_kernel(const __grid_constant__ ProbDesc d, int o0, int nr, int n_items) {
-    pre_walk<C, HESS, STAGES, CHERRY>(n_items, OneLevel{d, o0, nr});
+    pre_walk<C, HESS, STAGES, CHERRY>(n_items, OneLevel<CHERRY ? pre_cherry_ranges(C) : 1>{d, o0, nr});
 }
 // one level index of every problem of a batch (descriptors in device memory)
 template <int C, int STAGES, bool CHERRY>
 __global__ void __launch_bounds__(kLevelThreads) post_level_batch_kernel(const __grid_constant__ LevelBatch lb, int n_items) {
-    post_walk<C, STAGES, CHERRY>(n_items, BatchLevel{lb});
+    post_walk<C, STAGES, CHERRY>(n_items, BatchLevel<CHERRY ? post_cherry_ranges(C) : 1>{lb});
 }
 template <int C, bool HESS, int STAGES, bool CHERRY>
 __global__ void __launch_bounds__(kLevelThreads) pre_level_batch_kernel(const __grid_constant__ LevelBatch lb, int n_items) {
-    pre_walk<C, HESS, STAGES, CHERRY>(n_items, BatchLevel{lb});
+    pre_walk<C, HESS, STAGES, CHERRY>(n_items, BatchLevel<CHERRY ? pre_cherry_ranges(C) : 1>{lb});
 }
 
-constexpr int kPostStages = 2, kPreStages = 2, kCherryStages = 3;
+constexpr int kPostStages = 2, kPreStages = 2, kPostCherryStages = 3;
+// the pre-order cherry stage holds q_k's rows and four per-pattern arrays; for C <= 2, items of four
+// ranges in two stages (three blocks per SM) measured slightly faster than two ranges in three
+constexpr int pre_cherry_stages(int C) { return C <= 2 ? 2 : 3; }
 
 // blocks of a persistent level launch: every resident slot, at most one per item
 // (the attribute and the occupancy are set up once per device and instantiation)
@@ -501,7 +537,7 @@ cudaError_t launch_pdl_batch(K kernel, int blocks, size_t smem, cudaStream_t s, 
 template <int C, bool CHERRY>
 cudaError_t post_batch_c(const LevelBatch &lb, int n_sm, cudaStream_t s) {
     static DeviceOnce once;
-    constexpr int ST = CHERRY ? kCherryStages : kPostStages;
+    constexpr int ST = CHERRY ? kPostCherryStages : kPostStages;
     const int n_items = lb.base[lb.n];
     if (n_items <= 0) return cudaSuccess;
     const size_t smem = sizeof(Ring<PostStage<C, CHERRY>, ST>);
@@ -513,7 +549,7 @@ cudaError_t post_batch_c(const LevelBatch &lb, int n_sm, cudaStream_t s) {
 template <int C, bool HESS, bool CHERRY>
 cudaError_t pre_batch_c(const LevelBatch &lb, int n_sm, cudaStream_t s) {
     static DeviceOnce once;
-    constexpr int ST = CHERRY ? kCherryStages : kPreStages;
+    constexpr int ST = CHERRY ? pre_cherry_stages(C) : kPreStages;
     const int n_items = lb.base[lb.n];
     if (n_items <= 0) return cudaSuccess;
     const size_t smem = sizeof(Ring<PreStage<C, CHERRY>, ST>);
@@ -525,8 +561,8 @@ cudaError_t pre_batch_c(const LevelBatch &lb, int n_sm, cudaStream_t s) {
 template <int C, bool CHERRY>
 cudaError_t post_c(const ProbDesc &d, int o0, int nd, int n_sm, cudaStream_t s) {
     static DeviceOnce once;   // attribute and occupancy, once per device and instantiation
-    constexpr int ST = CHERRY ? kCherryStages : kPostStages;
-    const int nr = d.level_ranges, n_items = nd * nr;
+    constexpr int ST = CHERRY ? kPostCherryStages : kPostStages;
+    const int nr = CHERRY ? level_items_per_node(d.P, C, post_cherry_ranges(C)) : d.level_ranges, n_items = nd * nr;
     const size_t smem = sizeof(Ring<PostStage<C, CHERRY>, ST>);
     const int blocks = persistent_blocks(post_level_kernel<C, ST, CHERRY>, smem, n_sm, n_items, once);
     if (blocks < 0) return cudaErrorInvalidConfiguration;
@@ -536,8 +572,8 @@ cudaError_t post_c(const ProbDesc &d, int o0, int nd, int n_sm, cudaStream_t s) 
 template <int C, bool HESS, bool CHERRY>
 cudaError_t pre_c(const ProbDesc &d, int o0, int nd, int n_sm, cudaStream_t s) {
     static DeviceOnce once;
-    constexpr int ST = CHERRY ? kCherryStages : kPreStages;
-    const int nr = d.level_ranges, n_items = nd * nr;
+    constexpr int ST = CHERRY ? pre_cherry_stages(C) : kPreStages;
+    const int nr = CHERRY ? level_items_per_node(d.P, C, pre_cherry_ranges(C)) : d.level_ranges, n_items = nd * nr;
     const size_t smem = sizeof(Ring<PreStage<C, CHERRY>, ST>);
     const int blocks = persistent_blocks(pre_level_kernel<C, HESS, ST, CHERRY>, smem, n_sm, n_items, once);
     if (blocks < 0) return cudaErrorInvalidConfiguration;

@@ -67,39 +67,20 @@ __device__ __forceinline__ double col_entry(double e, int k, int j, unsigned mas
     return __shfl_sync(mask, e, k * 4 + j, 16);
 }
 
-template <int MAXB>
-__global__ void __launch_bounds__(128) pmatrix4_kernel(const __grid_constant__ BatchArgs<MAXB> a) {
-    pdl_launch_dependents();   // the first level kernel may be scheduled now; it waits for these tables
-    const int gid = (int)(blockIdx.x * blockDim.x + threadIdx.x);
-    const int mat = gid >> 4, lane16 = gid & 15, i = lane16 >> 2, j = lane16 & 3;
-    const int total = a.mat_base[a.n];
-    // whole 16-lane groups stay together; groups past the end leave together
-    if (mat >= total) return;
-    const unsigned mask = 0xFFFFu << (threadIdx.x & 16);
-    const int pid = find_problem<MAXB>(a.mat_base, a.n, mat);
-    const ProbDesc &d = a.d[pid];
-    const int item = mat - a.mat_base[pid];
-    const int br = item / d.C, l = item - br * d.C;
-    if (br == d.root) return;   // uniform within the group
-    double bl = d.b[br];
-    if (!(bl >= 0.0) || isinf(bl)) {
-        if (lane16 == 0) atomicOr(d.status, kStatusBadLength);
-        bl = 0.0;
-    }
-    const int model = d.bmodel ? d.bmodel[br] : 0;
-    const double *Qm = d.Qd + model * 16;
+// entry (i, j) of P = e^{Q b r} in the 16 lanes of one matrix (model row Qr of Q), of G = Q P, and
+// the row sums of both; a negative, infinite or NaN branch length is taken as 0 (the caller flags it)
+__device__ __forceinline__ void form_pmatrix(const ProbDesc &d, int model, const double (&Qr)[4], double bl, int l,
+                                             int lane16, int i, int j, unsigned mask, double &E, double &g, double &rs,
+                                             double &gs) {
+    if (!(bl >= 0.0) || isinf(bl)) bl = 0.0;
     const double t = bl * d.rates[l];
     double nrm = d.qnorm[model] * fabs(t);
     int sq = 0;
     while (nrm > 0.25 && sq < 1100) { nrm *= 0.5; ++sq; }
     const double x = t * ldexp(1.0, -sq);
-    double Qr[4];   // row i of Q
-#pragma unroll
-    for (int k = 0; k < 4; ++k) Qr[k] = Qm[i * 4 + k];
-    const double id = (i == j) ? 1.0 : 0.0;
     // entry (i, j) of e^{Q x} = sum_k (Q^k / k!)_ij x^k, the Q^k / k! precomputed per model
     const double *Mk = d.Mpow + (size_t)model * (kTaylorDeg + 1) * 16 + lane16;
-    double E = Mk[kTaylorDeg * 16];
+    E = Mk[kTaylorDeg * 16];
 #pragma unroll
     for (int k = kTaylorDeg - 1; k >= 0; --k) E = fma(E, x, Mk[k * 16]);
 #pragma unroll 1
@@ -112,14 +93,56 @@ __global__ void __launch_bounds__(128) pmatrix4_kernel(const __grid_constant__ B
         E = fma(r3, col_entry(E, 3, j, mask), s);
     }
     // G = Q P (entry (i, j)); row sums of P and of G (P and G applied to the all-ones vector)
-    double g = Qr[0] * col_entry(E, 0, j, mask);
+    g = Qr[0] * col_entry(E, 0, j, mask);
     g = fma(Qr[1], col_entry(E, 1, j, mask), g);
     g = fma(Qr[2], col_entry(E, 2, j, mask), g);
     g = fma(Qr[3], col_entry(E, 3, j, mask), g);
-    double rs = E + __shfl_xor_sync(mask, E, 1, 16);
+    rs = E + __shfl_xor_sync(mask, E, 1, 16);
     rs += __shfl_xor_sync(mask, rs, 2, 16);
-    double gs = g + __shfl_xor_sync(mask, g, 1, 16);
+    gs = g + __shfl_xor_sync(mask, g, 1, 16);
     gs += __shfl_xor_sync(mask, gs, 2, 16);
+}
+
+// Launched with programmatic serialisation: the matrices are formed while the previous launch (the
+// last evaluation's reduction) drains, and stored only after waiting for it, since until then the
+// tables they replace may still be read.  The branch length read before the wait is read again
+// after it and the matrix formed again if it changed (an input the previous launch wrote).  Every
+// thread waits before it leaves, so this launch completes only after the previous one.
+template <int MAXB>
+__global__ void __launch_bounds__(128) pmatrix4_kernel(const __grid_constant__ BatchArgs<MAXB> a) {
+    pdl_launch_dependents();   // the first level kernel may be scheduled now; it waits for these tables
+    const int gid = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    const int mat = gid >> 4, lane16 = gid & 15, i = lane16 >> 2, j = lane16 & 3;
+    const int total = a.mat_base[a.n];
+    // whole 16-lane groups stay together; groups past the end leave together
+    if (mat >= total) {
+        pdl_wait();
+        return;
+    }
+    const unsigned mask = 0xFFFFu << (threadIdx.x & 16);
+    const int pid = find_problem<MAXB>(a.mat_base, a.n, mat);
+    const ProbDesc &d = a.d[pid];
+    const int item = mat - a.mat_base[pid];
+    const int br = item / d.C, l = item - br * d.C;
+    if (br == d.root) {   // uniform within the group
+        pdl_wait();
+        return;
+    }
+    const int model = d.bmodel ? d.bmodel[br] : 0;
+    const double *Qm = d.Qd + model * 16;
+    double Qr[4];   // row i of Q
+#pragma unroll
+    for (int k = 0; k < 4; ++k) Qr[k] = Qm[i * 4 + k];
+    const double b0 = d.b[br];
+    double E, g, rs, gs;
+    form_pmatrix(d, model, Qr, b0, l, lane16, i, j, mask, E, g, rs, gs);
+    pdl_wait();
+    const double bl = __ldcg(d.b + br);   // (the same for the group's 16 lanes)
+    if (__double_as_longlong(bl) != __double_as_longlong(b0)) form_pmatrix(d, model, Qr, bl, l, lane16, i, j, mask, E, g, rs, gs);
+    if (!(bl >= 0.0) || isinf(bl)) {
+        if (lane16 == 0) atomicOr(d.status, kStatusBadLength);
+    }
+    const double id = (i == j) ? 1.0 : 0.0;
     if (d.precision == 1) {   // FP64 table: column c as two double2 = P[0..3][c]
         double *out = reinterpret_cast<double *>(d.Ptab64 + ((size_t)br * d.C + l) * kPtab64Pairs);
         out[j * 4 + i] = E;
@@ -743,29 +766,36 @@ __global__ void __launch_bounds__(kBlock, 1) tree4d_kernel(const __grid_constant
 // K5: fixed-order reduction over tile groups: one warp per branch (grad, hess), one per logL
 // ------------------------------------------------------------------------------------------
 
-// sum of v[lane], v[lane + 32], ... below ns: four independent loads in flight, fixed order
+// sum of v[lane], v[lane + 32], ... below ns in a fixed order: four accumulators, each pass of the
+// loop issuing its (up to) four loads independently, so a short row is one round trip
 __device__ __forceinline__ double lane_sum(const double *v, int ns, int lane) {
     double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    int j = lane;
-    for (; j + 96 < ns; j += 128) {
-        a0 += v[j];
-        a1 += v[j + 32];
-        a2 += v[j + 64];
-        a3 += v[j + 96];
+#pragma unroll 2
+    for (int j = lane; j < ns; j += 128) {
+        const double x0 = v[j];
+        const double x1 = j + 32 < ns ? v[j + 32] : 0.0;
+        const double x2 = j + 64 < ns ? v[j + 64] : 0.0;
+        const double x3 = j + 96 < ns ? v[j + 96] : 0.0;
+        a0 += x0;
+        a1 += x1;
+        a2 += x2;
+        a3 += x3;
     }
-    for (; j < ns; j += 32) a0 += v[j];
     return (a0 + a1) + (a2 + a3);
 }
 
+// one warp per (problem, branch) and one per problem's logL: blockIdx.y is the problem, so a block's
+// descriptor is uniform and no warp searches for its problem
 template <int MAXB>
 __global__ void __launch_bounds__(256) reduce_kernel(const __grid_constant__ BatchArgs<MAXB> a, int want_hess) {
+    // The next evaluation's transition-matrix launch may start now: it forms its matrices and waits
+    // for this launch before it stores them.
+    pdl_launch_dependents();
     pdl_wait();   // launched while the last pass drains: its slot sums are complete and visible after this
-    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const ProbDesc &d = a.d[blockIdx.y];
+    const int item = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
-    if (gw >= a.red_base[a.n]) return;
-    const int pid = find_problem<MAXB>(a.red_base, a.n, gw);
-    const ProbDesc &d = a.d[pid];
-    const int item = gw - a.red_base[pid];
+    if (item > d.n_nodes) return;
     if (item == d.n_nodes) {
         const double s = warp_sum(lane_sum(d.lpart, d.n_tg, lane));
         if (lane == 0 && d.out_logL) *d.out_logL = s;
@@ -877,8 +907,16 @@ template <int MAXB>
 cudaError_t launch_pmatrix(const BatchArgs<MAXB> &args, cudaStream_t s) {
     const int nmat = args.mat_base[args.n];
     if (args.n <= 0 || nmat <= 0) return cudaSuccess;
-    pmatrix4_kernel<MAXB><<<(nmat * 16 + 127) / 128, 128, 0, s>>>(args);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};   // programmatic dependent launch (the kernel waits before storing)
+    cfg.gridDim = dim3((unsigned)((nmat * 16 + 127) / 128));
+    cfg.blockDim = dim3(128);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, pmatrix4_kernel<MAXB>, args);
 }
 
 template <int MAXB>
@@ -901,10 +939,15 @@ cudaError_t launch_reduce(const BatchArgs<MAXB> &args, bool hess, cudaStream_t s
         logl = logl || args.d[i].out_logL;
     }
     if (!branches && !logl) return cudaSuccess;
-    // a forward part (logL only) needs one warp per problem, not one per branch
-    const int warps = branches ? args.red_base[args.n] : args.n;
+    // a forward part (logL only) needs one warp per problem; else a row of blocks per problem with
+    // a warp per branch and one for logL
+    int per = 0;
+    for (int i = 0; i < args.n; ++i) {
+        const int w = args.red_base[i + 1] - args.red_base[i];
+        per = per > w ? per : w;
+    }
     cudaLaunchConfig_t cfg = {};   // programmatic dependent launch (the kernel waits in pdl_wait)
-    cfg.gridDim = dim3((unsigned)((warps + 7) / 8));
+    cfg.gridDim = branches ? dim3((unsigned)((per + 7) / 8), (unsigned)args.n) : dim3((unsigned)((args.n + 7) / 8));
     cfg.blockDim = dim3(256);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];

@@ -345,3 +345,44 @@ def test_budget_admission():
         c.upload(wl.random_problem(200, 2000, n_states=4, n_cat=4, seed=17))
     assert e.value.status == _native.PG_ERR_OOM
     c.close()
+
+
+def test_branch_lengths_written_by_the_previous_launch(ctx):
+    """Two evaluations back to back on one stream, the second taking as its branch lengths the
+    gradient buffer the first one's reduction writes.  The second one's transition-matrix launch
+    may start while that reduction runs (it stores its tables only after waiting for it, and reads
+    b again then), so its results and status are those of the same evaluation from a copy of the
+    buffer made after a synchronisation, bit for bit.  Four taxa whose four tips differ at every
+    site, on branches of 1e-3: every branch carries a change in some most parsimonious history, so
+    every gradient entry but the root's (0) is positive and the gradient is a valid set of branch
+    lengths, while the zeros the buffer held before give P = I and a likelihood of 0."""
+    torch = pytest.importorskip("torch")
+    pr = wl.random_problem(4, 3000, n_states=4, n_cat=4, seed=23)
+    rng = np.random.default_rng(5)
+    pr["tip_states"] = np.ascontiguousarray(np.stack([rng.permutation(4) for _ in range(3000)], axis=1),
+                                            dtype=np.uint8)
+    pr["b"] = np.full_like(pr["b"], 1e-3)
+    h = ctx.upload(pr)
+    dev = torch.device("cuda")
+    b0 = torch.tensor(pr["b"], device=dev)
+    z = lambda n: torch.zeros(n, dtype=torch.float64, device=dev)   # noqa: E731
+    bits = lambda x: x.view(torch.int64)                              # noqa: E731
+    n = b0.numel()
+    l1, g1 = z(1), z(n)
+    h.eval_async(b0, l1, g1)
+    torch.cuda.synchronize()
+    assert h.status() == 0
+    assert (g1[:-1] > 0).all().item() and g1[-1].item() == 0.0
+    for _ in range(3):
+        la, ga, lb, gb = z(1), z(n), z(1), z(n)
+        h.eval_async(b0, la, ga)
+        h.eval_async(ga, lb, gb)   # ga is written by the launch just before
+        torch.cuda.synchronize()
+        assert h.status() == 0 and np.isfinite(lb.item())
+        assert torch.equal(bits(la), bits(l1)) and torch.equal(bits(ga), bits(g1))
+        lc, gc = z(1), z(n)
+        h.eval_async(ga.clone(), lc, gc)
+        torch.cuda.synchronize()
+        assert h.status() == 0
+        assert torch.equal(bits(lb), bits(lc)) and torch.equal(bits(gb), bits(gc))
+    h.close()
