@@ -304,8 +304,9 @@ class Handle:
         check(load().pg_backward_async(self._ptr, _dev_ptr(d_gscale), _dev_ptr(d_grad), _dev_ptr(d_hess),
                                        _stream(stream)))
 
-    def set_phase_timing(self, enable: bool):
-        check(load().pg_set_phase_timing(self._ptr, 1 if enable else 0))
+    def set_phase_timing(self, mode):
+        """pg_set_phase_timing: False/0 off, True/1 every phase boundary, 2 the pre-order levels only."""
+        check(load().pg_set_phase_timing(self._ptr, int(mode)))
 
     def phase_times(self) -> pg_phase_times:
         out = pg_phase_times()

@@ -301,6 +301,8 @@ cudaError_t launch_pre_level_batch(const LevelBatch &lb, int C, bool hess, int n
 // one post-order (pre-order) level [o0, o0 + nd) of a single FP32 problem (pg_levels.cu)
 // (cherry: every node of the level has two tip children)
 cudaError_t launch_post_level(const ProbDesc &d, int o0, int nd, int n_sm, bool cherry, cudaStream_t s);
-cudaError_t launch_pre_level(const ProbDesc &d, int o0, int nd, bool hess, int n_sm, bool cherry, cudaStream_t s);
+// programmatic = false: a plain launch (it starts once the previous kernel has completed)
+cudaError_t launch_pre_level(const ProbDesc &d, int o0, int nd, bool hess, int n_sm, bool cherry, cudaStream_t s,
+                             bool programmatic = true);
 
 }  // namespace pg

@@ -503,9 +503,11 @@ int persistent_blocks(K kernel, size_t smem, int n_sm, int n_items, DeviceOnce &
 }
 
 // launch with programmatic stream serialisation: the kernel may be scheduled while the previous
-// one drains, and waits for it in pdl_wait()
+// one drains, and waits for it in pdl_wait() (programmatic = false: a plain launch, pdl_wait() then
+// returns at once)
 template <class K>
-cudaError_t launch_pdl(K kernel, int blocks, size_t smem, cudaStream_t s, const ProbDesc &d, int o0, int nr, int n_items) {
+cudaError_t launch_pdl(K kernel, int blocks, size_t smem, cudaStream_t s, const ProbDesc &d, int o0, int nr, int n_items,
+                       bool programmatic = true) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)blocks);
     cfg.blockDim = dim3(kLevelThreads);
@@ -515,7 +517,7 @@ cudaError_t launch_pdl(K kernel, int blocks, size_t smem, cudaStream_t s, const 
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = programmatic ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kernel, d, o0, nr, n_items);
 }
 
@@ -570,14 +572,14 @@ cudaError_t post_c(const ProbDesc &d, int o0, int nd, int n_sm, cudaStream_t s) 
 }
 
 template <int C, bool HESS, bool CHERRY>
-cudaError_t pre_c(const ProbDesc &d, int o0, int nd, int n_sm, cudaStream_t s) {
+cudaError_t pre_c(const ProbDesc &d, int o0, int nd, int n_sm, cudaStream_t s, bool programmatic) {
     static DeviceOnce once;
     constexpr int ST = CHERRY ? pre_cherry_stages(C) : kPreStages;
     const int nr = CHERRY ? level_items_per_node(d.P, C, pre_cherry_ranges(C)) : d.level_ranges, n_items = nd * nr;
     const size_t smem = sizeof(Ring<PreStage<C, CHERRY>, ST>);
     const int blocks = persistent_blocks(pre_level_kernel<C, HESS, ST, CHERRY>, smem, n_sm, n_items, once);
     if (blocks < 0) return cudaErrorInvalidConfiguration;
-    return launch_pdl(pre_level_kernel<C, HESS, ST, CHERRY>, blocks, smem, s, d, o0, nr, n_items);
+    return launch_pdl(pre_level_kernel<C, HESS, ST, CHERRY>, blocks, smem, s, d, o0, nr, n_items, programmatic);
 }
 
 }  // namespace
@@ -596,24 +598,25 @@ cudaError_t launch_post_level(const ProbDesc &d, int o0, int nd, int n_sm, bool 
     }
 }
 
-cudaError_t launch_pre_level(const ProbDesc &d, int o0, int nd, bool hess, int n_sm, bool cherry, cudaStream_t s) {
+cudaError_t launch_pre_level(const ProbDesc &d, int o0, int nd, bool hess, int n_sm, bool cherry, cudaStream_t s,
+                             bool programmatic) {
     switch (d.C * 4 + (hess ? 2 : 0) + (cherry ? 1 : 0)) {
-        case 4: return pre_c<1, false, false>(d, o0, nd, n_sm, s);
-        case 5: return pre_c<1, false, true>(d, o0, nd, n_sm, s);
-        case 6: return pre_c<1, true, false>(d, o0, nd, n_sm, s);
-        case 7: return pre_c<1, true, true>(d, o0, nd, n_sm, s);
-        case 8: return pre_c<2, false, false>(d, o0, nd, n_sm, s);
-        case 9: return pre_c<2, false, true>(d, o0, nd, n_sm, s);
-        case 10: return pre_c<2, true, false>(d, o0, nd, n_sm, s);
-        case 11: return pre_c<2, true, true>(d, o0, nd, n_sm, s);
-        case 12: return pre_c<3, false, false>(d, o0, nd, n_sm, s);
-        case 13: return pre_c<3, false, true>(d, o0, nd, n_sm, s);
-        case 14: return pre_c<3, true, false>(d, o0, nd, n_sm, s);
-        case 15: return pre_c<3, true, true>(d, o0, nd, n_sm, s);
-        case 16: return pre_c<4, false, false>(d, o0, nd, n_sm, s);
-        case 17: return pre_c<4, false, true>(d, o0, nd, n_sm, s);
-        case 18: return pre_c<4, true, false>(d, o0, nd, n_sm, s);
-        case 19: return pre_c<4, true, true>(d, o0, nd, n_sm, s);
+        case 4: return pre_c<1, false, false>(d, o0, nd, n_sm, s, programmatic);
+        case 5: return pre_c<1, false, true>(d, o0, nd, n_sm, s, programmatic);
+        case 6: return pre_c<1, true, false>(d, o0, nd, n_sm, s, programmatic);
+        case 7: return pre_c<1, true, true>(d, o0, nd, n_sm, s, programmatic);
+        case 8: return pre_c<2, false, false>(d, o0, nd, n_sm, s, programmatic);
+        case 9: return pre_c<2, false, true>(d, o0, nd, n_sm, s, programmatic);
+        case 10: return pre_c<2, true, false>(d, o0, nd, n_sm, s, programmatic);
+        case 11: return pre_c<2, true, true>(d, o0, nd, n_sm, s, programmatic);
+        case 12: return pre_c<3, false, false>(d, o0, nd, n_sm, s, programmatic);
+        case 13: return pre_c<3, false, true>(d, o0, nd, n_sm, s, programmatic);
+        case 14: return pre_c<3, true, false>(d, o0, nd, n_sm, s, programmatic);
+        case 15: return pre_c<3, true, true>(d, o0, nd, n_sm, s, programmatic);
+        case 16: return pre_c<4, false, false>(d, o0, nd, n_sm, s, programmatic);
+        case 17: return pre_c<4, false, true>(d, o0, nd, n_sm, s, programmatic);
+        case 18: return pre_c<4, true, false>(d, o0, nd, n_sm, s, programmatic);
+        case 19: return pre_c<4, true, true>(d, o0, nd, n_sm, s, programmatic);
         default: return cudaErrorInvalidValue;
     }
 }
