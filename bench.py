@@ -662,9 +662,10 @@ def run_gpu(args):
         raise SystemExit(f"evaluation failed with status {h.status()}")
 
     # timed region: device-resident inputs and outputs, CUDA events on the launching stream; the
-    # library's events bracket the pre-order levels only (mode 2), since an event at every phase
-    # boundary (mode 1) would end the programmatic launch overlap there and lengthen the evaluation
-    h.set_phase_timing(2)
+    # library's events bracket the pre-order levels of every 8th evaluation (mode 3), since an event
+    # at every phase boundary (mode 1) would end the programmatic launch overlap there, and each
+    # timed event stalls the stream for a few microseconds
+    h.set_phase_timing(3)
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if dist is not None:
         dist.barrier()

@@ -330,10 +330,12 @@ typedef struct pg_phase_times {
 /* Per-phase timing of this handle's full evaluations: CUDA events recorded on the evaluation's
  * stream (asynchronously, no host synchronisation).  enable: 0 off; 1 at the six phase boundaries
  * (every field of pg_phase_times); 2 around the pre-order levels only (pre_levels_ms and evals; the
- * other times stay 0).  A timed event waits for all earlier work on the stream, so it also ends the
- * programmatic overlap of the kernels on either side: mode 1 changes the evaluation's own duration
- * more than mode 2.  Setting a mode clears the accumulated times.  Errors: PG_ERR_INVALID (NULL
- * handle, enable not 0, 1 or 2), PG_ERR_UNSUPPORTED (a problem evaluated in pattern chunks). */
+ * other times stay 0); 3 as 2 on every 8th full evaluation from the call (evals counts those).  A
+ * timed event waits for all earlier work on the stream, so it also ends the programmatic overlap of
+ * the kernels on either side and stalls the stream for a few microseconds: mode 1 changes the
+ * evaluation's own duration most, mode 3 least.  Setting a mode clears the accumulated times.
+ * Errors: PG_ERR_INVALID (NULL handle, enable not 0..3), PG_ERR_UNSUPPORTED (a problem evaluated in
+ * pattern chunks). */
 pg_status pg_set_phase_timing(pg_handle *h, int enable);
 
 /* Waits for the timed evaluations and returns their summed phase times. */

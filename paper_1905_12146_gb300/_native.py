@@ -305,7 +305,8 @@ class Handle:
                                        _stream(stream)))
 
     def set_phase_timing(self, mode):
-        """pg_set_phase_timing: False/0 off, True/1 every phase boundary, 2 the pre-order levels only."""
+        """pg_set_phase_timing: False/0 off, True/1 every phase boundary, 2 the pre-order levels only,
+        3 those of every 8th evaluation."""
         check(load().pg_set_phase_timing(self._ptr, int(mode)))
 
     def phase_times(self) -> pg_phase_times:

@@ -1304,6 +1304,9 @@ namespace {
 pg_status enqueue_chunked(pg_handle *h, int skip, const double *d_b, double *d_logL, double *d_grad,
                           double *d_hess, double *d_site_logL, const double *d_gscale, cudaStream_t s);
 
+// phase-timing mode 3 times the pre-order levels of one evaluation in this many
+constexpr long long kTimingEvery = 8;
+
 pg_status enqueue_single(pg_handle *h, int skip, const double *d_b, double *d_logL, double *d_grad,
                          double *d_hess, double *d_site_logL, const double *d_gscale, cudaStream_t s) {
     if (!h->chunks.empty()) return enqueue_chunked(h, skip, d_b, d_logL, d_grad, d_hess, d_site_logL, d_gscale, s);
@@ -1343,7 +1346,9 @@ pg_status enqueue_single(pg_handle *h, int skip, const double *d_b, double *d_lo
     // phase timing: events at the six phase boundaries (mode 1), or only around the pre-order
     // levels (mode 2: marks 3 and 4; a timed event waits for all earlier work, so each one also
     // ends the programmatic overlap of the launches on either side)
-    const int tmode = (fwd && bwd) ? h->timing : 0;
+    int tmode = (fwd && bwd) ? h->timing : 0;
+    if (tmode == 3) tmode = (h->timing_count % kTimingEvery == 0) ? 2 : 0;   // sampled
+    if (fwd && bwd) ++h->timing_count;
     const int n_ev = tmode == 1 ? 6 : (tmode == 2 ? 2 : 0);
     cudaEvent_t ev[6] = {};
     for (int i = 0; i < n_ev; ++i)
@@ -1758,8 +1763,9 @@ pg_status pg_set_phase_timing(pg_handle *h, int enable) {
     DeviceGuard g(h->ctx->device);
     for (cudaEvent_t x : h->events) cudaEventDestroy(x);
     h->events.clear();
-    if (enable < 0 || enable > 2) return fail(PG_ERR_INVALID, "phase-timing mode %d: 0, 1 or 2", enable);
+    if (enable < 0 || enable > 3) return fail(PG_ERR_INVALID, "phase-timing mode %d: 0, 1, 2 or 3", enable);
     h->timing = enable;
+    h->timing_count = 0;
     return PG_OK;
 }
 
@@ -1768,7 +1774,7 @@ pg_status pg_get_phase_times(pg_handle *h, pg_phase_times *out) {
     DeviceGuard g(h->ctx->device);
     pg_phase_times t{};
     double *ph[5] = {&t.pmatrix_ms, &t.post_levels_ms, &t.fused_ms, &t.pre_levels_ms, &t.reduce_ms};
-    if (h->timing == 2) {   // the pre-order levels only
+    if (h->timing >= 2) {   // the pre-order levels only
         for (size_t b = 0; b + 2 <= h->events.size(); b += 2) {
             PG_CUDA(cudaEventSynchronize(h->events[b + 1]));
             float ms = 0.f;

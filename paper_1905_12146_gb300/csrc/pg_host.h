@@ -36,7 +36,9 @@ struct pg_handle {
     int cut = 0;             // levels [0, cut) run as level kernels when evaluated alone
     std::vector<int> level_off;   // host copy of the level offsets
     std::vector<uint8_t> level_cherry;   // 1 when every node of the level has two tip children
-    int timing = 0;                // phase-timing mode: 0 off, 1 every phase, 2 the pre-order levels
+    int timing = 0;                // phase-timing mode: 0 off, 1 every phase, 2 the pre-order levels,
+                                   // 3 those of every kTimingEvery-th evaluation
+    long long timing_count = 0;    // full evaluations enqueued since the mode was set
     std::vector<cudaEvent_t> events;   // 6 per timed evaluation
     uint64_t post_levels_bytes = 0, fused_bytes = 0, pre_levels_bytes = 0;
     double *io_b = nullptr, *io_logL = nullptr, *io_grad = nullptr, *io_hess = nullptr,

@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kBlock, 2) top_kernel(const __grid_constant__ 
     const bool tables_early = d.cut > 0 || (d.skip & kSkipPost);
     if (tables_early) copy_tables();
     pdl_wait();                // the last post-order level has completed and its rows are visible
-    pdl_launch_dependents();   // the first pre-order level may be scheduled; it waits for this kernel
+    pdl_launch_dependents();   // a programmatic successor (a forward part's reduction) may be scheduled
     if (!tables_early) copy_tables();
 
     // boundary nodes' post-order rows and scales

@@ -390,7 +390,8 @@ def test_branch_lengths_written_by_the_previous_launch(ctx):
 
 def test_phase_timing_modes(ctx):
     """Phase timing: mode 1 times every phase, mode 2 only the pre-order levels (the other fields
-    stay 0); both count the evaluations; another mode is an invalid argument.  Timing changes no
+    stay 0), mode 3 those of every 8th evaluation; each counts the evaluations it timed; another
+    mode is an invalid argument.  Timing changes no
     result bit."""
     torch = pytest.importorskip("torch")
     from paper_1905_12146_gb300 import _native
@@ -399,25 +400,25 @@ def test_phase_timing_modes(ctx):
     dev = torch.device("cuda")
     b = torch.tensor(pr["b"], device=dev)
     outs = []
-    for mode in (1, 2, 0):
+    for mode in (1, 2, 3, 0):
         h.set_phase_timing(mode)
         lg, g = torch.zeros(1, dtype=torch.float64, device=dev), torch.zeros_like(b)
-        for _ in range(3):
+        for _ in range(9):
             h.eval_async(b, lg, g)
         torch.cuda.synchronize()
         pt = h.phase_times()
         outs.append((lg.clone(), g.clone()))
         if mode == 1:
-            assert pt.evals == 3 and pt.pre_levels_ms > 0 and pt.post_levels_ms > 0 and pt.total_ms > 0
-        elif mode == 2:
-            assert pt.evals == 3 and pt.pre_levels_ms > 0
+            assert pt.evals == 9 and pt.pre_levels_ms > 0 and pt.post_levels_ms > 0 and pt.total_ms > 0
+        elif mode in (2, 3):
+            assert pt.evals == (9 if mode == 2 else 2) and pt.pre_levels_ms > 0   # mode 3: the 1st and 9th
             assert pt.post_levels_ms == 0 and pt.pmatrix_ms == 0 and pt.total_ms == 0
         else:
             assert pt.evals == 0
     for lg, g in outs[1:]:
         assert torch.equal(lg, outs[0][0]) and torch.equal(g, outs[0][1])
     with pytest.raises(_native.PhyloGradError) as e:
-        h.set_phase_timing(3)
+        h.set_phase_timing(4)
     assert e.value.status == _native.PG_ERR_INVALID
     assert h.status() == 0
     h.close()
