@@ -265,7 +265,6 @@ __global__ void __launch_bounds__(kTcThreads, 3)
 m_post_tc_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtensorMap tm_post,
                  const __grid_constant__ CUtensorMap tm_tab, int o0, int n_pt) {
     extern __shared__ __align__(1024) unsigned char tc_raw[];
-    pdl_launch_dependents();   // the next level may be scheduled; its copies of rows wait for this one
     unsigned char *sm = align1024(tc_raw);
     unsigned char *XA = sm, *TB = sm + kRowTile;   // rows (then the result), D hi | D lo
     __shared__ __align__(8) uint64_t bar[2], drain_bar;
@@ -299,7 +298,12 @@ m_post_tc_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
         // Launched with programmatic stream serialisation: the first child's tables (complete before
         // the first tensor-core post-order level, which follows the cherry level's completion) go out
         // before the wait; the rows and scales that earlier levels wrote after it.
-        if (side == 0) pdl_wait();
+        if (side == 0) {
+            pdl_wait();
+            // the next level may be scheduled only now, after this wait (at the kernel's start it
+            // measured 3.071 against 3.055 ms per codon evaluation); its copies of rows wait for it
+            pdl_launch_dependents();
+        }
         if (t == 0 && !tip)
             for (int kb = 0; kb < 2; ++kb) tma_load_3d(XA + kb * kRowKB, &tm_post, kb * 32, p0, (c - N) * C + l, &bar[0]);
         // TF32 remainders: of internal rows, and of tip rows when some tip vectors are not exact
@@ -657,7 +661,6 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
                  const __grid_constant__ CUtensorMap tm_pre, const __grid_constant__ CUtensorMap tm_tab, int o0, int n_pt,
                  int n_cg) {
     extern __shared__ __align__(1024) unsigned char tc_raw[];
-    pdl_launch_dependents();   // the next level may be scheduled; its copies of q rows wait for this one
     if (smem_u32(tc_raw) & 1023u) {   // the layout needs a 1024-byte aligned base (see kPre2TcSmem)
         if (threadIdx.x == 0) atomicOr(d.status, kStatusTimeout);
         return;
@@ -745,6 +748,7 @@ m_pre_tc2_kernel(const __grid_constant__ MDesc d, const __grid_constant__ CUtens
         issue_tables_lo(l0);
     }
     pdl_wait();   // the previous level's q rows are complete and visible
+    pdl_launch_dependents();   // the next level may be scheduled (after this wait: 3.071 -> 3.068 ms)
     if (leader && !root) issue_qk(l0);
     for (int l = l0; l < l1 && ok; ++l) {
         const int Eq = (on && !root) ? __ldcg(d.qe + ((size_t)(k - N) * C + l) * d.Ps + p0 + t) : 0;
