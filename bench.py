@@ -11,8 +11,10 @@ logL plus the 1,998 branch gradients (FP32 partials, FP64 transition matrices an
 One JSON line is printed by rank 0.  ``value`` is evaluations/s with every input resident in HBM
 (device branch lengths, device outputs), timed with CUDA events; ``e2e`` is the same metric through
 the blocking host-pointer call (branch lengths copied from pinned host memory, logL and gradient
-copied back each step).  ``roofline`` is for the dominant kernel (the pre-order level kernels),
-``cpu_baseline`` the FP64 CPU oracle on a bounded sample of the same workload.
+copied back each step).  ``roofline`` is for the dominant kernel (the pre-order level kernels,
+timed by the library's events around them on every 8th evaluation of the timed region);
+``phases`` splits an evaluation by phase in a separate pass with an event at every phase boundary;
+``cpu_baseline`` is the FP64 CPU oracle on a bounded sample of the same workload.
 ``--impl reference`` times that oracle alone (there is no reference GPU implementation).
 
 Rank 0 then adds measured objects (skipped with ``--no-extras``): ``small`` (per-call latency of
