@@ -1370,7 +1370,7 @@ pg_status enqueue_single(pg_handle *h, int skip, const double *d_b, double *d_lo
     if (e == cudaSuccess) e = use_top ? pg::launch_top(a, hess, h->ctx->n_sm, s) : pg::launch_tree<1>(a, hess, s);
     mark(3);
     // The first pre-order level is a plain launch: scheduled while the top kernel ran (programmatic
-    // launch), it made the evaluation slower, 0.730 against 0.696 ms in the nucleotide configuration.
+    // launch), it made the evaluation slower, 0.730 against 0.694 ms in the nucleotide configuration.
     for (int lv = d.cut - 1; bwd && e == cudaSuccess && lv >= 0; --lv)
         e = pg::launch_pre_level(d, h->level_off[lv], h->level_off[lv + 1] - h->level_off[lv], hess, h->ctx->n_sm,
                                  h->level_cherry[lv] != 0, s, lv != d.cut - 1);
