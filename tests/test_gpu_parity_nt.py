@@ -422,3 +422,14 @@ def test_phase_timing_modes(ctx):
     assert e.value.status == _native.PG_ERR_INVALID
     assert h.status() == 0
     h.close()
+
+
+@pytest.mark.parametrize("n_cat", [1, 2])
+def test_single_problem_level_kernels_with_few_categories(ctx, oracle_mod, n_cat):
+    """A single problem with one or two rate categories that runs its wide levels in the level
+    kernels (cut 4-5 here): the cherry level's items cover four ranges of 256 patterns, and the
+    pattern count leaves the last item with ranges past the last pattern.  Parity with the oracle,
+    Hessian diagonal and per-site values included."""
+    pr = wl.random_problem(500, 2500 + 37 * n_cat, n_states=4, n_cat=n_cat, seed=40 + n_cat, b_mean=0.05,
+                           ambiguous=0.02)
+    _compare(ctx, oracle_mod, pr)
